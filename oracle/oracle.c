@@ -1,0 +1,734 @@
+/*
+ * oracle.c -- plain, sequential FP64 CPU oracle for deflated restarted GMRES(m).
+ *
+ * TEST INFRASTRUCTURE ONLY (tests/, __graft_entry__.smoke(), bench.py's CPU baseline).
+ * It shares no code with the CUDA library.  Written for a reader who checks it against
+ * the paper (arXiv:1906.04051) by eye: one loop per mathematical operation, FP64 only,
+ * no blocking, fusion or reordering.
+ */
+#include "oracle.h"
+
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------------------ */
+/* Q1 Galerkin finite elements (Sec. 3.1, Eqs. 6-8, written for the bilinear square).   */
+/* ------------------------------------------------------------------------------------ */
+
+int64_t orc_q1_nnz(int32_t n) {
+  /* interior rows couple to the 3x3 node patch; boundary rows hold only u_i = 0 */
+  int64_t interior = (int64_t)(n - 1) * (n - 1);
+  int64_t boundary = (int64_t)(n + 1) * (n + 1) - interior;
+  return 9 * interior + boundary;
+}
+
+void orc_q1_element(double h, double bx, double by, double* K1, double* C, double* M) {
+  /* 1-D linear shape functions l0 = 1 - s, l1 = s on [0,1]:
+   *   S[a][c] = int l_a' l_c'    Mr[a][c] = int l_a l_c    G[a][c] = int l_a l_c'
+   * The 2-D bilinear functions are phi_(a,b) = l_a(x/h) l_b(y/h).  On a square of side
+   * h the Jacobian factors cancel in the stiffness, give h for convection, h^2 for mass. */
+  const double S[2][2] = {{1.0, -1.0}, {-1.0, 1.0}};
+  const double Mr[2][2] = {{1.0 / 3.0, 1.0 / 6.0}, {1.0 / 6.0, 1.0 / 3.0}};
+  const double G[2][2] = {{-0.5, 0.5}, {-0.5, 0.5}};
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b)
+      for (int c = 0; c < 2; ++c)
+        for (int d = 0; d < 2; ++d) {
+          int i = a + 2 * b, j = c + 2 * d;
+          K1[4 * i + j] = S[a][c] * Mr[b][d] + Mr[a][c] * S[b][d];
+          C[4 * i + j] = h * (bx * G[a][c] * Mr[b][d] + by * Mr[a][c] * G[b][d]);
+          M[4 * i + j] = h * h * Mr[a][c] * Mr[b][d];
+        }
+}
+
+static int is_boundary(int32_t n, int32_t i, int32_t j) {
+  return i == 0 || j == 0 || i == n || j == n;
+}
+
+int orc_q1_assemble(int32_t n, const double* kappa, double bx, double by, const double* f,
+                    const double* u, int32_t* rowptr, int32_t* col, double* val, double* b) {
+  const int32_t np = n + 1;
+  const int32_t N = np * np;
+  /* sparsity pattern: mesh connectivity, node (i,j) -> j*(n+1)+i, columns ascending */
+  int64_t pos = 0;
+  for (int32_t j = 0; j < np; ++j)
+    for (int32_t i = 0; i < np; ++i) {
+      int32_t row = j * np + i;
+      rowptr[row] = (int32_t)pos;
+      if (is_boundary(n, i, j)) {
+        col[pos] = row;
+        val[pos] = 1.0; /* Dirichlet row replaced by u_i = 0 */
+        ++pos;
+      } else {
+        for (int dj = -1; dj <= 1; ++dj)
+          for (int di = -1; di <= 1; ++di) {
+            col[pos] = (j + dj) * np + (i + di);
+            val[pos] = 0.0;
+            ++pos;
+          }
+      }
+    }
+  rowptr[N] = (int32_t)pos;
+  for (int32_t k = 0; k < N; ++k) b[k] = 0.0;
+
+  double K1[16], C[16], M[16];
+  orc_q1_element(1.0 / n, bx, by, K1, C, M);
+  /* element loop: scatter K_e = kappa_e K1 + C into interior rows, b += M_e f_e - K_e u_e */
+  for (int32_t ej = 0; ej < n; ++ej)
+    for (int32_t ei = 0; ei < n; ++ei) {
+      double ke = kappa[ej * n + ei];
+      int32_t gi[4], ii[4], jj[4];
+      for (int l = 0; l < 4; ++l) {
+        ii[l] = ei + (l & 1);
+        jj[l] = ej + (l >> 1);
+        gi[l] = jj[l] * np + ii[l];
+      }
+      for (int a = 0; a < 4; ++a) {
+        if (is_boundary(n, ii[a], jj[a])) continue;
+        int32_t row = gi[a];
+        for (int c = 0; c < 4; ++c) {
+          double kac = ke * K1[4 * a + c] + C[4 * a + c];
+          int32_t k;
+          for (k = rowptr[row]; k < rowptr[row + 1]; ++k)
+            if (col[k] == gi[c]) break;
+          val[k] += kac;
+          b[row] += M[4 * a + c] * f[gi[c]];
+          if (u) b[row] -= kac * u[gi[c]];
+        }
+      }
+    }
+  return 0;
+}
+
+void orc_q1_kappa_grad(int32_t n, const double* lam, const double* x, double* grad) {
+  /* A depends on kappa_e only through the interior rows of element e: dA/dkappa_e = K1
+   * scattered into those rows; b does not depend on kappa.  dL/dkappa_e = -lam^T dA x. */
+  const int32_t np = n + 1;
+  double K1[16], C[16], M[16];
+  orc_q1_element(1.0 / n, 0.0, 0.0, K1, C, M);
+  for (int32_t ej = 0; ej < n; ++ej)
+    for (int32_t ei = 0; ei < n; ++ei) {
+      double g = 0.0;
+      for (int a = 0; a < 4; ++a) {
+        int32_t ia = ei + (a & 1), ja = ej + (a >> 1);
+        if (is_boundary(n, ia, ja)) continue;
+        double kx = 0.0;
+        for (int c = 0; c < 4; ++c) {
+          int32_t ic = ei + (c & 1), jc = ej + (c >> 1);
+          kx += K1[4 * a + c] * x[jc * np + ic];
+        }
+        g += lam[ja * np + ia] * kx;
+      }
+      grad[ej * n + ei] = -g;
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Sparse and dense building blocks                                                      */
+/* ------------------------------------------------------------------------------------ */
+
+void orc_spmv(int32_t N, const int32_t* rowptr, const int32_t* col, const double* val,
+              const double* x, double* y) {
+  for (int32_t i = 0; i < N; ++i) {
+    double s = 0.0;
+    for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) s += val[k] * x[col[k]];
+    y[i] = s;
+  }
+}
+
+void orc_transpose(int32_t N, const int32_t* rowptr, const int32_t* col, const double* val,
+                   int32_t* rowptr_t, int32_t* col_t, double* val_t) {
+  for (int32_t i = 0; i <= N; ++i) rowptr_t[i] = 0;
+  for (int32_t k = 0; k < rowptr[N]; ++k) rowptr_t[col[k] + 1]++;
+  for (int32_t i = 0; i < N; ++i) rowptr_t[i + 1] += rowptr_t[i];
+  int32_t* next = (int32_t*)malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+  for (int32_t i = 0; i < N; ++i) next[i] = rowptr_t[i];
+  /* rows visited in ascending order, so every transposed row comes out sorted */
+  for (int32_t i = 0; i < N; ++i)
+    for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      int32_t p = next[col[k]]++;
+      col_t[p] = i;
+      val_t[p] = val[k];
+    }
+  free(next);
+}
+
+static double dot(const double* a, const double* b, int32_t n) {
+  double s = 0.0;
+  for (int32_t i = 0; i < n; ++i) s += a[i] * b[i];
+  return s;
+}
+
+static double nrm2(const double* a, int32_t n) { return sqrt(dot(a, a, n)); }
+
+int orc_lu_factor(int32_t n, double* a, int32_t* piv) {
+  /* Gaussian elimination with partial pivoting (outer-product form) */
+  for (int32_t k = 0; k < n; ++k) {
+    int32_t p = k;
+    for (int32_t i = k + 1; i < n; ++i)
+      if (fabs(a[(size_t)i * n + k]) > fabs(a[(size_t)p * n + k])) p = i;
+    piv[k] = p;
+    if (a[(size_t)p * n + k] == 0.0) return k + 1;
+    if (p != k)
+      for (int32_t j = 0; j < n; ++j) {
+        double t = a[(size_t)k * n + j];
+        a[(size_t)k * n + j] = a[(size_t)p * n + j];
+        a[(size_t)p * n + j] = t;
+      }
+    for (int32_t i = k + 1; i < n; ++i) {
+      double l = a[(size_t)i * n + k] / a[(size_t)k * n + k];
+      a[(size_t)i * n + k] = l;
+      for (int32_t j = k + 1; j < n; ++j) a[(size_t)i * n + j] -= l * a[(size_t)k * n + j];
+    }
+  }
+  return 0;
+}
+
+void orc_lu_solve(int32_t n, const double* lu, const int32_t* piv, double* b) {
+  for (int32_t k = 0; k < n; ++k)
+    if (piv[k] != k) {
+      double t = b[k];
+      b[k] = b[piv[k]];
+      b[piv[k]] = t;
+    }
+  for (int32_t i = 0; i < n; ++i)
+    for (int32_t j = 0; j < i; ++j) b[i] -= lu[(size_t)i * n + j] * b[j];
+  for (int32_t i = n - 1; i >= 0; --i) {
+    for (int32_t j = i + 1; j < n; ++j) b[i] -= lu[(size_t)i * n + j] * b[j];
+    b[i] /= lu[(size_t)i * n + i];
+  }
+}
+
+/* Eigenvalues of the 2x2 block [[a, b], [c, d]]. */
+static void eig2(double a, double b, double c, double d, double* r1, double* i1, double* r2,
+                 double* i2) {
+  double p = 0.5 * (a - d);
+  double disc = p * p + b * c;
+  double mid = 0.5 * (a + d);
+  if (disc >= 0.0) {
+    double q = sqrt(disc);
+    double l1 = mid + (p >= 0.0 ? q : -q);
+    double det = a * d - b * c;
+    double l2 = (l1 != 0.0) ? det / l1 : mid - (p >= 0.0 ? q : -q);
+    *r1 = l1; *i1 = 0.0;
+    *r2 = l2; *i2 = 0.0;
+  } else {
+    double q = sqrt(-disc);
+    *r1 = mid; *i1 = q;
+    *r2 = mid; *i2 = -q;
+  }
+}
+
+int orc_hessenberg_eigs(int32_t n, const double* h, double* wr, double* wi) {
+  /* Francis double-shift QR iteration (implicit, with bulge chasing by 3x3 Householder
+   * reflectors), deflating at negligible subdiagonals.  Only the active diagonal block
+   * is transformed: the eigenvalues alone are wanted. */
+  double* a = (double*)malloc(sizeof(double) * (size_t)n * n);
+  memcpy(a, h, sizeof(double) * (size_t)n * n);
+#define A(i, j) a[(size_t)(i) * n + (j)]
+  double anorm = 0.0;
+  for (int32_t i = 0; i < n; ++i)
+    for (int32_t j = (i > 0 ? i - 1 : 0); j < n; ++j) anorm += fabs(A(i, j));
+  int32_t hi = n - 1;
+  int its = 0, total = 0;
+  while (hi >= 0) {
+    int32_t l;
+    for (l = hi; l > 0; --l) {
+      double s = fabs(A(l - 1, l - 1)) + fabs(A(l, l));
+      if (s == 0.0) s = anorm;
+      if (fabs(A(l, l - 1)) <= DBL_EPSILON * s) {
+        A(l, l - 1) = 0.0;
+        break;
+      }
+    }
+    if (l == hi) {
+      wr[hi] = A(hi, hi);
+      wi[hi] = 0.0;
+      --hi;
+      its = 0;
+      continue;
+    }
+    if (l == hi - 1) {
+      eig2(A(hi - 1, hi - 1), A(hi - 1, hi), A(hi, hi - 1), A(hi, hi), &wr[hi - 1], &wi[hi - 1],
+           &wr[hi], &wi[hi]);
+      hi -= 2;
+      its = 0;
+      continue;
+    }
+    if (++total > 60 * n) {
+      free(a);
+      return -1;
+    }
+    /* shifts: the eigenvalues of the trailing 2x2 block, as the roots of x^2 - s x + t;
+     * an exceptional shift breaks rare cycles after 10 and 20 sweeps without deflation */
+    double s, t;
+    if (its == 10 || its == 20) {
+      double w = fabs(A(hi, hi - 1)) + fabs(A(hi - 1, hi - 2));
+      double sig = A(hi, hi) + 0.75 * w;
+      s = 2.0 * sig;
+      t = sig * sig;
+    } else {
+      s = A(hi - 1, hi - 1) + A(hi, hi);
+      t = A(hi - 1, hi - 1) * A(hi, hi) - A(hi - 1, hi) * A(hi, hi - 1);
+    }
+    ++its;
+    /* first column of (H - s1 I)(H - s2 I) restricted to the block */
+    double x = A(l, l) * A(l, l) + A(l, l + 1) * A(l + 1, l) - s * A(l, l) + t;
+    double y = A(l + 1, l) * (A(l, l) + A(l + 1, l + 1) - s);
+    double z = A(l + 1, l) * A(l + 2, l + 1);
+    for (int32_t k = l; k <= hi - 2; ++k) {
+      double nrm = sqrt(x * x + y * y + z * z);
+      if (nrm != 0.0) {
+        double alpha = (x >= 0.0) ? -nrm : nrm; /* reflector maps (x,y,z) to alpha e1 */
+        double v0 = x - alpha, v1 = y, v2 = z;
+        double beta = 2.0 / (v0 * v0 + v1 * v1 + v2 * v2);
+        int32_t c0 = (k > l) ? k - 1 : l;
+        for (int32_t j = c0; j <= hi; ++j) {
+          double dd = beta * (v0 * A(k, j) + v1 * A(k + 1, j) + v2 * A(k + 2, j));
+          A(k, j) -= dd * v0;
+          A(k + 1, j) -= dd * v1;
+          A(k + 2, j) -= dd * v2;
+        }
+        if (k > l) {
+          A(k + 1, k - 1) = 0.0;
+          A(k + 2, k - 1) = 0.0;
+        }
+        int32_t r1 = (k + 3 < hi) ? k + 3 : hi;
+        for (int32_t i = l; i <= r1; ++i) {
+          double dd = beta * (A(i, k) * v0 + A(i, k + 1) * v1 + A(i, k + 2) * v2);
+          A(i, k) -= dd * v0;
+          A(i, k + 1) -= dd * v1;
+          A(i, k + 2) -= dd * v2;
+        }
+      }
+      x = A(k + 1, k);
+      y = A(k + 2, k);
+      if (k < hi - 2) z = A(k + 3, k);
+    }
+    /* last reflector acts on rows/columns hi-1, hi */
+    double nrm = sqrt(x * x + y * y);
+    if (nrm != 0.0) {
+      double alpha = (x >= 0.0) ? -nrm : nrm;
+      double v0 = x - alpha, v1 = y;
+      double beta = 2.0 / (v0 * v0 + v1 * v1);
+      int32_t c0 = (hi - 2 > l) ? hi - 2 : l;
+      for (int32_t j = c0; j <= hi; ++j) {
+        double dd = beta * (v0 * A(hi - 1, j) + v1 * A(hi, j));
+        A(hi - 1, j) -= dd * v0;
+        A(hi, j) -= dd * v1;
+      }
+      if (hi - 2 >= l) A(hi, hi - 2) = 0.0;
+      for (int32_t i = l; i <= hi; ++i) {
+        double dd = beta * (A(i, hi - 1) * v0 + A(i, hi) * v1);
+        A(i, hi - 1) -= dd * v0;
+        A(i, hi) -= dd * v1;
+      }
+    }
+  }
+#undef A
+  free(a);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Deflation preconditioner (Sec. 3.3, Eqs. 17-18)                                       */
+/* ------------------------------------------------------------------------------------ */
+
+struct orc_defl {
+  int32_t N, r;
+  const int32_t *rowptr, *col;
+  const double* val;
+  int32_t* agg;     /* copy of the aggregate map */
+  double* uscale;   /* 1/sqrt|agg_p|: U = W diag(uscale) has orthonormal columns */
+  double* T;        /* U^T A U, r x r row-major */
+  double* lu;       /* LU of T */
+  int32_t* piv;
+};
+
+static void defl_Ut(const orc_defl* d, const double* v, double* c) { /* c = U^T v */
+  for (int32_t p = 0; p < d->r; ++p) c[p] = 0.0;
+  for (int32_t i = 0; i < d->N; ++i)
+    if (d->agg[i] >= 0) c[d->agg[i]] += v[i];
+  for (int32_t p = 0; p < d->r; ++p) c[p] *= d->uscale[p];
+}
+
+static void defl_U_add(const orc_defl* d, const double* y, double* v) { /* v += U y */
+  for (int32_t i = 0; i < d->N; ++i)
+    if (d->agg[i] >= 0) v[i] += d->uscale[d->agg[i]] * y[d->agg[i]];
+}
+
+orc_defl* orc_defl_create(int32_t N, const int32_t* rowptr, const int32_t* col,
+                          const double* val, int32_t r, const int32_t* agg, int* err) {
+  *err = 0;
+  orc_defl* d = (orc_defl*)calloc(1, sizeof(orc_defl));
+  d->N = N;
+  d->r = r;
+  d->rowptr = rowptr;
+  d->col = col;
+  d->val = val;
+  d->agg = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+  memcpy(d->agg, agg, sizeof(int32_t) * (size_t)N);
+  d->uscale = (double*)calloc((size_t)r, sizeof(double));
+  int64_t* count = (int64_t*)calloc((size_t)r, sizeof(int64_t));
+  for (int32_t i = 0; i < N; ++i)
+    if (agg[i] >= 0) count[agg[i]]++;
+  for (int32_t p = 0; p < r; ++p) {
+    if (count[p] == 0) *err = -4; /* a zero column of W */
+    d->uscale[p] = count[p] > 0 ? 1.0 / sqrt((double)count[p]) : 0.0;
+  }
+  free(count);
+  d->T = (double*)calloc((size_t)r * r, sizeof(double));
+  d->lu = (double*)malloc(sizeof(double) * (size_t)r * r);
+  d->piv = (int32_t*)malloc(sizeof(int32_t) * (size_t)r);
+  if (*err) {
+    orc_defl_destroy(d);
+    return NULL;
+  }
+  /* T = U^T A U: entry (p,q) sums a_ij over i in p, j in q, scaled by uscale_p uscale_q */
+  for (int32_t i = 0; i < N; ++i) {
+    int32_t p = agg[i];
+    if (p < 0) continue;
+    for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      int32_t q = agg[col[k]];
+      if (q < 0) continue;
+      d->T[(size_t)p * r + q] += val[k] * d->uscale[p] * d->uscale[q];
+    }
+  }
+  memcpy(d->lu, d->T, sizeof(double) * (size_t)r * r);
+  if (orc_lu_factor(r, d->lu, d->piv) != 0) {
+    *err = -4;
+    orc_defl_destroy(d);
+    return NULL;
+  }
+  return d;
+}
+
+void orc_defl_destroy(orc_defl* d) {
+  if (!d) return;
+  free(d->agg);
+  free(d->uscale);
+  free(d->T);
+  free(d->lu);
+  free(d->piv);
+  free(d);
+}
+
+void orc_defl_T(const orc_defl* d, double* T) {
+  memcpy(T, d->T, sizeof(double) * (size_t)d->r * d->r);
+}
+
+void orc_defl_apply_Minv(const orc_defl* d, double mu, const double* v, double* z) {
+  /* z = M^-1 v = v + U (|mu| T^-1 - I) U^T v   (Eq. 17) */
+  double* c = (double*)malloc(sizeof(double) * (size_t)d->r);
+  double* y = (double*)malloc(sizeof(double) * (size_t)d->r);
+  defl_Ut(d, v, c);
+  memcpy(y, c, sizeof(double) * (size_t)d->r);
+  orc_lu_solve(d->r, d->lu, d->piv, y); /* y = T^-1 c */
+  for (int32_t p = 0; p < d->r; ++p) y[p] = fabs(mu) * y[p] - c[p];
+  memcpy(z, v, sizeof(double) * (size_t)d->N);
+  defl_U_add(d, y, z);
+  free(c);
+  free(y);
+}
+
+void orc_defl_apply_P(const orc_defl* d, const double* w, double* out) {
+  /* out = P w = w - A U T^-1 U^T w, the deflation projector with E = W^T A W taken in
+   * the orthonormal basis U of span(W) (P does not depend on that basis). */
+  double* c = (double*)malloc(sizeof(double) * (size_t)d->r);
+  double* t = (double*)calloc((size_t)d->N, sizeof(double));
+  double* at = (double*)malloc(sizeof(double) * (size_t)d->N);
+  defl_Ut(d, w, c);
+  orc_lu_solve(d->r, d->lu, d->piv, c);
+  defl_U_add(d, c, t);
+  orc_spmv(d->N, d->rowptr, d->col, d->val, t, at);
+  for (int32_t i = 0; i < d->N; ++i) out[i] = w[i] - at[i];
+  free(c);
+  free(t);
+  free(at);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* GMRES(m) (Sec. 3.2, Eqs. 10-15) with right deflation preconditioning (Eq. 16)         */
+/* ------------------------------------------------------------------------------------ */
+
+/* Operator of the Krylov space: w = A M^-1 v (EBP), w = P A v (projector) or w = A v. */
+static void apply_op(int32_t N, const int32_t* rowptr, const int32_t* col, const double* val,
+                     const orc_defl* d, int mode, double mu, const double* v, double* w,
+                     double* tmp) {
+  if (mode == ORC_DEFL_EBP) {
+    orc_defl_apply_Minv(d, mu, v, tmp);
+    orc_spmv(N, rowptr, col, val, tmp, w);
+  } else if (mode == ORC_DEFL_PROJECTOR) {
+    orc_spmv(N, rowptr, col, val, v, tmp);
+    orc_defl_apply_P(d, tmp, w);
+  } else {
+    orc_spmv(N, rowptr, col, val, v, w);
+  }
+}
+
+/* Orthogonalise w against V[:,0..j] (column-major, leading dimension N); hcol receives
+ * the j+1 projection coefficients and hcol[j+1] = ||w|| afterwards. */
+static void orthogonalise(int32_t N, const double* V, int32_t j, int ortho, double* w,
+                          double* hcol) {
+  if (ortho == ORC_MGS) {
+    for (int32_t i = 0; i <= j; ++i) {
+      const double* vi = V + (size_t)i * N;
+      hcol[i] = dot(vi, w, N);
+      for (int32_t t = 0; t < N; ++t) w[t] -= hcol[i] * vi[t];
+    }
+  } else {
+    /* CGS2: two classical Gram-Schmidt passes, the coefficients of both accumulate */
+    for (int32_t i = 0; i <= j; ++i) hcol[i] = 0.0;
+    double* hp = (double*)malloc(sizeof(double) * (size_t)(j + 1));
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int32_t i = 0; i <= j; ++i) hp[i] = dot(V + (size_t)i * N, w, N);
+      for (int32_t i = 0; i <= j; ++i) {
+        const double* vi = V + (size_t)i * N;
+        for (int32_t t = 0; t < N; ++t) w[t] -= hp[i] * vi[t];
+      }
+      for (int32_t i = 0; i <= j; ++i) hcol[i] += hp[i];
+    }
+    free(hp);
+  }
+  hcol[j + 1] = nrm2(w, N);
+}
+
+int orc_arnoldi(int32_t N, const int32_t* rowptr, const int32_t* col, const double* val,
+                const orc_defl* d, int32_t defl_mode, double mu, int32_t ortho,
+                const double* v0, int32_t k, double* V, double* H) {
+  double* w = (double*)malloc(sizeof(double) * (size_t)N);
+  double* tmp = (double*)malloc(sizeof(double) * (size_t)N);
+  double* hcol = (double*)malloc(sizeof(double) * (size_t)(k + 1));
+  memset(H, 0, sizeof(double) * (size_t)(k + 1) * k);
+  double beta = nrm2(v0, N);
+  for (int32_t t = 0; t < N; ++t) V[t] = v0[t] / beta;
+  int32_t done = 0;
+  for (int32_t j = 0; j < k; ++j) {
+    apply_op(N, rowptr, col, val, d, defl_mode, mu, V + (size_t)j * N, w, tmp);
+    orthogonalise(N, V, j, ortho, w, hcol);
+    for (int32_t i = 0; i <= j + 1; ++i) H[(size_t)i * k + j] = hcol[i];
+    done = j + 1;
+    if (hcol[j + 1] == 0.0) break;
+    for (int32_t t = 0; t < N; ++t) V[(size_t)(j + 1) * N + t] = w[t] / hcol[j + 1];
+  }
+  free(w);
+  free(tmp);
+  free(hcol);
+  return done;
+}
+
+static int has_nan(double v) { return v != v || isinf(v); }
+
+int orc_gmres(int32_t N, const int32_t* rowptr, const int32_t* col, const double* val,
+              const orc_defl* d, const double* b, const double* x0, const orc_opts* o,
+              double* x, orc_info* info, double* hist) {
+  const int32_t m = o->m;
+  const int mode = d ? o->defl_mode : ORC_DEFL_NONE;
+  memset(info, 0, sizeof(*info));
+  double* V = (double*)malloc(sizeof(double) * (size_t)N * (m + 1));
+  double* H = (double*)calloc((size_t)(m + 1) * m, sizeof(double));  /* rotated */
+  double* Hr = (double*)calloc((size_t)(m + 1) * m, sizeof(double)); /* as built */
+  double* cs = (double*)malloc(sizeof(double) * (size_t)m);
+  double* sn = (double*)malloc(sizeof(double) * (size_t)m);
+  double* g = (double*)malloc(sizeof(double) * (size_t)(m + 1));
+  double* y = (double*)malloc(sizeof(double) * (size_t)m);
+  double* hcol = (double*)malloc(sizeof(double) * (size_t)(m + 1));
+  double* w = (double*)malloc(sizeof(double) * (size_t)N);
+  double* tmp = (double*)malloc(sizeof(double) * (size_t)N);
+  double* r = (double*)malloc(sizeof(double) * (size_t)N);
+
+  for (int32_t i = 0; i < N; ++i) x[i] = x0 ? x0[i] : 0.0;
+
+  /* mu (Sec. 3.3): the largest eigenvalue, estimated from the Ritz values of H_m of the
+   * first cycle, which runs with M = I; or given; or bounded by the infinity norm. */
+  double mu = 0.0;
+  int defl_on = (mode == ORC_DEFL_PROJECTOR);
+  if (mode == ORC_DEFL_EBP) {
+    if (o->mu_mode == ORC_MU_USER) {
+      mu = o->mu_user;
+      defl_on = 1;
+    } else if (o->mu_mode == ORC_MU_NORM_INF) {
+      for (int32_t i = 0; i < N; ++i) {
+        double s = 0.0;
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) s += fabs(val[k]);
+        if (s > mu) mu = s;
+      }
+      defl_on = 1;
+    }
+  }
+
+  /* residual of the current iterate; with the projector, b - A x = P (b - A xhat) */
+  #define TRUE_RESIDUAL()                                   \
+    do {                                                     \
+      orc_spmv(N, rowptr, col, val, x, tmp);                 \
+      for (int32_t i_ = 0; i_ < N; ++i_) r[i_] = b[i_] - tmp[i_]; \
+      if (mode == ORC_DEFL_PROJECTOR) {                      \
+        orc_defl_apply_P(d, r, tmp);                         \
+        memcpy(r, tmp, sizeof(double) * (size_t)N);          \
+      }                                                      \
+    } while (0)
+
+  /* reference norm rho0 = ||b - A x0|| of the original system (Eq. 15) */
+  orc_spmv(N, rowptr, col, val, x, tmp);
+  for (int32_t i = 0; i < N; ++i) r[i] = b[i] - tmp[i];
+  double rho0 = o->r0_norm_ref > 0.0 ? o->r0_norm_ref : nrm2(r, N);
+  int status = 1;
+  int64_t steps = 0, cycles = 0;
+  double est = 1.0, truerel = 1.0;
+  if (has_nan(rho0)) {
+    status = -5;
+    goto done;
+  }
+  if (rho0 == 0.0) {
+    status = 0;
+    est = truerel = 0.0;
+    goto done;
+  }
+  if (mode == ORC_DEFL_PROJECTOR) TRUE_RESIDUAL();
+
+  for (;;) {
+    double beta = nrm2(r, N);
+    truerel = beta / rho0;
+    if (has_nan(beta)) {
+      status = -5;
+      break;
+    }
+    if (beta == 0.0 || (!o->fixed_iterations && truerel <= o->tol)) {
+      status = 0;
+      break;
+    }
+    if (steps >= o->maxit) {
+      status = 1;
+      break;
+    }
+    /* one cycle of GMRES(m): Arnoldi from v1 = r/beta, g = beta e1 */
+    for (int32_t i = 0; i < N; ++i) V[i] = r[i] / beta;
+    for (int32_t i = 0; i <= m; ++i) g[i] = 0.0;
+    g[0] = beta;
+    int32_t k = 0;
+    int use_defl = defl_on ? mode : ORC_DEFL_NONE;
+    for (int32_t j = 0; j < m && steps < o->maxit; ++j) {
+      apply_op(N, rowptr, col, val, d, use_defl, mu, V + (size_t)j * N, w, tmp);
+      orthogonalise(N, V, j, o->ortho, w, hcol);
+      double hnext = hcol[j + 1];
+      double hn2 = 0.0;
+      for (int32_t i = 0; i <= j + 1; ++i) {
+        Hr[(size_t)i * m + j] = hcol[i];
+        H[(size_t)i * m + j] = hcol[i];
+        hn2 += hcol[i] * hcol[i];
+      }
+      if (has_nan(hnext)) {
+        status = -5;
+        goto done;
+      }
+      /* apply the previous plane rotations to the new column (Eq. 12) */
+      for (int32_t i = 0; i < j; ++i) {
+        double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+      }
+      /* new rotation annihilating h_{j+1,j} */
+      double a = H[(size_t)j * m + j];
+      if (hnext == 0.0) {
+        cs[j] = 1.0;
+        sn[j] = 0.0;
+      } else {
+        double rho = hypot(a, hnext);
+        cs[j] = a / rho;
+        sn[j] = hnext / rho;
+        H[(size_t)j * m + j] = rho;
+      }
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++steps;
+      k = j + 1;
+      est = fabs(g[j + 1]) / rho0; /* ||b - A x_k|| = |gamma_{k+1}|  (Eq. 14) */
+      if (hist) {
+        hist[2 * (steps - 1)] = (double)j;
+        hist[2 * (steps - 1) + 1] = est;
+      }
+      if (hnext <= 1e-14 * sqrt(hn2)) break; /* (lucky) breakdown: K_j is invariant */
+      if (!o->fixed_iterations && est <= o->tol) break;
+      for (int32_t i = 0; i < N; ++i) V[(size_t)(j + 1) * N + i] = w[i] / hnext;
+    }
+    /* least squares solution by back substitution with R_k (Eq. 12) */
+    for (int32_t i = k - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int32_t l = i + 1; l < k; ++l) s -= H[(size_t)i * m + l] * y[l];
+      y[i] = s / H[(size_t)i * m + i];
+    }
+    /* x += M^-1 V_k y  (Eqs. 11 and 16) */
+    for (int32_t i = 0; i < N; ++i) w[i] = 0.0;
+    for (int32_t l = 0; l < k; ++l)
+      for (int32_t i = 0; i < N; ++i) w[i] += y[l] * V[(size_t)l * N + i];
+    if (use_defl == ORC_DEFL_EBP) {
+      orc_defl_apply_Minv(d, mu, w, tmp);
+      for (int32_t i = 0; i < N; ++i) x[i] += tmp[i];
+    } else {
+      for (int32_t i = 0; i < N; ++i) x[i] += w[i];
+    }
+    ++cycles;
+    if (mode == ORC_DEFL_EBP && !defl_on) {
+      /* Ritz values of H_k from the first cycle give |mu| */
+      double* hk = (double*)malloc(sizeof(double) * (size_t)k * k);
+      double* wr = (double*)malloc(sizeof(double) * (size_t)k);
+      double* wi = (double*)malloc(sizeof(double) * (size_t)k);
+      for (int32_t i = 0; i < k; ++i)
+        for (int32_t l = 0; l < k; ++l) hk[(size_t)i * k + l] = Hr[(size_t)i * m + l];
+      int e = orc_hessenberg_eigs(k, hk, wr, wi);
+      mu = 0.0;
+      for (int32_t i = 0; i < k; ++i) {
+        double md = hypot(wr[i], wi[i]);
+        if (md > mu) mu = md;
+      }
+      free(hk);
+      free(wr);
+      free(wi);
+      if (e != 0 || mu == 0.0) {
+        status = -4;
+        break;
+      }
+      defl_on = 1;
+    }
+    TRUE_RESIDUAL();
+  }
+  #undef TRUE_RESIDUAL
+
+done:
+  if (mode == ORC_DEFL_PROJECTOR && status >= 0) {
+    /* x = xhat + U T^-1 U^T (b - A xhat): adds the coarse component */
+    orc_spmv(N, rowptr, col, val, x, tmp);
+    for (int32_t i = 0; i < N; ++i) r[i] = b[i] - tmp[i];
+    double* c = (double*)malloc(sizeof(double) * (size_t)d->r);
+    defl_Ut(d, r, c);
+    orc_lu_solve(d->r, d->lu, d->piv, c);
+    defl_U_add(d, c, x);
+    free(c);
+  }
+  if (status >= 0 && rho0 > 0.0) {
+    orc_spmv(N, rowptr, col, val, x, tmp);
+    for (int32_t i = 0; i < N; ++i) r[i] = b[i] - tmp[i];
+    truerel = nrm2(r, N) / rho0;
+  }
+  info->iters = steps;
+  info->cycles = cycles;
+  info->status = status;
+  info->rel_res_est = est;
+  info->rel_res_true = truerel;
+  info->mu = mu;
+  free(V);
+  free(H);
+  free(Hr);
+  free(cs);
+  free(sn);
+  free(g);
+  free(y);
+  free(hcol);
+  free(w);
+  free(tmp);
+  free(r);
+  return status;
+}

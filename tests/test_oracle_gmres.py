@@ -1,0 +1,241 @@
+"""Pins for the oracle's deflated restarted GMRES(m) (Sec. 3.2-3.3, Eqs. 10-18).
+
+Each test fixes a property that the mathematics decides independently of the oracle:
+agreement with a sparse direct solve, finite termination, the monotone residual estimate,
+estimate = true residual under right preconditioning (Eq. 14), the Arnoldi relation
+(Eq. 13) checked with dense numpy algebra, the exact eigenvalue shift of the deflation
+preconditioner (Eq. 17), and the projector identity P A W = 0.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import workloads as W
+
+
+def _system(orc, n, pe=20.0, sigma=0.4, seed=11, px=2, py=2, f_kind="uniform"):
+    p = W.convdiff(n, pe=pe, sigma=sigma, seed=seed, px=px, py=py, f_kind=f_kind)
+    A, b = orc.q1_assemble(n, p.kappa, p.beta, p.f)
+    return p, A, b
+
+
+def _dense_U(agg, r):
+    N = len(agg)
+    U = np.zeros((N, r))
+    for p in range(r):
+        idx = np.nonzero(agg == p)[0]
+        U[idx, p] = 1.0 / np.sqrt(len(idx))
+    return U
+
+
+MODES = [("none", None), ("ebp", 1), ("projector", 2)]
+
+
+@pytest.mark.parametrize("n", [4, 8, 16])
+@pytest.mark.parametrize("mode", ["none", "ebp", "projector"])
+@pytest.mark.parametrize("ortho", [0, 1])
+def test_gmres_matches_direct_solve(orc, n, mode, ortho):
+    p, A, b = _system(orc, n)
+    xd = spla.spsolve(A.to_scipy().tocsc(), b)
+    defl = None if mode == "none" else orc.Deflation(A, p.agg, p.r)
+    dm = {"none": 0, "ebp": 1, "projector": 2}[mode]
+    x, info = orc.gmres(A, b, m=10, tol=1e-14, maxit=4000, defl=defl, defl_mode=dm, ortho=ortho)
+    assert info["status"] == 0, info
+    assert np.linalg.norm(x - xd) <= 1e-11 * np.linalg.norm(xd)
+    assert info["rel_res_true"] <= 1e-13
+
+
+@pytest.mark.parametrize("n", [4, 8])
+def test_exact_termination_without_restart(orc, n):
+    p, A, b = _system(orc, n)
+    N = A.n
+    x, info = orc.gmres(A, b, m=N, tol=1e-14, maxit=N)
+    assert info["iters"] <= N and info["cycles"] == 1
+    assert info["rel_res_true"] <= 1e-10
+
+
+def test_diagonal_with_k_distinct_eigenvalues(orc):
+    rng = np.random.default_rng(3)
+    N, k = 60, 5
+    d = rng.integers(1, k + 1, N).astype(float)
+    assert len(np.unique(d)) == k
+    A = orc.CSR(np.arange(N + 1), np.arange(N), d)
+    b = rng.standard_normal(N)
+    x, info = orc.gmres(A, b, m=20, tol=1e-12, maxit=100)
+    assert info["iters"] == k
+    np.testing.assert_allclose(x, b / d, rtol=1e-12)
+
+
+def test_identity_one_step(orc):
+    N = 17
+    A = orc.CSR(np.arange(N + 1), np.arange(N), np.ones(N))
+    b = np.arange(1.0, N + 1)
+    x, info = orc.gmres(A, b, m=5, tol=1e-14, maxit=10)
+    assert info["iters"] == 1 and info["status"] == 0
+    np.testing.assert_allclose(x, b, rtol=1e-15)
+
+
+def test_zero_rhs_returns_x0(orc):
+    p, A, b = _system(orc, 6)
+    x, info = orc.gmres(A, np.zeros(A.n), m=5)
+    assert info["iters"] == 0 and info["status"] == 0 and not np.any(x)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_residual_estimate_monotone_within_cycles(orc, mode):
+    p, A, b = _system(orc, 24, pe=60.0)
+    defl = None if mode == 0 else orc.Deflation(A, p.agg, p.r)
+    x, info, hist = orc.gmres(A, b, m=15, tol=1e-10, maxit=3000, defl=defl, defl_mode=mode,
+                              history=True)
+    assert info["status"] == 0
+    for t in range(1, len(hist)):
+        if hist[t, 0] > 0:  # same cycle as the previous step
+            assert hist[t, 1] <= hist[t - 1, 1] * (1 + 1e-13)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_estimate_equals_true_residual(orc, mode):
+    # right preconditioning keeps ||b - A x_k|| = |gamma_{k+1}| (Eq. 14)
+    p, A, b = _system(orc, 20, pe=30.0)
+    defl = None if mode == 0 else orc.Deflation(A, p.agg, p.r)
+    for maxit in (7, 23, 61):
+        x, info = orc.gmres(A, b, m=10, tol=0.0, maxit=maxit, defl=defl, defl_mode=mode,
+                            fixed_iterations=True, mu_mode=1, mu_user=4.0)
+        assert abs(info["rel_res_est"] - info["rel_res_true"]) <= 1e-10
+
+
+@pytest.mark.parametrize("defl_mode", [0, 1, 2])
+@pytest.mark.parametrize("ortho", [0, 1])
+def test_arnoldi_relation_dense(orc, defl_mode, ortho):
+    p, A, b = _system(orc, 12, pe=40.0, px=2, py=3)
+    Ad = A.to_scipy().toarray()
+    U = _dense_U(p.agg, p.r)
+    mu = 5.5
+    T = U.T @ Ad @ U
+    if defl_mode == 1:
+        Op = Ad @ (np.eye(A.n) + U @ (abs(mu) * np.linalg.inv(T) - np.eye(p.r)) @ U.T)
+    elif defl_mode == 2:
+        Op = (np.eye(A.n) - Ad @ U @ np.linalg.inv(T) @ U.T) @ Ad
+    else:
+        Op = Ad
+    defl = orc.Deflation(A, p.agg, p.r)
+    k = 25
+    V, H, done = orc.arnoldi(A, b, k, defl=defl, defl_mode=defl_mode, mu=mu, ortho=ortho)
+    assert done == k
+    scale = np.linalg.norm(Op, 2)
+    assert np.linalg.norm(Op @ V[:, :k] - V @ H) <= 1e-13 * scale * np.sqrt(k)
+    # CGS2 keeps orthogonality at rounding level; MGS loses it in proportion to the
+    # condition number of the Krylov basis, so only a loose bound applies to it
+    tol = 1e-13 if ortho == 0 else 1e-7
+    assert np.linalg.norm(V.T @ V - np.eye(k + 1)) <= tol
+    assert np.allclose(np.tril(H, -2), 0.0)
+
+
+def test_deflation_T_is_UtAU(orc):
+    p, A, b = _system(orc, 10, px=3, py=2)
+    U = _dense_U(p.agg, p.r)
+    defl = orc.Deflation(A, p.agg, p.r)
+    np.testing.assert_allclose(defl.T(), U.T @ A.to_scipy().toarray() @ U, rtol=1e-13,
+                               atol=1e-14)
+
+
+def test_ebp_moves_deflated_eigenvalues_to_mu(orc):
+    # U^T (A M^-1) U = |mu| I for any orthonormal U (Eq. 17 with T = U^T A U)
+    p, A, b = _system(orc, 10, px=2, py=2)
+    defl = orc.Deflation(A, p.agg, p.r)
+    U = _dense_U(p.agg, p.r)
+    mu = -7.25
+    AMU = np.stack([A.matvec(defl.apply_Minv(mu, U[:, q])) for q in range(p.r)], axis=1)
+    np.testing.assert_allclose(U.T @ AMU, abs(mu) * np.eye(p.r), atol=1e-13 * abs(mu))
+
+
+def test_ebp_exact_invariant_subspace(orc):
+    # block-diagonal A whose blocks have constant row sums: the aggregate indicators span
+    # an invariant subspace, so A M^-1 U = |mu| U and the other eigenvalues are unchanged
+    rng = np.random.default_rng(7)
+    r, s = 3, 5
+    blocks, lam = [], []
+    for q in range(r):
+        B = rng.standard_normal((s, s)) * 0.3
+        B += np.diag(2.0 + q - B.sum(axis=1))  # row sums equal 2 + q
+        blocks.append(B)
+        lam.append(2.0 + q)
+    Ad = sp.block_diag(blocks).toarray()
+    S = sp.csr_matrix(Ad)
+    S.sort_indices()
+    A = orc.CSR(S.indptr, S.indices, S.data)
+    agg = np.repeat(np.arange(r), s).astype(np.int32)
+    defl = orc.Deflation(A, agg, r)
+    mu = 9.0
+    Minv = np.stack([defl.apply_Minv(mu, e) for e in np.eye(r * s)], axis=1)
+    ev = np.sort_complex(np.linalg.eigvals(Ad @ Minv))
+    ref = list(np.linalg.eigvals(Ad))
+    for l in lam:  # each block gives up its constant-vector eigenvalue
+        j = int(np.argmin([abs(z - l) for z in ref]))
+        ref[j] = mu
+    np.testing.assert_allclose(np.sort_complex(np.array(ref)), ev, atol=1e-10)
+
+
+def test_projector_identities(orc):
+    p, A, b = _system(orc, 11, px=2, py=3)
+    defl = orc.Deflation(A, p.agg, p.r)
+    Wm = np.stack([(p.agg == q).astype(float) for q in range(p.r)], axis=1)
+    AW = np.stack([A.matvec(Wm[:, q]) for q in range(p.r)], axis=1)
+    PAW = np.stack([defl.apply_P(AW[:, q]) for q in range(p.r)], axis=1)
+    assert np.linalg.norm(PAW) <= 1e-13 * np.linalg.norm(AW)
+    rng = np.random.default_rng(1)
+    v = rng.standard_normal(A.n)
+    Pv = defl.apply_P(v)
+    assert np.linalg.norm(Wm.T @ Pv) <= 1e-12 * np.linalg.norm(v) * np.sqrt(A.n)
+    np.testing.assert_allclose(defl.apply_P(Pv), Pv, atol=1e-12 * np.linalg.norm(v))
+
+
+def test_empty_aggregate_is_rejected(orc):
+    p, A, b = _system(orc, 6)
+    agg = p.agg.copy()
+    agg[agg == 1] = 0  # aggregate 1 now has no node: W has a zero column
+    with pytest.raises(ValueError):
+        orc.Deflation(A, agg, p.r)
+
+
+def test_deflation_reduces_steps_on_workload1(orc):
+    p = W.workload1()
+    A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f)
+    defl = orc.Deflation(A, p.agg, p.r)
+    _, i_defl = orc.gmres(A, b, m=30, tol=1e-8, maxit=5000, defl=defl)
+    _, i_none = orc.gmres(A, b, m=30, tol=1e-8, maxit=5000)
+    assert i_defl["status"] == 0 and i_none["status"] == 0
+    assert i_defl["iters"] <= i_none["iters"]
+
+
+def test_mgs_and_cgs2_agree_at_fixed_iterations(orc):
+    p, A, b = _system(orc, 32, pe=50.0, px=4, py=4)
+    defl = orc.Deflation(A, p.agg, p.r)
+    kw = dict(m=20, tol=0.0, maxit=100, defl=defl, fixed_iterations=True, mu_mode=1,
+              mu_user=6.0)
+    x1, _ = orc.gmres(A, b, ortho=0, **kw)
+    x2, _ = orc.gmres(A, b, ortho=1, **kw)
+    assert np.linalg.norm(x1 - x2) <= 1e-10 * np.linalg.norm(x1)
+
+
+def test_ritz_mu_is_spectral_radius_estimate(orc):
+    # Ritz values lie in the field of values, so |mu| <= ||A||_2, and with a long first
+    # cycle |mu| approaches the spectral radius
+    p, A, b = _system(orc, 10, pe=5.0)
+    Ad = A.to_scipy().toarray()
+    rho = np.abs(np.linalg.eigvals(Ad)).max()
+    norm2 = np.linalg.norm(Ad, 2)
+    defl = orc.Deflation(A, p.agg, p.r)
+    mus = []
+    for m in (5, 20, 60):
+        _, info = orc.gmres(A, b, m=m, tol=1e-30, maxit=m + 1, defl=defl)
+        mus.append(info["mu"])
+    assert all(mu <= norm2 * (1 + 1e-12) for mu in mus)
+    assert abs(mus[-1] - rho) <= 0.02 * rho
+
+
+def test_maxit_reports_not_converged(orc):
+    p, A, b = _system(orc, 16)
+    x, info = orc.gmres(A, b, m=5, tol=1e-14, maxit=12)
+    assert info["status"] == 1 and info["iters"] == 12
