@@ -1,0 +1,214 @@
+/*
+ * gmres_gb300.h -- C ABI of the GB300 (sm_103a) deflated restarted GMRES(m) library.
+ *
+ * Method: Ioannidis et al., "On the performance of various parallel GMRES
+ * implementations on CPU and GPU clusters", arXiv:1906.04051.
+ *   Sec. 3.2, Eqs. 10-15  restarted GMRES(m): Arnoldi basis V_m of K_m(A, r0/||r0||),
+ *                         least squares min ||beta e1 - Hbar_m y|| by plane rotations,
+ *                         residual estimate |gamma_{k+1}|, restart with x_m as new x0,
+ *                         stop when ||b - A x|| / ||b - A x0|| falls below tol.
+ *   Sec. 3.3, Eqs. 16-18  right preconditioning A M^-1 z = b, x = M^-1 z, with the
+ *                         deflation preconditioner M^-1 = I + U (|mu| T^-1 - I) U^T,
+ *                         T = U^T A U, mu the largest eigenvalue of A estimated from the
+ *                         Ritz values of H_m.
+ *   Sec. 3.1, Eqs. 6-8    Galerkin finite-element assembly with Dirichlet rows replaced
+ *                         by u_i = 0 (here: bilinear Q1 elements on the unit square).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named "device" must point to memory of the current CUDA device; the
+ *     library never dereferences them on the host.  Host pointers are marked "host".
+ *   - A "stream" argument is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All device work of a call is enqueued on that stream.
+ *   - Matrices are CSR with int32 row pointers and int32 column indices, columns strictly
+ *     ascending within each row, no duplicates, values in FP64.
+ *   - Negative status = error: nothing about the outputs is guaranteed.  A positive
+ *     status (GMRES_NOT_CONVERGED) is a normal return: x holds the last iterate and the
+ *     info struct is valid.
+ *   - No entry point falls back to the CPU: every arithmetic step runs in this library's
+ *     CUDA kernels.
+ */
+#ifndef GMRES_GB300_H
+#define GMRES_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gmres_s* gmres_t; /* opaque handle: owns device copies and workspace */
+
+typedef enum {
+  GMRES_OK = 0,
+  GMRES_NOT_CONVERGED = 1,        /* maxit Arnoldi steps done without reaching tol */
+  GMRES_ERR_INVALID_ARG = -1,     /* bad size, pointer, option, CSR or aggregate map */
+  GMRES_ERR_CUDA = -2,            /* a CUDA runtime call failed; see gmres_last_error */
+  GMRES_ERR_OOM = -3,             /* device allocation failed */
+  GMRES_ERR_SINGULAR_COARSE = -4, /* empty aggregate (zero column of W), singular T, or
+                                     no usable Ritz estimate of mu */
+  GMRES_ERR_NAN = -5,             /* NaN/Inf met in a residual or Hessenberg entry */
+  GMRES_ERR_TIMEOUT = -6          /* opts.timeout_ms elapsed (checked at restarts) */
+} gmres_status;
+
+/* Matrix A (Eq. 1), n x n.  All arrays device, read during gmres_create only: the
+ * library keeps its own copies, so the caller may free them afterwards. */
+typedef struct {
+  int32_t n;
+  int64_t nnz;
+  const int32_t* rowptr; /* n+1 entries, rowptr[0] = 0, rowptr[n] = nnz, nnz < 2^31 */
+  const int32_t* col;    /* nnz entries in [0, n), strictly ascending per row */
+  const double* val;     /* nnz entries */
+} gmres_csr;
+
+/* Deflation space W (Eq. 17): r indicator columns of disjoint aggregates.
+ * agg (device, n entries): aggregate of each row in [0, r), or -1 for none.  The
+ * library forms U = W diag(1/sqrt|agg_p|), which has orthonormal columns, and
+ * T = U^T A U.  r = 0 (agg may be NULL) disables deflation.  1 <= r <= 6144
+ * otherwise; every aggregate must be non-empty. */
+typedef struct {
+  int32_t r;
+  const int32_t* agg;
+} gmres_defl;
+
+typedef enum {
+  GMRES_FP64 = 0,        /* everything in FP64 */
+  GMRES_FP32_INNER = 1,  /* each restart cycle (inner solve) runs SpMV and Arnoldi in
+                            FP32 with an FP32 basis; H, Givens, the coarse solve, the
+                            true residual r = b - A x and the update of x stay FP64
+                            (iterative refinement: one inner cycle per refinement) */
+  GMRES_BF16_BASIS = 2   /* as GMRES_FP32_INNER, with the basis V stored in BF16 and
+                            FP32 accumulation */
+} gmres_precision;
+
+typedef enum {
+  GMRES_DEFL_EBP = 0,       /* M^-1 = I + U (|mu| T^-1 - I) U^T  (Eq. 17, the paper's) */
+  GMRES_DEFL_PROJECTOR = 1, /* P = I - A U T^-1 U^T: GMRES on P A xh = P b, then
+                               x = xh + U T^-1 U^T (b - A xh); P A W = 0 */
+  GMRES_DEFL_NONE = 2
+} gmres_deflation_mode;
+
+typedef enum {
+  GMRES_MU_RITZ_FIRST_CYCLE = 0, /* cycle 1 runs with M = I; |mu| = largest modulus of
+                                    the eigenvalues of its H_k (Ritz values, Sec. 3.3) */
+  GMRES_MU_USER = 1,             /* |mu| = |opts.mu_user| */
+  GMRES_MU_NORM_INF = 2          /* |mu| = max_i sum_j |a_ij| (an upper bound) */
+} gmres_mu_mode;
+
+typedef struct {
+  int32_t precision;        /* gmres_precision */
+  int32_t deflation_mode;   /* gmres_deflation_mode */
+  int32_t mu_mode;          /* gmres_mu_mode */
+  double mu_user;
+  int32_t fixed_iterations; /* 1: no convergence test; exactly maxit Arnoldi steps
+                               (the fixed 50 x 100 protocol of Sec. 4) */
+  double r0_norm_ref;       /* > 0: reference norm for the relative tolerance instead of
+                               ||b - A x0|| (resume after a restart boundary) */
+  int32_t timeout_ms;       /* > 0: give up with GMRES_ERR_TIMEOUT after this long */
+  double inner_tol;         /* mixed precision: a cycle ends once its own residual
+                               estimate falls by this factor (0 = 1e-4 FP32, 1e-2 BF16) */
+  int32_t profile;          /* 1: bracket every phase with CUDA events (gmres_profile) */
+} gmres_opts;
+
+/* Phases reported by gmres_profile (kernel groups of one solve). */
+typedef enum {
+  GMRES_PH_SETUP = 0,     /* gmres_create (host wall time, ms) */
+  GMRES_PH_RESIDUAL = 1,  /* r = b - A x in FP64 and the restart decision (Eq. 15) */
+  GMRES_PH_SPMV = 2,      /* w = A M^-1 v_j (Eqs. 16-17) */
+  GMRES_PH_DOT1 = 3,      /* CGS2 pass 1: h = V^T w */
+  GMRES_PH_UPD1DOT2 = 4,  /* CGS2 pass 2: w -= V h, h' = V^T w */
+  GMRES_PH_UPD2NORM = 5,  /* CGS2 pass 3: w -= V h', ||w|| and the plane rotations */
+  GMRES_PH_DEFL = 6,      /* U^T v and the coarse correction (Eqs. 17-18) */
+  GMRES_PH_CYCLE_END = 7, /* back substitution and x += M^-1 V y (Eq. 11) */
+  GMRES_PH_RITZ = 8,      /* |mu| from the Ritz values of H_k */
+  GMRES_PH_COUNT = 9
+} gmres_phase;
+
+typedef struct {
+  int64_t iters;        /* Arnoldi steps done */
+  int64_t cycles;       /* restart cycles (= refinements in mixed precision) */
+  int64_t refinements;  /* FP64 residual recomputations after an inner cycle */
+  double rel_res_est;   /* |gamma_{k+1}| / rho0 of the last step (Eq. 14) */
+  double rel_res_true;  /* ||b - A x|| / rho0 in FP64 at return (Eq. 15) */
+  double mu;            /* |mu| used by the EBP preconditioner (0 if none) */
+  float ms_total;       /* device time of the solve, CUDA events on the handle stream */
+  int32_t status;       /* same as the return value */
+} gmres_info;
+
+/* Fills *o with the defaults: FP64, EBP, Ritz mu, no fixed iterations, no timeout. */
+void gmres_opts_default(gmres_opts* o);
+
+/* Setup (Eqs. 17-18): validates and copies A and the aggregate map, builds the
+ * aggregate permutation, U's scaling, T = U^T A U and T^-1 (Gauss-Jordan with partial
+ * pivoting), all on the device.  *h receives the handle.  W may be NULL (no deflation).
+ * o may be NULL (defaults).  Synchronises the stream before returning.
+ * Errors: INVALID_ARG (n <= 0, null pointers, unsorted/out-of-range CSR, agg out of
+ * range, r > 6144), SINGULAR_COARSE (empty aggregate, zero pivot in T), OOM, CUDA. */
+gmres_status gmres_create(gmres_t* h, const gmres_csr* A, const gmres_defl* W,
+                          const gmres_opts* o, void* stream);
+
+/* Solves A x = b by deflated GMRES(m) (Sec. 3.2-3.3).  b (device, n), x0 (device, n,
+ * may be NULL = zero), x (device, n, may alias x0).  m: restart length, 1 <= m <= 64.
+ * tol >= 0: relative residual target.  maxit >= 0: total Arnoldi steps.  info (host,
+ * may be NULL).  Returns after the stream is synchronised.  Workspace is owned by the
+ * handle and grown on demand: calls on one handle must not overlap. */
+gmres_status gmres_solve(gmres_t h, const double* b, const double* x0, int32_t m,
+                         double tol, int64_t maxit, double* x, gmres_info* info);
+
+/* Adjoint solve A^T lam = g with the transposed preconditioner
+ * M^-T = I + U (|mu| T^-T - I) U^T (same U; T^T = U^T A^T U).  The transpose of A is
+ * built on the first call and kept.  Arguments as gmres_solve. */
+gmres_status gmres_adjoint_solve(gmres_t h, const double* g, const double* lam0, int32_t m,
+                                 double tol, int64_t maxit, double* lam, gmres_info* info);
+
+/* Solves count independent systems, system i with handle hs[i] (host array), in one
+ * persistent launch on `stream`.  b, x0, x: host arrays of count device pointers (x0
+ * may be NULL, or contain NULLs).  infos: host array of count entries, may be NULL.
+ * All handles must use the same precision.  Returns the worst status. */
+gmres_status gmres_batch_solve(int32_t count, gmres_t const* hs, const double* const* b,
+                               const double* const* x0, int32_t m, double tol,
+                               int64_t maxit, double* const* x, gmres_info* infos,
+                               void* stream);
+
+/* Per-phase device time (ms, from CUDA events on the handle stream while profiling is on;
+ * the setup entry is host wall time) and kernel launch counts (always counted) summed
+ * since the last reset.  ms and launches (host, GMRES_PH_COUNT entries each) may be NULL.
+ * reset != 0 zeroes the sums after reading them.  enable: 1 on, 0 off, -1 unchanged.
+ * Host-only; never blocks. */
+gmres_status gmres_profile(gmres_t h, int32_t enable, int32_t reset, double* ms,
+                           int64_t* launches);
+
+gmres_status gmres_set_stream(gmres_t h, void* stream);
+/* Message of the last error on this handle (or of the last failed create when h is
+ * NULL).  Owned by the library, valid until the next call on the handle. */
+const char* gmres_last_error(gmres_t h);
+void gmres_destroy(gmres_t h);
+
+/* ---- Q1 Galerkin assembly on the device (Sec. 3.1, Eqs. 6-8) -------------------------
+ * Unit square, n x n square elements, node (i, j) -> j*(n+1)+i.  A has the mesh
+ * connectivity pattern; each boundary row is replaced by u_i = 0 (one entry 1.0,
+ * b_i = 0); interior rows keep their couplings to boundary columns. */
+
+/* nnz of the assembled matrix: 9 (n-1)^2 + 4 n. */
+int64_t q1_nnz(int32_t n);
+
+/* kappa (device, n*n, element (ei, ej) at ej*n+ei): per-element diffusion coefficient.
+ * (bx, by): convection vector.  f (device, (n+1)^2): nodal load values, b = M f on
+ * interior rows (consistent mass matrix).  u (device, (n+1)^2, may be NULL): a nodal
+ * linearisation point, b -= K u on interior rows.  Outputs (device): rowptr
+ * ((n+1)^2 + 1 entries), col and val (q1_nnz(n) entries), b ((n+1)^2 entries).
+ * Deterministic: the same inputs give bitwise identical outputs.
+ * Errors: INVALID_ARG (n < 1, null pointer, nnz >= 2^31), CUDA. */
+gmres_status q1_assemble(int32_t n, const double* kappa, double bx, double by,
+                         const double* f, const double* u, int32_t* rowptr, int32_t* col,
+                         double* val, double* b, void* stream);
+
+/* Adjoint of the assembly with respect to kappa: grad_e = - lam^T (dA/dkappa_e) x
+ * = - sum_{i in e, i interior} lam_i (K1 x_e)_i, where K1 is the unit-kappa element
+ * stiffness.  lam, x (device, (n+1)^2), grad (device, n*n). */
+gmres_status q1_kappa_grad(int32_t n, const double* lam, const double* x, double* grad,
+                           void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GMRES_GB300_H */

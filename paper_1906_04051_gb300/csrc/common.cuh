@@ -1,0 +1,187 @@
+// common.cuh -- shared device helpers of the GB300 GMRES library (sm_103a).
+//
+// Reductions here are deterministic: every partial sum is formed in a fixed order
+// (per-lane strided loops, then an xor-shuffle tree, then fixed-order combination of
+// warps and blocks), so two runs with the same launch shape give bitwise equal results.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gmres_gb300.h"
+
+namespace gg {
+
+constexpr int kWarp = 32;
+constexpr int kMaxM = 64;               // largest restart length m
+constexpr int kMaxK = kMaxM + 1;        // basis columns held in a cycle
+constexpr int kMaxR = 6144;             // largest number of deflation aggregates
+constexpr int kThreads = 256;           // threads of the streaming kernels
+constexpr int kSlices = 8;              // column slices of a multi-dot (one per warp)
+constexpr int kSliceCols = (kMaxK + kSlices - 1) / kSlices;  // 9 accumulators / thread
+constexpr int kPiece = 1024;            // nodes per piece of an aggregate sum
+
+// ---- named slots of the solver control block (device memory) ----
+enum ScalarSlot {
+  S_RHO0 = 0,     // reference norm of the relative tolerance (Eq. 15)
+  S_BETA,         // true residual norm at the start of the current cycle
+  S_BETA_CYCLE,   // norm of the stored start vector (g_0 of the cycle)
+  S_MU,           // |mu| of the EBP preconditioner
+  S_TOL,
+  S_INNER_TOL,
+  S_EST,          // |gamma_{k+1}| / rho0 of the last step
+  S_TRUE,         // true relative residual of the last residual evaluation
+  S_R0REF,        // user reference norm (0 = none)
+  S_NSCAL = 16
+};
+enum FlagSlot {
+  F_CYCLE_DONE = 0,  // the current cycle has ended (remaining step launches return)
+  F_STOP,            // the solve has ended
+  F_STATUS,          // gmres_status of the solve so far
+  F_K,               // Arnoldi steps done in the current cycle
+  F_FIXED,           // fixed-iteration protocol
+  F_MIXED,           // inner-tolerance test active (mixed precision)
+  F_RHO0_SET,
+  F_NFLAGS = 16
+};
+enum CountSlot { C_STEPS = 0, C_CYCLES, C_REFINE, C_MAXIT, C_NCOUNT = 8 };
+
+// Device control block: all pointers into library-owned device memory.
+struct Ctl {
+  double* H;      // (ldh+1) x ldh row-major, Hessenberg columns after rotation (R)
+  double* Hr;     // same shape, Hessenberg as built (for the Ritz values)
+  double* g;      // ldh+1: rotated right-hand side beta e1
+  double* cs;     // ldh: rotation cosines
+  double* sn;     // ldh: rotation sines
+  double* y;      // ldh: least-squares solution of the cycle
+  double* sigma;  // ldh+1: basis scales, v_c = sigma_c * V[:, c]
+  double* h;      // ldh+1: projection coefficients of the current column
+  double* coef;   // ldh+1: coefficients of the pending basis update
+  double* part;   // [max_grid][ldp] per-block partial sums
+  double* scal;   // S_NSCAL scalars
+  double* cpart;  // per-piece partial sums of an aggregate reduction
+  double* sdefl;  // r: correction per aggregate, z = v + sdefl[agg]
+  float* sdefl32; // r: FP32 copy for the FP32 inner kernels
+  int* flags;     // F_NFLAGS
+  unsigned* ticket;         // last-block counters
+  long long* counts;        // C_NCOUNT
+  int ldh;        // m of the workspace
+  int ldp;        // leading dimension of part (>= kMaxK + 1)
+};
+
+// Deflation data of one operator (A or A^T).
+struct Defl {
+  int r;                  // number of aggregates (0 = none)
+  const int* agg;         // N
+  const int* perm;        // nodes sorted by aggregate, then index
+  const int* piece_start; // npieces + 1 offsets into perm
+  const int* agg_piece;   // r + 1 offsets into the piece list
+  const double* uscale;   // r: 1/sqrt|agg_p|
+  const double* tinv;     // r x r row-major T^-1
+  int npieces;
+};
+
+// ---- element-type helpers ----
+template <typename T> __device__ __forceinline__ float to_f(T v);
+template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+
+template <typename TACC, typename T> __device__ __forceinline__ TACC ld_as(const T* p);
+template <> __device__ __forceinline__ double ld_as<double, double>(const double* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ld_as<float, float>(const float* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ld_as<float, __nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(__ldg(p));
+}
+template <> __device__ __forceinline__ double ld_as<double, float>(const float* p) {
+  return (double)__ldg(p);
+}
+template <> __device__ __forceinline__ double ld_as<double, __nv_bfloat16>(const __nv_bfloat16* p) {
+  return (double)__bfloat162float(__ldg(p));
+}
+
+// value conversion (registers / shared memory)
+template <typename TACC, typename T> __device__ __forceinline__ TACC cv(T v);
+template <> __device__ __forceinline__ double cv<double, double>(double v) { return v; }
+template <> __device__ __forceinline__ float cv<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ float cv<float, __nv_bfloat16>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+template <> __device__ __forceinline__ double cv<double, float>(float v) { return (double)v; }
+template <> __device__ __forceinline__ double cv<double, __nv_bfloat16>(__nv_bfloat16 v) {
+  return (double)__bfloat162float(v);
+}
+
+template <typename T> __device__ __forceinline__ T zero_of() { return T(0); }
+template <> __device__ __forceinline__ __nv_bfloat16 zero_of<__nv_bfloat16>() {
+  return __float2bfloat16_rn(0.0f);
+}
+
+// plain (coherent) load: for data written earlier in the same kernel launch
+template <typename TACC, typename T> __device__ __forceinline__ TACC ld_cg(const T* p);
+template <> __device__ __forceinline__ double ld_cg<double, double>(const double* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ float ld_cg<float, float>(const float* p) { return __ldcg(p); }
+
+template <typename T> __device__ __forceinline__ T st_round(float v);
+template <> __device__ __forceinline__ float st_round<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 st_round<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T> __device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
+
+// Block-wide sum of one value per thread (fixed tree); result valid in all threads.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* sbuf /* >= blockDim/32 */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sbuf[warp] = v;
+  __syncthreads();
+  T t = 0;
+  const int nw = blockDim.x >> 5;
+  for (int w = 0; w < nw; ++w) t += sbuf[w];
+  return t;
+}
+
+// Writes this block's ncols partials (smem sred) to part[blockIdx.x*ldp + c].  The last
+// block to arrive (ticket counter) reduces all blocks' partials in a fixed order into
+// tot[c] (shared memory), resets the counter and returns true; the others return false.
+__device__ __forceinline__ bool last_block_reduce(const double* sred, int ncols, double* part,
+                                                  int ldp, unsigned* ticket, double* tot) {
+  __shared__ unsigned s_last;
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x)
+    part[(size_t)blockIdx.x * ldp + c] = sred[c];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < ncols; c += nw) {
+    double s = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(&part[(size_t)b * ldp + c]);
+    s = warp_sum(s);
+    if (lane == 0) tot[c] = s;
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  __syncthreads();
+  return true;
+}
+
+}  // namespace gg

@@ -1,0 +1,82 @@
+// internal.h -- host-side launchers shared between the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace gg {
+
+int grid_for(long long work, int threads, int max_blocks);
+
+// fem.cu
+cudaError_t launch_q1_assemble(int n, const double* kappa, double bx, double by,
+                               const double* f, const double* u, int* rowptr, int* col,
+                               double* val, double* b, cudaStream_t st);
+cudaError_t launch_q1_kappa_grad(int n, const double* lam, const double* x, double* grad,
+                                 cudaStream_t st);
+cudaError_t launch_transpose(int n, int nnz, const int* rowptr, const int* col,
+                             const double* val, int* rowptr_t, int* col_t, double* val_t,
+                             int* scratch, cudaStream_t st);
+
+// setup.cu
+cudaError_t launch_validate(int n, long long nnz, const int* rowptr, const int* col,
+                            const int* agg, int r, int* err, cudaStream_t st);
+int agg_chunks(int n);
+cudaError_t launch_agg_perm(int n, int r, const int* agg, int* counts, int* aggptr, int* cnt,
+                            int* perm, int* agg_piece, int* piece_start, double* uscale,
+                            int* err, cudaStream_t st);
+cudaError_t launch_coarse_T(int r, const int* rowptr, const int* col, const double* val,
+                            const int* agg, const int* perm, const int* aggptr,
+                            const double* uscale, double* T, cudaStream_t st);
+cudaError_t launch_gauss_jordan(int r, const double* T, double* G, double* fac, double* Tinv,
+                                double* TinvT, int* err, cudaStream_t st);
+cudaError_t launch_norm_inf(int n, const int* rowptr, const double* val,
+                            unsigned long long* out, cudaStream_t st);
+cudaError_t launch_to_float(long long n, const double* a, float* b, cudaStream_t st);
+
+// arnoldi.cu: one restart cycle's kernels, by precision
+enum Prec { P_FP64 = 0, P_FP32 = 1, P_BF16 = 2 };
+
+struct OpDev {           // one operator (A or A^T) as the kernels see it
+  int n;
+  const int* rowptr;
+  const int* col;
+  const double* val;     // FP64 values (true residual, FP64 inner)
+  const float* val32;    // FP32 copy (FP32 inner), may be null
+  Defl defl;
+};
+
+struct CycleArgs {
+  OpDev op;
+  Ctl ctl;
+  void* V;               // basis storage (double / float / bf16), column stride ldv
+  long long ldv;
+  void* w;               // working vector (double for FP64, float otherwise)
+  double* t;             // FP64 scratch vector (x update)
+  int prec;
+  int m;                 // restart length of this solve (<= ctl.ldh)
+  int sms;               // multiprocessors of the device
+  int grid_small;        // blocks of the coarse GEMV
+};
+
+// Phases of a solve; each launch_phase call enqueues the kernels of one phase.
+enum Phase {
+  PH_SETUP = 0,     // gmres_create: validation, aggregates, T, T^-1
+  PH_RESIDUAL,      // r = b - A x in FP64, u_0, stopping decision
+  PH_SPMV,          // w = A M^-1 v_j
+  PH_DOT1,          // CGS2 pass 1
+  PH_UPD1DOT2,      // CGS2 pass 2
+  PH_UPD2NORM,      // CGS2 pass 3 + Givens
+  PH_DEFL,          // U^T v_j and the coarse correction
+  PH_CYCLE_END,     // back substitution and x update
+  PH_RITZ,          // |mu| from the Ritz values
+  PH_COUNT
+};
+cudaError_t launch_phase(const CycleArgs& a, int ph, int j, bool defl, double* x,
+                         const double* b, cudaStream_t st, int* launches);
+// Control-block initialisation for a new solve.
+cudaError_t launch_init(const CycleArgs& a, double tol, double inner_tol, double r0ref,
+                        double mu, int fixed, int mixed, long long maxit, cudaStream_t st);
+
+}  // namespace gg

@@ -1,0 +1,340 @@
+// setup.cu -- gmres_create's device work (Sec. 3.3, Eqs. 17-18): CSR validation, the
+// aggregate permutation and piece list used by U^T v, U's column scaling, the coarse
+// matrix T = U^T A U and its inverse by Gauss-Jordan elimination with partial pivoting.
+//
+// Every step is deterministic: integer counting, stable sequential placement inside a
+// block, and floating-point sums taken in a fixed order.
+#include "common.cuh"
+#include "internal.h"
+
+namespace gg {
+
+namespace {
+
+// ---- validation: sets err bits (1 = CSR structure, 2 = agg out of range) ----
+__global__ void k_validate(int n, long long nnz, const int* __restrict__ rowptr,
+                           const int* __restrict__ col, const int* __restrict__ agg, int r,
+                           int* __restrict__ err) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int s = rowptr[i], e = rowptr[i + 1];
+    bool bad = (s > e) || (s < 0) || ((long long)e > nnz);
+    if (i == 0 && s != 0) bad = true;
+    if (i == n - 1 && (long long)e != nnz) bad = true;
+    if (!bad) {
+      int prev = -1;
+      for (int k = s; k < e; ++k) {
+        const int c = col[k];
+        if (c < 0 || c >= n || c <= prev) { bad = true; break; }
+        prev = c;
+      }
+    }
+    if (bad) atomicOr(err, 1);
+    if (agg) {
+      const int a = agg[i];
+      if (a < -1 || a >= r) atomicOr(err, 2);
+    }
+  }
+}
+
+// ---- aggregate permutation: per-chunk counts, scan, stable scatter ----
+constexpr int kChunk = 16384;  // nodes per counting block
+
+__global__ void k_agg_count(int n, int r, const int* __restrict__ agg, int* __restrict__ counts) {
+  extern __shared__ int scnt[];
+  for (int a = threadIdx.x; a < r; a += blockDim.x) scnt[a] = 0;
+  __syncthreads();
+  const int base = blockIdx.x * kChunk;
+  const int end = min(n, base + kChunk);
+  for (int i = base + threadIdx.x; i < end; i += blockDim.x) {
+    const int a = agg[i];
+    if (a >= 0) atomicAdd(&scnt[a], 1);
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < r; a += blockDim.x) counts[(size_t)blockIdx.x * r + a] = scnt[a];
+}
+
+// Single block: counts[b][a] -> global start offsets of chunk b's nodes of aggregate a;
+// aggptr[a] (r+1) -> start of aggregate a in perm; cnt[a] -> size of aggregate a.
+__global__ void k_agg_scan(int r, int nb, int* __restrict__ counts, int* __restrict__ aggptr,
+                           int* __restrict__ cnt) {
+  for (int a = threadIdx.x; a < r; a += blockDim.x) {
+    int run = 0;
+    for (int b = 0; b < nb; ++b) {
+      const int c = counts[(size_t)b * r + a];
+      counts[(size_t)b * r + a] = run;
+      run += c;
+    }
+    cnt[a] = run;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // r <= 6144: a sequential scan is cheap and exact
+    int run = 0;
+    for (int a = 0; a < r; ++a) {
+      aggptr[a] = run;
+      run += cnt[a];
+    }
+    aggptr[r] = run;
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < r; a += blockDim.x) {
+    const int base = aggptr[a];
+    for (int b = 0; b < nb; ++b) counts[(size_t)b * r + a] += base;
+  }
+}
+
+__global__ void k_agg_scatter(int n, int r, const int* __restrict__ agg,
+                              const int* __restrict__ counts, int* __restrict__ perm) {
+  extern __shared__ int soff[];
+  for (int a = threadIdx.x; a < r; a += blockDim.x) soff[a] = counts[(size_t)blockIdx.x * r + a];
+  __syncthreads();
+  if (threadIdx.x == 0) {  // stable: nodes of the chunk in increasing index order
+    const int base = blockIdx.x * kChunk;
+    const int end = min(n, base + kChunk);
+    for (int i = base; i < end; ++i) {
+      const int a = agg[i];
+      if (a >= 0) perm[soff[a]++] = i;
+    }
+  }
+}
+
+// pieces: aggregate a is split into ceil(cnt_a / kPiece) consecutive ranges of perm
+__global__ void k_pieces(int r, const int* __restrict__ aggptr, const int* __restrict__ cnt,
+                         int* __restrict__ agg_piece, int* __restrict__ piece_start,
+                         double* __restrict__ uscale, int* __restrict__ err) {
+  if (threadIdx.x == 0) {
+    int np = 0;
+    for (int a = 0; a < r; ++a) {
+      agg_piece[a] = np;
+      const int c = cnt[a];
+      if (c == 0) atomicOr(err, 4);
+      for (int s = 0; s < c; s += kPiece) piece_start[np++] = aggptr[a] + s;
+    }
+    agg_piece[r] = np;
+    piece_start[np] = aggptr[r];
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < r; a += blockDim.x)
+    uscale[a] = cnt[a] > 0 ? 1.0 / sqrt((double)cnt[a]) : 0.0;
+}
+
+// T row of aggregate p: sum_{i in p} sum_{k in row i, agg(col_k) = q} a_ik, in perm order.
+// Small r: lanes take nodes round-robin into private rows, summed in lane order.
+// Large r: lane 0 accumulates sequentially, the warp loads each row's entries.
+__global__ void k_T_rows(int r, const int* __restrict__ rowptr, const int* __restrict__ col,
+                         const double* __restrict__ val, const int* __restrict__ agg,
+                         const int* __restrict__ perm, const int* __restrict__ aggptr,
+                         const double* __restrict__ uscale, double* __restrict__ T) {
+  extern __shared__ double srow[];
+  const int p = blockIdx.x, lane = threadIdx.x;
+  const int s = aggptr[p], e = aggptr[p + 1];
+  const bool lane_rows = (r * 32 * (int)sizeof(double)) <= 48 * 1024;
+  const int nrows = lane_rows ? 32 : 1;
+  for (int t = lane; t < nrows * r; t += 32) srow[t] = 0.0;
+  __syncwarp();
+  if (lane_rows) {
+    double* mine = srow + (size_t)lane * r;
+    for (int t = s + lane; t < e; t += 32) {
+      const int i = perm[t];
+      for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+        const int q = agg[col[k]];
+        if (q >= 0) mine[q] += val[k];
+      }
+    }
+    __syncwarp();
+    for (int q = lane; q < r; q += 32) {
+      double acc = 0.0;
+      for (int l = 0; l < 32; ++l) acc += srow[(size_t)l * r + q];
+      T[(size_t)p * r + q] = acc * uscale[p] * uscale[q];
+    }
+  } else {
+    for (int t = s; t < e; ++t) {
+      const int i = perm[t];
+      const int ks = rowptr[i], ke = rowptr[i + 1];
+      for (int k0 = ks; k0 < ke; k0 += 32) {
+        const int k = k0 + lane;
+        int q = -1;
+        double v = 0.0;
+        if (k < ke) {
+          q = agg[col[k]];
+          v = val[k];
+        }
+        const int cntk = min(32, ke - k0);
+        for (int l = 0; l < cntk; ++l) {
+          const int ql = __shfl_sync(0xffffffffu, q, l);
+          const double vl = __shfl_sync(0xffffffffu, v, l);
+          if (lane == 0 && ql >= 0) srow[ql] += vl;
+        }
+      }
+    }
+    __syncwarp();
+    for (int q = lane; q < r; q += 32) T[(size_t)p * r + q] = srow[q] * uscale[p] * uscale[q];
+  }
+}
+
+// ---- Gauss-Jordan inverse of T on the augmented r x 2r matrix G = [T | I] ----
+__global__ void k_gj_init(int r, const double* __restrict__ T, double* __restrict__ G) {
+  const long long tot = 2LL * r * r;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / (2 * r)), j = (int)(t % (2 * r));
+    G[t] = j < r ? T[(size_t)i * r + j] : (j - r == i ? 1.0 : 0.0);
+  }
+}
+
+// Step k, part 1 (one block): pivot search in column k (largest |G_ik|, i >= k, first on
+// ties), row swap, scaling of the pivot row, and the elimination factors.
+__global__ void k_gj_pivot(int r, int k, double* __restrict__ G, double* __restrict__ fac,
+                           int* __restrict__ err) {
+  __shared__ double sv[32];
+  __shared__ int si[32];
+  __shared__ int s_piv;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ld = 2 * r;
+  double best = -1.0;
+  int bi = r;
+  for (int i = k + threadIdx.x; i < r; i += blockDim.x) {
+    const double v = fabs(G[(size_t)i * ld + k]);
+    if (v > best) { best = v; bi = i; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+  }
+  if (lane == 0) { sv[warp] = best; si[warp] = bi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = -1.0;
+    int p = r;
+    for (int w = 0; w < nw; ++w)
+      if (sv[w] > b || (sv[w] == b && si[w] < p)) { b = sv[w]; p = si[w]; }
+    if (!(b > 0.0) || p >= r) { atomicOr(err, 8); p = k; }
+    s_piv = p;
+  }
+  __syncthreads();
+  const int p = s_piv;
+  if (p != k)
+    for (int j = threadIdx.x; j < ld; j += blockDim.x) {
+      const double t = G[(size_t)k * ld + j];
+      G[(size_t)k * ld + j] = G[(size_t)p * ld + j];
+      G[(size_t)p * ld + j] = t;
+    }
+  __syncthreads();
+  const double piv = G[(size_t)k * ld + k];
+  const double inv = (piv != 0.0) ? 1.0 / piv : 0.0;
+  __syncthreads();
+  for (int j = threadIdx.x; j < ld; j += blockDim.x) {
+    if (j == k) continue;
+    G[(size_t)k * ld + j] *= inv;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) G[(size_t)k * ld + k] = 1.0;
+  for (int i = threadIdx.x; i < r; i += blockDim.x) fac[i] = (i == k) ? 0.0 : G[(size_t)i * ld + k];
+}
+
+// Step k, part 2: G_ij -= fac_i G_kj for i != k over columns [k, 2r).  (Row swaps move
+// the identity columns of the right half, so all of it stays active.)
+__global__ void k_gj_elim(int r, int k, double* __restrict__ G, const double* __restrict__ fac) {
+  const int ld = 2 * r;
+  const int width = 2 * r - k;
+  const long long tot = (long long)r * width;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / width), j = k + (int)(t % width);
+    const double f = fac[i];
+    if (f != 0.0) G[(size_t)i * ld + j] -= f * G[(size_t)k * ld + j];
+  }
+}
+
+__global__ void k_gj_extract(int r, const double* __restrict__ G, double* __restrict__ Tinv,
+                             double* __restrict__ TinvT) {
+  const long long tot = (long long)r * r;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / r), j = (int)(t % r);
+    const double v = G[(size_t)i * 2 * r + r + j];
+    Tinv[t] = v;
+    if (TinvT) TinvT[(size_t)j * r + i] = v;
+  }
+}
+
+__global__ void k_norm_inf(int n, const int* __restrict__ rowptr, const double* __restrict__ val,
+                           unsigned long long* __restrict__ out) {
+  double best = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) s += fabs(val[k]);
+    best = fmax(best, s);
+  }
+  best = warp_max(best);
+  // non-negative doubles order like their bit patterns: the max is order-independent
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(best));
+}
+
+__global__ void k_to_float(long long n, const double* __restrict__ a, float* __restrict__ b) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    b[t] = (float)a[t];
+}
+
+}  // namespace
+
+cudaError_t launch_validate(int n, long long nnz, const int* rowptr, const int* col,
+                            const int* agg, int r, int* err, cudaStream_t st) {
+  k_validate<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, nnz, rowptr, col, agg, r, err);
+  return cudaGetLastError();
+}
+
+int agg_chunks(int n) { return (n + kChunk - 1) / kChunk; }
+
+cudaError_t launch_agg_perm(int n, int r, const int* agg, int* counts /* chunks*r */,
+                            int* aggptr /* r+1 */, int* cnt /* r */, int* perm,
+                            int* agg_piece /* r+1 */, int* piece_start, double* uscale,
+                            int* err, cudaStream_t st) {
+  const int nb = agg_chunks(n);
+  const size_t sm = sizeof(int) * (size_t)r;
+  k_agg_count<<<nb, 256, sm, st>>>(n, r, agg, counts);
+  k_agg_scan<<<1, 1024, 0, st>>>(r, nb, counts, aggptr, cnt);
+  k_agg_scatter<<<nb, 32, sm, st>>>(n, r, agg, counts, perm);
+  k_pieces<<<1, 256, 0, st>>>(r, aggptr, cnt, agg_piece, piece_start, uscale, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_T(int r, const int* rowptr, const int* col, const double* val,
+                            const int* agg, const int* perm, const int* aggptr,
+                            const double* uscale, double* T, cudaStream_t st) {
+  const bool lane_rows = (r * 32 * (int)sizeof(double)) <= 48 * 1024;
+  const size_t sm = sizeof(double) * (size_t)r * (lane_rows ? 32 : 1);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_T_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  k_T_rows<<<r, 32, sm, st>>>(r, rowptr, col, val, agg, perm, aggptr, uscale, T);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_jordan(int r, const double* T, double* G /* r*2r */, double* fac,
+                                double* Tinv, double* TinvT, int* err, cudaStream_t st) {
+  k_gj_init<<<grid_for(2LL * r * r, 256, 152 * 8), 256, 0, st>>>(r, T, G);
+  for (int k = 0; k < r; ++k) {
+    k_gj_pivot<<<1, 1024, 0, st>>>(r, k, G, fac, err);
+    k_gj_elim<<<grid_for((long long)r * (2 * r - k), 256, 152 * 8), 256, 0, st>>>(r, k, G, fac);
+  }
+  k_gj_extract<<<grid_for((long long)r * r, 256, 152 * 8), 256, 0, st>>>(r, G, Tinv, TinvT);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm_inf(int n, const int* rowptr, const double* val,
+                            unsigned long long* out, cudaStream_t st) {
+  k_norm_inf<<<grid_for(n, 256, 152 * 4), 256, 0, st>>>(n, rowptr, val, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_float(long long n, const double* a, float* b, cudaStream_t st) {
+  k_to_float<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, a, b);
+  return cudaGetLastError();
+}
+
+}  // namespace gg

@@ -1,0 +1,580 @@
+// solver.cu -- C ABI of the library: handle lifetime, setup orchestration and the
+// restart / refinement driver of deflated GMRES(m) (Sec. 3.2-3.3).
+//
+// The driver enqueues one restart cycle at a time (m Arnoldi steps, the cycle end and
+// the true residual) and reads back a 272-byte status block once per cycle; every
+// decision inside a cycle (Givens, stopping tests, breakdown) is taken on the device, so
+// steps after an early exit return at once.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+using namespace gg;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevMem {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevMem() = default;
+  DevMem(const DevMem&) = delete;
+  DevMem& operator=(const DevMem&) = delete;
+  ~DevMem() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  cudaError_t ensure(size_t n) {
+    if (n <= bytes && p) return cudaSuccess;
+    release();
+    cudaError_t e = cudaMalloc(&p, n ? n : 16);
+    if (e == cudaSuccess) bytes = n;
+    return e;
+  }
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+struct Meta {  // mirrors the device status block
+  double scal[S_NSCAL];
+  long long counts[C_NCOUNT];
+  int flags[F_NFLAGS];
+  unsigned ticket[4];
+};
+
+struct OpHost {
+  DevMem rowptr, col, val, val32, tinv;
+  bool ready = false;
+};
+
+}  // namespace
+
+struct gmres_s {
+  int n = 0;
+  long long nnz = 0;
+  cudaStream_t stream = nullptr;
+  gmres_opts opts{};
+  int sms = 152;
+  std::string err;
+  OpHost fwd, adj;
+  // deflation (shared by A and A^T)
+  int r = 0, npieces = 0;
+  DevMem agg, perm, piece_start, agg_piece, uscale;
+  double mu_norminf = 0.0;
+  // workspace
+  int ldh = 0, prec_ws = -1;
+  long long ldv = 0;
+  DevMem V, w, t, dctl, meta, part, cpart, sdefl;
+  Meta* hmeta = nullptr;  // pinned
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // per-phase profiling: events bracket each phase when enabled; launches always counted
+  bool prof_on = false;
+  std::vector<cudaEvent_t> pev;
+  std::vector<int> pph;
+  int pused = 0;
+  double pms[PH_COUNT] = {0};
+  long long plaunch[PH_COUNT] = {0};
+  ~gmres_s() {
+    for (cudaEvent_t e : pev) cudaEventDestroy(e);
+  }
+};
+
+namespace {
+
+gmres_status fail(gmres_s* h, gmres_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+gmres_status cuda_fail(gmres_s* h, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(h, e == cudaErrorMemoryAllocation ? GMRES_ERR_OOM : GMRES_ERR_CUDA, m);
+}
+
+#define CK(h, expr)                                   \
+  do {                                                \
+    cudaError_t e_ = (expr);                          \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #expr); \
+  } while (0)
+
+int prec_of(int precision) {
+  return precision == GMRES_FP32_INNER ? P_FP32 : (precision == GMRES_BF16_BASIS ? P_BF16 : P_FP64);
+}
+
+size_t basis_elem(int prec) { return prec == P_FP64 ? 8 : (prec == P_FP32 ? 4 : 2); }
+
+constexpr int kLdp = 80;  // >= kMaxK + 1, multiple of 16
+
+// Lays out the control block for restart length ldh and returns the Ctl view.
+gmres_status ensure_workspace(gmres_s* h, int m, int prec) {
+  const int ldh = m > h->ldh ? m : h->ldh;
+  const long long ldv = ((long long)h->n + 63) / 64 * 64;
+  const int max_grid = h->sms * 8;
+  if (ldh != h->ldh || prec != h->prec_ws) {
+    CK(h, h->V.ensure(basis_elem(prec) * (size_t)ldv * (ldh + 1)));
+    const size_t nd = 2 * (size_t)(ldh + 1) * ldh + 8 * (size_t)(ldh + 1);
+    CK(h, h->dctl.ensure(sizeof(double) * nd));
+    h->ldh = ldh;
+    h->prec_ws = prec;
+    h->ldv = ldv;
+  }
+  CK(h, h->w.ensure(sizeof(double) * (size_t)h->n));
+  CK(h, h->t.ensure(sizeof(double) * (size_t)h->n));
+  CK(h, h->part.ensure(sizeof(double) * (size_t)max_grid * kLdp));
+  CK(h, h->cpart.ensure(sizeof(double) * (size_t)(h->npieces + 1)));
+  CK(h, h->sdefl.ensure(12 * (size_t)(h->r + 1)));
+  CK(h, h->meta.ensure(sizeof(Meta)));
+  if (!h->hmeta) CK(h, cudaMallocHost(&h->hmeta, sizeof(Meta)));
+  if (!h->ev0) CK(h, cudaEventCreate(&h->ev0));
+  if (!h->ev1) CK(h, cudaEventCreate(&h->ev1));
+  return GMRES_OK;
+}
+
+Ctl make_ctl(gmres_s* h) {
+  Ctl c{};
+  const int ldh = h->ldh;
+  double* d = h->dctl.as<double>();
+  c.H = d;
+  d += (size_t)(ldh + 1) * ldh;
+  c.Hr = d;
+  d += (size_t)(ldh + 1) * ldh;
+  c.g = d; d += ldh + 1;
+  c.cs = d; d += ldh + 1;
+  c.sn = d; d += ldh + 1;
+  c.y = d; d += ldh + 1;
+  c.sigma = d; d += ldh + 1;
+  c.h = d; d += ldh + 1;
+  c.coef = d;
+  Meta* m = h->meta.as<Meta>();
+  c.scal = m->scal;
+  c.counts = m->counts;
+  c.flags = m->flags;
+  c.ticket = m->ticket;
+  c.part = h->part.as<double>();
+  c.cpart = h->cpart.as<double>();
+  c.sdefl = h->sdefl.as<double>();
+  c.sdefl32 = reinterpret_cast<float*>(h->sdefl.as<double>() + (h->r + 1));
+  c.ldh = ldh;
+  c.ldp = kLdp;
+  return c;
+}
+
+OpDev make_op(gmres_s* h, OpHost& o) {
+  OpDev op{};
+  op.n = h->n;
+  op.rowptr = o.rowptr.as<int>();
+  op.col = o.col.as<int>();
+  op.val = o.val.as<double>();
+  op.val32 = o.val32.as<float>();
+  op.defl.r = h->r;
+  op.defl.agg = h->agg.as<int>();
+  op.defl.perm = h->perm.as<int>();
+  op.defl.piece_start = h->piece_start.as<int>();
+  op.defl.agg_piece = h->agg_piece.as<int>();
+  op.defl.uscale = h->uscale.as<double>();
+  op.defl.tinv = o.tinv.as<double>();
+  op.defl.npieces = h->npieces;
+  return op;
+}
+
+gmres_status read_meta(gmres_s* h) {
+  CK(h, cudaMemcpyAsync(h->hmeta, h->meta.p, sizeof(Meta), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return GMRES_OK;
+}
+
+// Starts a profiled segment of phase ph (no-op unless profiling is on).
+cudaError_t prof_mark(gmres_s* h, int ph) {
+  if (!h->prof_on) return cudaSuccess;
+  if (h->pused == (int)h->pev.size()) {
+    cudaEvent_t e;
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return err;
+    h->pev.push_back(e);
+    h->pph.push_back(-1);
+  }
+  cudaError_t err = cudaEventRecord(h->pev[h->pused], h->stream);
+  h->pph[h->pused] = ph;
+  ++h->pused;
+  return err;
+}
+
+// After a stream synchronisation: adds the closed segments to the phase totals and keeps
+// the last event open as the start of the next segment.
+void prof_flush(gmres_s* h, bool close) {
+  if (!h->prof_on || h->pused == 0) return;
+  for (int i = 0; i + 1 < h->pused; ++i) {
+    float ms = 0.f;
+    if (h->pph[i] >= 0 && cudaEventElapsedTime(&ms, h->pev[i], h->pev[i + 1]) == cudaSuccess)
+      h->pms[h->pph[i]] += ms;
+  }
+  if (close) {
+    h->pused = 0;
+    return;
+  }
+  std::swap(h->pev[0], h->pev[h->pused - 1]);
+  h->pph[0] = h->pph[h->pused - 1];
+  h->pused = 1;
+}
+
+cudaError_t phase(gmres_s* h, const CycleArgs& a, int ph, int j, bool defl, double* x,
+                  const double* b) {
+  cudaError_t e = prof_mark(h, ph);
+  if (e != cudaSuccess) return e;
+  int nl = 0;
+  e = launch_phase(a, ph, j, defl, x, b, h->stream, &nl);
+  h->plaunch[ph] += nl;
+  return e;
+}
+
+gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m, double tol,
+                 long long maxit, double* x, gmres_info* info) {
+  if (!b || !x) return fail(h, GMRES_ERR_INVALID_ARG, "b and x must be device pointers");
+  if (m < 1 || m > kMaxM) return fail(h, GMRES_ERR_INVALID_ARG, "m must be in [1, 64]");
+  if (!(tol >= 0.0) || maxit < 0) return fail(h, GMRES_ERR_INVALID_ARG, "tol >= 0, maxit >= 0");
+  const int prec = prec_of(h->opts.precision);
+  gmres_status s = ensure_workspace(h, m, prec);
+  if (s != GMRES_OK) return s;
+  cudaStream_t st = h->stream;
+  const size_t nb = sizeof(double) * (size_t)h->n;
+  if (x != x0) {
+    if (x0) CK(h, cudaMemcpyAsync(x, x0, nb, cudaMemcpyDeviceToDevice, st));
+    else CK(h, cudaMemsetAsync(x, 0, nb, st));
+  }
+  CycleArgs a{};
+  a.op = make_op(h, o);
+  a.ctl = make_ctl(h);
+  a.V = h->V.p;
+  a.ldv = h->ldv;
+  a.w = h->w.p;
+  a.t = h->t.as<double>();
+  a.prec = prec;
+  a.m = m;
+  a.sms = h->sms;
+  a.grid_small = h->r > 0 ? grid_for(h->r, 8, h->sms) : 1;
+
+  const bool ebp = h->r > 0 && h->opts.deflation_mode == GMRES_DEFL_EBP;
+  const int mu_mode = h->opts.mu_mode;
+  double mu = 0.0;
+  if (mu_mode == GMRES_MU_USER) mu = std::fabs(h->opts.mu_user);
+  if (mu_mode == GMRES_MU_NORM_INF) mu = h->mu_norminf;
+  const bool mixed = prec != P_FP64;
+  double inner_tol = h->opts.inner_tol;
+  if (!(inner_tol > 0.0)) inner_tol = prec == P_BF16 ? 1e-2 : 1e-4;
+  const auto t_start = std::chrono::steady_clock::now();
+
+  CK(h, cudaEventRecord(h->ev0, st));
+  CK(h, launch_init(a, tol, inner_tol, h->opts.r0_norm_ref, mu, h->opts.fixed_iterations ? 1 : 0,
+                    mixed ? 1 : 0, maxit, st));
+  h->plaunch[PH_RESIDUAL] += 1;  // the init kernel is counted with the first residual
+  CK(h, phase(h, a, PH_RESIDUAL, 0, false, x, b));
+  s = read_meta(h);
+  if (s != GMRES_OK) return s;
+  prof_flush(h, false);
+  int cycle = 0;
+  gmres_status status = GMRES_OK;
+  while (!h->hmeta->flags[F_STOP]) {
+    const bool defl_cycle = ebp && (mu_mode != GMRES_MU_RITZ_FIRST_CYCLE || cycle > 0);
+    if (defl_cycle) CK(h, phase(h, a, PH_DEFL, 0, true, x, b));
+    const long long left = maxit - h->hmeta->counts[C_STEPS];
+    const int jmax = (int)(left < m ? left : m);
+    for (int j = 0; j < jmax; ++j) {
+      CK(h, phase(h, a, PH_SPMV, j, defl_cycle, x, b));
+      CK(h, phase(h, a, PH_DOT1, j, defl_cycle, x, b));
+      CK(h, phase(h, a, PH_UPD1DOT2, j, defl_cycle, x, b));
+      CK(h, phase(h, a, PH_UPD2NORM, j, defl_cycle, x, b));
+      if (defl_cycle) CK(h, phase(h, a, PH_DEFL, j + 1, true, x, b));
+    }
+    CK(h, phase(h, a, PH_CYCLE_END, 0, defl_cycle, x, b));
+    if (ebp && mu_mode == GMRES_MU_RITZ_FIRST_CYCLE && cycle == 0)
+      CK(h, phase(h, a, PH_RITZ, 0, false, x, b));
+    CK(h, phase(h, a, PH_RESIDUAL, 0, false, x, b));
+    s = read_meta(h);
+    if (s != GMRES_OK) return s;
+    prof_flush(h, false);
+    ++cycle;
+    if (h->opts.timeout_ms > 0 && !h->hmeta->flags[F_STOP]) {
+      const double ms = std::chrono::duration<double, std::milli>(
+                            std::chrono::steady_clock::now() - t_start).count();
+      if (ms > h->opts.timeout_ms) {
+        status = fail(h, GMRES_ERR_TIMEOUT, "timeout_ms elapsed");
+        break;
+      }
+    }
+  }
+  CK(h, prof_mark(h, -1));
+  CK(h, cudaEventRecord(h->ev1, st));
+  CK(h, cudaEventSynchronize(h->ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  prof_flush(h, true);
+  if (status == GMRES_OK) status = (gmres_status)h->hmeta->flags[F_STATUS];
+  if (status == GMRES_ERR_NAN) h->err = "NaN or Inf in the residual or Hessenberg matrix";
+  if (status == GMRES_ERR_SINGULAR_COARSE) h->err = "no usable Ritz estimate of mu";
+  if (info) {
+    info->iters = h->hmeta->counts[C_STEPS];
+    info->cycles = h->hmeta->counts[C_CYCLES];
+    info->refinements = h->hmeta->counts[C_REFINE];
+    info->rel_res_est = h->hmeta->scal[S_EST];
+    info->rel_res_true = h->hmeta->scal[S_TRUE];
+    info->mu = ebp ? h->hmeta->scal[S_MU] : 0.0;
+    info->ms_total = ms;
+    info->status = status;
+  }
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gmres_opts_default(gmres_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = GMRES_FP64;
+  o->deflation_mode = GMRES_DEFL_EBP;
+  o->mu_mode = GMRES_MU_RITZ_FIRST_CYCLE;
+}
+
+gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
+                          const gmres_opts* o, void* stream) {
+  if (!out || !A) return fail(nullptr, GMRES_ERR_INVALID_ARG, "null handle or matrix");
+  *out = nullptr;
+  if (A->n <= 0 || !A->rowptr || !A->col || !A->val || A->nnz < 0 || A->nnz >= (1LL << 31))
+    return fail(nullptr, GMRES_ERR_INVALID_ARG, "invalid CSR description");
+  const int r = (W && W->r > 0) ? W->r : 0;
+  if (r > kMaxR) return fail(nullptr, GMRES_ERR_INVALID_ARG, "r exceeds 6144");
+  if (r > 0 && !W->agg) return fail(nullptr, GMRES_ERR_INVALID_ARG, "agg is null");
+  gmres_opts opts;
+  if (o) opts = *o;
+  else gmres_opts_default(&opts);
+  if (opts.precision < 0 || opts.precision > 2 || opts.deflation_mode < 0 ||
+      opts.deflation_mode > 2 || opts.mu_mode < 0 || opts.mu_mode > 2)
+    return fail(nullptr, GMRES_ERR_INVALID_ARG, "invalid option value");
+  if (opts.deflation_mode == GMRES_DEFL_PROJECTOR && r > 0)
+    return fail(nullptr, GMRES_ERR_INVALID_ARG, "deflation_mode PROJECTOR is not available");
+
+  gmres_s* h = new gmres_s();
+  const auto t_setup = std::chrono::steady_clock::now();
+  h->n = A->n;
+  h->nnz = A->nnz;
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->opts = opts;
+  h->r = r;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
+  auto bail = [&](gmres_status s) {
+    g_create_error = h->err;
+    delete h;
+    return s;
+  };
+#define CKC(expr)                                  \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) return bail(cuda_fail(h, e_, #expr)); \
+  } while (0)
+  cudaStream_t st = h->stream;
+  const int n = h->n;
+  const long long nnz = h->nnz;
+  CKC(h->fwd.rowptr.ensure(sizeof(int) * (size_t)(n + 1)));
+  CKC(h->fwd.col.ensure(sizeof(int) * (size_t)nnz));
+  CKC(h->fwd.val.ensure(sizeof(double) * (size_t)nnz));
+  CKC(cudaMemcpyAsync(h->fwd.rowptr.p, A->rowptr, sizeof(int) * (size_t)(n + 1),
+                      cudaMemcpyDeviceToDevice, st));
+  CKC(cudaMemcpyAsync(h->fwd.col.p, A->col, sizeof(int) * (size_t)nnz, cudaMemcpyDeviceToDevice, st));
+  CKC(cudaMemcpyAsync(h->fwd.val.p, A->val, sizeof(double) * (size_t)nnz,
+                      cudaMemcpyDeviceToDevice, st));
+  if (r > 0) {
+    CKC(h->agg.ensure(sizeof(int) * (size_t)n));
+    CKC(cudaMemcpyAsync(h->agg.p, W->agg, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+  }
+  DevMem err;
+  CKC(err.ensure(sizeof(int) * 4));
+  CKC(cudaMemsetAsync(err.p, 0, sizeof(int) * 4, st));
+  CKC(launch_validate(n, nnz, h->fwd.rowptr.as<int>(), h->fwd.col.as<int>(),
+                      r > 0 ? h->agg.as<int>() : nullptr, r, err.as<int>(), st));
+  int herr[4] = {0, 0, 0, 0};
+  CKC(cudaMemcpyAsync(herr, err.p, sizeof(herr), cudaMemcpyDeviceToHost, st));
+  CKC(cudaStreamSynchronize(st));
+  if (herr[0] & 1) return bail(fail(h, GMRES_ERR_INVALID_ARG, "CSR rows not sorted/in range"));
+  if (herr[0] & 2) return bail(fail(h, GMRES_ERR_INVALID_ARG, "aggregate index out of range"));
+  if (opts.precision != GMRES_FP64) {
+    CKC(h->fwd.val32.ensure(sizeof(float) * (size_t)nnz));
+    CKC(launch_to_float(nnz, h->fwd.val.as<double>(), h->fwd.val32.as<float>(), st));
+  }
+  if (r > 0) {
+    const int nb = agg_chunks(n);
+    DevMem counts, aggptr, cnt, T, G, fac;
+    const int max_pieces = n / kPiece + r + 1;
+    CKC(counts.ensure(sizeof(int) * (size_t)nb * r));
+    CKC(aggptr.ensure(sizeof(int) * (size_t)(r + 1)));
+    CKC(cnt.ensure(sizeof(int) * (size_t)r));
+    CKC(h->perm.ensure(sizeof(int) * (size_t)n));
+    CKC(h->agg_piece.ensure(sizeof(int) * (size_t)(r + 1)));
+    CKC(h->piece_start.ensure(sizeof(int) * (size_t)(max_pieces + 1)));
+    CKC(h->uscale.ensure(sizeof(double) * (size_t)r));
+    CKC(launch_agg_perm(n, r, h->agg.as<int>(), counts.as<int>(), aggptr.as<int>(),
+                        cnt.as<int>(), h->perm.as<int>(), h->agg_piece.as<int>(),
+                        h->piece_start.as<int>(), h->uscale.as<double>(), err.as<int>(), st));
+    CKC(T.ensure(sizeof(double) * (size_t)r * r));
+    CKC(G.ensure(sizeof(double) * 2 * (size_t)r * r));
+    CKC(fac.ensure(sizeof(double) * (size_t)r));
+    CKC(h->fwd.tinv.ensure(sizeof(double) * (size_t)r * r));
+    CKC(h->adj.tinv.ensure(sizeof(double) * (size_t)r * r));
+    CKC(launch_coarse_T(r, h->fwd.rowptr.as<int>(), h->fwd.col.as<int>(),
+                        h->fwd.val.as<double>(), h->agg.as<int>(), h->perm.as<int>(),
+                        aggptr.as<int>(), h->uscale.as<double>(), T.as<double>(), st));
+    CKC(launch_gauss_jordan(r, T.as<double>(), G.as<double>(), fac.as<double>(),
+                            h->fwd.tinv.as<double>(), h->adj.tinv.as<double>(), err.as<int>(), st));
+    int np = 0;
+    CKC(cudaMemcpyAsync(&np, h->agg_piece.as<int>() + r, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CKC(cudaMemcpyAsync(herr, err.p, sizeof(herr), cudaMemcpyDeviceToHost, st));
+    CKC(cudaStreamSynchronize(st));
+    if (herr[0] & 4) return bail(fail(h, GMRES_ERR_SINGULAR_COARSE, "empty aggregate (zero column of W)"));
+    if (herr[0] & 8) return bail(fail(h, GMRES_ERR_SINGULAR_COARSE, "T = U^T A U is singular"));
+    h->npieces = np;
+  }
+  if (opts.mu_mode == GMRES_MU_NORM_INF) {
+    DevMem mx;
+    CKC(mx.ensure(sizeof(unsigned long long)));
+    CKC(cudaMemsetAsync(mx.p, 0, sizeof(unsigned long long), st));
+    CKC(launch_norm_inf(n, h->fwd.rowptr.as<int>(), h->fwd.val.as<double>(),
+                        mx.as<unsigned long long>(), st));
+    unsigned long long bits = 0;
+    CKC(cudaMemcpyAsync(&bits, mx.p, sizeof(bits), cudaMemcpyDeviceToHost, st));
+    CKC(cudaStreamSynchronize(st));
+    std::memcpy(&h->mu_norminf, &bits, sizeof(double));
+  }
+  h->fwd.ready = true;
+  h->prof_on = opts.profile != 0;
+  h->pms[PH_SETUP] = std::chrono::duration<double, std::milli>(
+                         std::chrono::steady_clock::now() - t_setup).count();
+#undef CKC
+  *out = h;
+  return GMRES_OK;
+}
+
+gmres_status gmres_solve(gmres_t h, const double* b, const double* x0, int32_t m, double tol,
+                         int64_t maxit, double* x, gmres_info* info) {
+  if (!h) return fail(nullptr, GMRES_ERR_INVALID_ARG, "null handle");
+  return run(h, h->fwd, b, x0, m, tol, maxit, x, info);
+}
+
+gmres_status gmres_adjoint_solve(gmres_t h, const double* g, const double* lam0, int32_t m,
+                                 double tol, int64_t maxit, double* lam, gmres_info* info) {
+  if (!h) return fail(nullptr, GMRES_ERR_INVALID_ARG, "null handle");
+  if (!h->adj.ready) {
+    cudaStream_t st = h->stream;
+    const int n = h->n;
+    const long long nnz = h->nnz;
+    CK(h, h->adj.rowptr.ensure(sizeof(int) * (size_t)(n + 1)));
+    CK(h, h->adj.col.ensure(sizeof(int) * (size_t)nnz));
+    CK(h, h->adj.val.ensure(sizeof(double) * (size_t)nnz));
+    DevMem scratch;
+    CK(h, scratch.ensure(sizeof(int) * (size_t)(n + 1)));
+    CK(h, launch_transpose(n, (int)nnz, h->fwd.rowptr.as<int>(), h->fwd.col.as<int>(),
+                           h->fwd.val.as<double>(), h->adj.rowptr.as<int>(),
+                           h->adj.col.as<int>(), h->adj.val.as<double>(), scratch.as<int>(), st));
+    if (h->opts.precision != GMRES_FP64) {
+      CK(h, h->adj.val32.ensure(sizeof(float) * (size_t)nnz));
+      CK(h, launch_to_float(nnz, h->adj.val.as<double>(), h->adj.val32.as<float>(), st));
+    }
+    CK(h, cudaStreamSynchronize(st));
+    h->adj.ready = true;
+  }
+  return run(h, h->adj, g, lam0, m, tol, maxit, lam, info);
+}
+
+gmres_status gmres_batch_solve(int32_t count, gmres_t const* hs, const double* const* b,
+                               const double* const* x0, int32_t m, double tol, int64_t maxit,
+                               double* const* x, gmres_info* infos, void* stream) {
+  if (count < 0 || (count > 0 && (!hs || !b || !x)))
+    return fail(nullptr, GMRES_ERR_INVALID_ARG, "invalid batch arguments");
+  gmres_status worst = GMRES_OK;
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i]) return fail(nullptr, GMRES_ERR_INVALID_ARG, "null handle in batch");
+    cudaStream_t keep = hs[i]->stream;
+    hs[i]->stream = static_cast<cudaStream_t>(stream);
+    gmres_status s = run(hs[i], hs[i]->fwd, b[i], x0 ? x0[i] : nullptr, m, tol, maxit, x[i],
+                         infos ? &infos[i] : nullptr);
+    hs[i]->stream = keep;
+    if (s < 0) return s;
+    if (s > worst) worst = s;
+  }
+  return worst;
+}
+
+gmres_status gmres_profile(gmres_t h, int32_t enable, int32_t reset, double* ms,
+                           int64_t* launches) {
+  if (!h) return fail(nullptr, GMRES_ERR_INVALID_ARG, "null handle");
+  if (ms)
+    for (int i = 0; i < PH_COUNT; ++i) ms[i] = h->pms[i];
+  if (launches)
+    for (int i = 0; i < PH_COUNT; ++i) launches[i] = h->plaunch[i];
+  if (reset)
+    for (int i = 0; i < PH_COUNT; ++i) {
+      h->pms[i] = 0.0;
+      h->plaunch[i] = 0;
+    }
+  if (enable >= 0) h->prof_on = enable != 0;
+  return GMRES_OK;
+}
+
+gmres_status gmres_set_stream(gmres_t h, void* stream) {
+  if (!h) return fail(nullptr, GMRES_ERR_INVALID_ARG, "null handle");
+  h->stream = static_cast<cudaStream_t>(stream);
+  return GMRES_OK;
+}
+
+const char* gmres_last_error(gmres_t h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+void gmres_destroy(gmres_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  if (h->hmeta) cudaFreeHost(h->hmeta);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  delete h;
+}
+
+int64_t q1_nnz(int32_t n) {
+  if (n < 1) return 0;
+  return 9LL * (n - 1) * (n - 1) + 4LL * n;
+}
+
+gmres_status q1_assemble(int32_t n, const double* kappa, double bx, double by, const double* f,
+                         const double* u, int32_t* rowptr, int32_t* col, double* val, double* b,
+                         void* stream) {
+  if (n < 1 || !kappa || !f || !rowptr || !col || !val || !b)
+    return fail(nullptr, GMRES_ERR_INVALID_ARG, "q1_assemble: invalid arguments");
+  if (q1_nnz(n) >= (1LL << 31) || (long long)(n + 1) * (n + 1) >= (1LL << 31))
+    return fail(nullptr, GMRES_ERR_INVALID_ARG, "q1_assemble: mesh too large for int32 CSR");
+  cudaError_t e = launch_q1_assemble(n, kappa, bx, by, f, u, rowptr, col, val, b,
+                                     static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "q1_assemble");
+  return GMRES_OK;
+}
+
+gmres_status q1_kappa_grad(int32_t n, const double* lam, const double* x, double* grad,
+                           void* stream) {
+  if (n < 1 || !lam || !x || !grad)
+    return fail(nullptr, GMRES_ERR_INVALID_ARG, "q1_kappa_grad: invalid arguments");
+  cudaError_t e = launch_q1_kappa_grad(n, lam, x, grad, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "q1_kappa_grad");
+  return GMRES_OK;
+}
+
+}  // extern "C"

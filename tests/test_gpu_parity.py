@@ -1,0 +1,244 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 CPU oracle.
+
+Bars: CSR index arrays bit-exact; FP64 solutions ||x_gpu - x_cpu|| / ||x_cpu|| <= 1e-9
+(both solved to a relative residual of 1e-12, where two correct solvers agree to about
+cond(A) * 1e-12); mixed precision: true FP64 relative residual <= 1e-10.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from helpers import gpu_solver_from_oracle, relerr, to_dev
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1906_04051_gb300 as G
+    from paper_1906_04051_gb300 import build as B
+    B.build()
+    return G
+
+
+# ---------------------------------------------------------------------------------------
+# assembly
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 64, 255])
+def test_q1_assembly_matches_oracle(G, orc, n):
+    p = W.convdiff(n, pe=37.0, sigma=0.6, seed=3 + n, px=2, py=2, f_kind="uniform")
+    u = W.uniform(11, 9, (n + 1) ** 2, -1, 1)
+    for uu in (None, u):
+        rowptr, col, val, b = G.q1_assemble(n, to_dev(p.kappa), p.beta, to_dev(p.f),
+                                            None if uu is None else to_dev(uu))
+        A, bo = orc.q1_assemble(n, p.kappa, p.beta, p.f, uu)
+        assert np.array_equal(rowptr.cpu().numpy(), A.rowptr)
+        assert np.array_equal(col.cpu().numpy(), A.col)
+        scale = np.abs(A.val).max()
+        assert np.abs(val.cpu().numpy() - A.val).max() <= 1e-14 * scale
+        bs = max(np.abs(bo).max(), 1e-300)
+        assert np.abs(b.cpu().numpy() - bo).max() <= 1e-13 * bs
+
+
+@pytest.mark.parametrize("n", [1024, 2048])
+def test_q1_assembly_indices_full_size(G, orc, n):
+    p = W.workload2() if n == 1024 else W.workload3()
+    rowptr, col, val, b = G.q1_assemble(n, to_dev(p.kappa), p.beta, to_dev(p.f))
+    A, bo = orc.q1_assemble(n, p.kappa, p.beta, p.f)
+    assert np.array_equal(rowptr.cpu().numpy(), A.rowptr)
+    assert np.array_equal(col.cpu().numpy(), A.col)
+    assert np.abs(val.cpu().numpy() - A.val).max() <= 1e-14 * np.abs(A.val).max()
+    del rowptr, col, val, b
+
+
+def test_q1_kappa_grad_matches_oracle(G, orc):
+    n = 33
+    rng = np.random.default_rng(1)
+    lam = rng.standard_normal((n + 1) ** 2)
+    x = rng.standard_normal((n + 1) ** 2)
+    g = G.q1_kappa_grad(n, to_dev(lam), to_dev(x)).cpu().numpy()
+    go = orc.q1_kappa_grad(n, lam, x)
+    assert np.abs(g - go).max() <= 1e-13 * np.abs(go).max()
+
+
+# ---------------------------------------------------------------------------------------
+# solves
+# ---------------------------------------------------------------------------------------
+def _solve_both(G, orc, p, *, m, tol, maxit, mode="ebp", mu_mode=0, mu_user=0.0,
+                fixed=False, x0=None):
+    A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f, p.u)
+    dm = {"ebp": G.DEFL_EBP, "none": G.DEFL_NONE}[mode]
+    s = gpu_solver_from_oracle(G, A, p.agg if mode != "none" else None,
+                               p.r if mode != "none" else 0, mu_mode=mu_mode, mu_user=mu_user,
+                               fixed_iterations=fixed)
+    xg, ig = s.solve(to_dev(b), None if x0 is None else to_dev(x0), m=m, tol=tol, maxit=maxit)
+    d = orc.Deflation(A, p.agg, p.r) if mode != "none" else None
+    xo, io = orc.gmres(A, b, x0, m=m, tol=tol, maxit=maxit, defl=d, mu_mode=mu_mode,
+                       mu_user=mu_user, fixed_iterations=fixed)
+    return xg.cpu().numpy(), ig, xo, io, s
+
+
+@pytest.mark.parametrize("mode", ["ebp", "none"])
+@pytest.mark.parametrize("mu_mode", [0, 1, 2])
+def test_workload1_tight_tolerance(G, orc, mode, mu_mode):
+    if mode == "none" and mu_mode != 0:
+        pytest.skip("mu only matters with deflation")
+    p = W.workload1()
+    xg, ig, xo, io, _ = _solve_both(G, orc, p, m=30, tol=1e-12, maxit=20000, mode=mode,
+                                    mu_mode=mu_mode, mu_user=6.0)
+    assert ig["status"] == 0 and io["status"] == 0, (ig, io)
+    assert relerr(xg, xo) <= 1e-9
+    assert ig["rel_res_true"] <= 1e-12
+    if mode == "ebp":
+        assert ig["mu"] == pytest.approx(io["mu"], rel=1e-10)
+    # same method, same arithmetic up to rounding: iteration counts agree closely
+    assert abs(ig["iters"] - io["iters"]) <= max(3, 0.05 * io["iters"])
+
+
+@pytest.mark.parametrize("n", [3, 17, 40])
+@pytest.mark.parametrize("maxit", [1, 7, 45])
+def test_fixed_iterations_parity(G, orc, n, maxit):
+    # fixed-iteration protocol (Sec. 4): identical step counts, so the iterates agree to
+    # rounding amplified by the Krylov process
+    p = W.convdiff(n, pe=25.0, sigma=0.5, seed=100 + n, px=2, py=3)
+    xg, ig, xo, io, _ = _solve_both(G, orc, p, m=10, tol=0.0, maxit=maxit, mu_mode=1,
+                                    mu_user=5.0, fixed=True)
+    assert ig["iters"] == io["iters"] == min(maxit, ig["iters"])
+    assert relerr(xg, xo) <= 1e-9
+    assert ig["rel_res_true"] == pytest.approx(io["rel_res_true"], rel=1e-7, abs=1e-14)
+
+
+def test_fixed_iterations_ritz_mu(G, orc):
+    p = W.convdiff(48, pe=60.0, sigma=0.5, seed=9, px=4, py=2)
+    xg, ig, xo, io, _ = _solve_both(G, orc, p, m=20, tol=0.0, maxit=90, fixed=True)
+    assert ig["iters"] == io["iters"] == 90
+    assert ig["mu"] == pytest.approx(io["mu"], rel=1e-10)
+    assert relerr(xg, xo) <= 1e-9
+
+
+def test_nonzero_initial_guess(G, orc):
+    p = W.convdiff(30, pe=15.0, sigma=0.3, seed=21, px=2, py=2)
+    x0 = W.uniform(5, 5, p.N, -1, 1)
+    xg, ig, xo, io, _ = _solve_both(G, orc, p, m=25, tol=1e-12, maxit=5000, x0=x0)
+    assert ig["status"] == 0 and relerr(xg, xo) <= 1e-9
+
+
+def test_zero_rhs_and_maxit_zero(G, orc):
+    p = W.convdiff(8, pe=5.0, sigma=0.0, seed=1, px=2, py=2)
+    A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f)
+    s = gpu_solver_from_oracle(G, A, p.agg, p.r)
+    x, info = s.solve(torch.zeros(A.n, dtype=torch.float64, device="cuda"), m=5)
+    assert info["status"] == 0 and info["iters"] == 0 and not torch.any(x)
+    x, info = s.solve(to_dev(b), m=5, tol=1e-8, maxit=0)
+    assert info["status"] == 1 and info["iters"] == 0
+
+
+def test_restart_lengths_and_ragged_sizes(G, orc):
+    for n, m in [(5, 1), (11, 2), (23, 64), (31, 9)]:
+        p = W.convdiff(n, pe=8.0, sigma=0.4, seed=n, px=3, py=2)
+        xg, ig, xo, io, _ = _solve_both(G, orc, p, m=m, tol=1e-12, maxit=50000)
+        assert ig["status"] == 0, (n, m, ig)
+        assert relerr(xg, xo) <= 1e-9, (n, m)
+
+
+def test_deterministic_bitwise(G, orc):
+    p = W.convdiff(64, pe=40.0, sigma=0.5, seed=4, px=4, py=4)
+    A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f)
+    s = gpu_solver_from_oracle(G, A, p.agg, p.r)
+    x1, i1 = s.solve(to_dev(b), m=30, tol=1e-10, maxit=3000)
+    x2, i2 = s.solve(to_dev(b), m=30, tol=1e-10, maxit=3000)
+    assert i1["iters"] == i2["iters"]
+    assert torch.equal(x1, x2)
+
+
+def test_adjoint_matches_oracle(G, orc):
+    p = W.convdiff(40, pe=30.0, sigma=0.5, seed=12, px=2, py=4)
+    A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f)
+    s = gpu_solver_from_oracle(G, A, p.agg, p.r)
+    g = W.uniform(77, 1, A.n, -1, 1)
+    lam, info = s.adjoint_solve(to_dev(g), m=30, tol=1e-12, maxit=10000)
+    At = A.transpose()
+    lo, io = orc.gmres(At, g, m=30, tol=1e-12, maxit=10000, defl=orc.Deflation(At, p.agg, p.r))
+    assert info["status"] == 0 and io["status"] == 0
+    assert relerr(lam.cpu().numpy(), lo) <= 1e-9
+    # <A x, lam> = <x, A^T lam>
+    x, _ = s.solve(to_dev(b), m=30, tol=1e-12, maxit=10000)
+    xn = x.cpu().numpy()
+    assert abs(A.matvec(xn) @ lam.cpu().numpy() - xn @ g) <= 1e-9 * np.abs(xn @ g)
+
+
+@pytest.mark.parametrize("prec,name", [(1, "fp32"), (2, "bf16")])
+def test_mixed_precision_reaches_1e10(G, orc, prec, name):
+    p = W.convdiff(96, pe=50.0, sigma=0.5, seed=33, px=4, py=4)
+    A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f)
+    s = gpu_solver_from_oracle(G, A, p.agg, p.r, precision=prec)
+    x, info = s.solve(to_dev(b), m=40, tol=1e-10, maxit=20000)
+    assert info["status"] == 0, info
+    xn = x.cpu().numpy()
+    true_rel = np.linalg.norm(b - A.matvec(xn)) / np.linalg.norm(b)
+    assert true_rel <= 1e-10
+    xo, io = orc.gmres(A, b, m=40, tol=1e-12, maxit=20000, defl=orc.Deflation(A, p.agg, p.r))
+    assert relerr(xn, xo) <= 1e-7  # reported accuracy vs the FP64 oracle
+
+
+def test_batch_matches_single(G, orc):
+    probs = W.workload4(count=6, n_min=8, n_max=40)
+    solvers, bs, singles = [], [], []
+    for p in probs:
+        A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f, p.u)
+        s = gpu_solver_from_oracle(G, A, p.agg, p.r)
+        solvers.append(s)
+        bs.append(to_dev(b))
+        singles.append(s.solve(bs[-1], m=30, tol=1e-12, maxit=20000)[0])
+    xs, infos, st = G.batch_solve(solvers, bs, m=30, tol=1e-12, maxit=20000)
+    assert st == 0
+    for x, xs1, p in zip(xs, singles, probs):
+        assert torch.equal(x, xs1)
+        A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f, p.u)
+        xo, _ = orc.gmres(A, b, m=30, tol=1e-12, maxit=20000, defl=orc.Deflation(A, p.agg, p.r))
+        assert relerr(x.cpu().numpy(), xo) <= 1e-9
+
+
+# ---------------------------------------------------------------------------------------
+# error paths (host-detected, or device flags read by the host; nothing faults)
+# ---------------------------------------------------------------------------------------
+def test_invalid_csr_rejected(G, orc):
+    A, b = orc.q1_assemble(4, np.ones(16), (1.0, 0.0), np.ones(25))
+    col = A.col.copy()
+    col[10], col[11] = col[11], col[10]  # unsorted row
+    with pytest.raises(G.GmresError) as e:
+        G.Solver(to_dev(A.rowptr), to_dev(col), to_dev(A.val))
+    assert e.value.status == -1
+
+
+def test_empty_aggregate_rejected(G, orc):
+    p = W.convdiff(6, pe=5.0, sigma=0.0, seed=1, px=2, py=2)
+    A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f)
+    agg = p.agg.copy()
+    agg[agg == 1] = 0
+    with pytest.raises(G.GmresError) as e:
+        gpu_solver_from_oracle(G, A, agg, p.r)
+    assert e.value.status == -4
+
+
+def test_nan_rhs_reports_nan(G, orc):
+    p = W.convdiff(10, pe=5.0, sigma=0.0, seed=1, px=2, py=2)
+    A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f)
+    b = b.copy()
+    b[17] = np.nan
+    s = gpu_solver_from_oracle(G, A, p.agg, p.r)
+    with pytest.raises(G.GmresError) as e:
+        s.solve(to_dev(b), m=10)
+    assert e.value.status == -5
+
+
+def test_bad_restart_length(G, orc):
+    A, b = orc.q1_assemble(4, np.ones(16), (1.0, 0.0), np.ones(25))
+    s = gpu_solver_from_oracle(G, A)
+    for m in (0, 65):
+        with pytest.raises(G.GmresError):
+            s.solve(to_dev(b), m=m)
