@@ -103,26 +103,6 @@ __device__ __forceinline__ int slices_for(int k) {
   return k >= 8 ? 8 : (k >= 4 ? 4 : (k >= 2 ? 2 : 1));
 }
 
-template <typename TACC>
-__device__ __forceinline__ void reduce_slices(const TACC (&acc)[kSliceCols], int k,
-                                              int nslice, double* swarp, double* sred) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nrg = kSlices / nslice;
-#pragma unroll
-  for (int i = 0; i < kSliceCols; ++i) {
-    const TACC v = warp_sum(acc[i]);
-    if (lane == 0) swarp[warp * kSliceCols + i] = (double)v;
-  }
-  __syncthreads();
-  for (int c = threadIdx.x; c < k; c += blockDim.x) {
-    const int s = c % nslice, i = c / nslice;
-    double sum = 0.0;
-    for (int g = 0; g < nrg; ++g) sum += swarp[(g * nslice + s) * kSliceCols + i];
-    sred[c] = sum;
-  }
-  __syncthreads();
-}
-
 // Number of columns of warp slice `slice` among k columns dealt round-robin to nslice
 // slices.  Each warp runs an instance unrolled for exactly that many columns (a
 // warp-uniform switch), so no floating-point instruction is issued under a false
@@ -166,12 +146,46 @@ __device__ __forceinline__ void slice_fma_smem(TACC (&acc)[kSliceCols], const TV
     default: break;                    \
   }
 
+// Per-block column sums of the warp-slice accumulators.  Lanes store their live
+// accumulators (nw of them) transposed in shared memory and one thread adds the 32 lane
+// values of a (warp, column) pair, which costs far fewer FP64 instructions than a
+// shuffle tree on every lane; row groups are then added in a fixed order.
+template <typename TACC>
+__device__ __forceinline__ void reduce_slices(const TACC (&acc)[kSliceCols], int nw, int k,
+                                              int nslice, double* sbuf /* 8*9*33 */,
+                                              double* swarp /* 8*9 */, double* sred) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nrg = kSlices / nslice;
+#pragma unroll
+  for (int i = 0; i < kSliceCols; ++i)
+    if (i < nw) sbuf[(warp * kSliceCols + i) * 33 + lane] = (double)acc[i];
+  __syncthreads();
+  for (int t = threadIdx.x; t < kSlices * kSliceCols; t += blockDim.x) {
+    const int wv = t / kSliceCols, i = t % kSliceCols;
+    if (i < slice_cols(k, wv % nslice, nslice)) {
+      const double* src = sbuf + (size_t)t * 33;
+      double s = 0.0;
+      for (int l = 0; l < 32; ++l) s += src[l];
+      swarp[t] = s;
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    const int sl = c % nslice, i = c / nslice;
+    double sum = 0.0;
+    for (int g = 0; g < nrg; ++g) sum += swarp[(g * nslice + sl) * kSliceCols + i];
+    sred[c] = sum;
+  }
+  __syncthreads();
+}
+
 // CGS2 pass 1: h_c = sigma_c (u_c . w), coef_c = sigma_c h_c.
 template <typename TV, typename TACC>
 __global__ void __launch_bounds__(kThreads)
     k_dot1(int N, const TV* __restrict__ V, long long ldv, int k, const TACC* __restrict__ w,
            Ctl ctl) {
   if (ctl.flags[F_CYCLE_DONE]) return;
+  __shared__ double sbuf[kSlices * kSliceCols * 33];
   __shared__ double swarp[kSlices * kSliceCols];
   __shared__ double sred[kMaxK];
   __shared__ double tot[kMaxK];
@@ -194,8 +208,8 @@ __global__ void __launch_bounds__(kThreads)
       }
     }
   }
-  reduce_slices(acc, k, nslice, swarp, sred);
-  if (!last_block_reduce(sred, k, ctl.part, ctl.ldp, ctl.ticket, tot)) return;
+  reduce_slices(acc, nw, k, nslice, sbuf, swarp, sred);
+  if (!last_block_reduce(sred, k, ctl.part, ctl.part2, ctl.ldp, ctl.ticket, tot)) return;
   for (int c = threadIdx.x; c < k; c += blockDim.x) {
     const double hc = ctl.sigma[c] * tot[c];
     ctl.h[c] = hc;
@@ -214,6 +228,7 @@ __global__ void __launch_bounds__(kThreads)
   TACC* sw = reinterpret_cast<TACC*>(smraw);           // kTile2
   TACC* spart = sw + kTile2;                            // 2 * kTile2
   TV* sV = reinterpret_cast<TV*>(spart + 2 * kTile2);   // k * kTile2
+  __shared__ double sbuf[kSlices * kSliceCols * 33];
   __shared__ double swarp[kSlices * kSliceCols];
   __shared__ double sred[kMaxK];
   __shared__ double tot[kMaxK];
@@ -264,8 +279,8 @@ __global__ void __launch_bounds__(kThreads)
     }
     __syncthreads();
   }
-  reduce_slices(acc, k, nslice, swarp, sred);
-  if (!last_block_reduce(sred, k, ctl.part, ctl.ldp, ctl.ticket, tot)) return;
+  reduce_slices(acc, nw, k, nslice, sbuf, swarp, sred);
+  if (!last_block_reduce(sred, k, ctl.part, ctl.part2, ctl.ldp, ctl.ticket, tot)) return;
   for (int c = threadIdx.x; c < k; c += blockDim.x) {
     const double h2 = ctl.sigma[c] * tot[c];
     ctl.h[c] += h2;
@@ -273,54 +288,77 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// Plane rotations and stopping tests of step j (Eqs. 12, 14), one thread.
+// Plane rotations and stopping tests of step j (Eqs. 12, 14), by the whole block: the
+// column, rotations and gamma are staged in shared memory, one thread applies the
+// rotations there (no dependent global-memory round trips), then all threads store.
 __device__ void givens_step(Ctl& ctl, int j, int m, double hnext) {
+  __shared__ double sh[kMaxK + 1], scs[kMaxK], ssn[kMaxK], sg[2];
+  __shared__ int sdone;
   const int ldh = ctl.ldh;
-  double hn2 = hnext * hnext;
-  for (int i = 0; i <= j; ++i) {
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
     const double hi = ctl.h[i];
+    sh[i] = hi;
     ctl.Hr[(size_t)i * ldh + j] = hi;
-    ctl.H[(size_t)i * ldh + j] = hi;
-    hn2 += hi * hi;
+    if (i < j) {
+      scs[i] = ctl.cs[i];
+      ssn[i] = ctl.sn[i];
+    }
   }
-  ctl.Hr[(size_t)(j + 1) * ldh + j] = hnext;
-  for (int i = 0; i < j; ++i) {
-    const double a = ctl.H[(size_t)i * ldh + j], b = ctl.H[(size_t)(i + 1) * ldh + j];
-    ctl.H[(size_t)i * ldh + j] = ctl.cs[i] * a + ctl.sn[i] * b;
-    ctl.H[(size_t)(i + 1) * ldh + j] = -ctl.sn[i] * a + ctl.cs[i] * b;
+  if (threadIdx.x == 0) {
+    ctl.Hr[(size_t)(j + 1) * ldh + j] = hnext;
+    sg[0] = ctl.g[j];
   }
-  const double a = ctl.H[(size_t)j * ldh + j];
-  if (hnext == 0.0) {
-    ctl.cs[j] = 1.0;
-    ctl.sn[j] = 0.0;
-  } else {
-    const double rho = hypot(a, hnext);
-    ctl.cs[j] = a / rho;
-    ctl.sn[j] = hnext / rho;
-    ctl.H[(size_t)j * ldh + j] = rho;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double hn2 = hnext * hnext;
+    for (int i = 0; i <= j; ++i) hn2 += sh[i] * sh[i];
+    for (int i = 0; i < j; ++i) {
+      const double a = sh[i], b = sh[i + 1];
+      sh[i] = scs[i] * a + ssn[i] * b;
+      sh[i + 1] = -ssn[i] * a + scs[i] * b;
+    }
+    const double a = sh[j];
+    double c = 1.0, sn = 0.0;
+    if (hnext != 0.0) {
+      const double rho = hypot(a, hnext);
+      c = a / rho;
+      sn = hnext / rho;
+      sh[j] = rho;
+    }
+    sh[j + 1] = 0.0;
+    scs[j] = c;
+    ssn[j] = sn;
+    const double gj = sg[0];
+    sg[1] = -sn * gj;
+    sg[0] = c * gj;
+    const long long steps = ++ctl.counts[C_STEPS];
+    ctl.flags[F_K] = j + 1;
+    const double est = fabs(sg[1]) / ctl.scal[S_RHO0];
+    ctl.scal[S_EST] = est;
+    ctl.sigma[j + 1] = hnext > 0.0 ? 1.0 / hnext : 0.0;
+    bool done = false;
+    if (!isfinite(hnext) || !isfinite(est)) {
+      ctl.flags[F_STATUS] = GMRES_ERR_NAN;
+      ctl.flags[F_STOP] = 1;
+      done = true;
+    }
+    if (hnext <= 1e-14 * sqrt(hn2)) done = true;  // breakdown: the Krylov space is invariant
+    if (!ctl.flags[F_FIXED] && est <= ctl.scal[S_TOL]) done = true;
+    if (ctl.flags[F_MIXED] && fabs(sg[1]) <= ctl.scal[S_INNER_TOL] * ctl.scal[S_BETA_CYCLE])
+      done = true;
+    if (steps >= ctl.counts[C_MAXIT]) done = true;
+    if (j + 1 >= m) done = true;
+    sdone = done ? 1 : 0;
   }
-  ctl.H[(size_t)(j + 1) * ldh + j] = 0.0;
-  const double gj = ctl.g[j];
-  ctl.g[j + 1] = -ctl.sn[j] * gj;
-  ctl.g[j] = ctl.cs[j] * gj;
-  const long long steps = ++ctl.counts[C_STEPS];
-  ctl.flags[F_K] = j + 1;
-  const double est = fabs(ctl.g[j + 1]) / ctl.scal[S_RHO0];
-  ctl.scal[S_EST] = est;
-  ctl.sigma[j + 1] = hnext > 0.0 ? 1.0 / hnext : 0.0;
-  bool done = false;
-  if (!isfinite(hnext) || !isfinite(est)) {
-    ctl.flags[F_STATUS] = GMRES_ERR_NAN;
-    ctl.flags[F_STOP] = 1;
-    done = true;
+  __syncthreads();
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) ctl.H[(size_t)i * ldh + j] = sh[i];
+  if (threadIdx.x == 0) {
+    ctl.cs[j] = scs[j];
+    ctl.sn[j] = ssn[j];
+    ctl.g[j] = sg[0];
+    ctl.g[j + 1] = sg[1];
+    if (sdone) ctl.flags[F_CYCLE_DONE] = 1;
   }
-  if (hnext <= 1e-14 * sqrt(hn2)) done = true;  // breakdown: the Krylov space is invariant
-  if (!ctl.flags[F_FIXED] && est <= ctl.scal[S_TOL]) done = true;
-  if (ctl.flags[F_MIXED] && fabs(ctl.g[j + 1]) <= ctl.scal[S_INNER_TOL] * ctl.scal[S_BETA_CYCLE])
-    done = true;
-  if (steps >= ctl.counts[C_MAXIT]) done = true;
-  if (j + 1 >= m) done = true;
-  if (done) ctl.flags[F_CYCLE_DONE] = 1;
 }
 
 // CGS2 pass 3: u_{j+1} = w - sum_c coef_c u_c (stored), h_{j+1,j} = ||u_{j+1}||.
@@ -365,8 +403,8 @@ __global__ void __launch_bounds__(kThreads)
   const double bs = block_sum((double)nrm, sbuf);
   if (threadIdx.x == 0) sred[0] = bs;
   __syncthreads();
-  if (!last_block_reduce(sred, 1, ctl.part, ctl.ldp, ctl.ticket, tot)) return;
-  if (threadIdx.x == 0) givens_step(ctl, k - 1, m, sqrt(tot[0]));
+  if (!last_block_reduce(sred, 1, ctl.part, ctl.part2, ctl.ldp, ctl.ticket, tot)) return;
+  givens_step(ctl, k - 1, m, sqrt(tot[0]));
 }
 
 // --------------------------------------------------------------------------------------
@@ -421,17 +459,32 @@ __global__ void __launch_bounds__(kThreads)
 // --------------------------------------------------------------------------------------
 // Cycle end
 // --------------------------------------------------------------------------------------
+// Back substitution R_k y = g (Eq. 12) on a shared-memory copy of R; coef = sigma o y.
 __global__ void k_backsolve(Ctl ctl) {
-  if (ctl.flags[F_STOP] || threadIdx.x != 0) return;
+  __shared__ double R[kMaxM * kMaxM];
+  __shared__ double sg[kMaxM], sy[kMaxM];
+  if (ctl.flags[F_STOP]) return;
   const int k = ctl.flags[F_K];
   const int ldh = ctl.ldh;
-  for (int i = k - 1; i >= 0; --i) {
-    double s = ctl.g[i];
-    for (int l = i + 1; l < k; ++l) s -= ctl.H[(size_t)i * ldh + l] * ctl.y[l];
-    ctl.y[i] = s / ctl.H[(size_t)i * ldh + i];
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    const int i = t / k, l = t % k;
+    R[t] = l >= i ? ctl.H[(size_t)i * ldh + l] : 0.0;
   }
-  for (int i = 0; i < k; ++i) ctl.coef[i] = ctl.sigma[i] * ctl.y[i];
-  ctl.counts[C_CYCLES]++;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sg[i] = ctl.g[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = k - 1; i >= 0; --i) {
+      double s = sg[i];
+      for (int l = i + 1; l < k; ++l) s -= R[i * k + l] * sy[l];
+      sy[i] = s / R[i * k + i];
+    }
+    ctl.counts[C_CYCLES]++;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    ctl.y[i] = sy[i];
+    ctl.coef[i] = ctl.sigma[i] * sy[i];
+  }
 }
 
 // t = V_k (sigma o y) in FP64; x += t directly, or t kept for the deflation correction.
@@ -515,7 +568,7 @@ __global__ void __launch_bounds__(kSpmvRows)
     sred[1] = b2;
   }
   __syncthreads();
-  if (!last_block_reduce(sred, 2, ctl.part, ctl.ldp, ctl.ticket, tot)) return;
+  if (!last_block_reduce(sred, 2, ctl.part, ctl.part2, ctl.ldp, ctl.ticket, tot)) return;
   if (threadIdx.x != 0) return;
   const double beta = sqrt(tot[0]);
   const double beta_s = sqrt(tot[1]);
@@ -712,7 +765,7 @@ __global__ void k_init(Ctl ctl, double tol, double inner_tol, double r0ref, doub
   ctl.flags[F_STATUS] = GMRES_NOT_CONVERGED;
   ctl.flags[F_CYCLE_DONE] = 1;
   ctl.counts[C_MAXIT] = maxit;
-  *ctl.ticket = 0u;
+  for (int i = 0; i < 1 + kMaxGroups; ++i) ctl.ticket[i] = 0u;
 }
 
 // ---- per-precision dispatch -----------------------------------------------------------
@@ -726,6 +779,14 @@ int resident_grid(F kernel, int threads, size_t smem, int sms) {
     per_sm = 1;
   if (per_sm > 8) per_sm = 8;
   return per_sm * sms;
+}
+
+// Blocks for `tiles` tiles with at most gmax resident blocks: every block gets the same
+// number of tiles (up to one), so no wave ends with a partial tail.
+inline int balanced(int tiles, int gmax) {
+  if (tiles < 1) return 1;
+  const int per = (tiles + gmax - 1) / gmax;
+  return (tiles + per - 1) / per;
 }
 
 template <typename TV, typename TA, typename TACC>
@@ -781,26 +842,26 @@ struct Kern {
         const int tiles = (N + kSpmvRows - 1) / kSpmvRows;
         const TV* xj = V + (size_t)j * a.ldv;
         if (defl)
-          k_spmv_step<TA, TV, TACC, true><<<grid_for(tiles, 1, g.spmv_d), kSpmvRows, 0, st>>>(
+          k_spmv_step<TA, TV, TACC, true><<<balanced(tiles, g.spmv_d), kSpmvRows, 0, st>>>(
               N, a.op.rowptr, a.op.col, vals(a), xj, j, d.agg, sdefl(a), w, a.ctl);
         else
-          k_spmv_step<TA, TV, TACC, false><<<grid_for(tiles, 1, g.spmv_n), kSpmvRows, 0, st>>>(
+          k_spmv_step<TA, TV, TACC, false><<<balanced(tiles, g.spmv_n), kSpmvRows, 0, st>>>(
               N, a.op.rowptr, a.op.col, vals(a), xj, j, nullptr, sdefl(a), w, a.ctl);
         nl = 1;
         break;
       }
       case PH_DOT1:
-        k_dot1<TV, TACC><<<grid_for((N + 255) / 256, 1, g.dot1), kThreads, 0, st>>>(
+        k_dot1<TV, TACC><<<balanced((N + 255) / 256, g.dot1), kThreads, 0, st>>>(
             N, V, a.ldv, k, w, a.ctl);
         nl = 1;
         break;
       case PH_UPD1DOT2:
-        k_upd1dot2<TV, TACC><<<grid_for((N + kTile2 - 1) / kTile2, 1, g.upd1[k]), kThreads,
+        k_upd1dot2<TV, TACC><<<balanced((N + kTile2 - 1) / kTile2, g.upd1[k]), kThreads,
                                smem_upd1(k), st>>>(N, V, a.ldv, k, w, a.ctl);
         nl = 1;
         break;
       case PH_UPD2NORM:
-        k_upd2norm<TV, TACC><<<grid_for((N + kThreads - 1) / kThreads, 1, g.upd2), kThreads, 0,
+        k_upd2norm<TV, TACC><<<balanced((N + kThreads - 1) / kThreads, g.upd2), kThreads, 0,
                                st>>>(N, Vm, a.ldv, k, w, a.ctl, a.m);
         nl = 1;
         break;
@@ -814,7 +875,7 @@ struct Kern {
         break;
       }
       case PH_CYCLE_END: {
-        k_backsolve<<<1, 32, 0, st>>>(a.ctl);
+        k_backsolve<<<1, 128, 0, st>>>(a.ctl);
         const int tiles = (N + kThreads - 1) / kThreads;
         if (defl) {
           k_xupdate<TV, true><<<grid_for(tiles, 1, g.xupd_d), kThreads, 0, st>>>(N, V, a.ldv, x,
@@ -833,7 +894,7 @@ struct Kern {
         break;
       }
       case PH_RESIDUAL:
-        k_residual<TV><<<grid_for((N + kSpmvRows - 1) / kSpmvRows, 1, g.resid), kSpmvRows, 0,
+        k_residual<TV><<<balanced((N + kSpmvRows - 1) / kSpmvRows, g.resid), kSpmvRows, 0,
                          st>>>(N, a.op.rowptr, a.op.col, a.op.val, x, b, Vm, a.ctl);
         nl = 1;
         break;

@@ -59,12 +59,13 @@ struct Ctl {
   double* h;      // ldh+1: projection coefficients of the current column
   double* coef;   // ldh+1: coefficients of the pending basis update
   double* part;   // [max_grid][ldp] per-block partial sums
+  double* part2;  // [kMaxGroups][ldp] per-group partial sums
   double* scal;   // S_NSCAL scalars
   double* cpart;  // per-piece partial sums of an aggregate reduction
   double* sdefl;  // r: correction per aggregate, z = v + sdefl[agg]
   float* sdefl32; // r: FP32 copy for the FP32 inner kernels
   int* flags;     // F_NFLAGS
-  unsigned* ticket;         // last-block counters
+  unsigned* ticket;         // 1 + kMaxGroups last-block counters (zero between kernels)
   long long* counts;        // C_NCOUNT
   int ldh;        // m of the workspace
   int ldp;        // leading dimension of part (>= kMaxK + 1)
@@ -158,28 +159,68 @@ __device__ __forceinline__ T block_sum(T v, T* sbuf /* >= blockDim/32 */) {
   return t;
 }
 
-// Writes this block's ncols partials (smem sred) to part[blockIdx.x*ldp + c].  The last
-// block to arrive (ticket counter) reduces all blocks' partials in a fixed order into
-// tot[c] (shared memory), resets the counter and returns true; the others return false.
+constexpr int kGroup = 32;      // blocks per first-level group of a grid reduction
+constexpr int kMaxGroups = 64;  // groups per grid (grid <= kGroup * kMaxGroups)
+
+// dst[c] = sum_{r < nrows} src[r * ldp + c] for c < ncols, in a fixed order: thread (c, q)
+// sums rows q, q + Q, ... (independent loads), then the Q partials are added in order.
+__device__ __forceinline__ void reduce_rows(const double* src, int nrows, int ncols, int ldp,
+                                            double* dst) {
+  __shared__ double scratch[256];
+  const int nt = blockDim.x < 256 ? blockDim.x : 256;
+  int Q = nt / ncols;
+  if (Q < 1) Q = 1;
+  if (Q > 16) Q = 16;
+  for (int idx = threadIdx.x; idx < ncols * Q; idx += blockDim.x) {
+    const int c = idx % ncols, q = idx / ncols;
+    double s0 = 0.0, s1 = 0.0;
+    int r = q;
+    for (; r + Q < nrows; r += 2 * Q) {
+      s0 += __ldcg(src + (size_t)r * ldp + c);
+      s1 += __ldcg(src + (size_t)(r + Q) * ldp + c);
+    }
+    if (r < nrows) s0 += __ldcg(src + (size_t)r * ldp + c);
+    scratch[q * ncols + c] = s0 + s1;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < Q; ++q) s += scratch[q * ncols + c];
+    dst[c] = s;
+  }
+  __syncthreads();
+}
+
+// Grid-wide deterministic reduction of per-block vectors.  Each block writes its ncols
+// partials (smem sred) to part[blockIdx.x * ldp + c].  The last block of each group of
+// kGroup blocks (ticket counters) sums its group into part2[group]; the last group to
+// finish sums the group partials into tot[c] (shared memory), resets the counters and
+// returns true.  Every other block returns false.  No block ever waits on another.
 __device__ __forceinline__ bool last_block_reduce(const double* sred, int ncols, double* part,
-                                                  int ldp, unsigned* ticket, double* tot) {
+                                                  double* part2, int ldp, unsigned* tickets,
+                                                  double* tot) {
   __shared__ unsigned s_last;
-  for (int c = threadIdx.x; c < ncols; c += blockDim.x)
-    part[(size_t)blockIdx.x * ldp + c] = sred[c];
+  const int G = gridDim.x, b = blockIdx.x;
+  const int ng = (G + kGroup - 1) / kGroup, g = b / kGroup;
+  const int gs = (G - g * kGroup) < kGroup ? (G - g * kGroup) : kGroup;
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) part[(size_t)b * ldp + c] = sred[c];
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+  if (threadIdx.x == 0) s_last = (atomicAdd(&tickets[1 + g], 1u) == (unsigned)gs - 1u) ? 1u : 0u;
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int c = warp; c < ncols; c += nw) {
-    double s = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(&part[(size_t)b * ldp + c]);
-    s = warp_sum(s);
-    if (lane == 0) tot[c] = s;
-  }
-  if (threadIdx.x == 0) *ticket = 0u;
+  reduce_rows(part + (size_t)g * kGroup * ldp, gs, ncols, ldp, tot);
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) part2[(size_t)g * ldp + c] = tot[c];
+  if (threadIdx.x == 0) tickets[1 + g] = 0u;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(&tickets[0], 1u) == (unsigned)ng - 1u) ? 1u : 0u;
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  reduce_rows(part2, ng, ncols, ldp, tot);
+  if (threadIdx.x == 0) tickets[0] = 0u;
   __syncthreads();
   return true;
 }

@@ -47,7 +47,6 @@ struct Meta {  // mirrors the device status block
   double scal[S_NSCAL];
   long long counts[C_NCOUNT];
   int flags[F_NFLAGS];
-  unsigned ticket[4];
 };
 
 struct OpHost {
@@ -72,7 +71,7 @@ struct gmres_s {
   // workspace
   int ldh = 0, prec_ws = -1;
   long long ldv = 0;
-  DevMem V, w, t, dctl, meta, part, cpart, sdefl;
+  DevMem V, w, t, dctl, meta, part, part2, tickets, cpart, sdefl;
   Meta* hmeta = nullptr;  // pinned
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // per-phase profiling: events bracket each phase when enabled; launches always counted
@@ -130,6 +129,11 @@ gmres_status ensure_workspace(gmres_s* h, int m, int prec) {
   CK(h, h->w.ensure(sizeof(double) * (size_t)h->n));
   CK(h, h->t.ensure(sizeof(double) * (size_t)h->n));
   CK(h, h->part.ensure(sizeof(double) * (size_t)max_grid * kLdp));
+  CK(h, h->part2.ensure(sizeof(double) * (size_t)kMaxGroups * kLdp));
+  if (!h->tickets.p) {
+    CK(h, h->tickets.ensure(sizeof(unsigned) * (1 + kMaxGroups)));
+    CK(h, cudaMemsetAsync(h->tickets.p, 0, sizeof(unsigned) * (1 + kMaxGroups), h->stream));
+  }
   CK(h, h->cpart.ensure(sizeof(double) * (size_t)(h->npieces + 1)));
   CK(h, h->sdefl.ensure(12 * (size_t)(h->r + 1)));
   CK(h, h->meta.ensure(sizeof(Meta)));
@@ -158,8 +162,9 @@ Ctl make_ctl(gmres_s* h) {
   c.scal = m->scal;
   c.counts = m->counts;
   c.flags = m->flags;
-  c.ticket = m->ticket;
+  c.ticket = h->tickets.as<unsigned>();
   c.part = h->part.as<double>();
+  c.part2 = h->part2.as<double>();
   c.cpart = h->cpart.as<double>();
   c.sdefl = h->sdefl.as<double>();
   c.sdefl32 = reinterpret_cast<float*>(h->sdefl.as<double>() + (h->r + 1));
@@ -459,6 +464,11 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
   h->prof_on = opts.profile != 0;
   h->pms[PH_SETUP] = std::chrono::duration<double, std::milli>(
                          std::chrono::steady_clock::now() - t_setup).count();
+  // kernels enqueued by the setup: validation, FP32 copy, aggregate permutation (4),
+  // coarse matrix, Gauss-Jordan (init, 2 per pivot, extract), infinity norm
+  h->plaunch[PH_SETUP] = 1 + (opts.precision != GMRES_FP64 ? 1 : 0) +
+                         (r > 0 ? 4 + 1 + 2 + 2LL * r : 0) +
+                         (opts.mu_mode == GMRES_MU_NORM_INF ? 1 : 0);
 #undef CKC
   *out = h;
   return GMRES_OK;
