@@ -154,6 +154,27 @@ gmres_status gmres_create(gmres_t* h, const gmres_csr* A, const gmres_defl* W,
 gmres_status gmres_solve(gmres_t h, const double* b, const double* x0, int32_t m,
                          double tol, int64_t maxit, double* x, gmres_info* info);
 
+/* Same solve as gmres_solve, but on success the call allocates no memory, on the device or
+ * the host (an error records its message in the handle, as every entry point does): the
+ * workspace it needs (Krylov basis, working vectors, control block, reduction
+ * partials) is carved from one 32 MiB array in the library's static device memory, which
+ * every device that loads the library holds until the process exits.  Intended for
+ * callers that must not allocate once set up: real-time loops with a frozen memory
+ * budget, or processes where a framework's caching allocator owns the device memory and
+ * an extra cudaMalloc could fail or fragment it.  The handle (from gmres_create, which
+ * does allocate) provides A and the deflation data.  The paper has no counterpart.
+ * Limits: the workspace, about 8 (m+1) round_up(n, 64) bytes for FP64 (half / a quarter
+ * of that basis for FP32 / BF16) plus about 1 MB, must fit in 32 MiB, otherwise
+ * GMRES_ERR_INVALID_ARG with a message naming the size.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device current: make
+ * that first call before any stream capture.  Every call on every handle shares the one
+ * array and it keeps the previous call's contents (the call clears what must start at
+ * zero): calls that overlap on the GPU, in any stream, race and give wrong results, so
+ * serialise them.  ms_total in info is host wall time.  Arguments, outputs and errors as
+ * gmres_solve; the per-phase profile of gmres_profile is not updated. */
+gmres_status gmres_solve_noalloc(gmres_t h, const double* b, const double* x0, int32_t m,
+                                 double tol, int64_t maxit, double* x, gmres_info* info);
+
 /* Adjoint solve A^T lam = g with the transposed preconditioner
  * M^-T = I + U (|mu| T^-T - I) U^T (same U; T^T = U^T A^T U).  The transpose of A is
  * built on the first call and kept.  Arguments as gmres_solve. */

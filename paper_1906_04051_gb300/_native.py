@@ -68,6 +68,8 @@ SIGNATURES = {
                               C.POINTER(gmres_info)]),
     "gmres_adjoint_solve": (C.c_int, [_P, _P, _P, C.c_int32, C.c_double, C.c_int64, _P,
                                       C.POINTER(gmres_info)]),
+    "gmres_solve_noalloc": (C.c_int, [_P, _P, _P, C.c_int32, C.c_double, C.c_int64, _P,
+                                      C.POINTER(gmres_info)]),
     "gmres_batch_solve": (C.c_int, [C.c_int32, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                                     C.c_int32, C.c_double, C.c_int64, C.POINTER(_P),
                                     C.POINTER(gmres_info), _P]),

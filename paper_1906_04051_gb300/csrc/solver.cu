@@ -338,6 +338,183 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
   return status;
 }
 
+// ---------------------------------------------------------------------------------------
+// Allocation-free solve.  The per-solve workspace (Krylov basis, working vectors, control
+// block, reduction partials) lives in one file-scope device array instead of memory
+// owned by the handle, so a successful call allocates nothing on the device or the host.
+// It is meant for callers that must not allocate once set up: a real-time loop with a
+// frozen memory budget, or a process whose device memory is owned by another allocator
+// (a framework's caching allocator) where an extra cudaMalloc could fail or fragment.
+// The handle (gmres_create, which does allocate) still holds A and the deflation data.
+// ---------------------------------------------------------------------------------------
+constexpr size_t kNoAllocBytes = (size_t)32 << 20;  // 32 MiB, held by every device that
+                                                    // loads the library until exit
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+unsigned char* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+
+// Device address of the scratch array for the current device.  In host code the array's
+// name is only a host-side stand-in, so the address is looked up once per device (with
+// that device current) and cached.  This first lookup on a device is the only set-up
+// step; make the first call on each device before any stream capture.
+cudaError_t noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<unsigned char*>(ptr);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+gmres_status run_noalloc(gmres_s* h, OpHost& o, const double* b, const double* x0, int m,
+                         double tol, long long maxit, double* x, gmres_info* info) {
+  if (!b || !x) return fail(h, GMRES_ERR_INVALID_ARG, "b and x must be device pointers");
+  if (m < 1 || m > kMaxM) return fail(h, GMRES_ERR_INVALID_ARG, "m must be in [1, 64]");
+  if (!(tol >= 0.0) || maxit < 0) return fail(h, GMRES_ERR_INVALID_ARG, "tol >= 0, maxit >= 0");
+  const int prec = prec_of(h->opts.precision);
+  const long long ldv = ((long long)h->n + 63) / 64 * 64;
+  const int max_grid = h->sms * 8;
+  // carve the workspace out of the static array, 256-byte aligned pieces
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off += (bytes + 255) / 256 * 256;
+    return at;
+  };
+  const size_t oV = take(basis_elem(prec) * (size_t)ldv * (m + 1));
+  const size_t oW = take(sizeof(double) * (size_t)ldv);
+  const size_t oT = take(sizeof(double) * (size_t)ldv);
+  const size_t oCtl = take(sizeof(double) * (2 * (size_t)(m + 1) * m + 8 * (size_t)(m + 1)));
+  const size_t oMeta = take(sizeof(Meta));
+  const size_t oPart = take(sizeof(double) * (size_t)max_grid * kLdp);
+  const size_t oPart2 = take(sizeof(double) * (size_t)kMaxGroups * kLdp);
+  const size_t oTick = take(sizeof(unsigned) * (1 + kMaxGroups));
+  const size_t oCpart = take(sizeof(double) * (size_t)(h->npieces + 1));
+  const size_t oSdefl = take(12 * (size_t)(h->r + 1));
+  if (off > kNoAllocBytes)
+    return fail(h, GMRES_ERR_INVALID_ARG,
+                "gmres_solve_noalloc: workspace of " + std::to_string(off) +
+                    " bytes exceeds the 33554432-byte static scratch (about (m+1)*n basis "
+                    "elements); use gmres_solve");
+  unsigned char* base = nullptr;
+  CK(h, noalloc_scratch(&base));
+  cudaStream_t st = h->stream;
+  // everything that must start at zero: ticket counters (the previous call's contents
+  // are otherwise kept)
+  CK(h, cudaMemsetAsync(base + oTick, 0, sizeof(unsigned) * (1 + kMaxGroups), st));
+  const size_t nb = sizeof(double) * (size_t)h->n;
+  if (x != x0) {
+    if (x0) CK(h, cudaMemcpyAsync(x, x0, nb, cudaMemcpyDeviceToDevice, st));
+    else CK(h, cudaMemsetAsync(x, 0, nb, st));
+  }
+  CycleArgs a{};
+  a.op = make_op(h, o);
+  Ctl& c = a.ctl;
+  double* d = reinterpret_cast<double*>(base + oCtl);
+  c.H = d; d += (size_t)(m + 1) * m;
+  c.Hr = d; d += (size_t)(m + 1) * m;
+  c.g = d; d += m + 1;
+  c.cs = d; d += m + 1;
+  c.sn = d; d += m + 1;
+  c.y = d; d += m + 1;
+  c.sigma = d; d += m + 1;
+  c.h = d; d += m + 1;
+  c.coef = d;
+  Meta* meta = reinterpret_cast<Meta*>(base + oMeta);
+  c.scal = meta->scal;
+  c.counts = meta->counts;
+  c.flags = meta->flags;
+  c.ticket = reinterpret_cast<unsigned*>(base + oTick);
+  c.part = reinterpret_cast<double*>(base + oPart);
+  c.part2 = reinterpret_cast<double*>(base + oPart2);
+  c.cpart = reinterpret_cast<double*>(base + oCpart);
+  c.sdefl = reinterpret_cast<double*>(base + oSdefl);
+  c.sdefl32 = reinterpret_cast<float*>(c.sdefl + (h->r + 1));
+  c.ldh = m;
+  c.ldp = kLdp;
+  a.V = base + oV;
+  a.ldv = ldv;
+  a.w = base + oW;
+  a.t = reinterpret_cast<double*>(base + oT);
+  a.prec = prec;
+  a.m = m;
+  a.sms = h->sms;
+  a.grid_small = h->r > 0 ? grid_for(h->r, 8, h->sms) : 1;
+
+  const bool ebp = h->r > 0 && h->opts.deflation_mode == GMRES_DEFL_EBP;
+  const int mu_mode = h->opts.mu_mode;
+  double mu = 0.0;
+  if (mu_mode == GMRES_MU_USER) mu = std::fabs(h->opts.mu_user);
+  if (mu_mode == GMRES_MU_NORM_INF) mu = h->mu_norminf;
+  const bool mixed = prec != P_FP64;
+  double inner_tol = h->opts.inner_tol;
+  if (!(inner_tol > 0.0)) inner_tol = prec == P_BF16 ? 1e-2 : 1e-4;
+  const auto t_start = std::chrono::steady_clock::now();
+  Meta hm;  // status block read back into host stack memory
+  auto read = [&]() -> gmres_status {
+    CK(h, cudaMemcpyAsync(&hm, meta, sizeof(Meta), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    return GMRES_OK;
+  };
+  CK(h, launch_init(a, tol, inner_tol, h->opts.r0_norm_ref, mu, h->opts.fixed_iterations ? 1 : 0,
+                    mixed ? 1 : 0, maxit, st));
+  CK(h, launch_phase(a, PH_RESIDUAL, 0, false, x, b, st, nullptr));
+  gmres_status s = read();
+  if (s != GMRES_OK) return s;
+  int cycle = 0;
+  gmres_status status = GMRES_OK;
+  while (!hm.flags[F_STOP]) {
+    const bool defl_cycle = ebp && (mu_mode != GMRES_MU_RITZ_FIRST_CYCLE || cycle > 0);
+    if (defl_cycle) CK(h, launch_phase(a, PH_DEFL, 0, true, x, b, st, nullptr));
+    const long long left = maxit - hm.counts[C_STEPS];
+    const int jmax = (int)(left < m ? left : m);
+    for (int j = 0; j < jmax; ++j) {
+      CK(h, launch_phase(a, PH_SPMV, j, defl_cycle, x, b, st, nullptr));
+      CK(h, launch_phase(a, PH_DOT1, j, defl_cycle, x, b, st, nullptr));
+      CK(h, launch_phase(a, PH_UPD1DOT2, j, defl_cycle, x, b, st, nullptr));
+      CK(h, launch_phase(a, PH_UPD2NORM, j, defl_cycle, x, b, st, nullptr));
+      if (defl_cycle) CK(h, launch_phase(a, PH_DEFL, j + 1, true, x, b, st, nullptr));
+    }
+    CK(h, launch_phase(a, PH_CYCLE_END, 0, defl_cycle, x, b, st, nullptr));
+    if (ebp && mu_mode == GMRES_MU_RITZ_FIRST_CYCLE && cycle == 0)
+      CK(h, launch_phase(a, PH_RITZ, 0, false, x, b, st, nullptr));
+    CK(h, launch_phase(a, PH_RESIDUAL, 0, false, x, b, st, nullptr));
+    s = read();
+    if (s != GMRES_OK) return s;
+    ++cycle;
+    if (h->opts.timeout_ms > 0 && !hm.flags[F_STOP]) {
+      const double ms = std::chrono::duration<double, std::milli>(
+                            std::chrono::steady_clock::now() - t_start).count();
+      if (ms > h->opts.timeout_ms) {
+        status = fail(h, GMRES_ERR_TIMEOUT, "timeout_ms elapsed");
+        break;
+      }
+    }
+  }
+  if (status == GMRES_OK) status = (gmres_status)hm.flags[F_STATUS];
+  if (status == GMRES_ERR_NAN) h->err = "NaN or Inf in the residual or Hessenberg matrix";
+  if (status == GMRES_ERR_SINGULAR_COARSE) h->err = "no usable Ritz estimate of mu";
+  if (info) {
+    info->iters = hm.counts[C_STEPS];
+    info->cycles = hm.counts[C_CYCLES];
+    info->refinements = hm.counts[C_REFINE];
+    info->rel_res_est = hm.scal[S_EST];
+    info->rel_res_true = hm.scal[S_TRUE];
+    info->mu = ebp ? hm.scal[S_MU] : 0.0;
+    info->ms_total = (float)std::chrono::duration<double, std::milli>(
+                         std::chrono::steady_clock::now() - t_start).count();
+    info->status = status;
+  }
+  return status;
+}
+
 }  // namespace
 
 extern "C" {
@@ -478,6 +655,12 @@ gmres_status gmres_solve(gmres_t h, const double* b, const double* x0, int32_t m
                          int64_t maxit, double* x, gmres_info* info) {
   if (!h) return fail(nullptr, GMRES_ERR_INVALID_ARG, "null handle");
   return run(h, h->fwd, b, x0, m, tol, maxit, x, info);
+}
+
+gmres_status gmres_solve_noalloc(gmres_t h, const double* b, const double* x0, int32_t m,
+                                 double tol, int64_t maxit, double* x, gmres_info* info) {
+  if (!h) return fail(nullptr, GMRES_ERR_INVALID_ARG, "null handle");
+  return run_noalloc(h, h->fwd, b, x0, m, tol, maxit, x, info);
 }
 
 gmres_status gmres_adjoint_solve(gmres_t h, const double* g, const double* lam0, int32_t m,
