@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace gg {
 
@@ -359,6 +360,341 @@ __device__ void givens_step(Ctl& ctl, int j, int m, double hnext) {
     ctl.g[j + 1] = sg[1];
     if (sdone) ctl.flags[F_CYCLE_DONE] = 1;
   }
+}
+
+// --------------------------------------------------------------------------------------
+// Pipelined CGS2 passes.  Tiles of TR rows x k basis columns (plus the matching piece of
+// w) are copied into a ring of 2-4 shared-memory stages by bulk asynchronous copies
+// (one per column segment, issued by one thread, completed through an mbarrier per
+// stage), so the copies of the next tile are in flight while the current one is
+// computed.  Rows past n are zero padding of V and w (ldv and the w buffer are rounded
+// up to 256 rows and zeroed at allocation), so tiles need no row guards when reading.
+// --------------------------------------------------------------------------------------
+constexpr int kMaxStages = 4;
+constexpr size_t kStageBytes = 40 * 1024;  // preferred stage size
+constexpr size_t kRingBytes = 60 * 1024;   // ring per block (three blocks per SM)
+
+template <typename TV, typename TACC>
+struct Ring {
+  unsigned char* base;
+  uint64_t* bars;
+  int k, TR, S;
+  size_t stage_bytes;
+  __device__ TV* vt(int st) const { return reinterpret_cast<TV*>(base + (size_t)st * stage_bytes); }
+  __device__ TACC* wt(int st) const {
+    return reinterpret_cast<TACC*>(base + (size_t)st * stage_bytes + (size_t)k * TR * sizeof(TV));
+  }
+  // warp 0: tile starting at row r0 into stage st (lane 0 announces the bytes, the lanes
+  // issue the column segments)
+  __device__ void issue(int st, long long r0, const TV* V, long long ldv, const TACC* w) const {
+    const int lane = threadIdx.x & 31;
+    const uint32_t vb = (uint32_t)(TR * sizeof(TV)), wb = (uint32_t)(TR * sizeof(TACC));
+    if (lane == 0) mbar_arrive_expect_tx(&bars[st], (uint32_t)k * vb + wb);
+    __syncwarp();
+    TV* dst = vt(st);
+    for (int c = lane; c < k; c += 32)
+      bulk_g2s(dst + (size_t)c * TR, V + (size_t)c * ldv + r0, vb, &bars[st]);
+    if (lane == 0) bulk_g2s(wt(st), w + r0, wb, &bars[st]);
+  }
+};
+
+__host__ __device__ inline size_t ring_stage_bytes(int k, int TR, size_t sv, size_t sa) {
+  return ((size_t)k * TR * sv + (size_t)TR * sa + 127) / 128 * 128;
+}
+
+// stages that fit the ring budget (2..4)
+__host__ __device__ inline int ring_stages(size_t stage_bytes) {
+  int S = (int)(kRingBytes / stage_bytes);
+  return S < 2 ? 2 : (S > kMaxStages ? kMaxStages : S);
+}
+
+// Streams this block's tiles (blockIdx.x, +gridDim.x, ...) through the ring and calls
+// body(stage, r0) for each.  Returns false (after recording GMRES_ERR_TIMEOUT and waiting,
+// with a bound, for this block's copies still in flight) if a copy never completes.
+template <typename TV, typename TACC, typename F>
+__device__ bool ring_run(const Ring<TV, TACC>& R, int N, const TV* V, long long ldv,
+                         const TACC* w, Ctl& ctl, F&& body) {
+  const int tiles = (N + R.TR - 1) / R.TR;
+  const int nt = (int)blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < R.S; ++st) mbar_init(&R.bars[st], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x < 32)
+    for (int i = 0; i < nt && i < R.S; ++i)
+      R.issue(i, (long long)(blockIdx.x + (size_t)i * gridDim.x) * R.TR, V, ldv, w);
+  int i = 0;
+  bool ok = true;
+  for (; i < nt; ++i) {
+    const int st = i % R.S;
+    ok = __syncthreads_and(mbar_wait(&R.bars[st], (uint32_t)((i / R.S) & 1)));
+    if (!ok) break;
+    body(st, (long long)(blockIdx.x + (size_t)i * gridDim.x) * R.TR);
+    __syncthreads();
+    if (threadIdx.x < 32 && i + R.S < nt)
+      R.issue(st, (long long)(blockIdx.x + (size_t)(i + R.S) * gridDim.x) * R.TR, V, ldv, w);
+  }
+  if (!ok) {
+    for (int j = i; j < nt && j < i + R.S; ++j)
+      mbar_wait(&R.bars[j % R.S], (uint32_t)((j / R.S) & 1));
+    if (threadIdx.x == 0) {
+      ctl.flags[F_STATUS] = GMRES_ERR_TIMEOUT;
+      ctl.flags[F_STOP] = 1;
+      ctl.flags[F_CYCLE_DONE] = 1;
+    }
+    __syncthreads();
+  }
+  return ok;
+}
+
+// 16-byte vectors of the basis type: VN consecutive rows per shared-memory load.
+template <typename TV> struct Vec;
+template <> struct Vec<double> { static constexpr int n = 2; };
+template <> struct Vec<float> { static constexpr int n = 4; };
+template <> struct Vec<__nv_bfloat16> { static constexpr int n = 8; };
+
+template <typename TACC>
+__device__ __forceinline__ void ld_vec(const double* p, TACC (&o)[2]) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  o[0] = (TACC)v.x;
+  o[1] = (TACC)v.y;
+}
+template <typename TACC>
+__device__ __forceinline__ void ld_vec(const float* p, TACC (&o)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x;
+  o[1] = v.y;
+  o[2] = v.z;
+  o[3] = v.w;
+}
+template <typename TACC>
+__device__ __forceinline__ void ld_vec(const __nv_bfloat16* p, TACC (&o)[8]) {
+  const uint4 v = *reinterpret_cast<const uint4*>(p);
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float2 f = __bfloat1622float2(h[e]);
+    o[2 * e] = f.x;
+    o[2 * e + 1] = f.y;
+  }
+}
+// VN accumulator-type values from shared memory (16-byte aligned)
+template <int VN>
+__device__ __forceinline__ void ld_acc(const double* p, double (&o)[VN]) {
+#pragma unroll
+  for (int e = 0; e < VN; e += 2) {
+    const double2 v = *reinterpret_cast<const double2*>(p + e);
+    o[e] = v.x;
+    o[e + 1] = v.y;
+  }
+}
+template <int VN>
+__device__ __forceinline__ void ld_acc(const float* p, float (&o)[VN]) {
+#pragma unroll
+  for (int e = 0; e < VN; e += 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p + e);
+    o[e] = v.x;
+    o[e + 1] = v.y;
+    o[e + 2] = v.z;
+    o[e + 3] = v.w;
+  }
+}
+
+// Dot phase of a tile: warp `slice` owns columns slice, slice+8, ... (NW of them) and its
+// lanes sweep all TR rows, VN rows per 16-byte load.
+template <int NW, typename TV, typename TACC>
+__device__ __forceinline__ void tile_dot(TACC (&acc)[kSliceCols], const TV* sV, const TACC* sw,
+                                         int TR, int slice, int lane) {
+  constexpr int VN = Vec<TV>::n;
+  for (int r = lane * VN; r < TR; r += 32 * VN) {
+    TACC wv[VN];
+    ld_acc<VN>(sw + r, wv);
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+      TACC v[VN];
+      ld_vec(sV + (size_t)(slice + kSlices * i) * TR + r, v);
+#pragma unroll
+      for (int e = 0; e < VN; ++e) acc[i] += v[e] * wv[e];
+    }
+  }
+}
+
+// Update phase of a tile: thread (sub, group) sums columns [sub*kq, ...) of coef_c u_c for
+// the VN rows of its group; partials land in spart[sub][row].  Returns the threads used.
+template <typename TV, typename TACC>
+__device__ __forceinline__ void tile_update(const TV* sV, int TR, int k, const TACC* scoef,
+                                            TACC* spart, int P) {
+  constexpr int VN = Vec<TV>::n;
+  const int ng = TR / VN;
+  if ((int)threadIdx.x >= ng * P) return;
+  const int sub = threadIdx.x / ng, r = (threadIdx.x % ng) * VN;
+  const int kq = (k + P - 1) / P;
+  const int c0 = sub * kq, c1 = min(k, c0 + kq);
+  TACC p[VN];
+#pragma unroll
+  for (int e = 0; e < VN; ++e) p[e] = 0;
+  for (int c = c0; c < c1; ++c) {
+    TACC v[VN];
+    ld_vec(sV + (size_t)c * TR + r, v);
+    const TACC cf = scoef[c];
+#pragma unroll
+    for (int e = 0; e < VN; ++e) p[e] += v[e] * cf;
+  }
+#pragma unroll
+  for (int e = 0; e < VN; ++e) spart[sub * TR + r + e] = p[e];
+}
+
+template <typename TACC> __host__ __device__ constexpr int update_splits(int TR, int VN) {
+  // column subsets per row group: FP64 keeps the combine short (the FP64 pipe is the
+  // bound), FP32 spreads the work over more threads
+  return (kThreads / (TR / VN)) < (sizeof(TACC) == 8 ? 2 : 4) ? (kThreads / (TR / VN))
+                                                              : (sizeof(TACC) == 8 ? 2 : 4);
+}
+
+// CGS2 pass 1 (pipelined): h_c = sigma_c (u_c . w), coef_c = sigma_c h_c.
+template <typename TV, typename TACC>
+__global__ void __launch_bounds__(kThreads)
+    k_pass1(int N, const TV* __restrict__ V, long long ldv, int k, int TR,
+            const TACC* __restrict__ w, Ctl ctl) {
+  if (ctl.flags[F_CYCLE_DONE]) return;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ uint64_t bars[kMaxStages];
+  __shared__ double swarp[kSlices * kSliceCols];
+  __shared__ double sred[kMaxK];
+  __shared__ double tot[kMaxK];
+  const size_t sb = ring_stage_bytes(k, TR, sizeof(TV), sizeof(TACC));
+  const Ring<TV, TACC> R{smraw, bars, k, TR, ring_stages(sb), sb};
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = slice_cols(k, warp, kSlices);
+  TACC acc[kSliceCols];
+#pragma unroll
+  for (int i = 0; i < kSliceCols; ++i) acc[i] = 0;
+  const bool ok = ring_run(R, N, V, ldv, w, ctl, [&](int st, long long) {
+#define GG_P1(NW) tile_dot<NW, TV, TACC>(acc, R.vt(st), R.wt(st), TR, warp, lane)
+    GG_SLICE_SWITCH(nw, GG_P1)
+#undef GG_P1
+  });
+  if (!ok) return;
+  reduce_slices(acc, nw, k, kSlices, reinterpret_cast<double*>(smraw), swarp, sred);
+  if (!last_block_reduce(sred, k, ctl.part, ctl.part2, ctl.ldp, ctl.ticket, tot)) return;
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    const double hc = ctl.sigma[c] * tot[c];
+    ctl.h[c] = hc;
+    ctl.coef[c] = ctl.sigma[c] * hc;
+  }
+}
+
+// CGS2 pass 2 (pipelined): w -= sum_c coef_c u_c; h'_c = sigma_c (u_c . w); h += h'.
+template <typename TV, typename TACC>
+__global__ void __launch_bounds__(kThreads)
+    k_pass2(int N, const TV* __restrict__ V, long long ldv, int k, int TR,
+            TACC* __restrict__ w, Ctl ctl) {
+  if (ctl.flags[F_CYCLE_DONE]) return;
+  constexpr int VN = Vec<TV>::n;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ uint64_t bars[kMaxStages];
+  __shared__ double swarp[kSlices * kSliceCols];
+  __shared__ double sred[kMaxK];
+  __shared__ double tot[kMaxK];
+  __shared__ TACC scoef[kMaxK];
+  __shared__ __align__(16) TACC spart[4 * 256];
+  __shared__ __align__(16) TACC sw2[256];
+  const size_t sb = ring_stage_bytes(k, TR, sizeof(TV), sizeof(TACC));
+  const Ring<TV, TACC> R{smraw, bars, k, TR, ring_stages(sb), sb};
+  for (int c = threadIdx.x; c < k; c += blockDim.x) scoef[c] = (TACC)ctl.coef[c];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = slice_cols(k, warp, kSlices);
+  const int P = update_splits<TACC>(TR, VN);
+  const int ng = TR / VN;
+  TACC acc[kSliceCols];
+#pragma unroll
+  for (int i = 0; i < kSliceCols; ++i) acc[i] = 0;
+  const bool ok = ring_run(R, N, V, ldv, (const TACC*)w, ctl, [&](int st, long long r0) {
+    const TV* sV = R.vt(st);
+    const TACC* sw = R.wt(st);
+    tile_update<TV, TACC>(sV, TR, k, scoef, spart, P);
+    __syncthreads();
+    if ((int)threadIdx.x < ng) {
+      const int r = threadIdx.x * VN;
+#pragma unroll
+      for (int e = 0; e < VN; ++e) {
+        TACC acc_p = spart[r + e];
+        for (int q = 1; q < P; ++q) acc_p += spart[q * TR + r + e];
+        const TACC wn = sw[r + e] - acc_p;
+        sw2[r + e] = wn;
+        if (r0 + r + e < N) w[r0 + r + e] = wn;
+      }
+    }
+    __syncthreads();
+#define GG_P2(NW) tile_dot<NW, TV, TACC>(acc, sV, sw2, TR, warp, lane)
+    GG_SLICE_SWITCH(nw, GG_P2)
+#undef GG_P2
+  });
+  if (!ok) return;
+  reduce_slices(acc, nw, k, kSlices, reinterpret_cast<double*>(smraw), swarp, sred);
+  if (!last_block_reduce(sred, k, ctl.part, ctl.part2, ctl.ldp, ctl.ticket, tot)) return;
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    const double h2 = ctl.sigma[c] * tot[c];
+    ctl.h[c] += h2;
+    ctl.coef[c] = ctl.sigma[c] * h2;
+  }
+}
+
+// CGS2 pass 3 (pipelined): u_{j+1} = w - sum_c coef_c u_c (stored), h_{j+1,j} = ||u_{j+1}||,
+// then the plane rotations and stopping tests in the last block.
+template <typename TV, typename TACC>
+__global__ void __launch_bounds__(kThreads)
+    k_pass3(int N, TV* __restrict__ V, long long ldv, int k, int TR,
+            const TACC* __restrict__ w, Ctl ctl, int m) {
+  if (ctl.flags[F_CYCLE_DONE]) return;
+  constexpr int VN = Vec<TV>::n;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ uint64_t bars[kMaxStages];
+  __shared__ TACC scoef[kMaxK];
+  __shared__ __align__(16) TACC spart[4 * 256];
+  __shared__ double sbuf[kThreads / 32];
+  __shared__ double sred[1];
+  __shared__ double tot[1];
+  const size_t sb = ring_stage_bytes(k, TR, sizeof(TV), sizeof(TACC));
+  const Ring<TV, TACC> R{smraw, bars, k, TR, ring_stages(sb), sb};
+  for (int c = threadIdx.x; c < k; c += blockDim.x) scoef[c] = (TACC)ctl.coef[c];
+  const int P = update_splits<TACC>(TR, VN);
+  const int ng = TR / VN;
+  TV* __restrict__ vout = V + (size_t)k * ldv;
+  TACC nrm = 0;
+  const bool ok = ring_run(R, N, (const TV*)V, ldv, w, ctl, [&](int st, long long r0) {
+    const TV* sV = R.vt(st);
+    const TACC* sw = R.wt(st);
+    tile_update<TV, TACC>(sV, TR, k, scoef, spart, P);
+    __syncthreads();
+    if ((int)threadIdx.x < ng) {
+      const int r = threadIdx.x * VN;
+#pragma unroll
+      for (int e = 0; e < VN; ++e) {
+        if (r0 + r + e < N) {
+          TACC acc_p = spart[r + e];
+          for (int q = 1; q < P; ++q) acc_p += spart[q * TR + r + e];
+          const TACC wn = sw[r + e] - acc_p;
+          TV stv;
+          if constexpr (sizeof(TV) == sizeof(TACC)) {
+            stv = (TV)wn;
+          } else {
+            stv = st_round<TV>((float)wn);
+          }
+          vout[r0 + r + e] = stv;
+          const TACC sv = cv<TACC, TV>(stv);
+          nrm += sv * sv;
+        }
+      }
+    }
+  });
+  if (!ok) return;
+  const double bs = block_sum((double)nrm, sbuf);
+  if (threadIdx.x == 0) sred[0] = bs;
+  __syncthreads();
+  if (!last_block_reduce(sred, 1, ctl.part, ctl.part2, ctl.ldp, ctl.ticket, tot)) return;
+  givens_step(ctl, k - 1, m, sqrt(tot[0]));
 }
 
 // CGS2 pass 3: u_{j+1} = w - sum_c coef_c u_c (stored), h_{j+1,j} = ||u_{j+1}||.
@@ -795,7 +1131,25 @@ struct Kern {
     int spmv_d = 0, spmv_n = 0, dot1 = 0, upd2 = 0, resid = 0, xupd_d = 0, xupd_n = 0,
         xapply = 0, aggsum = 0;
     int upd1[kMaxK + 1] = {0};
+    int tr[kMaxK + 1] = {0};
+    int p1[kMaxK + 1] = {0}, p2[kMaxK + 1] = {0}, p3[kMaxK + 1] = {0};
   };
+  // Tile height of the pipelined passes (256/128/64 rows, at least 32 16-byte vectors):
+  // the largest whose stage fits 40 KB, so that a double-buffered ring leaves room for
+  // three resident blocks per SM (the FP64 passes rely on other blocks to fill the FP64
+  // pipe while one block waits at a barrier).
+  static int tile_rows(int k) {
+    const int lo = 32 * Vec<TV>::n;
+    for (int tr = 256; tr > lo; tr >>= 1)
+      if (ring_stage_bytes(k, tr, sizeof(TV), sizeof(TACC)) <= kStageBytes) return tr;
+    return lo;
+  }
+  static size_t ring_smem(int k) {
+    const size_t sb = ring_stage_bytes(k, tile_rows(k), sizeof(TV), sizeof(TACC));
+    const size_t need = (size_t)ring_stages(sb) * sb;
+    const size_t reduce = sizeof(double) * kSlices * kSliceCols * 33;  // reused after the ring
+    return need > reduce ? need : (reduce + 127) / 128 * 128;
+  }
   static Grids& grids(int sms) {
     static Grids g;
     static int for_sms = -1;
@@ -808,8 +1162,13 @@ struct Kern {
       g.xupd_d = resident_grid(k_xupdate<TV, true>, kThreads, 0, sms);
       g.xupd_n = resident_grid(k_xupdate<TV, false>, kThreads, 0, sms);
       g.xapply = resident_grid(k_xapply, kThreads, 0, sms);
-      for (int k = 1; k <= kMaxK; ++k)
+      for (int k = 1; k <= kMaxK; ++k) {
         g.upd1[k] = resident_grid(k_upd1dot2<TV, TACC>, kThreads, smem_upd1(k), sms);
+        g.tr[k] = tile_rows(k);
+        g.p1[k] = resident_grid(k_pass1<TV, TACC>, kThreads, ring_smem(k), sms);
+        g.p2[k] = resident_grid(k_pass2<TV, TACC>, kThreads, ring_smem(k), sms);
+        g.p3[k] = resident_grid(k_pass3<TV, TACC>, kThreads, ring_smem(k), sms);
+      }
       for_sms = sms;
     }
     return g;
@@ -850,21 +1209,27 @@ struct Kern {
         nl = 1;
         break;
       }
-      case PH_DOT1:
-        k_dot1<TV, TACC><<<balanced((N + 255) / 256, g.dot1), kThreads, 0, st>>>(
-            N, V, a.ldv, k, w, a.ctl);
+      case PH_DOT1: {
+        const int tr = g.tr[k];
+        k_pass1<TV, TACC><<<grid_for((N + tr - 1) / tr, 1, g.p1[k]), kThreads, ring_smem(k), st>>>(
+            N, V, a.ldv, k, tr, w, a.ctl);
         nl = 1;
         break;
-      case PH_UPD1DOT2:
-        k_upd1dot2<TV, TACC><<<balanced((N + kTile2 - 1) / kTile2, g.upd1[k]), kThreads,
-                               smem_upd1(k), st>>>(N, V, a.ldv, k, w, a.ctl);
+      }
+      case PH_UPD1DOT2: {
+        const int tr = g.tr[k];
+        k_pass2<TV, TACC><<<grid_for((N + tr - 1) / tr, 1, g.p2[k]), kThreads, ring_smem(k), st>>>(
+            N, V, a.ldv, k, tr, w, a.ctl);
         nl = 1;
         break;
-      case PH_UPD2NORM:
-        k_upd2norm<TV, TACC><<<balanced((N + kThreads - 1) / kThreads, g.upd2), kThreads, 0,
-                               st>>>(N, Vm, a.ldv, k, w, a.ctl, a.m);
+      }
+      case PH_UPD2NORM: {
+        const int tr = g.tr[k];
+        k_pass3<TV, TACC><<<grid_for((N + tr - 1) / tr, 1, g.p3[k]), kThreads, ring_smem(k), st>>>(
+            N, Vm, a.ldv, k, tr, w, a.ctl, a.m);
         nl = 1;
         break;
+      }
       case PH_DEFL: {  // U^T v_j and the correction for column j
         const TV* xj = V + (size_t)j * a.ldv;
         k_aggsum<TV><<<(d.npieces + 7) / 8, kThreads, 0, st>>>(xj, d, a.ctl.cpart, a.ctl.flags,
@@ -910,10 +1275,19 @@ struct Kern {
   }
 
   static cudaError_t prepare() {
-    // pass 2 may need more than the default 48 KB of dynamic shared memory
-    return cudaFuncSetAttribute(k_upd1dot2<TV, TACC>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_upd1(kMaxK));
+    // the passes may need more than the default 48 KB of dynamic shared memory
+    cudaError_t e = cudaFuncSetAttribute(k_upd1dot2<TV, TACC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_upd1(kMaxK));
+    size_t mx = 0;
+    for (int k = 1; k <= kMaxK; ++k) mx = ring_smem(k) > mx ? ring_smem(k) : mx;
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_pass1<TV, TACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_pass2<TV, TACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_pass3<TV, TACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+    return e;
   }
 };
 

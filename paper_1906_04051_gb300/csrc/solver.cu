@@ -116,18 +116,25 @@ constexpr int kLdp = 80;  // >= kMaxK + 1, multiple of 16
 // Lays out the control block for restart length ldh and returns the Ctl view.
 gmres_status ensure_workspace(gmres_s* h, int m, int prec) {
   const int ldh = m > h->ldh ? m : h->ldh;
-  const long long ldv = ((long long)h->n + 63) / 64 * 64;
+  // columns padded to 256 rows: the pipelined passes copy whole 256-row-aligned tiles,
+  // and the padding rows stay zero (never written after this memset)
+  const long long ldv = ((long long)h->n + 255) / 256 * 256;
   const int max_grid = h->sms * 8;
   if (ldh != h->ldh || prec != h->prec_ws) {
-    CK(h, h->V.ensure(basis_elem(prec) * (size_t)ldv * (ldh + 1)));
+    const size_t vbytes = basis_elem(prec) * (size_t)ldv * (ldh + 1);
+    CK(h, h->V.ensure(vbytes));
+    CK(h, cudaMemsetAsync(h->V.p, 0, vbytes, h->stream));
     const size_t nd = 2 * (size_t)(ldh + 1) * ldh + 8 * (size_t)(ldh + 1);
     CK(h, h->dctl.ensure(sizeof(double) * nd));
     h->ldh = ldh;
     h->prec_ws = prec;
     h->ldv = ldv;
   }
-  CK(h, h->w.ensure(sizeof(double) * (size_t)h->n));
-  CK(h, h->t.ensure(sizeof(double) * (size_t)h->n));
+  if (!h->w.p) {
+    CK(h, h->w.ensure(sizeof(double) * (size_t)ldv));
+    CK(h, cudaMemsetAsync(h->w.p, 0, sizeof(double) * (size_t)ldv, h->stream));
+  }
+  CK(h, h->t.ensure(sizeof(double) * (size_t)ldv));
   CK(h, h->part.ensure(sizeof(double) * (size_t)max_grid * kLdp));
   CK(h, h->part2.ensure(sizeof(double) * (size_t)kMaxGroups * kLdp));
   if (!h->tickets.p) {
@@ -379,7 +386,7 @@ gmres_status run_noalloc(gmres_s* h, OpHost& o, const double* b, const double* x
   if (m < 1 || m > kMaxM) return fail(h, GMRES_ERR_INVALID_ARG, "m must be in [1, 64]");
   if (!(tol >= 0.0) || maxit < 0) return fail(h, GMRES_ERR_INVALID_ARG, "tol >= 0, maxit >= 0");
   const int prec = prec_of(h->opts.precision);
-  const long long ldv = ((long long)h->n + 63) / 64 * 64;
+  const long long ldv = ((long long)h->n + 255) / 256 * 256;
   const int max_grid = h->sms * 8;
   // carve the workspace out of the static array, 256-byte aligned pieces
   size_t off = 0;
@@ -406,9 +413,10 @@ gmres_status run_noalloc(gmres_s* h, OpHost& o, const double* b, const double* x
   unsigned char* base = nullptr;
   CK(h, noalloc_scratch(&base));
   cudaStream_t st = h->stream;
-  // everything that must start at zero: ticket counters (the previous call's contents
-  // are otherwise kept)
+  // everything that must start at zero (the previous call's contents are otherwise kept):
+  // ticket counters, and the basis and working vector, whose padding rows past n are read
   CK(h, cudaMemsetAsync(base + oTick, 0, sizeof(unsigned) * (1 + kMaxGroups), st));
+  CK(h, cudaMemsetAsync(base + oV, 0, oW + sizeof(double) * (size_t)ldv - oV, st));
   const size_t nb = sizeof(double) * (size_t)h->n;
   if (x != x0) {
     if (x0) CK(h, cudaMemcpyAsync(x, x0, nb, cudaMemcpyDeviceToDevice, st));
