@@ -167,6 +167,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-sample-steps", type=int, default=M)
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the time-to-1e-10 comparison on q1-n2048")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -295,6 +297,35 @@ def main():
         e2e = {"value": world * args.steps / (e_tot / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # ---- time to a true relative residual of 1e-10 on q1-n2048: FP64 vs FP32 / BF16 inner
+    mixed = None
+    if rank == 0 and not args.no_mixed:
+        del x, flush
+        torch.cuda.empty_cache()
+        p3 = W.workload3()
+        r3, c3, v3, b3 = G.q1_assemble(p3.n, t(p3.kappa), p3.beta, t(p3.f))
+        a3 = t(p3.agg, torch.int32)
+        mixed = {"workload": "q1-n2048 GMRES(40), r = 64, tol 1e-10 (true FP64 residual)"}
+        xs = {}
+        for name, prec in (("fp64", G.FP64), ("fp32_inner", G.FP32_INNER),
+                           ("bf16_basis", G.BF16_BASIS)):
+            s3 = G.Solver(r3, c3, v3, a3, p3.r, precision=prec)
+            ev0.record(stream)
+            x3, i3 = s3.solve(b3, m=p3.m, tol=1e-10, maxit=60000)
+            ev1.record(stream)
+            ev1.synchronize()
+            s3.close()
+            xs[name] = x3
+            mixed[name] = {"ms": ev0.elapsed_time(ev1), "iters": i3["iters"],
+                           "refinements": i3["refinements"], "status": i3["status"],
+                           "rel_res_true": i3["rel_res_true"]}
+        for name in ("fp32_inner", "bf16_basis"):
+            mixed[name]["speedup_vs_fp64"] = mixed["fp64"]["ms"] / mixed[name]["ms"]
+            mixed[name]["rel_err_vs_fp64"] = float(
+                torch.linalg.vector_norm(xs[name] - xs["fp64"]) /
+                torch.linalg.vector_norm(xs["fp64"]))
+        del xs
+
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -316,6 +347,7 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clocks,
             "e2e": e2e,
+            "mixed_precision": mixed,
             "cpu_baseline": cb,
         }
         print(json.dumps(out), flush=True)

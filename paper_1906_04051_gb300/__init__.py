@@ -14,3 +14,6 @@ __all__ = [
     "FP64", "FP32_INNER", "BF16_BASIS", "DEFL_EBP", "DEFL_PROJECTOR", "DEFL_NONE",
     "MU_RITZ_FIRST_CYCLE", "MU_USER", "MU_NORM_INF",
 ]
+from .autograd import GmresSolve, Q1Setup, q1_solve  # noqa: E402
+
+__all__ += ["GmresSolve", "Q1Setup", "q1_solve"]
