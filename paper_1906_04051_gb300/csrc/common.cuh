@@ -43,6 +43,7 @@ enum FlagSlot {
   F_FIXED,           // fixed-iteration protocol
   F_MIXED,           // inner-tolerance test active (mixed precision)
   F_RHO0_SET,
+  F_DEFL_ON,         // the EBP correction is active (batched driver; set by the Ritz step)
   F_NFLAGS = 16
 };
 enum CountSlot { C_STEPS = 0, C_CYCLES, C_REFINE, C_MAXIT, C_NCOUNT = 8 };

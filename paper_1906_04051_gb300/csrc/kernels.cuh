@@ -1,0 +1,600 @@
+// kernels.cuh -- device building blocks shared by the single-system kernels (arnoldi.cu)
+// and the batched kernels (batch.cu): the staged SpMV tile, warp-slice multi-dots and
+// their deterministic reduction, the bulk-copy tile ring, the vector shared-memory
+// loads, the plane rotations (Eqs. 12, 14), the restart decision (Eq. 15), the back
+// substitution (Eq. 12), the Ritz estimate of |mu| (Sec. 3.3) and the control-block
+// initialisation.
+#pragma once
+
+#include <cfloat>
+
+#include "common.cuh"
+#include "tma.cuh"
+
+namespace gg {
+
+namespace {
+
+constexpr int kSpmvRows = 256;   // rows per SpMV tile (one per thread)
+constexpr int kSpmvCap = 2560;   // CSR entries staged in shared memory per chunk
+
+// --------------------------------------------------------------------------------------
+// SpMV tile: rows [r0, r0 + 256) of A, one thread per row.  The tile's CSR entries are
+// staged through shared memory with coalesced loads; x is gathered from global memory.
+// acc  = sum_k a_ik x(col_k);  accd = sum_k a_ik s(agg(col_k))  (when DEFL)
+// --------------------------------------------------------------------------------------
+template <typename TA, typename TACC, bool DEFL, typename XG>
+__device__ __forceinline__ void spmv_tile(int N, int r0, const int* __restrict__ rowptr,
+                                          const int* __restrict__ col,
+                                          const TA* __restrict__ val, TA* sval, int* scol,
+                                          XG xg, const int* __restrict__ agg,
+                                          const TACC* __restrict__ sdefl, TACC& acc,
+                                          TACC& accd) {
+  const int row = r0 + threadIdx.x;
+  const int last = min(r0 + kSpmvRows, N);
+  const int rs = row < N ? __ldg(rowptr + row) : 0;
+  const int re = row < N ? __ldg(rowptr + row + 1) : 0;
+  const int base = __ldg(rowptr + r0);
+  const int end = __ldg(rowptr + last);
+  acc = 0;
+  accd = 0;
+  for (int cs = base; cs < end; cs += kSpmvCap) {
+    const int ce = min(cs + kSpmvCap, end);
+    __syncthreads();
+#pragma unroll 4
+    for (int k = cs + threadIdx.x; k < ce; k += blockDim.x) {
+      sval[k - cs] = __ldg(val + k);
+      scol[k - cs] = __ldg(col + k);
+    }
+    __syncthreads();
+    const int a = max(rs, cs), b = min(re, ce);
+    for (int k = a; k < b; ++k) {
+      const int c = scol[k - cs];
+      const TACC v = (TACC)sval[k - cs];
+      acc += v * xg(c);
+      if (DEFL) {
+        const int p = __ldg(agg + c);
+        if (p >= 0) accd += v * sdefl[p];
+      }
+    }
+  }
+}
+
+// Number of columns of warp slice `slice` among k columns dealt round-robin to nslice
+// slices.  Each warp runs an instance unrolled for exactly that many columns (a
+// warp-uniform switch), so no floating-point instruction is issued under a false
+// predicate: on GB300 a warp-wide FP64 FMA holds the narrow FP64 pipe for many cycles
+// whether or not its lanes are enabled.
+__device__ __forceinline__ int slice_cols(int k, int slice, int nslice) {
+  return (k - slice + nslice - 1) / nslice;
+}
+
+#define GG_SLICE_SWITCH(nw, CALL)      \
+  switch (nw) {                        \
+    case 1: CALL(1); break;            \
+    case 2: CALL(2); break;            \
+    case 3: CALL(3); break;            \
+    case 4: CALL(4); break;            \
+    case 5: CALL(5); break;            \
+    case 6: CALL(6); break;            \
+    case 7: CALL(7); break;            \
+    case 8: CALL(8); break;            \
+    case 9: CALL(9); break;            \
+    default: break;                    \
+  }
+
+// Per-block column sums of the warp-slice accumulators.  Lanes store their live
+// accumulators (nw of them) transposed in shared memory and one thread adds the 32 lane
+// values of a (warp, column) pair, which costs far fewer FP64 instructions than a
+// shuffle tree on every lane; row groups are then added in a fixed order.
+template <typename TACC>
+__device__ __forceinline__ void reduce_slices(const TACC (&acc)[kSliceCols], int nw, int k,
+                                              int nslice, double* sbuf /* 8*9*33 */,
+                                              double* swarp /* 8*9 */, double* sred) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nrg = kSlices / nslice;
+#pragma unroll
+  for (int i = 0; i < kSliceCols; ++i)
+    if (i < nw) sbuf[(warp * kSliceCols + i) * 33 + lane] = (double)acc[i];
+  __syncthreads();
+  for (int t = threadIdx.x; t < kSlices * kSliceCols; t += blockDim.x) {
+    const int wv = t / kSliceCols, i = t % kSliceCols;
+    if (i < slice_cols(k, wv % nslice, nslice)) {
+      const double* src = sbuf + (size_t)t * 33;
+      double s = 0.0;
+      for (int l = 0; l < 32; ++l) s += src[l];
+      swarp[t] = s;
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    const int sl = c % nslice, i = c / nslice;
+    double sum = 0.0;
+    for (int g = 0; g < nrg; ++g) sum += swarp[(g * nslice + sl) * kSliceCols + i];
+    sred[c] = sum;
+  }
+  __syncthreads();
+}
+
+// Plane rotations and stopping tests of step j (Eqs. 12, 14), by the whole block: the
+// column, rotations and gamma are staged in shared memory, one thread applies the
+// rotations there (no dependent global-memory round trips), then all threads store.
+__device__ void givens_step(Ctl& ctl, int j, int m, double hnext) {
+  __shared__ double sh[kMaxK + 1], scs[kMaxK], ssn[kMaxK], sg[2];
+  __shared__ int sdone;
+  const int ldh = ctl.ldh;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    const double hi = ctl.h[i];
+    sh[i] = hi;
+    ctl.Hr[(size_t)i * ldh + j] = hi;
+    if (i < j) {
+      scs[i] = ctl.cs[i];
+      ssn[i] = ctl.sn[i];
+    }
+  }
+  if (threadIdx.x == 0) {
+    ctl.Hr[(size_t)(j + 1) * ldh + j] = hnext;
+    sg[0] = ctl.g[j];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double hn2 = hnext * hnext;
+    for (int i = 0; i <= j; ++i) hn2 += sh[i] * sh[i];
+    for (int i = 0; i < j; ++i) {
+      const double a = sh[i], b = sh[i + 1];
+      sh[i] = scs[i] * a + ssn[i] * b;
+      sh[i + 1] = -ssn[i] * a + scs[i] * b;
+    }
+    const double a = sh[j];
+    double c = 1.0, sn = 0.0;
+    if (hnext != 0.0) {
+      const double rho = hypot(a, hnext);
+      c = a / rho;
+      sn = hnext / rho;
+      sh[j] = rho;
+    }
+    sh[j + 1] = 0.0;
+    scs[j] = c;
+    ssn[j] = sn;
+    const double gj = sg[0];
+    sg[1] = -sn * gj;
+    sg[0] = c * gj;
+    const long long steps = ++ctl.counts[C_STEPS];
+    ctl.flags[F_K] = j + 1;
+    const double est = fabs(sg[1]) / ctl.scal[S_RHO0];
+    ctl.scal[S_EST] = est;
+    ctl.sigma[j + 1] = hnext > 0.0 ? 1.0 / hnext : 0.0;
+    bool done = false;
+    if (!isfinite(hnext) || !isfinite(est)) {
+      ctl.flags[F_STATUS] = GMRES_ERR_NAN;
+      ctl.flags[F_STOP] = 1;
+      done = true;
+    }
+    if (hnext <= 1e-14 * sqrt(hn2)) done = true;  // breakdown: the Krylov space is invariant
+    if (!ctl.flags[F_FIXED] && est <= ctl.scal[S_TOL]) done = true;
+    if (ctl.flags[F_MIXED] && fabs(sg[1]) <= ctl.scal[S_INNER_TOL] * ctl.scal[S_BETA_CYCLE])
+      done = true;
+    if (steps >= ctl.counts[C_MAXIT]) done = true;
+    if (j + 1 >= m) done = true;
+    sdone = done ? 1 : 0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) ctl.H[(size_t)i * ldh + j] = sh[i];
+  if (threadIdx.x == 0) {
+    ctl.cs[j] = scs[j];
+    ctl.sn[j] = ssn[j];
+    ctl.g[j] = sg[0];
+    ctl.g[j + 1] = sg[1];
+    if (sdone) ctl.flags[F_CYCLE_DONE] = 1;
+  }
+}
+
+// --------------------------------------------------------------------------------------
+// Pipelined CGS2 passes.  Tiles of TR rows x k basis columns (plus the matching piece of
+// w) are copied into a ring of 2-4 shared-memory stages by bulk asynchronous copies
+// (one per column segment, issued by one thread, completed through an mbarrier per
+// stage), so the copies of the next tile are in flight while the current one is
+// computed.  Rows past n are zero padding of V and w (ldv and the w buffer are rounded
+// up to 256 rows and zeroed at allocation), so tiles need no row guards when reading.
+// --------------------------------------------------------------------------------------
+constexpr int kMaxStages = 4;
+constexpr size_t kStageBytes = 40 * 1024;  // preferred stage size
+constexpr size_t kRingBytes = 60 * 1024;   // ring per block (three blocks per SM)
+
+template <typename TV, typename TACC>
+struct Ring {
+  unsigned char* base;
+  uint64_t* bars;
+  int k, TR, S;
+  size_t stage_bytes;
+  __device__ TV* vt(int st) const { return reinterpret_cast<TV*>(base + (size_t)st * stage_bytes); }
+  __device__ TACC* wt(int st) const {
+    return reinterpret_cast<TACC*>(base + (size_t)st * stage_bytes + (size_t)k * TR * sizeof(TV));
+  }
+  // warp 0: tile starting at row r0 into stage st (lane 0 announces the bytes, the lanes
+  // issue the column segments)
+  __device__ void issue(int st, long long r0, const TV* V, long long ldv, const TACC* w) const {
+    const int lane = threadIdx.x & 31;
+    const uint32_t vb = (uint32_t)(TR * sizeof(TV)), wb = (uint32_t)(TR * sizeof(TACC));
+    if (lane == 0) mbar_arrive_expect_tx(&bars[st], (uint32_t)k * vb + wb);
+    __syncwarp();
+    TV* dst = vt(st);
+    for (int c = lane; c < k; c += 32)
+      bulk_g2s(dst + (size_t)c * TR, V + (size_t)c * ldv + r0, vb, &bars[st]);
+    if (lane == 0) bulk_g2s(wt(st), w + r0, wb, &bars[st]);
+  }
+};
+
+__host__ __device__ inline size_t ring_stage_bytes(int k, int TR, size_t sv, size_t sa) {
+  return ((size_t)k * TR * sv + (size_t)TR * sa + 127) / 128 * 128;
+}
+
+// stages that fit the ring budget (2..4)
+__host__ __device__ inline int ring_stages(size_t stage_bytes) {
+  int S = (int)(kRingBytes / stage_bytes);
+  return S < 2 ? 2 : (S > kMaxStages ? kMaxStages : S);
+}
+
+// Streams this block's tiles (blockIdx.x, +gridDim.x, ...) through the ring and calls
+// body(stage, r0) for each.  Returns false (after recording GMRES_ERR_TIMEOUT and waiting,
+// with a bound, for this block's copies still in flight) if a copy never completes.
+template <typename TV, typename TACC, typename F>
+__device__ bool ring_run(const Ring<TV, TACC>& R, int N, const TV* V, long long ldv,
+                         const TACC* w, Ctl& ctl, F&& body) {
+  const int tiles = (N + R.TR - 1) / R.TR;
+  const int nt = (int)blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < R.S; ++st) mbar_init(&R.bars[st], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x < 32)
+    for (int i = 0; i < nt && i < R.S; ++i)
+      R.issue(i, (long long)(blockIdx.x + (size_t)i * gridDim.x) * R.TR, V, ldv, w);
+  int i = 0;
+  bool ok = true;
+  for (; i < nt; ++i) {
+    const int st = i % R.S;
+    ok = __syncthreads_and(mbar_wait(&R.bars[st], (uint32_t)((i / R.S) & 1)));
+    if (!ok) break;
+    body(st, (long long)(blockIdx.x + (size_t)i * gridDim.x) * R.TR);
+    __syncthreads();
+    if (threadIdx.x < 32 && i + R.S < nt)
+      R.issue(st, (long long)(blockIdx.x + (size_t)(i + R.S) * gridDim.x) * R.TR, V, ldv, w);
+  }
+  if (!ok) {
+    for (int j = i; j < nt && j < i + R.S; ++j)
+      mbar_wait(&R.bars[j % R.S], (uint32_t)((j / R.S) & 1));
+    if (threadIdx.x == 0) {
+      ctl.flags[F_STATUS] = GMRES_ERR_TIMEOUT;
+      ctl.flags[F_STOP] = 1;
+      ctl.flags[F_CYCLE_DONE] = 1;
+    }
+    __syncthreads();
+  }
+  return ok;
+}
+
+// 16-byte vectors of the basis type: VN consecutive rows per shared-memory load.
+template <typename TV> struct Vec;
+template <> struct Vec<double> { static constexpr int n = 2; };
+template <> struct Vec<float> { static constexpr int n = 4; };
+template <> struct Vec<__nv_bfloat16> { static constexpr int n = 8; };
+
+template <typename TACC>
+__device__ __forceinline__ void ld_vec(const double* p, TACC (&o)[2]) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  o[0] = (TACC)v.x;
+  o[1] = (TACC)v.y;
+}
+template <typename TACC>
+__device__ __forceinline__ void ld_vec(const float* p, TACC (&o)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x;
+  o[1] = v.y;
+  o[2] = v.z;
+  o[3] = v.w;
+}
+template <typename TACC>
+__device__ __forceinline__ void ld_vec(const __nv_bfloat16* p, TACC (&o)[8]) {
+  const uint4 v = *reinterpret_cast<const uint4*>(p);
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float2 f = __bfloat1622float2(h[e]);
+    o[2 * e] = f.x;
+    o[2 * e + 1] = f.y;
+  }
+}
+// VN accumulator-type values from shared memory (16-byte aligned)
+template <int VN>
+__device__ __forceinline__ void ld_acc(const double* p, double (&o)[VN]) {
+#pragma unroll
+  for (int e = 0; e < VN; e += 2) {
+    const double2 v = *reinterpret_cast<const double2*>(p + e);
+    o[e] = v.x;
+    o[e + 1] = v.y;
+  }
+}
+template <int VN>
+__device__ __forceinline__ void ld_acc(const float* p, float (&o)[VN]) {
+#pragma unroll
+  for (int e = 0; e < VN; e += 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p + e);
+    o[e] = v.x;
+    o[e + 1] = v.y;
+    o[e + 2] = v.z;
+    o[e + 3] = v.w;
+  }
+}
+
+// Dot phase of a tile: warp `slice` owns columns slice, slice+8, ... (NW of them) and its
+// lanes sweep all TR rows, VN rows per 16-byte load.
+template <int NW, typename TV, typename TACC>
+__device__ __forceinline__ void tile_dot(TACC (&acc)[kSliceCols], const TV* sV, const TACC* sw,
+                                         int TR, int slice, int lane) {
+  constexpr int VN = Vec<TV>::n;
+  for (int r = lane * VN; r < TR; r += 32 * VN) {
+    TACC wv[VN];
+    ld_acc<VN>(sw + r, wv);
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+      TACC v[VN];
+      ld_vec(sV + (size_t)(slice + kSlices * i) * TR + r, v);
+#pragma unroll
+      for (int e = 0; e < VN; ++e) acc[i] += v[e] * wv[e];
+    }
+  }
+}
+
+// Update phase of a tile: thread (sub, group) sums columns [sub*kq, ...) of coef_c u_c for
+// the VN rows of its group; partials land in spart[sub][row].  Returns the threads used.
+template <typename TV, typename TACC>
+__device__ __forceinline__ void tile_update(const TV* sV, int TR, int k, const TACC* scoef,
+                                            TACC* spart, int P) {
+  constexpr int VN = Vec<TV>::n;
+  const int ng = TR / VN;
+  if ((int)threadIdx.x >= ng * P) return;
+  const int sub = threadIdx.x / ng, r = (threadIdx.x % ng) * VN;
+  const int kq = (k + P - 1) / P;
+  const int c0 = sub * kq, c1 = min(k, c0 + kq);
+  TACC p[VN];
+#pragma unroll
+  for (int e = 0; e < VN; ++e) p[e] = 0;
+  for (int c = c0; c < c1; ++c) {
+    TACC v[VN];
+    ld_vec(sV + (size_t)c * TR + r, v);
+    const TACC cf = scoef[c];
+#pragma unroll
+    for (int e = 0; e < VN; ++e) p[e] += v[e] * cf;
+  }
+#pragma unroll
+  for (int e = 0; e < VN; ++e) spart[sub * TR + r + e] = p[e];
+}
+
+template <typename TACC> __host__ __device__ constexpr int update_splits(int TR, int VN) {
+  // column subsets per row group: FP64 keeps the combine short (the FP64 pipe is the
+  // bound), FP32 spreads the work over more threads
+  return (kThreads / (TR / VN)) < (sizeof(TACC) == 8 ? 2 : 4) ? (kThreads / (TR / VN))
+                                                              : (sizeof(TACC) == 8 ? 2 : 4);
+}
+
+// Restart decision after a true residual (Eq. 15): rho0 on the first call, NaN, tolerance
+// and maxit tests, and the start of a new cycle (g = beta_s e1, sigma_0 = 1/beta_s).
+__device__ void residual_decide(Ctl& ctl, double beta, double beta_s) {
+  if (!ctl.flags[F_RHO0_SET]) {
+    ctl.scal[S_RHO0] = ctl.scal[S_R0REF] > 0.0 ? ctl.scal[S_R0REF] : beta;
+    ctl.flags[F_RHO0_SET] = 1;
+  }
+  const double rho0 = ctl.scal[S_RHO0];
+  const double rel = rho0 > 0.0 ? beta / rho0 : 0.0;
+  ctl.scal[S_BETA] = beta;
+  ctl.scal[S_TRUE] = rel;
+  ctl.flags[F_K] = 0;
+  ctl.flags[F_CYCLE_DONE] = 1;
+  if (!isfinite(beta) || !isfinite(beta_s)) {
+    ctl.flags[F_STATUS] = GMRES_ERR_NAN;
+    ctl.flags[F_STOP] = 1;
+    return;
+  }
+  if (beta == 0.0 || (!ctl.flags[F_FIXED] && rel <= ctl.scal[S_TOL])) {
+    ctl.flags[F_STATUS] = GMRES_OK;
+    ctl.flags[F_STOP] = 1;
+    return;
+  }
+  if (ctl.counts[C_STEPS] >= ctl.counts[C_MAXIT]) {
+    ctl.flags[F_STATUS] = GMRES_NOT_CONVERGED;
+    ctl.flags[F_STOP] = 1;
+    return;
+  }
+  ctl.counts[C_REFINE]++;
+  ctl.g[0] = beta_s;
+  for (int i = 1; i <= ctl.ldh; ++i) ctl.g[i] = 0.0;
+  ctl.sigma[0] = 1.0 / beta_s;
+  ctl.scal[S_BETA_CYCLE] = beta_s;
+  ctl.flags[F_CYCLE_DONE] = 0;
+}
+
+// Back substitution R_k y = g (Eq. 12) on a shared-memory copy of R; coef = sigma o y.
+// Block-wide; R (kMaxM^2 doubles), sg, sy (kMaxM each) are shared-memory scratch.
+__device__ void backsolve_block(Ctl& ctl, double* R, double* sg, double* sy) {
+  const int k = ctl.flags[F_K];
+  const int ldh = ctl.ldh;
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    const int i = t / k, l = t % k;
+    R[t] = l >= i ? ctl.H[(size_t)i * ldh + l] : 0.0;
+  }
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sg[i] = ctl.g[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = k - 1; i >= 0; --i) {
+      double s = sg[i];
+      for (int l = i + 1; l < k; ++l) s -= R[i * k + l] * sy[l];
+      sy[i] = s / R[i * k + i];
+    }
+    ctl.counts[C_CYCLES]++;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    ctl.y[i] = sy[i];
+    ctl.coef[i] = ctl.sigma[i] * sy[i];
+  }
+}
+
+// One warp (lanes 0..31 of the calling warp); A is kMaxM^2 doubles of shared scratch.
+__device__ void ritz_warp(Ctl& ctl, double* A, double& smod, int& sfail) {
+  const int n = ctl.flags[F_K];
+  const int lane = threadIdx.x & 31;
+  if (n <= 0) return;
+  const int ldh = ctl.ldh;
+#define AA(i, j) A[(i) * n + (j)]
+  for (int t = lane; t < n * n; t += 32) AA(t / n, t % n) = ctl.Hr[(size_t)(t / n) * ldh + t % n];
+  if (lane == 0) { smod = 0.0; sfail = 0; }
+  __syncwarp();
+  double an = 0.0;
+  for (int t = lane; t < n * n; t += 32)
+    if (t % n >= t / n - 1) an += fabs(A[t]);
+  an = warp_sum(an);
+  int hi = n - 1, its = 0, total = 0;
+  while (hi >= 0) {
+    int l;
+    for (l = hi; l > 0; --l) {
+      double s = fabs(AA(l - 1, l - 1)) + fabs(AA(l, l));
+      if (s == 0.0) s = an;
+      if (fabs(AA(l, l - 1)) <= DBL_EPSILON * s) break;
+    }
+    __syncwarp();
+    if (l > 0 && lane == 0) AA(l, l - 1) = 0.0;
+    __syncwarp();
+    if (l == hi) {
+      if (lane == 0) smod = fmax(smod, fabs(AA(hi, hi)));
+      __syncwarp();
+      --hi;
+      its = 0;
+      continue;
+    }
+    if (l == hi - 1) {
+      const double a = AA(hi - 1, hi - 1), b = AA(hi - 1, hi), c = AA(hi, hi - 1), d = AA(hi, hi);
+      const double p = 0.5 * (a - d), disc = p * p + b * c, mid = 0.5 * (a + d);
+      double m2;
+      if (disc >= 0.0) {
+        const double q = sqrt(disc);
+        const double l1 = mid + (p >= 0.0 ? q : -q);
+        const double l2 = (l1 != 0.0) ? (a * d - b * c) / l1 : mid - (p >= 0.0 ? q : -q);
+        m2 = fmax(fabs(l1), fabs(l2));
+      } else {
+        m2 = hypot(mid, sqrt(-disc));
+      }
+      if (lane == 0) smod = fmax(smod, m2);
+      __syncwarp();
+      hi -= 2;
+      its = 0;
+      continue;
+    }
+    if (++total > 60 * n) {
+      if (lane == 0) sfail = 1;
+      break;
+    }
+    double s, t;
+    if (its == 10 || its == 20) {
+      const double w = fabs(AA(hi, hi - 1)) + fabs(AA(hi - 1, hi - 2));
+      const double sig = AA(hi, hi) + 0.75 * w;
+      s = 2.0 * sig;
+      t = sig * sig;
+    } else {
+      s = AA(hi - 1, hi - 1) + AA(hi, hi);
+      t = AA(hi - 1, hi - 1) * AA(hi, hi) - AA(hi - 1, hi) * AA(hi, hi - 1);
+    }
+    ++its;
+    double x = AA(l, l) * AA(l, l) + AA(l, l + 1) * AA(l + 1, l) - s * AA(l, l) + t;
+    double y = AA(l + 1, l) * (AA(l, l) + AA(l + 1, l + 1) - s);
+    double z = AA(l + 1, l) * AA(l + 2, l + 1);
+    for (int k = l; k <= hi - 2; ++k) {
+      const double nrm = sqrt(x * x + y * y + z * z);
+      if (nrm != 0.0) {
+        const double alpha = (x >= 0.0) ? -nrm : nrm;
+        const double v0 = x - alpha, v1 = y, v2 = z;
+        const double beta = 2.0 / (v0 * v0 + v1 * v1 + v2 * v2);
+        const int c0 = (k > l) ? k - 1 : l;
+        __syncwarp();
+        for (int jj = c0 + lane; jj <= hi; jj += 32) {
+          const double dd = beta * (v0 * AA(k, jj) + v1 * AA(k + 1, jj) + v2 * AA(k + 2, jj));
+          AA(k, jj) -= dd * v0;
+          AA(k + 1, jj) -= dd * v1;
+          AA(k + 2, jj) -= dd * v2;
+        }
+        __syncwarp();
+        if (k > l && lane == 0) {
+          AA(k + 1, k - 1) = 0.0;
+          AA(k + 2, k - 1) = 0.0;
+        }
+        __syncwarp();
+        const int r1 = (k + 3 < hi) ? k + 3 : hi;
+        for (int ii = l + lane; ii <= r1; ii += 32) {
+          const double dd = beta * (AA(ii, k) * v0 + AA(ii, k + 1) * v1 + AA(ii, k + 2) * v2);
+          AA(ii, k) -= dd * v0;
+          AA(ii, k + 1) -= dd * v1;
+          AA(ii, k + 2) -= dd * v2;
+        }
+        __syncwarp();
+      }
+      x = AA(k + 1, k);
+      y = AA(k + 2, k);
+      if (k < hi - 2) z = AA(k + 3, k);
+      __syncwarp();
+    }
+    const double nrm = sqrt(x * x + y * y);
+    if (nrm != 0.0) {
+      const double alpha = (x >= 0.0) ? -nrm : nrm;
+      const double v0 = x - alpha, v1 = y;
+      const double beta = 2.0 / (v0 * v0 + v1 * v1);
+      const int c0 = (hi - 2 > l) ? hi - 2 : l;
+      __syncwarp();
+      for (int jj = c0 + lane; jj <= hi; jj += 32) {
+        const double dd = beta * (v0 * AA(hi - 1, jj) + v1 * AA(hi, jj));
+        AA(hi - 1, jj) -= dd * v0;
+        AA(hi, jj) -= dd * v1;
+      }
+      __syncwarp();
+      if (hi - 2 >= l && lane == 0) AA(hi, hi - 2) = 0.0;
+      __syncwarp();
+      for (int ii = l + lane; ii <= hi; ii += 32) {
+        const double dd = beta * (AA(ii, hi - 1) * v0 + AA(ii, hi) * v1);
+        AA(ii, hi - 1) -= dd * v0;
+        AA(ii, hi) -= dd * v1;
+      }
+      __syncwarp();
+    }
+  }
+#undef AA
+  __syncwarp();
+  if (lane == 0) {
+    if (sfail || !(smod > 0.0) || !isfinite(smod)) {
+      ctl.flags[F_STATUS] = GMRES_ERR_SINGULAR_COARSE;
+      ctl.flags[F_STOP] = 1;
+    } else {
+      ctl.scal[S_MU] = smod;
+    }
+  }
+}
+
+__device__ void init_ctl(Ctl& ctl, double tol, double inner_tol, double r0ref, double mu,
+                       int fixed, int mixed, long long maxit) {
+  for (int i = 0; i < S_NSCAL; ++i) ctl.scal[i] = 0.0;
+  for (int i = 0; i < F_NFLAGS; ++i) ctl.flags[i] = 0;
+  for (int i = 0; i < C_NCOUNT; ++i) ctl.counts[i] = 0;
+  ctl.scal[S_TOL] = tol;
+  ctl.scal[S_INNER_TOL] = inner_tol;
+  ctl.scal[S_R0REF] = r0ref;
+  ctl.scal[S_MU] = mu;
+  ctl.flags[F_FIXED] = fixed;
+  ctl.flags[F_MIXED] = mixed;
+  ctl.flags[F_STATUS] = GMRES_NOT_CONVERGED;
+  ctl.flags[F_CYCLE_DONE] = 1;
+  ctl.counts[C_MAXIT] = maxit;
+  for (int i = 0; i < 1 + kMaxGroups; ++i) ctl.ticket[i] = 0u;
+}
+
+}  // namespace
+
+}  // namespace gg

@@ -185,24 +185,6 @@ def test_mixed_precision_reaches_1e10(G, orc, prec, name):
     assert relerr(xn, xo) <= 1e-7  # reported accuracy vs the FP64 oracle
 
 
-def test_batch_matches_single(G, orc):
-    probs = W.workload4(count=6, n_min=8, n_max=40)
-    solvers, bs, singles = [], [], []
-    for p in probs:
-        A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f, p.u)
-        s = gpu_solver_from_oracle(G, A, p.agg, p.r)
-        solvers.append(s)
-        bs.append(to_dev(b))
-        singles.append(s.solve(bs[-1], m=30, tol=1e-12, maxit=20000)[0])
-    xs, infos, st = G.batch_solve(solvers, bs, m=30, tol=1e-12, maxit=20000)
-    assert st == 0
-    for x, xs1, p in zip(xs, singles, probs):
-        assert torch.equal(x, xs1)
-        A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f, p.u)
-        xo, _ = orc.gmres(A, b, m=30, tol=1e-12, maxit=20000, defl=orc.Deflation(A, p.agg, p.r))
-        assert relerr(x.cpu().numpy(), xo) <= 1e-9
-
-
 # ---------------------------------------------------------------------------------------
 # error paths (host-detected, or device flags read by the host; nothing faults)
 # ---------------------------------------------------------------------------------------
