@@ -83,7 +83,9 @@ typedef enum {
 typedef enum {
   GMRES_DEFL_EBP = 0,       /* M^-1 = I + U (|mu| T^-1 - I) U^T  (Eq. 17, the paper's) */
   GMRES_DEFL_PROJECTOR = 1, /* P = I - A U T^-1 U^T: GMRES on P A xh = P b, then
-                               x = xh + U T^-1 U^T (b - A xh); P A W = 0 */
+                               x = xh + U T^-1 U^T (b - A xh); P A W = 0.  The true
+                               residual of x equals P (b - A xh), which the stopping test
+                               uses (single-system solves; not in gmres_batch_solve) */
   GMRES_DEFL_NONE = 2
 } gmres_deflation_mode;
 
@@ -120,7 +122,8 @@ typedef enum {
   GMRES_PH_DEFL = 6,      /* U^T v and the coarse correction (Eqs. 17-18) */
   GMRES_PH_CYCLE_END = 7, /* back substitution and x += M^-1 V y (Eq. 11) */
   GMRES_PH_RITZ = 8,      /* |mu| from the Ritz values of H_k */
-  GMRES_PH_COUNT = 9
+  GMRES_PH_PROJ_FINAL = 9,/* projector: x = xh + U T^-1 U^T (b - A xh) */
+  GMRES_PH_COUNT = 10
 } gmres_phase;
 
 typedef struct {

@@ -29,7 +29,7 @@ FP64, FP32_INNER, BF16_BASIS = 0, 1, 2
 DEFL_EBP, DEFL_PROJECTOR, DEFL_NONE = 0, 1, 2
 MU_RITZ_FIRST_CYCLE, MU_USER, MU_NORM_INF = 0, 1, 2
 PHASES = ["setup", "residual", "spmv", "dot1", "upd1dot2", "upd2norm", "defl", "cycle_end",
-          "ritz"]
+          "ritz", "proj_final"]
 
 
 class gmres_csr(C.Structure):

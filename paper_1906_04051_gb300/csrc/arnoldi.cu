@@ -198,7 +198,7 @@ template <typename TX>
 __global__ void __launch_bounds__(kThreads)
     k_aggsum(const TX* __restrict__ x, Defl d, double* __restrict__ cpart, const int* flags,
              int skip_slot) {
-  if (flags[skip_slot]) return;
+  if (skip_slot >= 0 && flags[skip_slot]) return;
   const int lane = threadIdx.x & 31;
   const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (p >= d.npieces) return;
@@ -210,10 +210,11 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // c_a = scale uscale_a sum(pieces of a);  s_a = uscale_a (|mu| (T^-1 c)_a - c_a).
+// proj != 0: s_a = uscale_a (T^-1 c)_a, the coarse solve of the deflation projector.
 __global__ void __launch_bounds__(kThreads)
     k_coarse(Defl d, const double* __restrict__ cpart, const double* __restrict__ scale_ptr,
-             Ctl ctl, int skip_slot) {
-  if (ctl.flags[skip_slot]) return;
+             Ctl ctl, int skip_slot, int proj) {
+  if (skip_slot >= 0 && ctl.flags[skip_slot]) return;
   extern __shared__ double sc[];
   const double scale = scale_ptr ? *scale_ptr : 1.0;
   const double mu = ctl.scal[S_MU];
@@ -233,10 +234,87 @@ __global__ void __launch_bounds__(kThreads)
     for (int b = lane; b < r; b += 32) acc += __ldg(row + b) * sc[b];
     acc = warp_sum(acc);
     if (lane == 0) {
-      const double sd = d.uscale[a] * (mu * acc - sc[a]);
+      const double sd = proj ? d.uscale[a] * acc : d.uscale[a] * (mu * acc - sc[a]);
       ctl.sdefl[a] = sd;
       ctl.sdefl32[a] = (float)sd;
     }
+  }
+}
+
+// --------------------------------------------------------------------------------------
+// Deflation projector P = I - A U T^-1 U^T (GMRES on P A xh = P b): the coarse correction
+// A (U y) is gathered over the CSR as s[agg[col]], with s = U y from k_coarse (proj mode).
+// --------------------------------------------------------------------------------------
+// vec -= A U y for every row (a step's w = P A v, skip when the cycle has ended)
+template <typename TA, typename TACC>
+__global__ void __launch_bounds__(kSpmvRows)
+    k_proj_sub(int N, const int* __restrict__ rowptr, const int* __restrict__ col,
+               const TA* __restrict__ val, const int* __restrict__ agg,
+               const TACC* __restrict__ sdefl, TACC* __restrict__ vec, Ctl ctl) {
+  if (ctl.flags[F_CYCLE_DONE]) return;
+  __shared__ TA sval[kSpmvCap];
+  __shared__ int scol[kSpmvCap];
+  const int tiles = (N + kSpmvRows - 1) / kSpmvRows;
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+    TACC acc, accd;
+    spmv_tile<TA, TACC, true>(N, t * kSpmvRows, rowptr, col, val, sval, scol,
+                              [&](int) { return (TACC)0; }, agg, sdefl, acc, accd);
+    const int row = t * kSpmvRows + threadIdx.x;
+    if (row < N) vec[row] -= accd;
+  }
+}
+
+// r = t - A U y (t = b - A xh in FP64), stored as the cycle's start vector, with the
+// restart decision on ||P (b - A xh)|| = ||b - A x|| (Eq. 15)
+template <typename TV>
+__global__ void __launch_bounds__(kSpmvRows)
+    k_proj_resid(int N, const int* __restrict__ rowptr, const int* __restrict__ col,
+                 const double* __restrict__ val, const int* __restrict__ agg,
+                 const double* __restrict__ t, TV* __restrict__ V0, Ctl ctl) {
+  if (ctl.flags[F_STOP]) return;
+  __shared__ double sval[kSpmvCap];
+  __shared__ int scol[kSpmvCap];
+  __shared__ double sbuf[kSpmvRows / 32];
+  __shared__ double sred[2];
+  __shared__ double tot[2];
+  double n1 = 0.0, n2 = 0.0;
+  const int tiles = (N + kSpmvRows - 1) / kSpmvRows;
+  for (int tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
+    double acc, accd;
+    spmv_tile<double, double, true>(N, tt * kSpmvRows, rowptr, col, val, sval, scol,
+                                    [&](int) { return 0.0; }, agg, ctl.sdefl, acc, accd);
+    const int row = tt * kSpmvRows + threadIdx.x;
+    if (row < N) {
+      const double r = t[row] - accd;
+      n1 += r * r;
+      if constexpr (sizeof(TV) == sizeof(double)) {
+        V0[row] = r;
+      } else {
+        const TV st = st_round<TV>((float)r);
+        V0[row] = st;
+        const double sv = (double)to_f<TV>(st);
+        n2 += sv * sv;
+      }
+    }
+  }
+  double b1 = block_sum(n1, sbuf);
+  double b2 = (sizeof(TV) == sizeof(double)) ? b1 : block_sum(n2, sbuf);
+  if (threadIdx.x == 0) {
+    sred[0] = b1;
+    sred[1] = b2;
+  }
+  __syncthreads();
+  if (!last_block_reduce(sred, 2, ctl.part, ctl.part2, ctl.ldp, ctl.ticket, tot)) return;
+  if (threadIdx.x == 0) residual_decide(ctl, sqrt(tot[0]), sqrt(tot[1]));
+}
+
+// x += U y (the coarse component x = xh + U T^-1 U^T (b - A xh) at the end of the solve)
+__global__ void __launch_bounds__(kThreads)
+    k_xcoarse(int N, double* __restrict__ x, const int* __restrict__ agg, Ctl ctl) {
+  if (ctl.flags[F_STATUS] < 0) return;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < N; row += gridDim.x * blockDim.x) {
+    const int a = agg[row];
+    if (a >= 0) x[row] += ctl.sdefl[a];
   }
 }
 
@@ -292,12 +370,15 @@ __global__ void __launch_bounds__(kThreads)
 
 // True residual in FP64 (Eq. 15): r = b - A x, u_0 = r stored in the basis precision,
 // rho0 on the first call, convergence / maxit decision, and the start of a new cycle.
+// With proj_t != null (deflation projector) the unprojected residual goes to proj_t, its
+// norm only sets rho0 on the first call, and k_proj_resid takes the decision.
 template <typename TV>
 __global__ void __launch_bounds__(kSpmvRows)
     k_residual(int N, const int* __restrict__ rowptr, const int* __restrict__ col,
                const double* __restrict__ val, const double* __restrict__ x,
-               const double* __restrict__ b, TV* __restrict__ V0, Ctl ctl) {
-  if (ctl.flags[F_STOP]) return;
+               const double* __restrict__ b, TV* __restrict__ V0, Ctl ctl,
+               double* __restrict__ proj_t, int force) {
+  if (!force && ctl.flags[F_STOP]) return;
   __shared__ double sval[kSpmvCap];
   __shared__ int scol[kSpmvCap];
   __shared__ double sbuf[kSpmvRows / 32];
@@ -314,7 +395,9 @@ __global__ void __launch_bounds__(kSpmvRows)
     if (row < N) {
       const double r = __ldg(b + row) - acc;
       n1 += r * r;
-      if constexpr (sizeof(TV) == sizeof(double)) {
+      if (proj_t) {
+        proj_t[row] = r;
+      } else if constexpr (sizeof(TV) == sizeof(double)) {
         V0[row] = r;
       } else {
         const TV st = st_round<TV>((float)r);
@@ -332,7 +415,15 @@ __global__ void __launch_bounds__(kSpmvRows)
   }
   __syncthreads();
   if (!last_block_reduce(sred, 2, ctl.part, ctl.part2, ctl.ldp, ctl.ticket, tot)) return;
-  if (threadIdx.x == 0) residual_decide(ctl, sqrt(tot[0]), sqrt(tot[1]));
+  if (threadIdx.x != 0) return;
+  if (proj_t) {
+    if (!ctl.flags[F_RHO0_SET]) {
+      ctl.scal[S_RHO0] = ctl.scal[S_R0REF] > 0.0 ? ctl.scal[S_R0REF] : sqrt(tot[0]);
+      ctl.flags[F_RHO0_SET] = 1;
+    }
+    return;
+  }
+  residual_decide(ctl, sqrt(tot[0]), sqrt(tot[1]));
 }
 
 // --------------------------------------------------------------------------------------
@@ -442,13 +533,23 @@ struct Kern {
       case PH_SPMV: {
         const int tiles = (N + kSpmvRows - 1) / kSpmvRows;
         const TV* xj = V + (size_t)j * a.ldv;
-        if (defl)
+        if (a.proj) {  // w = P A v_j = A v_j - A U T^-1 U^T A v_j
+          k_spmv_step<TA, TV, TACC, false><<<balanced(tiles, g.spmv_n), kSpmvRows, 0, st>>>(
+              N, a.op.rowptr, a.op.col, vals(a), xj, j, nullptr, sdefl(a), w, a.ctl);
+          k_aggsum<TACC><<<(d.npieces + 7) / 8, kThreads, 0, st>>>(w, d, a.ctl.cpart,
+                                                                  a.ctl.flags, F_CYCLE_DONE);
+          k_coarse<<<a.grid_small, kThreads, sizeof(double) * d.r, st>>>(
+              d, a.ctl.cpart, nullptr, a.ctl, F_CYCLE_DONE, 1);
+          k_proj_sub<TA, TACC><<<balanced(tiles, g.spmv_d), kSpmvRows, 0, st>>>(
+              N, a.op.rowptr, a.op.col, vals(a), d.agg, sdefl(a), w, a.ctl);
+          nl = 4;
+        } else if (defl)
           k_spmv_step<TA, TV, TACC, true><<<balanced(tiles, g.spmv_d), kSpmvRows, 0, st>>>(
               N, a.op.rowptr, a.op.col, vals(a), xj, j, d.agg, sdefl(a), w, a.ctl);
         else
           k_spmv_step<TA, TV, TACC, false><<<balanced(tiles, g.spmv_n), kSpmvRows, 0, st>>>(
               N, a.op.rowptr, a.op.col, vals(a), xj, j, nullptr, sdefl(a), w, a.ctl);
-        nl = 1;
+        if (!a.proj) nl = 1;
         break;
       }
       case PH_DOT1: {
@@ -477,7 +578,7 @@ struct Kern {
         k_aggsum<TV><<<(d.npieces + 7) / 8, kThreads, 0, st>>>(xj, d, a.ctl.cpart, a.ctl.flags,
                                                               F_CYCLE_DONE);
         k_coarse<<<a.grid_small, kThreads, sizeof(double) * d.r, st>>>(
-            d, a.ctl.cpart, a.ctl.sigma + j, a.ctl, F_CYCLE_DONE);
+            d, a.ctl.cpart, a.ctl.sigma + j, a.ctl, F_CYCLE_DONE, 0);
         nl = 2;
         break;
       }
@@ -490,7 +591,7 @@ struct Kern {
           k_aggsum<double><<<(d.npieces + 7) / 8, kThreads, 0, st>>>(a.t, d, a.ctl.cpart,
                                                                     a.ctl.flags, F_STOP);
           k_coarse<<<a.grid_small, kThreads, sizeof(double) * d.r, st>>>(d, a.ctl.cpart,
-                                                                        nullptr, a.ctl, F_STOP);
+                                                                        nullptr, a.ctl, F_STOP, 0);
           k_xapply<<<grid_for(tiles, 1, g.xapply), kThreads, 0, st>>>(N, x, a.t, d.agg, a.ctl);
           nl = 5;
         } else {
@@ -500,11 +601,38 @@ struct Kern {
         }
         break;
       }
-      case PH_RESIDUAL:
-        k_residual<TV><<<balanced((N + kSpmvRows - 1) / kSpmvRows, g.resid), kSpmvRows, 0,
-                         st>>>(N, a.op.rowptr, a.op.col, a.op.val, x, b, Vm, a.ctl);
-        nl = 1;
+      case PH_RESIDUAL: {
+        const int tiles = (N + kSpmvRows - 1) / kSpmvRows;
+        if (a.proj) {  // r = P (b - A xh), the true residual of x = xh + U T^-1 U^T (b - A xh)
+          k_residual<TV><<<balanced(tiles, g.resid), kSpmvRows, 0, st>>>(
+              N, a.op.rowptr, a.op.col, a.op.val, x, b, Vm, a.ctl, a.t, 0);
+          k_aggsum<double><<<(d.npieces + 7) / 8, kThreads, 0, st>>>(a.t, d, a.ctl.cpart,
+                                                                    a.ctl.flags, F_STOP);
+          k_coarse<<<a.grid_small, kThreads, sizeof(double) * d.r, st>>>(
+              d, a.ctl.cpart, nullptr, a.ctl, F_STOP, 1);
+          k_proj_resid<TV><<<balanced(tiles, g.resid), kSpmvRows, 0, st>>>(
+              N, a.op.rowptr, a.op.col, a.op.val, d.agg, a.t, Vm, a.ctl);
+          nl = 4;
+        } else {
+          k_residual<TV><<<balanced(tiles, g.resid), kSpmvRows, 0, st>>>(
+              N, a.op.rowptr, a.op.col, a.op.val, x, b, Vm, a.ctl, nullptr, 0);
+          nl = 1;
+        }
         break;
+      }
+      case PH_PROJ_FINAL: {  // x = xh + U T^-1 U^T (b - A xh)
+        const int tiles = (N + kSpmvRows - 1) / kSpmvRows;
+        k_residual<TV><<<balanced(tiles, g.resid), kSpmvRows, 0, st>>>(
+            N, a.op.rowptr, a.op.col, a.op.val, x, b, Vm, a.ctl, a.t, 1);
+        k_aggsum<double><<<(d.npieces + 7) / 8, kThreads, 0, st>>>(a.t, d, a.ctl.cpart,
+                                                                  a.ctl.flags, -1);
+        k_coarse<<<a.grid_small, kThreads, sizeof(double) * d.r, st>>>(d, a.ctl.cpart, nullptr,
+                                                                      a.ctl, -1, 1);
+        k_xcoarse<<<grid_for((N + kThreads - 1) / kThreads, 1, g.xapply), kThreads, 0, st>>>(
+            N, x, d.agg, a.ctl);
+        nl = 4;
+        break;
+      }
       case PH_RITZ:
         k_ritz<<<1, 32, 0, st>>>(a.ctl);
         nl = 1;

@@ -56,6 +56,7 @@ struct CycleArgs {
   double* t;             // FP64 scratch vector (x update)
   int prec;
   int m;                 // restart length of this solve (<= ctl.ldh)
+  int proj;              // deflation projector instead of the EBP preconditioner
   int sms;               // multiprocessors of the device
   int grid_small;        // blocks of the coarse GEMV
 };
@@ -71,6 +72,7 @@ enum Phase {
   PH_DEFL,          // U^T v_j and the coarse correction
   PH_CYCLE_END,     // back substitution and x update
   PH_RITZ,          // |mu| from the Ritz values
+  PH_PROJ_FINAL,    // projector: x = xh + U T^-1 U^T (b - A xh)
   PH_COUNT
 };
 cudaError_t launch_phase(const CycleArgs& a, int ph, int j, bool defl, double* x,

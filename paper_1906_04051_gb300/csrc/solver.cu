@@ -87,6 +87,7 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
   a.m = m;
   a.sms = h->sms;
   a.grid_small = h->r > 0 ? grid_for(h->r, 8, h->sms) : 1;
+  a.proj = (h->r > 0 && h->opts.deflation_mode == GMRES_DEFL_PROJECTOR) ? 1 : 0;
 
   const bool ebp = h->r > 0 && h->opts.deflation_mode == GMRES_DEFL_EBP;
   const int mu_mode = h->opts.mu_mode;
@@ -137,6 +138,8 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
       }
     }
   }
+  if (a.proj && status == GMRES_OK && h->hmeta->flags[F_STATUS] >= 0)
+    CK(h, phase(h, a, PH_PROJ_FINAL, 0, false, x, b));
   CK(h, prof_mark(h, -1));
   CK(h, cudaEventRecord(h->ev1, st));
   CK(h, cudaEventSynchronize(h->ev1));
@@ -269,6 +272,7 @@ gmres_status run_noalloc(gmres_s* h, OpHost& o, const double* b, const double* x
   a.m = m;
   a.sms = h->sms;
   a.grid_small = h->r > 0 ? grid_for(h->r, 8, h->sms) : 1;
+  a.proj = (h->r > 0 && h->opts.deflation_mode == GMRES_DEFL_PROJECTOR) ? 1 : 0;
 
   const bool ebp = h->r > 0 && h->opts.deflation_mode == GMRES_DEFL_EBP;
   const int mu_mode = h->opts.mu_mode;
@@ -320,6 +324,10 @@ gmres_status run_noalloc(gmres_s* h, OpHost& o, const double* b, const double* x
       }
     }
   }
+  if (a.proj && status == GMRES_OK && hm.flags[F_STATUS] >= 0) {
+    CK(h, launch_phase(a, PH_PROJ_FINAL, 0, false, x, b, st, nullptr));
+    CK(h, cudaStreamSynchronize(st));
+  }
   if (status == GMRES_OK) status = (gmres_status)hm.flags[F_STATUS];
   if (status == GMRES_ERR_NAN) h->err = "NaN or Inf in the residual or Hessenberg matrix";
   if (status == GMRES_ERR_SINGULAR_COARSE) h->err = "no usable Ritz estimate of mu";
@@ -364,8 +372,6 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
   if (opts.precision < 0 || opts.precision > 2 || opts.deflation_mode < 0 ||
       opts.deflation_mode > 2 || opts.mu_mode < 0 || opts.mu_mode > 2)
     return fail(nullptr, GMRES_ERR_INVALID_ARG, "invalid option value");
-  if (opts.deflation_mode == GMRES_DEFL_PROJECTOR && r > 0)
-    return fail(nullptr, GMRES_ERR_INVALID_ARG, "deflation_mode PROJECTOR is not available");
 
   gmres_s* h = new gmres_s();
   const auto t_setup = std::chrono::steady_clock::now();

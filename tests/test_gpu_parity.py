@@ -71,21 +71,22 @@ def test_q1_kappa_grad_matches_oracle(G, orc):
 def _solve_both(G, orc, p, *, m, tol, maxit, mode="ebp", mu_mode=0, mu_user=0.0,
                 fixed=False, x0=None):
     A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f, p.u)
-    dm = {"ebp": G.DEFL_EBP, "none": G.DEFL_NONE}[mode]
+    dm = {"ebp": G.DEFL_EBP, "none": G.DEFL_NONE, "proj": G.DEFL_PROJECTOR}[mode]
     s = gpu_solver_from_oracle(G, A, p.agg if mode != "none" else None,
                                p.r if mode != "none" else 0, mu_mode=mu_mode, mu_user=mu_user,
-                               fixed_iterations=fixed)
+                               fixed_iterations=fixed, deflation_mode=dm)
     xg, ig = s.solve(to_dev(b), None if x0 is None else to_dev(x0), m=m, tol=tol, maxit=maxit)
     d = orc.Deflation(A, p.agg, p.r) if mode != "none" else None
-    xo, io = orc.gmres(A, b, x0, m=m, tol=tol, maxit=maxit, defl=d, mu_mode=mu_mode,
-                       mu_user=mu_user, fixed_iterations=fixed)
+    odm = {"ebp": orc.DEFL_EBP, "none": orc.DEFL_NONE, "proj": orc.DEFL_PROJECTOR}[mode]
+    xo, io = orc.gmres(A, b, x0, m=m, tol=tol, maxit=maxit, defl=d, defl_mode=odm,
+                       mu_mode=mu_mode, mu_user=mu_user, fixed_iterations=fixed)
     return xg.cpu().numpy(), ig, xo, io, s
 
 
-@pytest.mark.parametrize("mode", ["ebp", "none"])
+@pytest.mark.parametrize("mode", ["ebp", "none", "proj"])
 @pytest.mark.parametrize("mu_mode", [0, 1, 2])
 def test_workload1_tight_tolerance(G, orc, mode, mu_mode):
-    if mode == "none" and mu_mode != 0:
+    if mode != "ebp" and mu_mode != 0:
         pytest.skip("mu only matters with deflation")
     p = W.workload1()
     xg, ig, xo, io, _ = _solve_both(G, orc, p, m=30, tol=1e-12, maxit=20000, mode=mode,
@@ -101,12 +102,13 @@ def test_workload1_tight_tolerance(G, orc, mode, mu_mode):
 
 @pytest.mark.parametrize("n", [3, 17, 40])
 @pytest.mark.parametrize("maxit", [1, 7, 45])
-def test_fixed_iterations_parity(G, orc, n, maxit):
+@pytest.mark.parametrize("mode", ["ebp", "proj"])
+def test_fixed_iterations_parity(G, orc, n, maxit, mode):
     # fixed-iteration protocol (Sec. 4): identical step counts, so the iterates agree to
     # rounding amplified by the Krylov process
     p = W.convdiff(n, pe=25.0, sigma=0.5, seed=100 + n, px=2, py=3)
     xg, ig, xo, io, _ = _solve_both(G, orc, p, m=10, tol=0.0, maxit=maxit, mu_mode=1,
-                                    mu_user=5.0, fixed=True)
+                                    mu_user=5.0, fixed=True, mode=mode)
     assert ig["iters"] == io["iters"] == min(maxit, ig["iters"])
     assert relerr(xg, xo) <= 1e-9
     assert ig["rel_res_true"] == pytest.approx(io["rel_res_true"], rel=1e-7, abs=1e-14)
@@ -172,10 +174,11 @@ def test_adjoint_matches_oracle(G, orc):
 
 
 @pytest.mark.parametrize("prec,name", [(1, "fp32"), (2, "bf16")])
-def test_mixed_precision_reaches_1e10(G, orc, prec, name):
+@pytest.mark.parametrize("dmode", [0, 1])
+def test_mixed_precision_reaches_1e10(G, orc, prec, name, dmode):
     p = W.convdiff(96, pe=50.0, sigma=0.5, seed=33, px=4, py=4)
     A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f)
-    s = gpu_solver_from_oracle(G, A, p.agg, p.r, precision=prec)
+    s = gpu_solver_from_oracle(G, A, p.agg, p.r, precision=prec, deflation_mode=dmode)
     x, info = s.solve(to_dev(b), m=40, tol=1e-10, maxit=20000)
     assert info["status"] == 0, info
     xn = x.cpu().numpy()
