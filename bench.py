@@ -169,6 +169,8 @@ def main():
     ap.add_argument("--ref-sample-steps", type=int, default=M)
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the time-to-1e-10 comparison on q1-n2048")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched (one graph launch) vs sequential comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -326,6 +328,44 @@ def main():
                 torch.linalg.vector_norm(xs["fp64"]))
         del xs
 
+    # ---- q1-batch256: one graph launch for 256 systems vs 256 sequential FP64 solves -----
+    batched = None
+    if rank == 0 and not args.no_batched:
+        torch.cuda.empty_cache()
+        probs = W.workload4()
+        sysd = []
+        for q in probs:
+            rq, cq, vq, bq = G.q1_assemble(q.n, t(q.kappa), q.beta, t(q.f), t(q.u))
+            sysd.append((rq, cq, vq, bq, t(q.agg, torch.int32), q.r))
+        bl = [d[3] for d in sysd]
+        maxit4, tol4 = 4000, 1e-10
+        batched = {"workload": "q1-batch256: 256 Picard systems, 4.34M DOF, GMRES(30), "
+                               "8 EBP deflation vectors each, tol 1e-10, maxit 4000"}
+        for name, prec in (("fp64_batched", G.FP64), ("fp32_inner_batched", G.FP32_INNER)):
+            sv = [G.Solver(d[0], d[1], d[2], d[4], d[5], precision=prec) for d in sysd]
+            G.batch_solve(sv, bl, m=30, tol=tol4, maxit=maxit4)  # first call: autotune + graph
+            ev0.record(stream)
+            _, inf4, _ = G.batch_solve(sv, bl, m=30, tol=tol4, maxit=maxit4)
+            ev1.record(stream)
+            ev1.synchronize()
+            batched[name] = {"ms": ev0.elapsed_time(ev1),
+                             "converged": sum(i["status"] == 0 for i in inf4),
+                             "steps": sum(i["iters"] for i in inf4), "graph_launches": 1}
+            if prec == G.FP64:
+                ev0.record(stream)
+                seq = [s4.solve(b4, m=30, tol=tol4, maxit=maxit4)[1] for s4, b4 in zip(sv, bl)]
+                ev1.record(stream)
+                ev1.synchronize()
+                batched["fp64_sequential"] = {
+                    "ms": ev0.elapsed_time(ev1), "converged": sum(i["status"] == 0 for i in seq),
+                    "steps": sum(i["iters"] for i in seq)}
+            for s4 in sv:
+                s4.close()
+        base = batched["fp64_sequential"]["ms"]
+        for name in ("fp64_batched", "fp32_inner_batched"):
+            batched[name]["speedup_vs_fp64_sequential"] = base / batched[name]["ms"]
+        del sysd, bl
+
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -348,6 +388,7 @@ def main():
             "clocks": clocks,
             "e2e": e2e,
             "mixed_precision": mixed,
+            "batched": batched,
             "cpu_baseline": cb,
         }
         print(json.dumps(out), flush=True)

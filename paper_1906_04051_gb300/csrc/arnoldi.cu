@@ -111,14 +111,12 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     if ((int)threadIdx.x < ng) {
       const int r = threadIdx.x * VN;
+      TACC wn[VN];
+      tile_combine<VN, TACC>(sw, spart, TR, P, r, wn);
+      st_acc<VN>(sw2 + r, wn);
 #pragma unroll
-      for (int e = 0; e < VN; ++e) {
-        TACC acc_p = spart[r + e];
-        for (int q = 1; q < P; ++q) acc_p += spart[q * TR + r + e];
-        const TACC wn = sw[r + e] - acc_p;
-        sw2[r + e] = wn;
-        if (r0 + r + e < N) w[r0 + r + e] = wn;
-      }
+      for (int e = 0; e < VN; ++e)
+        if (r0 + r + e < N) w[r0 + r + e] = wn[e];
     }
     __syncthreads();
 #define GG_P2(NW) tile_dot<NW, TV, TACC>(acc, sV, sw2, TR, warp, lane)
@@ -164,12 +162,12 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     if ((int)threadIdx.x < ng) {
       const int r = threadIdx.x * VN;
+      TACC wnv[VN];
+      tile_combine<VN, TACC>(sw, spart, TR, P, r, wnv);
 #pragma unroll
       for (int e = 0; e < VN; ++e) {
         if (r0 + r + e < N) {
-          TACC acc_p = spart[r + e];
-          for (int q = 1; q < P; ++q) acc_p += spart[q * TR + r + e];
-          const TACC wn = sw[r + e] - acc_p;
+          const TACC wn = wnv[e];
           TV stv;
           if constexpr (sizeof(TV) == sizeof(TACC)) {
             stv = (TV)wn;

@@ -360,14 +360,12 @@ __global__ void __launch_bounds__(kThreads) kb_pass2(BTab tab, int k) {
     if ((int)threadIdx.x < ng) {
       const int r = threadIdx.x * VN;
       TACC* w = static_cast<TACC*>(S.w);
+      TACC wn[VN];
+      tile_combine<VN, TACC>(sw, spart, TR, P, r, wn);
+      st_acc<VN>(sw2 + r, wn);
 #pragma unroll
-      for (int e = 0; e < VN; ++e) {
-        TACC accp = spart[r + e];
-        for (int q = 1; q < P; ++q) accp += spart[q * TR + r + e];
-        const TACC wn = sw[r + e] - accp;
-        sw2[r + e] = wn;
-        if (r0 + r + e < S.n) w[r0 + r + e] = wn;
-      }
+      for (int e = 0; e < VN; ++e)
+        if (r0 + r + e < S.n) w[r0 + r + e] = wn[e];
     }
     __syncthreads();
 #define GG_B2(NW) tile_dot<NW, TV, TACC>(acc, sV, sw2, TR, warp, lane)
@@ -415,12 +413,12 @@ __global__ void __launch_bounds__(kThreads) kb_pass3(BTab tab, int k) {
     if ((int)threadIdx.x < ng) {
       const int r = threadIdx.x * VN;
       TV* vout = static_cast<TV*>(S.V) + (size_t)k * S.ldv;
+      TACC wnv[VN];
+      tile_combine<VN, TACC>(sw, spart, TR, P, r, wnv);
 #pragma unroll
       for (int e = 0; e < VN; ++e) {
         if (r0 + r + e < S.n) {
-          TACC accp = spart[r + e];
-          for (int q = 1; q < P; ++q) accp += spart[q * TR + r + e];
-          const TACC wn = sw[r + e] - accp;
+          const TACC wn = wnv[e];
           TV stv;
           if constexpr (sizeof(TV) == sizeof(TACC)) {
             stv = (TV)wn;

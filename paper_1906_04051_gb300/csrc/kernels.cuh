@@ -48,7 +48,27 @@ __device__ __forceinline__ void spmv_tile(int N, int r0, const int* __restrict__
     }
     __syncthreads();
     const int a = max(rs, cs), b = min(re, ce);
-    for (int k = a; k < b; ++k) {
+    int k = a;
+    for (; k + 3 < b; k += 4) {  // four independent gathers in flight
+      const int c0 = scol[k - cs], c1 = scol[k + 1 - cs], c2 = scol[k + 2 - cs],
+                c3 = scol[k + 3 - cs];
+      const TACC x0 = xg(c0), x1 = xg(c1), x2 = xg(c2), x3 = xg(c3);
+      const TACC v0 = (TACC)sval[k - cs], v1 = (TACC)sval[k + 1 - cs],
+                 v2 = (TACC)sval[k + 2 - cs], v3 = (TACC)sval[k + 3 - cs];
+      acc += v0 * x0;
+      acc += v1 * x1;
+      acc += v2 * x2;
+      acc += v3 * x3;
+      if (DEFL) {
+        const int p0 = __ldg(agg + c0), p1 = __ldg(agg + c1), p2 = __ldg(agg + c2),
+                  p3 = __ldg(agg + c3);
+        if (p0 >= 0) accd += v0 * sdefl[p0];
+        if (p1 >= 0) accd += v1 * sdefl[p1];
+        if (p2 >= 0) accd += v2 * sdefl[p2];
+        if (p3 >= 0) accd += v3 * sdefl[p3];
+      }
+    }
+    for (; k < b; ++k) {
       const int c = scol[k - cs];
       const TACC v = (TACC)sval[k - cs];
       acc += v * xg(c);
@@ -328,6 +348,38 @@ __device__ __forceinline__ void ld_acc(const float* p, float (&o)[VN]) {
   }
 }
 
+// VN accumulator-type values to shared memory (16-byte aligned)
+template <int VN>
+__device__ __forceinline__ void st_acc(double* p, const double (&v)[VN]) {
+#pragma unroll
+  for (int e = 0; e < VN; e += 2) *reinterpret_cast<double2*>(p + e) = make_double2(v[e], v[e + 1]);
+}
+template <int VN>
+__device__ __forceinline__ void st_acc(float* p, const float (&v)[VN]) {
+#pragma unroll
+  for (int e = 0; e < VN; e += 4)
+    *reinterpret_cast<float4*>(p + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+}
+
+// Combine of a tile's update: for the VN rows at r, wn = sw - sum_q spart[q] (vector
+// shared-memory accesses: no bank conflicts).
+template <int VN, typename TACC>
+__device__ __forceinline__ void tile_combine(const TACC* sw, const TACC* spart, int TR, int P,
+                                             int r, TACC (&wn)[VN]) {
+  TACC acc[VN];
+  ld_acc<VN>(spart + r, acc);
+  for (int q = 1; q < P; ++q) {
+    TACC t[VN];
+    ld_acc<VN>(spart + q * TR + r, t);
+#pragma unroll
+    for (int e = 0; e < VN; ++e) acc[e] += t[e];
+  }
+  TACC wv[VN];
+  ld_acc<VN>(sw + r, wv);
+#pragma unroll
+  for (int e = 0; e < VN; ++e) wn[e] = wv[e] - acc[e];
+}
+
 // Dot phase of a tile: warp `slice` owns columns slice, slice+8, ... (NW of them) and its
 // lanes sweep all TR rows, VN rows per 16-byte load.
 template <int NW, typename TV, typename TACC>
@@ -368,8 +420,7 @@ __device__ __forceinline__ void tile_update(const TV* sV, int TR, int k, const T
 #pragma unroll
     for (int e = 0; e < VN; ++e) p[e] += v[e] * cf;
   }
-#pragma unroll
-  for (int e = 0; e < VN; ++e) spart[sub * TR + r + e] = p[e];
+  st_acc<VN>(spart + sub * TR + r, p);
 }
 
 template <typename TACC> __host__ __device__ constexpr int update_splits(int TR, int VN) {

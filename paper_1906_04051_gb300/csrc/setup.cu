@@ -181,10 +181,11 @@ __global__ void k_gj_init(int r, const double* __restrict__ T, double* __restric
   }
 }
 
-// Step k, part 1 (one block): pivot search in column k (largest |G_ik|, i >= k, first on
-// ties), row swap, scaling of the pivot row, and the elimination factors.
-__global__ void k_gj_pivot(int r, int k, double* __restrict__ G, double* __restrict__ fac,
-                           int* __restrict__ err) {
+// Pivot step for column k, run by one block: the largest |G_ik| over i >= k (first on
+// ties; candidates come from pmax/pidx partials when given, else from a scan), row swap
+// k <-> p, scaling of row k, and the elimination factors fac_i = G_ik (fac_k = 0).
+__device__ void gj_pivot_block(int r, int k, double* __restrict__ G, double* __restrict__ fac,
+                               int* __restrict__ err) {
   __shared__ double sv[32];
   __shared__ int si[32];
   __shared__ int s_piv;
@@ -193,7 +194,7 @@ __global__ void k_gj_pivot(int r, int k, double* __restrict__ G, double* __restr
   double best = -1.0;
   int bi = r;
   for (int i = k + threadIdx.x; i < r; i += blockDim.x) {
-    const double v = fabs(G[(size_t)i * ld + k]);
+    const double v = fabs(__ldcg(&G[(size_t)i * ld + k]));
     if (v > best) { best = v; bi = i; }
   }
 #pragma unroll
@@ -216,35 +217,51 @@ __global__ void k_gj_pivot(int r, int k, double* __restrict__ G, double* __restr
   const int p = s_piv;
   if (p != k)
     for (int j = threadIdx.x; j < ld; j += blockDim.x) {
-      const double t = G[(size_t)k * ld + j];
-      G[(size_t)k * ld + j] = G[(size_t)p * ld + j];
+      const double t = __ldcg(&G[(size_t)k * ld + j]);
+      G[(size_t)k * ld + j] = __ldcg(&G[(size_t)p * ld + j]);
       G[(size_t)p * ld + j] = t;
     }
   __syncthreads();
-  const double piv = G[(size_t)k * ld + k];
+  const double piv = __ldcg(&G[(size_t)k * ld + k]);
   const double inv = (piv != 0.0) ? 1.0 / piv : 0.0;
   __syncthreads();
-  for (int j = threadIdx.x; j < ld; j += blockDim.x) {
-    if (j == k) continue;
-    G[(size_t)k * ld + j] *= inv;
-  }
+  for (int j = threadIdx.x; j < ld; j += blockDim.x)
+    if (j != k) G[(size_t)k * ld + j] = __ldcg(&G[(size_t)k * ld + j]) * inv;
   __syncthreads();
   if (threadIdx.x == 0) G[(size_t)k * ld + k] = 1.0;
-  for (int i = threadIdx.x; i < r; i += blockDim.x) fac[i] = (i == k) ? 0.0 : G[(size_t)i * ld + k];
+  for (int i = threadIdx.x; i < r; i += blockDim.x)
+    fac[i] = (i == k) ? 0.0 : __ldcg(&G[(size_t)i * ld + k]);
 }
 
-// Step k, part 2: G_ij -= fac_i G_kj for i != k over columns [k, 2r).  (Row swaps move
-// the identity columns of the right half, so all of it stays active.)
-__global__ void k_gj_elim(int r, int k, double* __restrict__ G, const double* __restrict__ fac) {
+__global__ void k_gj_pivot0(int r, double* __restrict__ G, double* __restrict__ fac,
+                            int* __restrict__ err) {
+  gj_pivot_block(r, 0, G, fac, err);
+}
+
+// Step k: G_ij -= fac_i G_kj for i != k over columns [k, 2r) (row swaps move the identity
+// columns of the right half, so all of it stays active); each block owns whole rows.  The
+// last block to finish (ticket) performs the pivot step of column k + 1.
+__global__ void __launch_bounds__(1024)
+    k_gj_step(int r, int k, double* __restrict__ G, double* __restrict__ fac,
+              unsigned* __restrict__ ticket, int* __restrict__ err) {
+  __shared__ unsigned s_last;
   const int ld = 2 * r;
-  const int width = 2 * r - k;
-  const long long tot = (long long)r * width;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t / width), j = k + (int)(t % width);
+  for (int i = blockIdx.x; i < r; i += gridDim.x) {
     const double f = fac[i];
-    if (f != 0.0) G[(size_t)i * ld + j] -= f * G[(size_t)k * ld + j];
+    if (f == 0.0) continue;
+    const double* prow = G + (size_t)k * ld;
+    double* row = G + (size_t)i * ld;
+    for (int j = k + threadIdx.x; j < ld; j += blockDim.x) row[j] -= f * __ldcg(prow + j);
   }
+  if (k + 1 >= r) return;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  gj_pivot_block(r, k + 1, G, fac, err);
+  if (threadIdx.x == 0) *ticket = 0u;
 }
 
 __global__ void k_gj_extract(int r, const double* __restrict__ G, double* __restrict__ Tinv,
@@ -317,11 +334,36 @@ cudaError_t launch_coarse_T(int r, const int* rowptr, const int* col, const doub
 
 cudaError_t launch_gauss_jordan(int r, const double* T, double* G /* r*2r */, double* fac,
                                 double* Tinv, double* TinvT, int* err, cudaStream_t st) {
+  // one launch per column, captured into a CUDA graph (launch gaps of a plain loop of r
+  // kernels would dominate for r ~ 1000)
+  unsigned* ticket = reinterpret_cast<unsigned*>(fac + r);  // fac has r + 1 doubles
+  cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
   k_gj_init<<<grid_for(2LL * r * r, 256, 152 * 8), 256, 0, st>>>(r, T, G);
-  for (int k = 0; k < r; ++k) {
-    k_gj_pivot<<<1, 1024, 0, st>>>(r, k, G, fac, err);
-    k_gj_elim<<<grid_for((long long)r * (2 * r - k), 256, 152 * 8), 256, 0, st>>>(r, k, G, fac);
+  k_gj_pivot0<<<1, 1024, 0, st>>>(r, G, fac, err);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = r < 2 * sms ? r : 2 * sms;
+  cudaStream_t cap;
+  if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    for (int k = 0; k < r; ++k) k_gj_step<<<grid, 256, 0, cap>>>(r, k, G, fac, ticket, err);
+    const cudaError_t le = cudaGetLastError();
+    e = cudaStreamEndCapture(cap, &g);
+    if (e == cudaSuccess) e = le;
   }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ex, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (ex) cudaGraphExecDestroy(ex);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess) return e;
   k_gj_extract<<<grid_for((long long)r * r, 256, 152 * 8), 256, 0, st>>>(r, G, Tinv, TinvT);
   return cudaGetLastError();
 }

@@ -438,7 +438,7 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
                         h->piece_start.as<int>(), h->uscale.as<double>(), err.as<int>(), st));
     CKC(T.ensure(sizeof(double) * (size_t)r * r));
     CKC(G.ensure(sizeof(double) * 2 * (size_t)r * r));
-    CKC(fac.ensure(sizeof(double) * (size_t)r));
+    CKC(fac.ensure(sizeof(double) * (size_t)(r + 1)));
     CKC(h->fwd.tinv.ensure(sizeof(double) * (size_t)r * r));
     CKC(h->adj.tinv.ensure(sizeof(double) * (size_t)r * r));
     CKC(launch_coarse_T(r, h->fwd.rowptr.as<int>(), h->fwd.col.as<int>(),
@@ -472,7 +472,7 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
   // kernels enqueued by the setup: validation, FP32 copy, aggregate permutation (4),
   // coarse matrix, Gauss-Jordan (init, 2 per pivot, extract), infinity norm
   h->plaunch[PH_SETUP] = 1 + (opts.precision != GMRES_FP64 ? 1 : 0) +
-                         (r > 0 ? 4 + 1 + 2 + 2LL * r : 0) +
+                         (r > 0 ? 4 + 1 + 3 + (long long)r : 0) +
                          (opts.mu_mode == GMRES_MU_NORM_INF ? 1 : 0);
 #undef CKC
   *out = h;
