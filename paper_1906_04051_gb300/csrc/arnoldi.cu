@@ -25,24 +25,86 @@ namespace gg {
 
 namespace {
 
+// w = sigma_j A u_j, or with deflation w = sigma_j [A | A W] [u_j; s'] = A (v_j + U s) with
+// s' = s / sigma_j the coarse correction of u_j (the extended rows carry the A W entries
+// with column index N + a).  A thread per row reads its entries straight from global
+// memory, four at a time (L1 absorbs the strided access), which keeps many independent
+// loads in flight without staging or block barriers.
 template <typename TA, typename TV, typename TACC, bool DEFL>
-__global__ void __launch_bounds__(kSpmvRows)
+__global__ void __launch_bounds__(kThreads)
     k_spmv_step(int N, const int* __restrict__ rowptr, const int* __restrict__ col,
                 const TA* __restrict__ val, const TV* __restrict__ x, int j,
-                const int* __restrict__ agg, const TACC* __restrict__ sdefl,
-                TACC* __restrict__ w, Ctl ctl) {
+                const TACC* __restrict__ sdefl, TACC* __restrict__ w, Ctl ctl) {
   if (ctl.flags[F_CYCLE_DONE]) return;
-  __shared__ TA sval[kSpmvCap];
-  __shared__ int scol[kSpmvCap];
   const TACC sigma = (TACC)ctl.sigma[j];
-  const int tiles = (N + kSpmvRows - 1) / kSpmvRows;
-  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
-    TACC acc, accd;
-    spmv_tile<TA, TACC, DEFL>(
-        N, t * kSpmvRows, rowptr, col, val, sval, scol,
-        [&](int c) { return ld_as<TACC, TV>(x + c); }, agg, sdefl, acc, accd);
-    const int row = t * kSpmvRows + threadIdx.x;
-    if (row < N) w[row] = sigma * acc + accd;
+  auto g = [&](int c) -> TACC {
+    if constexpr (DEFL) return c < N ? ld_as<TACC, TV>(x + c) : sdefl[c - N];
+    else return ld_as<TACC, TV>(x + c);
+  };
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const int rs = __ldg(rowptr + i), re = __ldg(rowptr + i + 1);
+    TACC acc0 = 0, acc1 = 0;
+    int k = rs;
+    for (; k + 3 < re; k += 4) {
+      int c[4];
+      TACC v[4], xv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        c[u] = __ldg(col + k + u);
+        v[u] = (TACC)__ldg(val + k + u);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) xv[u] = g(c[u]);
+      acc0 += v[0] * xv[0];
+      acc1 += v[1] * xv[1];
+      acc0 += v[2] * xv[2];
+      acc1 += v[3] * xv[3];
+    }
+    for (; k < re; ++k) acc0 += (TACC)__ldg(val + k) * g(__ldg(col + k));
+    w[i] = sigma * (acc0 + acc1);
+  }
+}
+
+// The same product with A in diagonal storage: row i sums dval[q][i] x[i + off_q] over the
+// nd diagonals (coalesced loads of the values and of the shifted x; an index past either
+// end is clamped to a valid row, where the stored value is 0), plus the A W row.
+template <typename TA, typename TV, typename TACC, bool DEFL>
+__global__ void __launch_bounds__(kThreads)
+    k_spmv_dia(int N, DiaOffsets dia, long long ldd, const TA* __restrict__ dval,
+               const TV* __restrict__ x, int j, Defl d, const TA* __restrict__ auval,
+               const TACC* __restrict__ sdefl, TACC* __restrict__ w, Ctl ctl) {
+  if (ctl.flags[F_CYCLE_DONE]) return;
+  __shared__ int soff[kMaxDiag];
+#pragma unroll
+  for (int q = 0; q < kMaxDiag; ++q)
+    if ((int)threadIdx.x == q) soff[q] = dia.off[q];
+  __syncthreads();
+  const TACC sigma = (TACC)ctl.sigma[j];
+  const int nd = dia.nd;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    TACC acc0 = 0, acc1 = 0;
+    int q = 0;
+    for (; q + 3 < nd; q += 4) {
+      int c[4];
+      TACC a[4], xv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) c[u] = min(max(i + soff[q + u], 0), N - 1);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = (TACC)__ldg(dval + (q + u) * ldd + i);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) xv[u] = ld_as<TACC, TV>(x + c[u]);
+      acc0 += a[0] * xv[0];
+      acc1 += a[1] * xv[1];
+      acc0 += a[2] * xv[2];
+      acc1 += a[3] * xv[3];
+    }
+    for (; q < nd; ++q) {
+      const int c = min(max(i + soff[q], 0), N - 1);
+      acc0 += (TACC)__ldg(dval + q * ldd + i) * ld_as<TACC, TV>(x + c);
+    }
+    TACC acc = acc0 + acc1;
+    if constexpr (DEFL) acc += au_row<TA, TACC>(i, d.aurp, d.aucol, auval, sdefl);
+    w[i] = sigma * acc;
   }
 }
 
@@ -190,8 +252,10 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // --------------------------------------------------------------------------------------
-// Deflation: U^T x by pieces (warp per piece), then s = U (|mu| T^-1 - I) c.
+// Deflation: c = scale U^T x by pieces (warp per piece), then s = U (|mu| T^-1 - I) c.
 // --------------------------------------------------------------------------------------
+// Piece sums: a warp per piece, up to 32 gathers in flight per lane (pieces hold at most
+// kPiece = 1024 nodes, so one batch), two accumulators per lane.
 template <typename TX>
 __global__ void __launch_bounds__(kThreads)
     k_aggsum(const TX* __restrict__ x, Defl d, double* __restrict__ cpart, const int* flags,
@@ -201,26 +265,52 @@ __global__ void __launch_bounds__(kThreads)
   const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (p >= d.npieces) return;
   const int s = d.piece_start[p], e = d.piece_start[p + 1];
-  double acc = 0.0;
-  for (int t = s + lane; t < e; t += 32) acc += ld_as<double, TX>(x + d.perm[t]);
-  acc = warp_sum(acc);
-  if (lane == 0) cpart[p] = acc;
+  double acc0 = 0.0, acc1 = 0.0;
+  for (int t0 = s; t0 < e; t0 += 32 * 32) {
+    int q[32];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
+      const int t = t0 + lane + 32 * u;
+      q[u] = t < e ? __ldg(d.perm + t) : -1;
+    }
+    double v[32];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) v[u] = q[u] >= 0 ? ld_as<double, TX>(x + q[u]) : 0.0;
+#pragma unroll
+    for (int u = 0; u < 32; u += 2) {
+      acc0 += v[u];
+      acc1 += v[u + 1];
+    }
+  }
+  const double sum = warp_sum(acc0 + acc1);
+  if (lane == 0) cpart[p] = sum;
 }
 
-// c_a = scale uscale_a sum(pieces of a);  s_a = uscale_a (|mu| (T^-1 c)_a - c_a).
-// proj != 0: s_a = uscale_a (T^-1 c)_a, the coarse solve of the deflation projector.
+// c_a = scale uscale_a sum(pieces of a) into shared memory (piece sums staged through
+// shared memory when they fit), then y = T^-1 c by a warp per row (32 loads in flight
+// per lane, two accumulators) and s_a = uscale_a (|mu| y_a - c_a), or s_a = uscale_a y_a
+// for the deflation projector.
+constexpr int kCoarseStage = 4096;  // piece sums staged in shared memory (32 KB)
+
 __global__ void __launch_bounds__(kThreads)
     k_coarse(Defl d, const double* __restrict__ cpart, const double* __restrict__ scale_ptr,
              Ctl ctl, int skip_slot, int proj) {
   if (skip_slot >= 0 && ctl.flags[skip_slot]) return;
-  extern __shared__ double sc[];
+  extern __shared__ double sc[];                 // r entries
+  __shared__ double spc[kCoarseStage];
   const double scale = scale_ptr ? *scale_ptr : 1.0;
   const double mu = ctl.scal[S_MU];
   const int r = d.r;
+  const bool staged = d.npieces <= kCoarseStage;
+  if (staged)
+    for (int p = threadIdx.x; p < d.npieces; p += blockDim.x) spc[p] = __ldg(cpart + p);
+  __syncthreads();
+  const double* pc = staged ? spc : cpart;
   for (int a = threadIdx.x; a < r; a += blockDim.x) {
-    double s = 0.0;
-    for (int p = d.agg_piece[a]; p < d.agg_piece[a + 1]; ++p) s += cpart[p];
-    sc[a] = scale * d.uscale[a] * s;
+    const int lo = __ldg(d.agg_piece + a), hi = __ldg(d.agg_piece + a + 1);
+    double sum = 0.0;
+    for (int q = lo; q < hi; ++q) sum += pc[q];
+    sc[a] = scale * __ldg(d.uscale + a) * sum;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -228,11 +318,25 @@ __global__ void __launch_bounds__(kThreads)
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int a = gw; a < r; a += nw) {
     const double* row = d.tinv + (size_t)a * r;
-    double acc = 0.0;
-    for (int b = lane; b < r; b += 32) acc += __ldg(row + b) * sc[b];
-    acc = warp_sum(acc);
+    double acc0 = 0.0, acc1 = 0.0;
+    for (int b0 = 0; b0 < r; b0 += 32 * 32) {
+      double t[32];
+#pragma unroll
+      for (int u = 0; u < 32; ++u) {
+        const int b = b0 + lane + 32 * u;
+        t[u] = b < r ? __ldg(row + b) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 32; u += 2) {
+        const int b = b0 + lane + 32 * u;
+        if (b < r) acc0 += t[u] * sc[b];
+        if (b + 32 < r) acc1 += t[u + 1] * sc[b + 32];
+      }
+    }
+    const double y = warp_sum(acc0 + acc1);
     if (lane == 0) {
-      const double sd = proj ? d.uscale[a] * acc : d.uscale[a] * (mu * acc - sc[a]);
+      const double us = __ldg(d.uscale + a);
+      const double sd = proj ? us * y : us * (mu * y - sc[a]);
       ctl.sdefl[a] = sd;
       ctl.sdefl32[a] = (float)sd;
     }
@@ -245,54 +349,34 @@ __global__ void __launch_bounds__(kThreads)
 // --------------------------------------------------------------------------------------
 // vec -= A U y for every row (a step's w = P A v, skip when the cycle has ended)
 template <typename TA, typename TACC>
-__global__ void __launch_bounds__(kSpmvRows)
-    k_proj_sub(int N, const int* __restrict__ rowptr, const int* __restrict__ col,
-               const TA* __restrict__ val, const int* __restrict__ agg,
-               const TACC* __restrict__ sdefl, TACC* __restrict__ vec, Ctl ctl) {
+__global__ void __launch_bounds__(kThreads)
+    k_proj_sub(int N, Defl d, const TA* __restrict__ auval, const TACC* __restrict__ sdefl,
+               TACC* __restrict__ vec, Ctl ctl) {
   if (ctl.flags[F_CYCLE_DONE]) return;
-  __shared__ TA sval[kSpmvCap];
-  __shared__ int scol[kSpmvCap];
-  const int tiles = (N + kSpmvRows - 1) / kSpmvRows;
-  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
-    TACC acc, accd;
-    spmv_tile<TA, TACC, true>(N, t * kSpmvRows, rowptr, col, val, sval, scol,
-                              [&](int) { return (TACC)0; }, agg, sdefl, acc, accd);
-    const int row = t * kSpmvRows + threadIdx.x;
-    if (row < N) vec[row] -= accd;
-  }
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < N; row += gridDim.x * blockDim.x)
+    vec[row] -= au_row<TA, TACC>(row, d.aurp, d.aucol, auval, sdefl);
 }
 
 // r = t - A U y (t = b - A xh in FP64), stored as the cycle's start vector, with the
 // restart decision on ||P (b - A xh)|| = ||b - A x|| (Eq. 15)
 template <typename TV>
 __global__ void __launch_bounds__(kSpmvRows)
-    k_proj_resid(int N, const int* __restrict__ rowptr, const int* __restrict__ col,
-                 const double* __restrict__ val, const int* __restrict__ agg,
-                 const double* __restrict__ t, TV* __restrict__ V0, Ctl ctl) {
+    k_proj_resid(int N, Defl d, const double* __restrict__ t, TV* __restrict__ V0, Ctl ctl) {
   if (ctl.flags[F_STOP]) return;
-  __shared__ double sval[kSpmvCap];
-  __shared__ int scol[kSpmvCap];
   __shared__ double sbuf[kSpmvRows / 32];
   __shared__ double sred[2];
   __shared__ double tot[2];
   double n1 = 0.0, n2 = 0.0;
-  const int tiles = (N + kSpmvRows - 1) / kSpmvRows;
-  for (int tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
-    double acc, accd;
-    spmv_tile<double, double, true>(N, tt * kSpmvRows, rowptr, col, val, sval, scol,
-                                    [&](int) { return 0.0; }, agg, ctl.sdefl, acc, accd);
-    const int row = tt * kSpmvRows + threadIdx.x;
-    if (row < N) {
-      const double r = t[row] - accd;
-      n1 += r * r;
-      if constexpr (sizeof(TV) == sizeof(double)) {
-        V0[row] = r;
-      } else {
-        const TV st = st_round<TV>((float)r);
-        V0[row] = st;
-        const double sv = (double)to_f<TV>(st);
-        n2 += sv * sv;
-      }
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < N; row += gridDim.x * blockDim.x) {
+    const double r = t[row] - au_row<double, double>(row, d.aurp, d.aucol, d.auval, ctl.sdefl);
+    n1 += r * r;
+    if constexpr (sizeof(TV) == sizeof(double)) {
+      V0[row] = r;
+    } else {
+      const TV st = st_round<TV>((float)r);
+      V0[row] = st;
+      const double sv = (double)to_f<TV>(st);
+      n2 += sv * sv;
     }
   }
   double b1 = block_sum(n1, sbuf);
@@ -491,8 +575,7 @@ struct Kern {
     static Grids g;
     static int for_sms = -1;
     if (for_sms != sms) {
-      g.spmv_d = resident_grid(k_spmv_step<TA, TV, TACC, true>, kSpmvRows, 0, sms);
-      g.spmv_n = resident_grid(k_spmv_step<TA, TV, TACC, false>, kSpmvRows, 0, sms);
+      g.spmv_d = resident_grid(k_proj_sub<TA, TACC>, kThreads, 0, sms);
       g.resid = resident_grid(k_residual<TV>, kSpmvRows, 0, sms);
       g.xupd_d = resident_grid(k_xupdate<TV, true>, kThreads, 0, sms);
       g.xupd_n = resident_grid(k_xupdate<TV, false>, kThreads, 0, sms);
@@ -511,9 +594,35 @@ struct Kern {
     if constexpr (sizeof(TA) == sizeof(double)) return a.op.val;
     else return a.op.val32;
   }
+  static const TA* dvals(const CycleArgs& a) {
+    if constexpr (sizeof(TA) == sizeof(double)) return a.op.dval;
+    else return a.op.dval32;
+  }
+  static const TA* xvals(const CycleArgs& a) {
+    if constexpr (sizeof(TA) == sizeof(double)) return a.op.xval;
+    else return a.op.xval32;
+  }
+  static const TA* auvals(const CycleArgs& a) {
+    if constexpr (sizeof(TA) == sizeof(double)) return a.op.defl.auval;
+    else return a.op.defl.auval32;
+  }
   static const TACC* sdefl(const CycleArgs& a) {
     if constexpr (sizeof(TACC) == sizeof(double)) return a.ctl.sdefl;
     else return a.ctl.sdefl32;
+  }
+
+  // c = scale U^T x, then s = U (|mu| T^-1 - I) c (proj: s = U T^-1 c); c sits after the
+  // piece sums in the cpart buffer
+  template <typename TX>
+  static void coarse(const CycleArgs& a, const TX* x, const double* scale, int skip, int proj,
+                     cudaStream_t st) {
+    const Defl& d = a.op.defl;
+    const int gp = d.npieces > 0 ? (d.npieces + 7) / 8 : 1;
+    k_aggsum<TX><<<gp, kThreads, 0, st>>>(x, d, a.ctl.cpart, a.ctl.flags, skip);
+    const int rows = (d.r + 7) / 8;
+    const int gc = rows < 2 * a.sms ? rows : 2 * a.sms;
+    k_coarse<<<gc > 0 ? gc : 1, kThreads, sizeof(double) * d.r, st>>>(d, a.ctl.cpart, scale,
+                                                                       a.ctl, skip, proj);
   }
 
   static cudaError_t phase(const CycleArgs& a, int ph, int j, bool defl, double* x,
@@ -531,22 +640,34 @@ struct Kern {
       case PH_SPMV: {
         const int tiles = (N + kSpmvRows - 1) / kSpmvRows;
         const TV* xj = V + (size_t)j * a.ldv;
-        if (a.proj) {  // w = P A v_j = A v_j - A U T^-1 U^T A v_j
-          k_spmv_step<TA, TV, TACC, false><<<balanced(tiles, g.spmv_n), kSpmvRows, 0, st>>>(
-              N, a.op.rowptr, a.op.col, vals(a), xj, j, nullptr, sdefl(a), w, a.ctl);
-          k_aggsum<TACC><<<(d.npieces + 7) / 8, kThreads, 0, st>>>(w, d, a.ctl.cpart,
-                                                                  a.ctl.flags, F_CYCLE_DONE);
-          k_coarse<<<a.grid_small, kThreads, sizeof(double) * d.r, st>>>(
-              d, a.ctl.cpart, nullptr, a.ctl, F_CYCLE_DONE, 1);
+        const int gd = grid_for((N + kThreads - 1) / kThreads, 1, 8 * sms);
+        if (a.op.dia.nd > 0) {  // banded A: diagonal storage
+          if (defl && !a.proj)
+            k_spmv_dia<TA, TV, TACC, true><<<gd, kThreads, 0, st>>>(
+                N, a.op.dia, a.op.ldd, dvals(a), xj, j, d, auvals(a), sdefl(a), w, a.ctl);
+          else
+            k_spmv_dia<TA, TV, TACC, false><<<gd, kThreads, 0, st>>>(
+                N, a.op.dia, a.op.ldd, dvals(a), xj, j, d, auvals(a), sdefl(a), w, a.ctl);
+          nl = 1;
+          if (a.proj) {  // w = P A v_j
+            coarse(a, (const TACC*)w, nullptr, F_CYCLE_DONE, 1, st);
+            k_proj_sub<TA, TACC><<<balanced(tiles, g.spmv_d), kSpmvRows, 0, st>>>(
+                N, d, auvals(a), sdefl(a), w, a.ctl);
+            nl = 4;
+          }
+        } else if (a.proj) {  // w = P A v_j = A v_j - A U T^-1 U^T A v_j
+          k_spmv_step<TA, TV, TACC, false><<<gd, kThreads, 0, st>>>(
+              N, a.op.rowptr, a.op.col, vals(a), xj, j, sdefl(a), w, a.ctl);
+          coarse(a, (const TACC*)w, nullptr, F_CYCLE_DONE, 1, st);
           k_proj_sub<TA, TACC><<<balanced(tiles, g.spmv_d), kSpmvRows, 0, st>>>(
-              N, a.op.rowptr, a.op.col, vals(a), d.agg, sdefl(a), w, a.ctl);
+              N, d, auvals(a), sdefl(a), w, a.ctl);
           nl = 4;
         } else if (defl)
-          k_spmv_step<TA, TV, TACC, true><<<balanced(tiles, g.spmv_d), kSpmvRows, 0, st>>>(
-              N, a.op.rowptr, a.op.col, vals(a), xj, j, d.agg, sdefl(a), w, a.ctl);
+          k_spmv_step<TA, TV, TACC, true><<<gd, kThreads, 0, st>>>(
+              N, a.op.xrp, a.op.xcol, xvals(a), xj, j, sdefl(a), w, a.ctl);
         else
-          k_spmv_step<TA, TV, TACC, false><<<balanced(tiles, g.spmv_n), kSpmvRows, 0, st>>>(
-              N, a.op.rowptr, a.op.col, vals(a), xj, j, nullptr, sdefl(a), w, a.ctl);
+          k_spmv_step<TA, TV, TACC, false><<<gd, kThreads, 0, st>>>(
+              N, a.op.rowptr, a.op.col, vals(a), xj, j, sdefl(a), w, a.ctl);
         if (!a.proj) nl = 1;
         break;
       }
@@ -573,10 +694,7 @@ struct Kern {
       }
       case PH_DEFL: {  // U^T v_j and the correction for column j
         const TV* xj = V + (size_t)j * a.ldv;
-        k_aggsum<TV><<<(d.npieces + 7) / 8, kThreads, 0, st>>>(xj, d, a.ctl.cpart, a.ctl.flags,
-                                                              F_CYCLE_DONE);
-        k_coarse<<<a.grid_small, kThreads, sizeof(double) * d.r, st>>>(
-            d, a.ctl.cpart, a.ctl.sigma + j, a.ctl, F_CYCLE_DONE, 0);
+        coarse(a, xj, nullptr, F_CYCLE_DONE, 0, st);  // s' = s / sigma_j
         nl = 2;
         break;
       }
@@ -586,10 +704,7 @@ struct Kern {
         if (defl) {
           k_xupdate<TV, true><<<grid_for(tiles, 1, g.xupd_d), kThreads, 0, st>>>(N, V, a.ldv, x,
                                                                                 a.t, a.ctl);
-          k_aggsum<double><<<(d.npieces + 7) / 8, kThreads, 0, st>>>(a.t, d, a.ctl.cpart,
-                                                                    a.ctl.flags, F_STOP);
-          k_coarse<<<a.grid_small, kThreads, sizeof(double) * d.r, st>>>(d, a.ctl.cpart,
-                                                                        nullptr, a.ctl, F_STOP, 0);
+          coarse(a, (const double*)a.t, nullptr, F_STOP, 0, st);
           k_xapply<<<grid_for(tiles, 1, g.xapply), kThreads, 0, st>>>(N, x, a.t, d.agg, a.ctl);
           nl = 5;
         } else {
@@ -604,12 +719,8 @@ struct Kern {
         if (a.proj) {  // r = P (b - A xh), the true residual of x = xh + U T^-1 U^T (b - A xh)
           k_residual<TV><<<balanced(tiles, g.resid), kSpmvRows, 0, st>>>(
               N, a.op.rowptr, a.op.col, a.op.val, x, b, Vm, a.ctl, a.t, 0);
-          k_aggsum<double><<<(d.npieces + 7) / 8, kThreads, 0, st>>>(a.t, d, a.ctl.cpart,
-                                                                    a.ctl.flags, F_STOP);
-          k_coarse<<<a.grid_small, kThreads, sizeof(double) * d.r, st>>>(
-              d, a.ctl.cpart, nullptr, a.ctl, F_STOP, 1);
-          k_proj_resid<TV><<<balanced(tiles, g.resid), kSpmvRows, 0, st>>>(
-              N, a.op.rowptr, a.op.col, a.op.val, d.agg, a.t, Vm, a.ctl);
+          coarse(a, (const double*)a.t, nullptr, F_STOP, 1, st);
+          k_proj_resid<TV><<<balanced(tiles, g.resid), kSpmvRows, 0, st>>>(N, d, a.t, Vm, a.ctl);
           nl = 4;
         } else {
           k_residual<TV><<<balanced(tiles, g.resid), kSpmvRows, 0, st>>>(
@@ -622,10 +733,7 @@ struct Kern {
         const int tiles = (N + kSpmvRows - 1) / kSpmvRows;
         k_residual<TV><<<balanced(tiles, g.resid), kSpmvRows, 0, st>>>(
             N, a.op.rowptr, a.op.col, a.op.val, x, b, Vm, a.ctl, a.t, 1);
-        k_aggsum<double><<<(d.npieces + 7) / 8, kThreads, 0, st>>>(a.t, d, a.ctl.cpart,
-                                                                  a.ctl.flags, -1);
-        k_coarse<<<a.grid_small, kThreads, sizeof(double) * d.r, st>>>(d, a.ctl.cpart, nullptr,
-                                                                      a.ctl, -1, 1);
+        coarse(a, (const double*)a.t, nullptr, -1, 1, st);
         k_xcoarse<<<grid_for((N + kThreads - 1) / kThreads, 1, g.xapply), kThreads, 0, st>>>(
             N, x, d.agg, a.ctl);
         nl = 4;

@@ -73,6 +73,13 @@ struct Ctl {
 };
 
 // Deflation data of one operator (A or A^T).
+// Diagonal storage of a banded operator: a_{i, i + off[d]} = dval[d * ldd + i].
+constexpr int kMaxDiag = 32;
+struct DiaOffsets {
+  int nd;
+  int off[kMaxDiag];
+};
+
 struct Defl {
   int r;                  // number of aggregates (0 = none)
   const int* agg;         // N
@@ -82,6 +89,12 @@ struct Defl {
   const double* uscale;   // r: 1/sqrt|agg_p|
   const double* tinv;     // r x r row-major T^-1
   int npieces;
+  // A W (W = the 0/1 aggregate indicator) in CSR: row i holds, for each aggregate a met
+  // in row i of A, the sum of the row's entries in the columns of a
+  const int* aurp;        // N + 1
+  const int* aucol;       // aggregate ids
+  const double* auval;
+  const float* auval32;   // FP32 copy (FP32 inner), may be null
 };
 
 // ---- element-type helpers ----
@@ -164,7 +177,8 @@ constexpr int kGroup = 32;      // blocks per first-level group of a grid reduct
 constexpr int kMaxGroups = 64;  // groups per grid (grid <= kGroup * kMaxGroups)
 
 // dst[c] = sum_{r < nrows} src[r * ldp + c] for c < ncols, in a fixed order: thread (c, q)
-// sums rows q, q + Q, ... (independent loads), then the Q partials are added in order.
+// sums rows q, q + Q, ... (independent loads), then the Q partials are added as a
+// pairwise tree (short dependent chains of FP64 adds).
 __device__ __forceinline__ void reduce_rows(const double* src, int nrows, int ncols, int ldp,
                                             double* dst) {
   __shared__ double scratch[256];
@@ -184,11 +198,14 @@ __device__ __forceinline__ void reduce_rows(const double* src, int nrows, int nc
     scratch[q * ncols + c] = s0 + s1;
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
-    double s = 0.0;
-    for (int q = 0; q < Q; ++q) s += scratch[q * ncols + c];
-    dst[c] = s;
+  for (int h = 1; h < Q; h <<= 1) {  // pairwise tree over the Q partials
+    for (int idx = threadIdx.x; idx < ncols * Q; idx += blockDim.x) {
+      const int c = idx % ncols, q = idx / ncols;
+      if ((q & (2 * h - 1)) == 0 && q + h < Q) scratch[q * ncols + c] += scratch[(q + h) * ncols + c];
+    }
+    __syncthreads();
   }
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) dst[c] = scratch[c];
   __syncthreads();
 }
 

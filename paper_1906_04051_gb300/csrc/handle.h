@@ -2,6 +2,8 @@
 // the single-system driver (solver.cu) and the batched driver (batch.cu).
 #pragma once
 
+#include <algorithm>
+
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -45,6 +47,11 @@ struct Meta {  // mirrors the device status block
 
 struct OpHost {
   DevMem rowptr, col, val, val32, tinv;
+  DevMem aurp, aucol, auval, auval32;  // A W in CSR (projector, residual)
+  DevMem xrp, xcol, xval, xval32;      // [A | A W] rows (deflated SpMV of a step)
+  DevMem dval, dval32;                 // diagonal storage (banded operators)
+  DiaOffsets dia{};
+  long long ldd = 0;
   bool ready = false;
 };
 
@@ -170,6 +177,82 @@ inline Ctl make_ctl(gmres_s* h) {
   return c;
 }
 
+// Diagonal storage of operator o when it has at most kMaxDiag distinct diagonals and they
+// are at least 80 % filled (the Q1 stencils: 9 diagonals, 99.6 % filled); otherwise the
+// CSR kernels are used.
+inline gmres_status build_dia(gmres_s* h, OpHost& o) {
+  cudaStream_t st = h->stream;
+  const int n = h->n;
+  o.dia.nd = 0;
+  DevMem slots;
+  CK(h, slots.ensure(sizeof(int) * 65));
+  int* sl = slots.as<int>();
+  CK(h, launch_dia_detect(n, o.rowptr.as<int>(), o.col.as<int>(), sl, sl + 64, st));
+  int hs[65];
+  CK(h, cudaMemcpyAsync(hs, sl, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  if (hs[64] > kMaxDiag || hs[64] < 1) return GMRES_OK;
+  DiaOffsets offs{};
+  for (int i = 0; i < 64; ++i)
+    if (hs[i] != dia_empty_slot()) offs.off[offs.nd++] = hs[i];
+  std::sort(offs.off, offs.off + offs.nd);
+  if ((double)h->nnz < 0.8 * (double)offs.nd * (double)n) return GMRES_OK;
+  const long long ldd = ((long long)n + 31) / 32 * 32;
+  const size_t cnt = (size_t)offs.nd * (size_t)ldd;
+  CK(h, o.dval.ensure(sizeof(double) * cnt));
+  CK(h, cudaMemsetAsync(o.dval.p, 0, sizeof(double) * cnt, st));
+  const bool f32 = h->opts.precision != GMRES_FP64;
+  if (f32) {
+    CK(h, o.dval32.ensure(sizeof(float) * cnt));
+    CK(h, cudaMemsetAsync(o.dval32.p, 0, sizeof(float) * cnt, st));
+  }
+  CK(h, launch_dia_fill(n, o.rowptr.as<int>(), o.col.as<int>(), o.val.as<double>(), offs, ldd,
+                        o.dval.as<double>(), f32 ? o.dval32.as<float>() : nullptr, st));
+  CK(h, cudaStreamSynchronize(st));
+  o.dia = offs;
+  o.ldd = ldd;
+  return GMRES_OK;
+}
+
+// A W of operator o in CSR (count, scan, fill; one host read of the entry count)
+inline gmres_status build_au(gmres_s* h, OpHost& o) {
+  cudaStream_t st = h->stream;
+  const int n = h->n;
+  DevMem cnt, bsum;
+  CK(h, cnt.ensure(sizeof(int) * (size_t)n));
+  CK(h, bsum.ensure(sizeof(int) * (size_t)(au_scan_blocks(n) + 1)));
+  CK(h, o.aurp.ensure(sizeof(int) * (size_t)(n + 1)));
+  CK(h, launch_au_rows(n, o.rowptr.as<int>(), o.col.as<int>(), h->agg.as<int>(), cnt.as<int>(),
+                       bsum.as<int>(), o.aurp.as<int>(), st));
+  int nau = 0;
+  CK(h, cudaMemcpyAsync(&nau, o.aurp.as<int>() + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  const size_t cap = nau > 0 ? (size_t)nau : 1;
+  CK(h, o.aucol.ensure(sizeof(int) * cap));
+  CK(h, o.auval.ensure(sizeof(double) * cap));
+  if (h->opts.precision != GMRES_FP64) CK(h, o.auval32.ensure(sizeof(float) * cap));
+  CK(h, launch_au_fill(n, o.rowptr.as<int>(), o.col.as<int>(), o.val.as<double>(),
+                       h->agg.as<int>(), o.aurp.as<int>(), o.aucol.as<int>(),
+                       o.auval.as<double>(),
+                       h->opts.precision != GMRES_FP64 ? o.auval32.as<float>() : nullptr, st));
+  const bool f32 = h->opts.precision != GMRES_FP64;
+  if (h->opts.deflation_mode == GMRES_DEFL_EBP) {
+    const long long nnz = h->nnz;
+    CK(h, o.xrp.ensure(sizeof(int) * (size_t)(n + 1)));
+    CK(h, o.xcol.ensure(sizeof(int) * (size_t)(nnz + nau)));
+    CK(h, o.xval.ensure(sizeof(double) * (size_t)(nnz + nau)));
+    if (f32) CK(h, o.xval32.ensure(sizeof(float) * (size_t)(nnz + nau)));
+    CK(h, launch_ext_csr(n, o.rowptr.as<int>(), o.col.as<int>(), o.val.as<double>(),
+                         f32 ? o.val32.as<float>() : nullptr, o.aurp.as<int>(),
+                         o.aucol.as<int>(), o.auval.as<double>(),
+                         f32 ? o.auval32.as<float>() : nullptr, o.xrp.as<int>(),
+                         o.xcol.as<int>(), o.xval.as<double>(),
+                         f32 ? o.xval32.as<float>() : nullptr, st));
+  }
+  CK(h, cudaStreamSynchronize(st));
+  return GMRES_OK;
+}
+
 inline OpDev make_op(gmres_s* h, OpHost& o) {
   OpDev op{};
   op.n = h->n;
@@ -185,6 +268,18 @@ inline OpDev make_op(gmres_s* h, OpHost& o) {
   op.defl.uscale = h->uscale.as<double>();
   op.defl.tinv = o.tinv.as<double>();
   op.defl.npieces = h->npieces;
+  op.defl.aurp = o.aurp.as<int>();
+  op.defl.aucol = o.aucol.as<int>();
+  op.defl.auval = o.auval.as<double>();
+  op.defl.auval32 = o.auval32.as<float>();
+  op.dia = o.dia;
+  op.ldd = o.ldd;
+  op.dval = o.dval.as<double>();
+  op.dval32 = o.dval32.as<float>();
+  op.xrp = o.xrp.as<int>();
+  op.xcol = o.xcol.as<int>();
+  op.xval = o.xval.as<double>();
+  op.xval32 = o.xval32.as<float>();
   return op;
 }
 

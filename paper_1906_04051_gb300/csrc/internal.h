@@ -34,6 +34,22 @@ cudaError_t launch_gauss_jordan(int r, const double* T, double* G, double* fac, 
 cudaError_t launch_norm_inf(int n, const int* rowptr, const double* val,
                             unsigned long long* out, cudaStream_t st);
 cudaError_t launch_to_float(long long n, const double* a, float* b, cudaStream_t st);
+int au_scan_blocks(int n);
+cudaError_t launch_au_rows(int n, const int* rowptr, const int* col, const int* agg, int* cnt,
+                           int* bsum, int* aurp, cudaStream_t st);
+cudaError_t launch_au_fill(int n, const int* rowptr, const int* col, const double* val,
+                           const int* agg, const int* aurp, int* aucol, double* auval,
+                           float* auval32, cudaStream_t st);
+cudaError_t launch_dia_detect(int n, const int* rowptr, const int* col, int* slots, int* count,
+                              cudaStream_t st);
+int dia_empty_slot();
+cudaError_t launch_dia_fill(int n, const int* rowptr, const int* col, const double* val,
+                            const DiaOffsets& offs, long long ldd, double* dval, float* dval32,
+                            cudaStream_t st);
+cudaError_t launch_ext_csr(int n, const int* rowptr, const int* col, const double* val,
+                           const float* val32, const int* aurp, const int* aucol,
+                           const double* auval, const float* auval32, int* xrp, int* xcol,
+                           double* xval, float* xval32, cudaStream_t st);
 
 // arnoldi.cu: one restart cycle's kernels, by precision
 enum Prec { P_FP64 = 0, P_FP32 = 1, P_BF16 = 2 };
@@ -45,6 +61,16 @@ struct OpDev {           // one operator (A or A^T) as the kernels see it
   const double* val;     // FP64 values (true residual, FP64 inner)
   const float* val32;    // FP32 copy (FP32 inner), may be null
   Defl defl;
+  // diagonal storage (dia.nd = 0: none), ldd elements per diagonal
+  DiaOffsets dia;
+  long long ldd;
+  const double* dval;
+  const float* dval32;
+  // rows [A | A W] (column n + a = aggregate a), for the deflated SpMV of a step
+  const int* xrp;
+  const int* xcol;
+  const double* xval;
+  const float* xval32;
 };
 
 struct CycleArgs {

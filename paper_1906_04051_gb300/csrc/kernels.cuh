@@ -80,6 +80,20 @@ __device__ __forceinline__ void spmv_tile(int N, int r0, const int* __restrict__
   }
 }
 
+// Coarse part of a deflated SpMV row: (A U s)_i = sum over the aggregates a met in row i
+// of (A W)_ia * s_a, with A W stored in CSR (usually one entry per row), s = U-scaled
+// coarse correction indexed by aggregate.
+template <typename TA, typename TACC>
+__device__ __forceinline__ TACC au_row(int row, const int* __restrict__ aurp,
+                                       const int* __restrict__ aucol,
+                                       const TA* __restrict__ auval,
+                                       const TACC* __restrict__ s) {
+  const int b = __ldg(aurp + row), e = __ldg(aurp + row + 1);
+  TACC acc = 0;
+  for (int q = b; q < e; ++q) acc += (TACC)__ldg(auval + q) * s[__ldg(aucol + q)];
+  return acc;
+}
+
 // Number of columns of warp slice `slice` among k columns dealt round-robin to nslice
 // slices.  Each warp runs an instance unrolled for exactly that many columns (a
 // warp-uniform switch), so no floating-point instruction is issued under a false
@@ -104,9 +118,20 @@ __device__ __forceinline__ int slice_cols(int k, int slice, int nslice) {
   }
 
 // Per-block column sums of the warp-slice accumulators.  Lanes store their live
-// accumulators (nw of them) transposed in shared memory and one thread adds the 32 lane
-// values of a (warp, column) pair, which costs far fewer FP64 instructions than a
-// shuffle tree on every lane; row groups are then added in a fixed order.
+// accumulators (nw of them) transposed in shared memory; each (warp, column) pair is then
+// summed by two threads, 16 lane values each as a pairwise tree, and one shuffle: the
+// dependent chain of FP64 adds is 5 deep instead of 32 (a lone FP64 add costs the
+// narrow FP64 pipe as much as a full warp's).  Row groups are then added in a fixed
+// order.
+__device__ __forceinline__ double tree16(const double* v) {
+  double a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = v[2 * i] + v[2 * i + 1];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) a[i] = a[2 * i] + a[2 * i + 1];
+  return (a[0] + a[1]) + (a[2] + a[3]);
+}
+
 template <typename TACC>
 __device__ __forceinline__ void reduce_slices(const TACC (&acc)[kSliceCols], int nw, int k,
                                               int nslice, double* sbuf /* 8*9*33 */,
@@ -117,14 +142,18 @@ __device__ __forceinline__ void reduce_slices(const TACC (&acc)[kSliceCols], int
   for (int i = 0; i < kSliceCols; ++i)
     if (i < nw) sbuf[(warp * kSliceCols + i) * 33 + lane] = (double)acc[i];
   __syncthreads();
-  for (int t = threadIdx.x; t < kSlices * kSliceCols; t += blockDim.x) {
-    const int wv = t / kSliceCols, i = t % kSliceCols;
-    if (i < slice_cols(k, wv % nslice, nslice)) {
-      const double* src = sbuf + (size_t)t * 33;
-      double s = 0.0;
-      for (int l = 0; l < 32; ++l) s += src[l];
-      swarp[t] = s;
+  for (int t0 = 0; t0 < 2 * kSlices * kSliceCols; t0 += blockDim.x) {
+    const int t = t0 + (int)threadIdx.x;
+    const int pair = t >> 1, half = t & 1;
+    double s = 0.0;
+    bool live = false;
+    if (pair < kSlices * kSliceCols) {
+      const int wv = pair / kSliceCols, i = pair % kSliceCols;
+      live = i < slice_cols(k, wv % nslice, nslice);
+      if (live) s = tree16(sbuf + (size_t)pair * 33 + half * 16);
     }
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    if (live && half == 0) swarp[pair] = s;
   }
   __syncthreads();
   for (int c = threadIdx.x; c < k; c += blockDim.x) {
@@ -136,54 +165,84 @@ __device__ __forceinline__ void reduce_slices(const TACC (&acc)[kSliceCols], int
   __syncthreads();
 }
 
-// Plane rotations and stopping tests of step j (Eqs. 12, 14), by the whole block: the
-// column, rotations and gamma are staged in shared memory, one thread applies the
-// rotations there (no dependent global-memory round trips), then all threads store.
+// Plane rotations and stopping tests of step j (Eqs. 12, 14), by warp 0 of the calling
+// block (the other threads return at once).  Lane l holds rows 2l and 2l+1 of the new
+// Hessenberg column (j < kMaxM = 64).  Applying the j earlier rotations is a linear
+// recurrence in the value carried down the column,
+//   t_0 = h_0,  t_{i+1} = -sn_i t_i + cs_i h_{i+1},  rotated h_i = cs_i t_i + sn_i h_{i+1},
+// so the carried values come from a warp scan of the affine maps t -> -sn_i t + cs_i h_{i+1}
+// (5 shuffle levels) instead of a 2j-deep chain of dependent FP64 operations on one
+// thread; the divisions of the new rotation and of 1/||w|| run in one SIMT division.
+__device__ __forceinline__ void affine_compose(double& A, double& B, double Ae, double Be) {
+  // (A, B) <- (A, B) o (Ae, Be): t -> A (Ae t + Be) + B
+  B = fma(A, Be, B);
+  A = A * Ae;
+}
+
 __device__ void givens_step(Ctl& ctl, int j, int m, double hnext) {
-  __shared__ double sh[kMaxK + 1], scs[kMaxK], ssn[kMaxK], sg[2];
-  __shared__ int sdone;
+  if (threadIdx.x >= 32) return;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x;
   const int ldh = ctl.ldh;
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-    const double hi = ctl.h[i];
-    sh[i] = hi;
-    ctl.Hr[(size_t)i * ldh + j] = hi;
-    if (i < j) {
-      scs[i] = ctl.cs[i];
-      ssn[i] = ctl.sn[i];
-    }
+  const int i0 = 2 * lane, i1 = 2 * lane + 1;
+  const double h0 = i0 <= j ? ctl.h[i0] : 0.0;
+  const double h1 = i1 <= j ? ctl.h[i1] : 0.0;
+  const double c0 = i0 < j ? ctl.cs[i0] : 1.0, s0 = i0 < j ? ctl.sn[i0] : 0.0;
+  const double c1 = i1 < j ? ctl.cs[i1] : 1.0, s1 = i1 < j ? ctl.sn[i1] : 0.0;
+  const double gj = ctl.g[j];
+  if (i0 <= j) ctl.Hr[(size_t)i0 * ldh + j] = h0;
+  if (i1 <= j) ctl.Hr[(size_t)i1 * ldh + j] = h1;
+  if (lane == 0) ctl.Hr[(size_t)(j + 1) * ldh + j] = hnext;
+  const double hn2 = fma(hnext, hnext, warp_sum(fma(h1, h1, h0 * h0)));
+  const double h2 = __shfl_down_sync(full, h0, 1);  // h_{2l+2}
+  // maps of rotations 2l and 2l+1 (identity past j - 1) and their composition
+  const double a0 = i0 < j ? -s0 : 1.0, b0 = i0 < j ? c0 * h1 : 0.0;
+  const double a1 = i1 < j ? -s1 : 1.0, b1 = i1 < j ? c1 * h2 : 0.0;
+  double A = a1, B = b1;
+  affine_compose(A, B, a0, b0);
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {  // inclusive scan, later maps applied last
+    const double Ap = __shfl_up_sync(full, A, d), Bp = __shfl_up_sync(full, B, d);
+    if (lane >= d) affine_compose(A, B, Ap, Bp);
   }
-  if (threadIdx.x == 0) {
-    ctl.Hr[(size_t)(j + 1) * ldh + j] = hnext;
-    sg[0] = ctl.g[j];
+  double PA = __shfl_up_sync(full, A, 1), PB = __shfl_up_sync(full, B, 1);
+  if (lane == 0) { PA = 1.0; PB = 0.0; }
+  const double t0 = __shfl_sync(full, h0, 0);
+  const double tc0 = fma(PA, t0, PB);     // t_{2l}
+  const double tc1 = fma(a0, tc0, b0);    // t_{2l+1}
+  const double r0 = fma(c0, tc0, s0 * h1);  // rotated h_{2l}
+  const double r1 = fma(c1, tc1, s1 * h2);  // rotated h_{2l+1}
+  // a = t_j, the last entry before the new rotation
+  const double a = __shfl_sync(full, (j & 1) ? tc1 : tc0, j >> 1);
+  double rho = 0.0;
+  if (lane == 0 && hnext != 0.0) rho = hypot(a, hnext);
+  rho = __shfl_sync(full, rho, 0);
+  // lane 0: cs_j = a / rho, lane 1: sn_j = hnext / rho, lane 2: sigma_{j+1} = 1 / hnext
+  double q = 0.0;
+  if (lane < 3) {
+    const double num = lane == 0 ? a : (lane == 1 ? hnext : 1.0);
+    const double den = lane == 2 ? hnext : rho;
+    const bool use = lane == 2 ? (hnext > 0.0) : (hnext != 0.0);
+    q = use ? num / den : (lane == 0 ? 1.0 : 0.0);
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double hn2 = hnext * hnext;
-    for (int i = 0; i <= j; ++i) hn2 += sh[i] * sh[i];
-    for (int i = 0; i < j; ++i) {
-      const double a = sh[i], b = sh[i + 1];
-      sh[i] = scs[i] * a + ssn[i] * b;
-      sh[i + 1] = -ssn[i] * a + scs[i] * b;
-    }
-    const double a = sh[j];
-    double c = 1.0, sn = 0.0;
-    if (hnext != 0.0) {
-      const double rho = hypot(a, hnext);
-      c = a / rho;
-      sn = hnext / rho;
-      sh[j] = rho;
-    }
-    sh[j + 1] = 0.0;
-    scs[j] = c;
-    ssn[j] = sn;
-    const double gj = sg[0];
-    sg[1] = -sn * gj;
-    sg[0] = c * gj;
+  const double c = __shfl_sync(full, q, 0), sn = __shfl_sync(full, q, 1);
+  const double sig = __shfl_sync(full, q, 2);
+  // rotated column: rows < j from the scan, row j = rho (or a when hnext = 0), row j+1 = 0
+  const double hj = hnext != 0.0 ? rho : a;
+  if (i0 <= j + 1) ctl.H[(size_t)i0 * ldh + j] = i0 < j ? r0 : (i0 == j ? hj : 0.0);
+  if (i1 <= j + 1) ctl.H[(size_t)i1 * ldh + j] = i1 < j ? r1 : (i1 == j ? hj : 0.0);
+  if (lane == 0 && j + 1 >= 64) ctl.H[(size_t)(j + 1) * ldh + j] = 0.0;  // row 64 (m = 64)
+  if (lane == 0) {
+    const double sg1 = -sn * gj, sg0 = c * gj;
+    ctl.cs[j] = c;
+    ctl.sn[j] = sn;
+    ctl.g[j] = sg0;
+    ctl.g[j + 1] = sg1;
     const long long steps = ++ctl.counts[C_STEPS];
     ctl.flags[F_K] = j + 1;
-    const double est = fabs(sg[1]) / ctl.scal[S_RHO0];
+    const double est = fabs(sg1) / ctl.scal[S_RHO0];
     ctl.scal[S_EST] = est;
-    ctl.sigma[j + 1] = hnext > 0.0 ? 1.0 / hnext : 0.0;
+    ctl.sigma[j + 1] = sig;
     bool done = false;
     if (!isfinite(hnext) || !isfinite(est)) {
       ctl.flags[F_STATUS] = GMRES_ERR_NAN;
@@ -192,20 +251,11 @@ __device__ void givens_step(Ctl& ctl, int j, int m, double hnext) {
     }
     if (hnext <= 1e-14 * sqrt(hn2)) done = true;  // breakdown: the Krylov space is invariant
     if (!ctl.flags[F_FIXED] && est <= ctl.scal[S_TOL]) done = true;
-    if (ctl.flags[F_MIXED] && fabs(sg[1]) <= ctl.scal[S_INNER_TOL] * ctl.scal[S_BETA_CYCLE])
+    if (ctl.flags[F_MIXED] && fabs(sg1) <= ctl.scal[S_INNER_TOL] * ctl.scal[S_BETA_CYCLE])
       done = true;
     if (steps >= ctl.counts[C_MAXIT]) done = true;
     if (j + 1 >= m) done = true;
-    sdone = done ? 1 : 0;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) ctl.H[(size_t)i * ldh + j] = sh[i];
-  if (threadIdx.x == 0) {
-    ctl.cs[j] = scs[j];
-    ctl.sn[j] = ssn[j];
-    ctl.g[j] = sg[0];
-    ctl.g[j + 1] = sg[1];
-    if (sdone) ctl.flags[F_CYCLE_DONE] = 1;
+    if (done) ctl.flags[F_CYCLE_DONE] = 1;
   }
 }
 

@@ -295,6 +295,191 @@ __global__ void k_to_float(long long n, const double* __restrict__ a, float* __r
     b[t] = (float)a[t];
 }
 
+// ---- coarse rows AU: per row i and aggregate a met in row i, (AU W^-1)_ia = sum of a_ik
+// over the row's entries whose column lies in aggregate a (unscaled, U = W diag(uscale)).
+// Entries of a row are kept in order of first occurrence; each sum runs in CSR order.
+__device__ __forceinline__ bool first_of_agg(const int* __restrict__ col,
+                                             const int* __restrict__ agg, int s, int k, int a) {
+  for (int q = s; q < k; ++q)
+    if (agg[col[q]] == a) return false;
+  return true;
+}
+
+__global__ void k_au_count(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                           const int* __restrict__ agg, int* __restrict__ cnt) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int s = rowptr[i], e = rowptr[i + 1];
+    int c = 0;
+    for (int k = s; k < e; ++k) {
+      const int a = agg[col[k]];
+      if (a >= 0 && first_of_agg(col, agg, s, k, a)) ++c;
+    }
+    cnt[i] = c;
+  }
+}
+
+// exclusive scan of cnt[0, n) into out[0, n], out[n] = total; 1024 entries per block
+constexpr int kScanBlock = 1024;
+
+__device__ __forceinline__ int block_excl_scan(int v, int* sw /* 32 */, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sw[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int t = lane < (int)(blockDim.x >> 5) ? sw[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    sw[lane] = t;
+  }
+  __syncthreads();
+  const int before = warp > 0 ? sw[warp - 1] : 0;
+  *total = sw[31];
+  __syncthreads();
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanBlock)
+    k_scan_sums(int n, const int* __restrict__ cnt, int* __restrict__ bsum) {
+  __shared__ int sw[32];
+  const int i = blockIdx.x * kScanBlock + threadIdx.x;
+  int tot;
+  block_excl_scan(i < n ? cnt[i] : 0, sw, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// one block: bsum[0, nb) -> exclusive offsets, bsum[nb] = total
+__global__ void __launch_bounds__(kScanBlock) k_scan_top(int nb, int* __restrict__ bsum) {
+  __shared__ int sw[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < nb; b0 += kScanBlock) {
+    const int b = b0 + threadIdx.x;
+    const int v = b < nb ? bsum[b] : 0;
+    int tot;
+    const int ex = block_excl_scan(v, sw, &tot);
+    if (b < nb) bsum[b] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+__global__ void __launch_bounds__(kScanBlock)
+    k_scan_apply(int n, int nb, const int* __restrict__ cnt, const int* __restrict__ bsum,
+                 int* __restrict__ out) {
+  __shared__ int sw[32];
+  const int i = blockIdx.x * kScanBlock + threadIdx.x;
+  int tot;
+  const int ex = block_excl_scan(i < n ? cnt[i] : 0, sw, &tot);
+  if (i < n) out[i] = bsum[blockIdx.x] + ex;
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = bsum[nb];
+}
+
+__global__ void k_au_fill(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                          const double* __restrict__ val, const int* __restrict__ agg,
+                          const int* __restrict__ aurp, int* __restrict__ aucol,
+                          double* __restrict__ auval, float* __restrict__ auval32) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int s = rowptr[i], e = rowptr[i + 1];
+    int q = aurp[i];
+    for (int k = s; k < e; ++k) {
+      const int a = agg[col[k]];
+      if (a < 0 || !first_of_agg(col, agg, s, k, a)) continue;
+      double sum = 0.0;
+      for (int k2 = k; k2 < e; ++k2)
+        if (agg[col[k2]] == a) sum += val[k2];
+      aucol[q] = a;
+      auval[q] = sum;
+      if (auval32) auval32[q] = (float)sum;
+      ++q;
+    }
+  }
+}
+
+// ---- extended rows [A | A W] for the deflated SpMV: row i holds A's entries, then its
+// A W entries with column index n + a (a = aggregate) ----
+__global__ void k_ext_rows(int n, const int* __restrict__ rowptr, const int* __restrict__ aurp,
+                           int* __restrict__ xrp) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x)
+    xrp[i] = rowptr[i] + aurp[i];
+}
+
+__global__ void k_ext_fill(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                           const double* __restrict__ val, const float* __restrict__ val32,
+                           const int* __restrict__ aurp, const int* __restrict__ aucol,
+                           const double* __restrict__ auval, const float* __restrict__ auval32,
+                           const int* __restrict__ xrp, int* __restrict__ xcol,
+                           double* __restrict__ xval, float* __restrict__ xval32) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int q = xrp[i];
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k, ++q) {
+      xcol[q] = col[k];
+      xval[q] = val[k];
+      if (xval32) xval32[q] = val32[k];
+    }
+    for (int k = aurp[i]; k < aurp[i + 1]; ++k, ++q) {
+      xcol[q] = n + aucol[k];
+      xval[q] = auval[k];
+      if (xval32) xval32[q] = auval32[k];
+    }
+  }
+}
+
+// ---- diagonal storage: the distinct offsets col - row of A (a lock-free insert into a
+// 64-slot open-addressing table; more than kMaxDiag distinct offsets sets the overflow
+// count), then dval[d * ldd + i] = a_{i, i + off_d} (0 where the entry is absent) ----
+constexpr int kDiagSlots = 64;
+constexpr int kDiagEmpty = (int)0x80000000;
+
+__global__ void k_dia_detect(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                             int* __restrict__ slots, int* __restrict__ count) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      const int off = col[k] - i;
+      int h = (int)(((unsigned)off * 2654435761u) >> 26);  // 6 bits
+      for (int probe = 0; probe < kDiagSlots; ++probe, h = (h + 1) & (kDiagSlots - 1)) {
+        const int cur = *(volatile int*)(slots + h);
+        if (cur == off) break;
+        if (cur == kDiagEmpty) {
+          const int prev = atomicCAS(slots + h, kDiagEmpty, off);
+          if (prev == kDiagEmpty) {
+            atomicAdd(count, 1);
+            break;
+          }
+          if (prev == off) break;
+        }
+      }
+      if (*(volatile int*)count > kMaxDiag) return;  // too many: no diagonal storage
+    }
+  }
+}
+
+__global__ void k_dia_fill(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                           const double* __restrict__ val, DiaOffsets offs, long long ldd,
+                           double* __restrict__ dval, float* __restrict__ dval32) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      const int off = col[k] - i;
+      int d = 0;
+      while (d < offs.nd && offs.off[d] != off) ++d;
+      if (d == offs.nd) continue;  // cannot happen after a complete detection
+      dval[d * ldd + i] = val[k];
+      if (dval32) dval32[d * ldd + i] = (float)val[k];
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_validate(int n, long long nnz, const int* rowptr, const int* col,
@@ -376,6 +561,63 @@ cudaError_t launch_norm_inf(int n, const int* rowptr, const double* val,
 
 cudaError_t launch_to_float(long long n, const double* a, float* b, cudaStream_t st) {
   k_to_float<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, a, b);
+  return cudaGetLastError();
+}
+
+}  // namespace gg
+
+namespace gg {
+
+int au_scan_blocks(int n) { return (n + kScanBlock - 1) / kScanBlock; }
+
+cudaError_t launch_au_rows(int n, const int* rowptr, const int* col, const int* agg,
+                           int* cnt /* n */, int* bsum /* blocks + 1 */, int* aurp /* n + 1 */,
+                           cudaStream_t st) {
+  const int nb = au_scan_blocks(n);
+  k_au_count<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, rowptr, col, agg, cnt);
+  k_scan_sums<<<nb, kScanBlock, 0, st>>>(n, cnt, bsum);
+  k_scan_top<<<1, kScanBlock, 0, st>>>(nb, bsum);
+  k_scan_apply<<<nb, kScanBlock, 0, st>>>(n, nb, cnt, bsum, aurp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_au_fill(int n, const int* rowptr, const int* col, const double* val,
+                           const int* agg, const int* aurp, int* aucol, double* auval,
+                           float* auval32, cudaStream_t st) {
+  k_au_fill<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, rowptr, col, val, agg, aurp, aucol,
+                                                       auval, auval32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ext_csr(int n, const int* rowptr, const int* col, const double* val,
+                           const float* val32, const int* aurp, const int* aucol,
+                           const double* auval, const float* auval32, int* xrp, int* xcol,
+                           double* xval, float* xval32, cudaStream_t st) {
+  k_ext_rows<<<grid_for(n + 1LL, 256, 152 * 8), 256, 0, st>>>(n, rowptr, aurp, xrp);
+  k_ext_fill<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, rowptr, col, val, val32, aurp, aucol,
+                                                        auval, auval32, xrp, xcol, xval, xval32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dia_detect(int n, const int* rowptr, const int* col, int* slots /* 64 */,
+                              int* count, cudaStream_t st) {
+  int init[kDiagSlots];
+  for (int i = 0; i < kDiagSlots; ++i) init[i] = kDiagEmpty;
+  cudaError_t e = cudaMemcpyAsync(slots, init, sizeof(init), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(count, 0, sizeof(int), st)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;  // init is a stack array
+  k_dia_detect<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, rowptr, col, slots, count);
+  return cudaGetLastError();
+}
+
+int dia_empty_slot() { return kDiagEmpty; }
+
+cudaError_t launch_dia_fill(int n, const int* rowptr, const int* col, const double* val,
+                            const DiaOffsets& offs, long long ldd, double* dval, float* dval32,
+                            cudaStream_t st) {
+  k_dia_fill<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, rowptr, col, val, offs, ldd, dval,
+                                                        dval32);
   return cudaGetLastError();
 }
 

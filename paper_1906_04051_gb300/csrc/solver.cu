@@ -454,6 +454,14 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
     if (herr[0] & 8) return bail(fail(h, GMRES_ERR_SINGULAR_COARSE, "T = U^T A U is singular"));
     h->npieces = np;
   }
+  if (r > 0 && opts.deflation_mode != GMRES_DEFL_NONE) {
+    const gmres_status s_au = build_au(h, h->fwd);
+    if (s_au != GMRES_OK) return bail(s_au);
+  }
+  {
+    const gmres_status s_dia = build_dia(h, h->fwd);
+    if (s_dia != GMRES_OK) return bail(s_dia);
+  }
   if (opts.mu_mode == GMRES_MU_NORM_INF) {
     DevMem mx;
     CKC(mx.ensure(sizeof(unsigned long long)));
@@ -470,9 +478,14 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
   h->pms[PH_SETUP] = std::chrono::duration<double, std::milli>(
                          std::chrono::steady_clock::now() - t_setup).count();
   // kernels enqueued by the setup: validation, FP32 copy, aggregate permutation (4),
-  // coarse matrix, Gauss-Jordan (init, 2 per pivot, extract), infinity norm
+  // coarse matrix, Gauss-Jordan (init, first pivot, one per column, extract), A W (count,
+  // three scan passes, fill), the rows [A | A W] (2), diagonal storage (detect, fill),
+  // infinity norm
   h->plaunch[PH_SETUP] = 1 + (opts.precision != GMRES_FP64 ? 1 : 0) +
                          (r > 0 ? 4 + 1 + 3 + (long long)r : 0) +
+                         (r > 0 && opts.deflation_mode != GMRES_DEFL_NONE ? 5 : 0) +
+                         (r > 0 && opts.deflation_mode == GMRES_DEFL_EBP ? 2 : 0) +
+                         1 + (h->fwd.dia.nd > 0 ? 1 : 0) +
                          (opts.mu_mode == GMRES_MU_NORM_INF ? 1 : 0);
 #undef CKC
   *out = h;
@@ -511,6 +524,12 @@ gmres_status gmres_adjoint_solve(gmres_t h, const double* g, const double* lam0,
       CK(h, launch_to_float(nnz, h->adj.val.as<double>(), h->adj.val32.as<float>(), st));
     }
     CK(h, cudaStreamSynchronize(st));
+    if (h->r > 0 && h->opts.deflation_mode != GMRES_DEFL_NONE) {
+      const gmres_status s_au = build_au(h, h->adj);
+      if (s_au != GMRES_OK) return s_au;
+    }
+    const gmres_status s_dia = build_dia(h, h->adj);
+    if (s_dia != GMRES_OK) return s_dia;
     h->adj.ready = true;
   }
   return run(h, h->adj, g, lam0, m, tol, maxit, lam, info);
