@@ -82,7 +82,10 @@ __global__ void __launch_bounds__(kThreads)
   const TACC sigma = (TACC)ctl.sigma[j];
   const int nd = dia.nd;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    TACC acc0 = 0, acc1 = 0;
+    // one FMA chain per row (no partial-sum combines: the FP64 pipe is the bound here,
+    // and other warps hide the chain's latency)
+    TACC acc = 0;
+    if constexpr (DEFL) acc = au_row<TA, TACC>(i, d.aurp, d.aucol, auval, sdefl);
     int q = 0;
     for (; q + 3 < nd; q += 4) {
       int c[4];
@@ -93,17 +96,13 @@ __global__ void __launch_bounds__(kThreads)
       for (int u = 0; u < 4; ++u) a[u] = (TACC)__ldg(dval + (q + u) * ldd + i);
 #pragma unroll
       for (int u = 0; u < 4; ++u) xv[u] = ld_as<TACC, TV>(x + c[u]);
-      acc0 += a[0] * xv[0];
-      acc1 += a[1] * xv[1];
-      acc0 += a[2] * xv[2];
-      acc1 += a[3] * xv[3];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc += a[u] * xv[u];
     }
     for (; q < nd; ++q) {
       const int c = min(max(i + soff[q], 0), N - 1);
-      acc0 += (TACC)__ldg(dval + q * ldd + i) * ld_as<TACC, TV>(x + c);
+      acc += (TACC)__ldg(dval + q * ldd + i) * ld_as<TACC, TV>(x + c);
     }
-    TACC acc = acc0 + acc1;
-    if constexpr (DEFL) acc += au_row<TA, TACC>(i, d.aurp, d.aucol, auval, sdefl);
     w[i] = sigma * acc;
   }
 }
@@ -212,6 +211,9 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ double tot[1];
   const size_t sb = ring_stage_bytes(k, TR, sizeof(TV), sizeof(TACC));
   const Ring<TV, TACC> R{smraw, bars, k, TR, ring_stages(sb), sb};
+  // the rotations of Eq. 12 that do not need h_{j+1,j}, off the critical path: the last
+  // block has the fewest tiles when they do not divide evenly
+  if (blockIdx.x == gridDim.x - 1) givens_prep(ctl, k - 1);
   for (int c = threadIdx.x; c < k; c += blockDim.x) scoef[c] = (TACC)ctl.coef[c];
   const int P = update_splits<TACC>(TR, VN);
   const int ng = TR / VN;
@@ -248,14 +250,14 @@ __global__ void __launch_bounds__(kThreads)
   if (threadIdx.x == 0) sred[0] = bs;
   __syncthreads();
   if (!last_block_reduce(sred, 1, ctl.part, ctl.part2, ctl.ldp, ctl.ticket, tot)) return;
-  givens_step(ctl, k - 1, m, sqrt(tot[0]));
+  givens_finish(ctl, k - 1, m, sqrt(tot[0]));
 }
 
 // --------------------------------------------------------------------------------------
 // Deflation: c = scale U^T x by pieces (warp per piece), then s = U (|mu| T^-1 - I) c.
 // --------------------------------------------------------------------------------------
 // Piece sums: a warp per piece, up to 32 gathers in flight per lane (pieces hold at most
-// kPiece = 1024 nodes, so one batch), two accumulators per lane.
+// kPiece = 1024 nodes, so one batch), four accumulators per lane (short FP64 chains).
 template <typename TX>
 __global__ void __launch_bounds__(kThreads)
     k_aggsum(const TX* __restrict__ x, Defl d, double* __restrict__ cpart, const int* flags,
@@ -265,7 +267,7 @@ __global__ void __launch_bounds__(kThreads)
   const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (p >= d.npieces) return;
   const int s = d.piece_start[p], e = d.piece_start[p + 1];
-  double acc0 = 0.0, acc1 = 0.0;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int t0 = s; t0 < e; t0 += 32 * 32) {
     int q[32];
 #pragma unroll
@@ -277,18 +279,15 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int u = 0; u < 32; ++u) v[u] = q[u] >= 0 ? ld_as<double, TX>(x + q[u]) : 0.0;
 #pragma unroll
-    for (int u = 0; u < 32; u += 2) {
-      acc0 += v[u];
-      acc1 += v[u + 1];
-    }
+    for (int u = 0; u < 32; ++u) acc[u & 3] += v[u];
   }
-  const double sum = warp_sum(acc0 + acc1);
+  const double sum = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
   if (lane == 0) cpart[p] = sum;
 }
 
 // c_a = scale uscale_a sum(pieces of a) into shared memory (piece sums staged through
 // shared memory when they fit), then y = T^-1 c by a warp per row (32 loads in flight
-// per lane, two accumulators) and s_a = uscale_a (|mu| y_a - c_a), or s_a = uscale_a y_a
+// per lane, four accumulators) and s_a = uscale_a (|mu| y_a - c_a), or s_a = uscale_a y_a
 // for the deflation projector.
 constexpr int kCoarseStage = 4096;  // piece sums staged in shared memory (32 KB)
 
@@ -306,11 +305,13 @@ __global__ void __launch_bounds__(kThreads)
     for (int p = threadIdx.x; p < d.npieces; p += blockDim.x) spc[p] = __ldg(cpart + p);
   __syncthreads();
   const double* pc = staged ? spc : cpart;
+#pragma unroll 4
   for (int a = threadIdx.x; a < r; a += blockDim.x) {
     const int lo = __ldg(d.agg_piece + a), hi = __ldg(d.agg_piece + a + 1);
+    const double us = __ldg(d.uscale + a);
     double sum = 0.0;
     for (int q = lo; q < hi; ++q) sum += pc[q];
-    sc[a] = scale * __ldg(d.uscale + a) * sum;
+    sc[a] = scale * us * sum;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(kThreads)
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int a = gw; a < r; a += nw) {
     const double* row = d.tinv + (size_t)a * r;
-    double acc0 = 0.0, acc1 = 0.0;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int b0 = 0; b0 < r; b0 += 32 * 32) {
       double t[32];
 #pragma unroll
@@ -327,13 +328,12 @@ __global__ void __launch_bounds__(kThreads)
         t[u] = b < r ? __ldg(row + b) : 0.0;
       }
 #pragma unroll
-      for (int u = 0; u < 32; u += 2) {
+      for (int u = 0; u < 32; ++u) {
         const int b = b0 + lane + 32 * u;
-        if (b < r) acc0 += t[u] * sc[b];
-        if (b + 32 < r) acc1 += t[u + 1] * sc[b + 32];
+        if (b < r) acc[u & 3] += t[u] * sc[b];
       }
     }
-    const double y = warp_sum(acc0 + acc1);
+    const double y = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
     if (lane == 0) {
       const double us = __ldg(d.uscale + a);
       const double sd = proj ? us * y : us * (mu * y - sc[a]);

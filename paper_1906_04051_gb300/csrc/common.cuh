@@ -33,6 +33,8 @@ enum ScalarSlot {
   S_EST,          // |gamma_{k+1}| / rho0 of the last step
   S_TRUE,         // true relative residual of the last residual evaluation
   S_R0REF,        // user reference norm (0 = none)
+  S_GIV_A,        // t_j: entry j of the step's column after the earlier rotations
+  S_GIV_HN2,      // sum of h_ij^2 over i <= j (breakdown test)
   S_NSCAL = 16
 };
 enum FlagSlot {
@@ -176,36 +178,31 @@ __device__ __forceinline__ T block_sum(T v, T* sbuf /* >= blockDim/32 */) {
 constexpr int kGroup = 32;      // blocks per first-level group of a grid reduction
 constexpr int kMaxGroups = 64;  // groups per grid (grid <= kGroup * kMaxGroups)
 
-// dst[c] = sum_{r < nrows} src[r * ldp + c] for c < ncols, in a fixed order: thread (c, q)
-// sums rows q, q + Q, ... (independent loads), then the Q partials are added as a
-// pairwise tree (short dependent chains of FP64 adds).
+// dst[c] = sum_{r < nrows} src[r * ldp + c] for c < ncols, in a fixed order: the Q
+// threads of a column (Q a power of two, consecutive lanes) sum rows q, q + Q, ... with
+// two accumulators and independent loads, then combine by shuffles (no block barriers).
 __device__ __forceinline__ void reduce_rows(const double* src, int nrows, int ncols, int ldp,
                                             double* dst) {
-  __shared__ double scratch[256];
-  const int nt = blockDim.x < 256 ? blockDim.x : 256;
-  int Q = nt / ncols;
-  if (Q < 1) Q = 1;
-  if (Q > 16) Q = 16;
-  for (int idx = threadIdx.x; idx < ncols * Q; idx += blockDim.x) {
-    const int c = idx % ncols, q = idx / ncols;
+  int Q = 1;
+  while (Q * 2 <= 32 && Q * 2 * ncols <= (int)blockDim.x) Q *= 2;
+  const int lanes = ncols * Q;
+  const int rounds = (lanes + blockDim.x - 1) / blockDim.x;
+  for (int rd = 0; rd < rounds; ++rd) {
+    const int idx = rd * blockDim.x + threadIdx.x;
+    const int c = idx / Q, q = idx % Q;
     double s0 = 0.0, s1 = 0.0;
-    int r = q;
-    for (; r + Q < nrows; r += 2 * Q) {
-      s0 += __ldcg(src + (size_t)r * ldp + c);
-      s1 += __ldcg(src + (size_t)(r + Q) * ldp + c);
+    if (c < ncols) {
+      int r = q;
+      for (; r + Q < nrows; r += 2 * Q) {
+        s0 += __ldcg(src + (size_t)r * ldp + c);
+        s1 += __ldcg(src + (size_t)(r + Q) * ldp + c);
+      }
+      if (r < nrows) s0 += __ldcg(src + (size_t)r * ldp + c);
     }
-    if (r < nrows) s0 += __ldcg(src + (size_t)r * ldp + c);
-    scratch[q * ncols + c] = s0 + s1;
+    double v = s0 + s1;
+    for (int o = 1; o < Q; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (c < ncols && q == 0) dst[c] = v;
   }
-  __syncthreads();
-  for (int h = 1; h < Q; h <<= 1) {  // pairwise tree over the Q partials
-    for (int idx = threadIdx.x; idx < ncols * Q; idx += blockDim.x) {
-      const int c = idx % ncols, q = idx / ncols;
-      if ((q & (2 * h - 1)) == 0 && q + h < Q) scratch[q * ncols + c] += scratch[(q + h) * ncols + c];
-    }
-    __syncthreads();
-  }
-  for (int c = threadIdx.x; c < ncols; c += blockDim.x) dst[c] = scratch[c];
   __syncthreads();
 }
 
@@ -222,21 +219,25 @@ __device__ __forceinline__ bool last_block_reduce(const double* sred, int ncols,
   const int ng = (G + kGroup - 1) / kGroup, g = b / kGroup;
   const int gs = (G - g * kGroup) < kGroup ? (G - g * kGroup) : kGroup;
   for (int c = threadIdx.x; c < ncols; c += blockDim.x) part[(size_t)b * ldp + c] = sred[c];
-  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(&tickets[1 + g], 1u) == (unsigned)gs - 1u) ? 1u : 0u;
+  if (threadIdx.x == 0) {  // the block's writes are ordered before thread 0's fence
+    __threadfence();
+    s_last = (atomicAdd(&tickets[1 + g], 1u) == (unsigned)gs - 1u) ? 1u : 0u;
+    if (s_last) __threadfence();
+  }
   __syncthreads();
   if (!s_last) return false;
-  __threadfence();
   reduce_rows(part + (size_t)g * kGroup * ldp, gs, ncols, ldp, tot);
   for (int c = threadIdx.x; c < ncols; c += blockDim.x) part2[(size_t)g * ldp + c] = tot[c];
-  if (threadIdx.x == 0) tickets[1 + g] = 0u;
-  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(&tickets[0], 1u) == (unsigned)ng - 1u) ? 1u : 0u;
+  if (threadIdx.x == 0) {
+    tickets[1 + g] = 0u;
+    __threadfence();
+    s_last = (atomicAdd(&tickets[0], 1u) == (unsigned)ng - 1u) ? 1u : 0u;
+    if (s_last) __threadfence();
+  }
   __syncthreads();
   if (!s_last) return false;
-  __threadfence();
   reduce_rows(part2, ng, ncols, ldp, tot);
   if (threadIdx.x == 0) tickets[0] = 0u;
   __syncthreads();

@@ -179,7 +179,10 @@ __device__ __forceinline__ void affine_compose(double& A, double& B, double Ae, 
   A = A * Ae;
 }
 
-__device__ void givens_step(Ctl& ctl, int j, int m, double hnext) {
+// First half, independent of h_{j+1,j} (it only needs h from the projections): the
+// earlier rotations applied to column j (rows < j of H written), the unrotated column
+// stored in Hr, and t_j and sum h_ij^2 left in the scalar slots for the second half.
+__device__ void givens_prep(Ctl& ctl, int j) {
   if (threadIdx.x >= 32) return;
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x;
@@ -189,11 +192,9 @@ __device__ void givens_step(Ctl& ctl, int j, int m, double hnext) {
   const double h1 = i1 <= j ? ctl.h[i1] : 0.0;
   const double c0 = i0 < j ? ctl.cs[i0] : 1.0, s0 = i0 < j ? ctl.sn[i0] : 0.0;
   const double c1 = i1 < j ? ctl.cs[i1] : 1.0, s1 = i1 < j ? ctl.sn[i1] : 0.0;
-  const double gj = ctl.g[j];
   if (i0 <= j) ctl.Hr[(size_t)i0 * ldh + j] = h0;
   if (i1 <= j) ctl.Hr[(size_t)i1 * ldh + j] = h1;
-  if (lane == 0) ctl.Hr[(size_t)(j + 1) * ldh + j] = hnext;
-  const double hn2 = fma(hnext, hnext, warp_sum(fma(h1, h1, h0 * h0)));
+  const double hsq = warp_sum(fma(h1, h1, h0 * h0));
   const double h2 = __shfl_down_sync(full, h0, 1);  // h_{2l+2}
   // maps of rotations 2l and 2l+1 (identity past j - 1) and their composition
   const double a0 = i0 < j ? -s0 : 1.0, b0 = i0 < j ? c0 * h1 : 0.0;
@@ -206,14 +207,35 @@ __device__ void givens_step(Ctl& ctl, int j, int m, double hnext) {
     if (lane >= d) affine_compose(A, B, Ap, Bp);
   }
   double PA = __shfl_up_sync(full, A, 1), PB = __shfl_up_sync(full, B, 1);
-  if (lane == 0) { PA = 1.0; PB = 0.0; }
+  if (lane == 0) {
+    PA = 1.0;
+    PB = 0.0;
+  }
   const double t0 = __shfl_sync(full, h0, 0);
-  const double tc0 = fma(PA, t0, PB);     // t_{2l}
-  const double tc1 = fma(a0, tc0, b0);    // t_{2l+1}
+  const double tc0 = fma(PA, t0, PB);       // t_{2l}
+  const double tc1 = fma(a0, tc0, b0);      // t_{2l+1}
   const double r0 = fma(c0, tc0, s0 * h1);  // rotated h_{2l}
   const double r1 = fma(c1, tc1, s1 * h2);  // rotated h_{2l+1}
-  // a = t_j, the last entry before the new rotation
+  if (i0 < j) ctl.H[(size_t)i0 * ldh + j] = r0;
+  if (i1 < j) ctl.H[(size_t)i1 * ldh + j] = r1;
   const double a = __shfl_sync(full, (j & 1) ? tc1 : tc0, j >> 1);
+  if (lane == 0) {
+    ctl.scal[S_GIV_A] = a;
+    ctl.scal[S_GIV_HN2] = hsq;
+  }
+}
+
+// Second half: the new rotation from t_j and h_{j+1,j}, gamma update, 1 / ||w|| for the
+// lazy normalisation, and the stopping tests (Eqs. 12, 14), by warp 0.
+__device__ void givens_finish(Ctl& ctl, int j, int m, double hnext) {
+  if (threadIdx.x >= 32) return;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x;
+  const int ldh = ctl.ldh;
+  const double a = __ldcg(&ctl.scal[S_GIV_A]);
+  const double hn2 = fma(hnext, hnext, __ldcg(&ctl.scal[S_GIV_HN2]));
+  const double gj = ctl.g[j];
+  if (lane == 0) ctl.Hr[(size_t)(j + 1) * ldh + j] = hnext;
   double rho = 0.0;
   if (lane == 0 && hnext != 0.0) rho = hypot(a, hnext);
   rho = __shfl_sync(full, rho, 0);
@@ -227,12 +249,9 @@ __device__ void givens_step(Ctl& ctl, int j, int m, double hnext) {
   }
   const double c = __shfl_sync(full, q, 0), sn = __shfl_sync(full, q, 1);
   const double sig = __shfl_sync(full, q, 2);
-  // rotated column: rows < j from the scan, row j = rho (or a when hnext = 0), row j+1 = 0
-  const double hj = hnext != 0.0 ? rho : a;
-  if (i0 <= j + 1) ctl.H[(size_t)i0 * ldh + j] = i0 < j ? r0 : (i0 == j ? hj : 0.0);
-  if (i1 <= j + 1) ctl.H[(size_t)i1 * ldh + j] = i1 < j ? r1 : (i1 == j ? hj : 0.0);
-  if (lane == 0 && j + 1 >= 64) ctl.H[(size_t)(j + 1) * ldh + j] = 0.0;  // row 64 (m = 64)
   if (lane == 0) {
+    ctl.H[(size_t)j * ldh + j] = hnext != 0.0 ? rho : a;
+    ctl.H[(size_t)(j + 1) * ldh + j] = 0.0;
     const double sg1 = -sn * gj, sg0 = c * gj;
     ctl.cs[j] = c;
     ctl.sn[j] = sn;
@@ -257,6 +276,12 @@ __device__ void givens_step(Ctl& ctl, int j, int m, double hnext) {
     if (j + 1 >= m) done = true;
     if (done) ctl.flags[F_CYCLE_DONE] = 1;
   }
+}
+
+__device__ void givens_step(Ctl& ctl, int j, int m, double hnext) {
+  givens_prep(ctl, j);
+  __syncwarp();
+  givens_finish(ctl, j, m, hnext);
 }
 
 // --------------------------------------------------------------------------------------
