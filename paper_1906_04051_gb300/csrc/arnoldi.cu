@@ -18,6 +18,8 @@
 // true residual r = b - A x in FP64 (Eq. 15), which also starts the next cycle.
 //
 // All floating-point reductions are formed in a fixed order (deterministic).
+#include <utility>
+
 #include "internal.h"
 #include "kernels.cuh"
 
@@ -35,6 +37,8 @@ __global__ void __launch_bounds__(kThreads)
     k_spmv_step(int N, const int* __restrict__ rowptr, const int* __restrict__ col,
                 const TA* __restrict__ val, const TV* __restrict__ x, int j,
                 const TACC* __restrict__ sdefl, TACC* __restrict__ w, Ctl ctl) {
+  pdl_wait();
+  pdl_trigger();
   if (ctl.flags[F_CYCLE_DONE]) return;
   const TACC sigma = (TACC)ctl.sigma[j];
   auto g = [&](int c) -> TACC {
@@ -67,43 +71,76 @@ __global__ void __launch_bounds__(kThreads)
 
 // The same product with A in diagonal storage: row i sums dval[q][i] x[i + off_q] over the
 // nd diagonals (coalesced loads of the values and of the shifted x; an index past either
-// end is clamped to a valid row, where the stored value is 0), plus the A W row.
+// end is clamped to a valid row, where the stored value is 0), plus the A W row.  Each
+// thread takes kDiaRows rows (independent FMA chains).  With deflation the kernels
+// between the step's basis column and this SpMV (U^T v, T^-1 c) do not write x or the
+// operator, so the diagonal part runs before pdl_wait() and overlaps the coarse solve;
+// only the A W part needs its output s'.
+constexpr int kDiaRows = 4;
+
+template <typename TA, typename TV, typename TACC>
+__device__ __forceinline__ TACC dia_row(int i, int N, const int* soff, int nd, long long ldd,
+                                        const TA* __restrict__ dval, const TV* __restrict__ x) {
+  TACC acc = 0;
+  int q = 0;
+  for (; q + 3 < nd; q += 4) {
+    int c[4];
+    TACC a[4], xv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) c[u] = min(max(i + soff[q + u], 0), N - 1);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a[u] = (TACC)__ldg(dval + (q + u) * ldd + i);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) xv[u] = ld_as<TACC, TV>(x + c[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc += a[u] * xv[u];
+  }
+  for (; q < nd; ++q) {
+    const int c = min(max(i + soff[q], 0), N - 1);
+    acc += (TACC)__ldg(dval + q * ldd + i) * ld_as<TACC, TV>(x + c);
+  }
+  return acc;
+}
+
 template <typename TA, typename TV, typename TACC, bool DEFL>
 __global__ void __launch_bounds__(kThreads)
     k_spmv_dia(int N, DiaOffsets dia, long long ldd, const TA* __restrict__ dval,
                const TV* __restrict__ x, int j, Defl d, const TA* __restrict__ auval,
                const TACC* __restrict__ sdefl, TACC* __restrict__ w, Ctl ctl) {
-  if (ctl.flags[F_CYCLE_DONE]) return;
   __shared__ int soff[kMaxDiag];
 #pragma unroll
   for (int q = 0; q < kMaxDiag; ++q)
     if ((int)threadIdx.x == q) soff[q] = dia.off[q];
   __syncthreads();
-  const TACC sigma = (TACC)ctl.sigma[j];
   const int nd = dia.nd;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    // one FMA chain per row (no partial-sum combines: the FP64 pipe is the bound here,
-    // and other warps hide the chain's latency)
-    TACC acc = 0;
-    if constexpr (DEFL) acc = au_row<TA, TACC>(i, d.aurp, d.aucol, auval, sdefl);
-    int q = 0;
-    for (; q + 3 < nd; q += 4) {
-      int c[4];
-      TACC a[4], xv[4];
+  const int i0 = blockIdx.x * blockDim.x * kDiaRows + threadIdx.x;
+  TACC acc[kDiaRows];
+  if constexpr (DEFL) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) c[u] = min(max(i + soff[q + u], 0), N - 1);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = (TACC)__ldg(dval + (q + u) * ldd + i);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) xv[u] = ld_as<TACC, TV>(x + c[u]);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) acc += a[u] * xv[u];
+    for (int u = 0; u < kDiaRows; ++u) {
+      const int i = i0 + u * blockDim.x;
+      acc[u] = i < N ? dia_row<TA, TV, TACC>(i, N, soff, nd, ldd, dval, x) : (TACC)0;
     }
-    for (; q < nd; ++q) {
-      const int c = min(max(i + soff[q], 0), N - 1);
-      acc += (TACC)__ldg(dval + q * ldd + i) * ld_as<TACC, TV>(x + c);
+  }
+  pdl_wait();
+  pdl_trigger();
+  if (ctl.flags[F_CYCLE_DONE]) return;
+  if constexpr (!DEFL) {
+#pragma unroll
+    for (int u = 0; u < kDiaRows; ++u) {
+      const int i = i0 + u * blockDim.x;
+      acc[u] = i < N ? dia_row<TA, TV, TACC>(i, N, soff, nd, ldd, dval, x) : (TACC)0;
     }
-    w[i] = sigma * acc;
+  }
+  const TACC sigma = (TACC)ctl.sigma[j];
+#pragma unroll
+  for (int u = 0; u < kDiaRows; ++u) {
+    const int i = i0 + u * blockDim.x;
+    if (i < N) {
+      TACC v = acc[u];
+      if constexpr (DEFL) v += au_row<TA, TACC>(i, d.aurp, d.aucol, auval, sdefl);
+      w[i] = sigma * v;
+    }
   }
 }
 
@@ -112,7 +149,6 @@ template <typename TV, typename TACC>
 __global__ void __launch_bounds__(kThreads)
     k_pass1(int N, const TV* __restrict__ V, long long ldv, int k, int TR,
             const TACC* __restrict__ w, Ctl ctl) {
-  if (ctl.flags[F_CYCLE_DONE]) return;
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ uint64_t bars[kMaxStages];
   __shared__ double swarp[kSlices * kSliceCols];
@@ -125,7 +161,8 @@ __global__ void __launch_bounds__(kThreads)
   TACC acc[kSliceCols];
 #pragma unroll
   for (int i = 0; i < kSliceCols; ++i) acc[i] = 0;
-  const bool ok = ring_run(R, N, V, ldv, w, ctl, [&](int st, long long) {
+  // w is the predecessor's (the SpMV's) output: its slices are copied after the wait
+  const bool ok = ring_run(R, N, V, ldv, w, ctl, false, [] {}, [&](int st, long long) {
 #define GG_P1(NW) tile_dot<NW, TV, TACC>(acc, R.vt(st), R.wt(st), TR, warp, lane)
     GG_SLICE_SWITCH(nw, GG_P1)
 #undef GG_P1
@@ -145,7 +182,6 @@ template <typename TV, typename TACC>
 __global__ void __launch_bounds__(kThreads)
     k_pass2(int N, const TV* __restrict__ V, long long ldv, int k, int TR,
             TACC* __restrict__ w, Ctl ctl) {
-  if (ctl.flags[F_CYCLE_DONE]) return;
   constexpr int VN = Vec<TV>::n;
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ uint64_t bars[kMaxStages];
@@ -157,7 +193,6 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ __align__(16) TACC sw2[256];
   const size_t sb = ring_stage_bytes(k, TR, sizeof(TV), sizeof(TACC));
   const Ring<TV, TACC> R{smraw, bars, k, TR, ring_stages(sb), sb};
-  for (int c = threadIdx.x; c < k; c += blockDim.x) scoef[c] = (TACC)ctl.coef[c];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = slice_cols(k, warp, kSlices);
   const int P = update_splits<TACC>(TR, VN);
@@ -165,7 +200,11 @@ __global__ void __launch_bounds__(kThreads)
   TACC acc[kSliceCols];
 #pragma unroll
   for (int i = 0; i < kSliceCols; ++i) acc[i] = 0;
-  const bool ok = ring_run(R, N, V, ldv, (const TACC*)w, ctl, [&](int st, long long r0) {
+  // w (the SpMV's output) is final before the wait; the coefficients are pass 1's output
+  auto post = [&] {
+    for (int c = threadIdx.x; c < k; c += blockDim.x) scoef[c] = (TACC)ctl.coef[c];
+  };
+  const bool ok = ring_run(R, N, V, ldv, (const TACC*)w, ctl, true, post, [&](int st, long long r0) {
     const TV* sV = R.vt(st);
     const TACC* sw = R.wt(st);
     tile_update<TV, TACC>(sV, TR, k, scoef, spart, P);
@@ -200,7 +239,6 @@ template <typename TV, typename TACC>
 __global__ void __launch_bounds__(kThreads)
     k_pass3(int N, TV* __restrict__ V, long long ldv, int k, int TR,
             const TACC* __restrict__ w, Ctl ctl, int m) {
-  if (ctl.flags[F_CYCLE_DONE]) return;
   constexpr int VN = Vec<TV>::n;
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ uint64_t bars[kMaxStages];
@@ -211,15 +249,19 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ double tot[1];
   const size_t sb = ring_stage_bytes(k, TR, sizeof(TV), sizeof(TACC));
   const Ring<TV, TACC> R{smraw, bars, k, TR, ring_stages(sb), sb};
-  // the rotations of Eq. 12 that do not need h_{j+1,j}, off the critical path: the last
-  // block has the fewest tiles when they do not divide evenly
-  if (blockIdx.x == gridDim.x - 1) givens_prep(ctl, k - 1);
-  for (int c = threadIdx.x; c < k; c += blockDim.x) scoef[c] = (TACC)ctl.coef[c];
+  // after the wait: pass 2's coefficients, and the rotations of Eq. 12 that do not need
+  // h_{j+1,j}, off the critical path (the last block has the fewest tiles when they do
+  // not divide evenly)
+  auto post = [&] {
+    for (int c = threadIdx.x; c < k; c += blockDim.x) scoef[c] = (TACC)ctl.coef[c];
+    if (blockIdx.x == gridDim.x - 1) givens_prep(ctl, k - 1);
+  };
   const int P = update_splits<TACC>(TR, VN);
   const int ng = TR / VN;
   TV* __restrict__ vout = V + (size_t)k * ldv;
   TACC nrm = 0;
-  const bool ok = ring_run(R, N, (const TV*)V, ldv, w, ctl, [&](int st, long long r0) {
+  // w is pass 2's output: its slices are copied after the wait
+  const bool ok = ring_run(R, N, (const TV*)V, ldv, w, ctl, false, post, [&](int st, long long r0) {
     const TV* sV = R.vt(st);
     const TACC* sw = R.wt(st);
     tile_update<TV, TACC>(sV, TR, k, scoef, spart, P);
@@ -262,18 +304,28 @@ template <typename TX>
 __global__ void __launch_bounds__(kThreads)
     k_aggsum(const TX* __restrict__ x, Defl d, double* __restrict__ cpart, const int* flags,
              int skip_slot) {
-  if (skip_slot >= 0 && flags[skip_slot]) return;
   const int lane = threadIdx.x & 31;
   const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (p >= d.npieces) return;
-  const int s = d.piece_start[p], e = d.piece_start[p + 1];
+  const bool live = p < d.npieces;
+  const int s = live ? d.piece_start[p] : 0, e = live ? d.piece_start[p + 1] : 0;
+  // the permutation is static: the first batch of indexes is loaded before the wait
+  int q[32];
+#pragma unroll
+  for (int u = 0; u < 32; ++u) {
+    const int t = s + lane + 32 * u;
+    q[u] = t < e ? __ldg(d.perm + t) : -1;
+  }
+  pdl_wait();
+  pdl_trigger();
+  if (!live || (skip_slot >= 0 && flags[skip_slot])) return;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int t0 = s; t0 < e; t0 += 32 * 32) {
-    int q[32];
+    if (t0 != s) {
 #pragma unroll
-    for (int u = 0; u < 32; ++u) {
-      const int t = t0 + lane + 32 * u;
-      q[u] = t < e ? __ldg(d.perm + t) : -1;
+      for (int u = 0; u < 32; ++u) {
+        const int t = t0 + lane + 32 * u;
+        q[u] = t < e ? __ldg(d.perm + t) : -1;
+      }
     }
     double v[32];
 #pragma unroll
@@ -294,12 +346,28 @@ constexpr int kCoarseStage = 4096;  // piece sums staged in shared memory (32 KB
 __global__ void __launch_bounds__(kThreads)
     k_coarse(Defl d, const double* __restrict__ cpart, const double* __restrict__ scale_ptr,
              Ctl ctl, int skip_slot, int proj) {
-  if (skip_slot >= 0 && ctl.flags[skip_slot]) return;
   extern __shared__ double sc[];                 // r entries
   __shared__ double spc[kCoarseStage];
+  const int r = d.r;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  // T^-1 is static: the first 32 entries per lane of the warp's first row are loaded
+  // before the wait
+  double t[32];
+  {
+    const double* row = d.tinv + (size_t)(gw < r ? gw : 0) * r;
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
+      const int b = lane + 32 * u;
+      t[u] = (gw < r && b < r) ? __ldg(row + b) : 0.0;
+    }
+  }
+  pdl_wait();
+  pdl_trigger();
+  if (skip_slot >= 0 && ctl.flags[skip_slot]) return;
   const double scale = scale_ptr ? *scale_ptr : 1.0;
   const double mu = ctl.scal[S_MU];
-  const int r = d.r;
   const bool staged = d.npieces <= kCoarseStage;
   if (staged)
     for (int p = threadIdx.x; p < d.npieces; p += blockDim.x) spc[p] = __ldg(cpart + p);
@@ -314,18 +382,16 @@ __global__ void __launch_bounds__(kThreads)
     sc[a] = scale * us * sum;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int a = gw; a < r; a += nw) {
     const double* row = d.tinv + (size_t)a * r;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int b0 = 0; b0 < r; b0 += 32 * 32) {
-      double t[32];
+      if (a != gw || b0 != 0) {
 #pragma unroll
-      for (int u = 0; u < 32; ++u) {
-        const int b = b0 + lane + 32 * u;
-        t[u] = b < r ? __ldg(row + b) : 0.0;
+        for (int u = 0; u < 32; ++u) {
+          const int b = b0 + lane + 32 * u;
+          t[u] = b < r ? __ldg(row + b) : 0.0;
+        }
       }
 #pragma unroll
       for (int u = 0; u < 32; ++u) {
@@ -352,6 +418,8 @@ template <typename TA, typename TACC>
 __global__ void __launch_bounds__(kThreads)
     k_proj_sub(int N, Defl d, const TA* __restrict__ auval, const TACC* __restrict__ sdefl,
                TACC* __restrict__ vec, Ctl ctl) {
+  pdl_wait();
+  pdl_trigger();
   if (ctl.flags[F_CYCLE_DONE]) return;
   for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < N; row += gridDim.x * blockDim.x)
     vec[row] -= au_row<TA, TACC>(row, d.aurp, d.aucol, auval, sdefl);
@@ -548,6 +616,25 @@ inline int balanced(int tiles, int gmax) {
   return (tiles + per - 1) / per;
 }
 
+// Launch with programmatic stream serialisation (the kernel may start while its
+// predecessor finishes; see pdl_wait) when pdl, else as a plain launch.  Launch errors
+// surface through cudaGetLastError like those of <<<>>>.
+template <typename... Exp, typename... Act>
+void launch_k(bool pdl, void (*kern)(Exp...), int grid, int block, size_t smem,
+              cudaStream_t st, Act&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, std::forward<Act>(args)...);
+}
+
 template <typename TV, typename TA, typename TACC>
 struct Kern {
   struct Grids {
@@ -615,14 +702,15 @@ struct Kern {
   // piece sums in the cpart buffer
   template <typename TX>
   static void coarse(const CycleArgs& a, const TX* x, const double* scale, int skip, int proj,
-                     cudaStream_t st) {
+                     cudaStream_t st, bool pdl = false) {
     const Defl& d = a.op.defl;
     const int gp = d.npieces > 0 ? (d.npieces + 7) / 8 : 1;
-    k_aggsum<TX><<<gp, kThreads, 0, st>>>(x, d, a.ctl.cpart, a.ctl.flags, skip);
+    launch_k(pdl, k_aggsum<TX>, gp, kThreads, 0, st, x, d, a.ctl.cpart, (const int*)a.ctl.flags,
+             skip);
     const int rows = (d.r + 7) / 8;
     const int gc = rows < 2 * a.sms ? rows : 2 * a.sms;
-    k_coarse<<<gc > 0 ? gc : 1, kThreads, sizeof(double) * d.r, st>>>(d, a.ctl.cpart, scale,
-                                                                       a.ctl, skip, proj);
+    launch_k(pdl, k_coarse, gc > 0 ? gc : 1, kThreads, sizeof(double) * d.r, st, d,
+             (const double*)a.ctl.cpart, scale, a.ctl, skip, proj);
   }
 
   static cudaError_t phase(const CycleArgs& a, int ph, int j, bool defl, double* x,
@@ -638,63 +726,57 @@ struct Kern {
     int nl = 0;
     switch (ph) {
       case PH_SPMV: {
-        const int tiles = (N + kSpmvRows - 1) / kSpmvRows;
         const TV* xj = V + (size_t)j * a.ldv;
+        const bool pdl = a.pdl != 0;
         const int gd = grid_for((N + kThreads - 1) / kThreads, 1, 8 * sms);
         if (a.op.dia.nd > 0) {  // banded A: diagonal storage
+          const int gdd = (N + kThreads * kDiaRows - 1) / (kThreads * kDiaRows);
           if (defl && !a.proj)
-            k_spmv_dia<TA, TV, TACC, true><<<gd, kThreads, 0, st>>>(
-                N, a.op.dia, a.op.ldd, dvals(a), xj, j, d, auvals(a), sdefl(a), w, a.ctl);
+            launch_k(pdl, k_spmv_dia<TA, TV, TACC, true>, gdd, kThreads, 0, st, N, a.op.dia,
+                     a.op.ldd, dvals(a), xj, j, d, auvals(a), sdefl(a), w, a.ctl);
           else
-            k_spmv_dia<TA, TV, TACC, false><<<gd, kThreads, 0, st>>>(
-                N, a.op.dia, a.op.ldd, dvals(a), xj, j, d, auvals(a), sdefl(a), w, a.ctl);
-          nl = 1;
-          if (a.proj) {  // w = P A v_j
-            coarse(a, (const TACC*)w, nullptr, F_CYCLE_DONE, 1, st);
-            k_proj_sub<TA, TACC><<<balanced(tiles, g.spmv_d), kSpmvRows, 0, st>>>(
-                N, d, auvals(a), sdefl(a), w, a.ctl);
-            nl = 4;
-          }
-        } else if (a.proj) {  // w = P A v_j = A v_j - A U T^-1 U^T A v_j
-          k_spmv_step<TA, TV, TACC, false><<<gd, kThreads, 0, st>>>(
-              N, a.op.rowptr, a.op.col, vals(a), xj, j, sdefl(a), w, a.ctl);
-          coarse(a, (const TACC*)w, nullptr, F_CYCLE_DONE, 1, st);
-          k_proj_sub<TA, TACC><<<balanced(tiles, g.spmv_d), kSpmvRows, 0, st>>>(
-              N, d, auvals(a), sdefl(a), w, a.ctl);
+            launch_k(pdl, k_spmv_dia<TA, TV, TACC, false>, gdd, kThreads, 0, st, N, a.op.dia,
+                     a.op.ldd, dvals(a), xj, j, d, auvals(a), sdefl(a), w, a.ctl);
+        } else if (defl && !a.proj) {
+          launch_k(pdl, k_spmv_step<TA, TV, TACC, true>, gd, kThreads, 0, st, N, a.op.xrp,
+                   a.op.xcol, xvals(a), xj, j, sdefl(a), w, a.ctl);
+        } else {
+          launch_k(pdl, k_spmv_step<TA, TV, TACC, false>, gd, kThreads, 0, st, N, a.op.rowptr,
+                   a.op.col, vals(a), xj, j, sdefl(a), w, a.ctl);
+        }
+        nl = 1;
+        if (a.proj) {  // w = P A v_j = A v_j - A U T^-1 U^T A v_j
+          coarse(a, (const TACC*)w, nullptr, F_CYCLE_DONE, 1, st, pdl);
+          launch_k(pdl, k_proj_sub<TA, TACC>, g.spmv_d, kThreads, 0, st, N, d, auvals(a),
+                   sdefl(a), w, a.ctl);
           nl = 4;
-        } else if (defl)
-          k_spmv_step<TA, TV, TACC, true><<<gd, kThreads, 0, st>>>(
-              N, a.op.xrp, a.op.xcol, xvals(a), xj, j, sdefl(a), w, a.ctl);
-        else
-          k_spmv_step<TA, TV, TACC, false><<<gd, kThreads, 0, st>>>(
-              N, a.op.rowptr, a.op.col, vals(a), xj, j, sdefl(a), w, a.ctl);
-        if (!a.proj) nl = 1;
+        }
         break;
       }
       case PH_DOT1: {
         const int tr = g.tr[k];
-        k_pass1<TV, TACC><<<grid_for((N + tr - 1) / tr, 1, g.p1[k]), kThreads, ring_smem(k), st>>>(
-            N, V, a.ldv, k, tr, w, a.ctl);
+        launch_k(a.pdl != 0, k_pass1<TV, TACC>, grid_for((N + tr - 1) / tr, 1, g.p1[k]),
+                 kThreads, ring_smem(k), st, N, V, a.ldv, k, tr, (const TACC*)w, a.ctl);
         nl = 1;
         break;
       }
       case PH_UPD1DOT2: {
         const int tr = g.tr[k];
-        k_pass2<TV, TACC><<<grid_for((N + tr - 1) / tr, 1, g.p2[k]), kThreads, ring_smem(k), st>>>(
-            N, V, a.ldv, k, tr, w, a.ctl);
+        launch_k(a.pdl != 0, k_pass2<TV, TACC>, grid_for((N + tr - 1) / tr, 1, g.p2[k]),
+                 kThreads, ring_smem(k), st, N, V, a.ldv, k, tr, w, a.ctl);
         nl = 1;
         break;
       }
       case PH_UPD2NORM: {
         const int tr = g.tr[k];
-        k_pass3<TV, TACC><<<grid_for((N + tr - 1) / tr, 1, g.p3[k]), kThreads, ring_smem(k), st>>>(
-            N, Vm, a.ldv, k, tr, w, a.ctl, a.m);
+        launch_k(a.pdl != 0, k_pass3<TV, TACC>, grid_for((N + tr - 1) / tr, 1, g.p3[k]),
+                 kThreads, ring_smem(k), st, N, Vm, a.ldv, k, tr, (const TACC*)w, a.ctl, a.m);
         nl = 1;
         break;
       }
       case PH_DEFL: {  // U^T v_j and the correction for column j
         const TV* xj = V + (size_t)j * a.ldv;
-        coarse(a, xj, nullptr, F_CYCLE_DONE, 0, st);  // s' = s / sigma_j
+        coarse(a, xj, nullptr, F_CYCLE_DONE, 0, st, a.pdl != 0);  // s' = s / sigma_j
         nl = 2;
         break;
       }

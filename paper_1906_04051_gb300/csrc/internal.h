@@ -85,6 +85,7 @@ struct CycleArgs {
   int proj;              // deflation projector instead of the EBP preconditioner
   int sms;               // multiprocessors of the device
   int grid_small;        // blocks of the coarse GEMV
+  int pdl;               // step kernels with programmatic dependent launch
 };
 
 // Phases of a solve; each launch_phase call enqueues the kernels of one phase.

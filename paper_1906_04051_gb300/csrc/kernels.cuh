@@ -15,6 +15,19 @@ namespace gg {
 
 namespace {
 
+// Programmatic dependent launch (the step kernels are launched with programmatic stream
+// serialisation): pdl_wait() blocks until the previous kernel in the stream has
+// completed and its writes are visible; pdl_trigger() lets the next kernel start its
+// own prologue.  Each step kernel triggers only after its own wait, so when a kernel
+// starts, every kernel before its immediate predecessor has completed: the prologue
+// before pdl_wait() may read anything the predecessor does not write (static operator
+// data, basis columns of earlier steps), never its outputs.  Launched without the
+// attribute, both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 constexpr int kSpmvRows = 256;   // rows per SpMV tile (one per thread)
 constexpr int kSpmvCap = 2560;   // CSR entries staged in shared memory per chunk
 
@@ -306,9 +319,10 @@ struct Ring {
   __device__ TACC* wt(int st) const {
     return reinterpret_cast<TACC*>(base + (size_t)st * stage_bytes + (size_t)k * TR * sizeof(TV));
   }
-  // warp 0: tile starting at row r0 into stage st (lane 0 announces the bytes, the lanes
-  // issue the column segments)
-  __device__ void issue(int st, long long r0, const TV* V, long long ldv, const TACC* w) const {
+  // warp 0: tile starting at row r0 into stage st (lane 0 announces the bytes of the whole
+  // stage, the lanes issue the column segments; the slice of w too when with_w)
+  __device__ void issue_v(int st, long long r0, const TV* V, long long ldv, const TACC* w,
+                          bool with_w) const {
     const int lane = threadIdx.x & 31;
     const uint32_t vb = (uint32_t)(TR * sizeof(TV)), wb = (uint32_t)(TR * sizeof(TACC));
     if (lane == 0) mbar_arrive_expect_tx(&bars[st], (uint32_t)k * vb + wb);
@@ -316,7 +330,12 @@ struct Ring {
     TV* dst = vt(st);
     for (int c = lane; c < k; c += 32)
       bulk_g2s(dst + (size_t)c * TR, V + (size_t)c * ldv + r0, vb, &bars[st]);
-    if (lane == 0) bulk_g2s(wt(st), w + r0, wb, &bars[st]);
+    if (with_w && lane == 0) bulk_g2s(wt(st), w + r0, wb, &bars[st]);
+  }
+  // warp 0: the slice of w of a stage whose columns were issued without it
+  __device__ void issue_w(int st, long long r0, const TACC* w) const {
+    if ((threadIdx.x & 31) == 0)
+      bulk_g2s(wt(st), w + r0, (uint32_t)(TR * sizeof(TACC)), &bars[st]);
   }
 };
 
@@ -331,31 +350,56 @@ __host__ __device__ inline int ring_stages(size_t stage_bytes) {
 }
 
 // Streams this block's tiles (blockIdx.x, +gridDim.x, ...) through the ring and calls
-// body(stage, r0) for each.  Returns false (after recording GMRES_ERR_TIMEOUT and waiting,
-// with a bound, for this block's copies still in flight) if a copy never completes.
-template <typename TV, typename TACC, typename F>
+// body(stage, r0) for each.  The copies of the basis columns for the first stages are
+// issued before pdl_wait() (the columns 0..k-1 are final by then); the slice of w joins
+// them before the wait too when w_early (w is not written by the predecessor), after it
+// otherwise.  After the wait, post_wait() runs on all threads (loads of the
+// predecessor's outputs); when the cycle has ended the copies in flight are drained and
+// false is returned, as it is (after recording GMRES_ERR_TIMEOUT and draining, with a
+// bound) when a copy never completes.
+template <typename TV, typename TACC, typename F, typename PW>
 __device__ bool ring_run(const Ring<TV, TACC>& R, int N, const TV* V, long long ldv,
-                         const TACC* w, Ctl& ctl, F&& body) {
+                         const TACC* w, Ctl& ctl, bool w_early, PW&& post_wait, F&& body) {
+  __shared__ int s_pre;
   const int tiles = (N + R.TR - 1) / R.TR;
   const int nt = (int)blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int first = nt < R.S ? nt : R.S;
+  auto r0_of = [&](int i) { return (long long)(blockIdx.x + (size_t)i * gridDim.x) * R.TR; };
   if (threadIdx.x == 0) {
     for (int st = 0; st < R.S; ++st) mbar_init(&R.bars[st], 1);
     mbar_fence_init();
+    // a cycle that has visibly ended already needs no prefetch (a stale read only costs
+    // a wasted prefetch; the decision below is taken after the wait)
+    s_pre = *(volatile const int*)&ctl.flags[F_CYCLE_DONE] ? 0 : 1;
   }
   __syncthreads();
-  if (threadIdx.x < 32)
-    for (int i = 0; i < nt && i < R.S; ++i)
-      R.issue(i, (long long)(blockIdx.x + (size_t)i * gridDim.x) * R.TR, V, ldv, w);
+  const bool pre = s_pre != 0;
+  if (pre && threadIdx.x < 32)
+    for (int i = 0; i < first; ++i) R.issue_v(i, r0_of(i), V, ldv, w, w_early);
+  pdl_wait();
+  pdl_trigger();
+  const bool done = ctl.flags[F_CYCLE_DONE] != 0;
+  if (pre && !w_early && threadIdx.x < 32)
+    for (int i = 0; i < first; ++i) R.issue_w(i, r0_of(i), w);
+  if (done) {
+    if (pre)
+      for (int i = 0; i < first; ++i) mbar_wait(&R.bars[i], 0u);
+    __syncthreads();
+    return false;
+  }
+  if (!pre && threadIdx.x < 32)
+    for (int i = 0; i < first; ++i) R.issue_v(i, r0_of(i), V, ldv, w, true);
+  post_wait();
+  __syncthreads();
   int i = 0;
   bool ok = true;
   for (; i < nt; ++i) {
     const int st = i % R.S;
     ok = __syncthreads_and(mbar_wait(&R.bars[st], (uint32_t)((i / R.S) & 1)));
     if (!ok) break;
-    body(st, (long long)(blockIdx.x + (size_t)i * gridDim.x) * R.TR);
+    body(st, r0_of(i));
     __syncthreads();
-    if (threadIdx.x < 32 && i + R.S < nt)
-      R.issue(st, (long long)(blockIdx.x + (size_t)(i + R.S) * gridDim.x) * R.TR, V, ldv, w);
+    if (threadIdx.x < 32 && i + R.S < nt) R.issue_v(st, r0_of(i + R.S), V, ldv, w, true);
   }
   if (!ok) {
     for (int j = i; j < nt && j < i + R.S; ++j)

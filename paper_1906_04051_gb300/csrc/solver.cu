@@ -87,6 +87,7 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
   a.m = m;
   a.sms = h->sms;
   a.grid_small = h->r > 0 ? grid_for(h->r, 8, h->sms) : 1;
+  a.pdl = h->prof_on ? 0 : 1;  // per-phase events would serialise the launches anyway
   a.proj = (h->r > 0 && h->opts.deflation_mode == GMRES_DEFL_PROJECTOR) ? 1 : 0;
 
   const bool ebp = h->r > 0 && h->opts.deflation_mode == GMRES_DEFL_EBP;
@@ -272,6 +273,7 @@ gmres_status run_noalloc(gmres_s* h, OpHost& o, const double* b, const double* x
   a.m = m;
   a.sms = h->sms;
   a.grid_small = h->r > 0 ? grid_for(h->r, 8, h->sms) : 1;
+  a.pdl = h->prof_on ? 0 : 1;  // per-phase events would serialise the launches anyway
   a.proj = (h->r > 0 && h->opts.deflation_mode == GMRES_DEFL_PROJECTOR) ? 1 : 0;
 
   const bool ebp = h->r > 0 && h->opts.deflation_mode == GMRES_DEFL_EBP;
