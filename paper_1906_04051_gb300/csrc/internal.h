@@ -29,7 +29,8 @@ cudaError_t launch_agg_perm(int n, int r, const int* agg, int* counts, int* aggp
 cudaError_t launch_coarse_T(int r, const int* rowptr, const int* col, const double* val,
                             const int* agg, const int* perm, const int* aggptr,
                             const double* uscale, double* T, cudaStream_t st);
-cudaError_t launch_gauss_jordan(int r, const double* T, double* G, double* fac, double* Tinv,
+size_t gj_aux_bytes(int r);
+cudaError_t launch_gauss_jordan(int r, const double* T, double* G, void* aux, double* Tinv,
                                 double* TinvT, int* err, cudaStream_t st);
 cudaError_t launch_norm_inf(int n, const int* rowptr, const double* val,
                             unsigned long long* out, cudaStream_t st);

@@ -171,108 +171,207 @@ __global__ void k_T_rows(int r, const int* __restrict__ rowptr, const int* __res
   }
 }
 
-// ---- Gauss-Jordan inverse of T on the augmented r x 2r matrix G = [T | I] ----
-__global__ void k_gj_init(int r, const double* __restrict__ T, double* __restrict__ G) {
+// ---- T^-1 by Gauss-Jordan elimination with partial pivoting on G = [T | I] (r x 2r,
+// row-major), without row exchanges: the pivot of step k is the row p_k, among the rows
+// not yet used as pivots, with the largest |G_ik| (the lowest index on ties).  Row p_k is
+// normalised lazily (its factor 1/G_{p_k k} is kept as a pending row scale and applied
+// when the row is next updated), and its identity entry is placed in right-hand column
+// r + k when the row becomes the pivot, so the right-hand columns in use at step k are
+// exactly [r, r + k] and every step updates r entries per row.  With P the pivot
+// permutation (P e_k = e_{p_k}) the right half ends as P T^-1 P, from which T^-1 is read
+// back.  Each step is one kernel; every block reduces the previous step's per-block
+// pivot candidates itself (deterministic: fixed tie rule, fixed update order).
+constexpr int kGjMaxBlocks = 1024;  // blocks of a Gauss-Jordan step
+
+struct GjAux {
+  double* pinv;     // r: 1 / pivot of step k
+  double* pscale;   // r: pending row scale (1 unless the row was the last pivot)
+  double* cval;     // per-block pivot candidates, two buffers (by step parity)
+  int* piv;         // r: pivot row of step k
+  int* slot;        // r: step at which row i was the pivot
+  int* used;        // r: row i has been a pivot
+  int* cidx;
+  int* err;
+};
+
+__global__ void k_gj_init(int r, const double* __restrict__ T, double* __restrict__ G,
+                          GjAux x) {
   const long long tot = 2LL * r * r;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
        t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t / (2 * r)), j = (int)(t % (2 * r));
-    G[t] = j < r ? T[(size_t)i * r + j] : (j - r == i ? 1.0 : 0.0);
+    G[t] = j < r ? T[(size_t)i * r + j] : 0.0;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < r; i += gridDim.x * blockDim.x) {
+    x.pscale[i] = 1.0;
+    x.used[i] = 0;
   }
 }
 
-// Pivot step for column k, run by one block: the largest |G_ik| over i >= k (first on
-// ties; candidates come from pmax/pidx partials when given, else from a scan), row swap
-// k <-> p, scaling of row k, and the elimination factors fac_i = G_ik (fac_k = 0).
-__device__ void gj_pivot_block(int r, int k, double* __restrict__ G, double* __restrict__ fac,
-                               int* __restrict__ err) {
+// (value, index) argmax: larger value, then lower index
+__device__ __forceinline__ void argmax_merge(double& v, int& i, double ov, int oi) {
+  if (ov > v || (ov == v && oi < i)) {
+    v = ov;
+    i = oi;
+  }
+}
+
+// block-wide argmax; the result is valid in thread 0
+__device__ void block_argmax(double& v, int& i) {
   __shared__ double sv[32];
   __shared__ int si[32];
-  __shared__ int s_piv;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int ld = 2 * r;
-  double best = -1.0;
-  int bi = r;
-  for (int i = k + threadIdx.x; i < r; i += blockDim.x) {
-    const double v = fabs(__ldcg(&G[(size_t)i * ld + k]));
-    if (v > best) { best = v; bi = i; }
-  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+    argmax_merge(v, i, ov, oi);
   }
-  if (lane == 0) { sv[warp] = best; si[warp] = bi; }
+  __syncthreads();
+  if (lane == 0) {
+    sv[warp] = v;
+    si[warp] = i;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < nw ? sv[lane] : -1.0;
+    i = lane < nw ? si[lane] : 0x7fffffff;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+      argmax_merge(v, i, ov, oi);
+    }
+  }
+}
+
+// pivot of column 0: per-block candidate slots of the "previous step" (buffer 1), with
+// the column's argmax in slot 0 and no candidate elsewhere (one block)
+__global__ void k_gj_first(int r, const double* __restrict__ G, GjAux x, int nslots) {
+  double v = -1.0;
+  int i = 0x7fffffff;
+  for (int t = threadIdx.x; t < r; t += blockDim.x)
+    argmax_merge(v, i, fabs(G[(size_t)t * 2 * r]), t);
+  block_argmax(v, i);
+  double* cv = x.cval + kGjMaxBlocks;
+  int* ci = x.cidx + kGjMaxBlocks;
+  for (int b = threadIdx.x; b < nslots; b += blockDim.x) {
+    cv[b] = -1.0;
+    ci[b] = 0x7fffffff;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double b = -1.0;
-    int p = r;
-    for (int w = 0; w < nw; ++w)
-      if (sv[w] > b || (sv[w] == b && si[w] < p)) { b = sv[w]; p = si[w]; }
-    if (!(b > 0.0) || p >= r) { atomicOr(err, 8); p = k; }
-    s_piv = p;
+    cv[0] = v;
+    ci[0] = i;
   }
-  __syncthreads();
-  const int p = s_piv;
-  if (p != k)
-    for (int j = threadIdx.x; j < ld; j += blockDim.x) {
-      const double t = __ldcg(&G[(size_t)k * ld + j]);
-      G[(size_t)k * ld + j] = __ldcg(&G[(size_t)p * ld + j]);
-      G[(size_t)p * ld + j] = t;
-    }
-  __syncthreads();
-  const double piv = __ldcg(&G[(size_t)k * ld + k]);
-  const double inv = (piv != 0.0) ? 1.0 / piv : 0.0;
-  __syncthreads();
-  for (int j = threadIdx.x; j < ld; j += blockDim.x)
-    if (j != k) G[(size_t)k * ld + j] = __ldcg(&G[(size_t)k * ld + j]) * inv;
-  __syncthreads();
-  if (threadIdx.x == 0) G[(size_t)k * ld + k] = 1.0;
-  for (int i = threadIdx.x; i < r; i += blockDim.x)
-    fac[i] = (i == k) ? 0.0 : __ldcg(&G[(size_t)i * ld + k]);
 }
 
-__global__ void k_gj_pivot0(int r, double* __restrict__ G, double* __restrict__ fac,
-                            int* __restrict__ err) {
-  gj_pivot_block(r, 0, G, fac, err);
-}
+// Step k.  Every block first reduces the previous step's per-block candidates to the
+// pivot row p_k (the same result in every block, so no block waits on another) and
+// forms 1/G_{p_k k}; block 0 records the pivot and the block owning row p_k places its
+// identity entry.  Then every row i != p_k gets
+//   row_i <- s_i row_i - (s_i G_ik / G_{p_k k}) row_{p_k}   (s_i its pending scale)
+// over the active columns [k+1, r) and [r, r + k], a warp per row, and the rows not yet
+// used propose |G_{i,k+1}| for the next step (candidate buffers alternate by step).
+constexpr int kGjRowsPerBlock = 8;  // warps of a step block
 
-// Step k: G_ij -= fac_i G_kj for i != k over columns [k, 2r) (row swaps move the identity
-// columns of the right half, so all of it stays active); each block owns whole rows.  The
-// last block to finish (ticket) performs the pivot step of column k + 1.
-__global__ void __launch_bounds__(1024)
-    k_gj_step(int r, int k, double* __restrict__ G, double* __restrict__ fac,
-              unsigned* __restrict__ ticket, int* __restrict__ err) {
-  __shared__ unsigned s_last;
+__global__ void __launch_bounds__(32 * kGjRowsPerBlock)
+    k_gj_step(int r, int k, double* __restrict__ G, GjAux x) {
+  extern __shared__ double sprow[];  // active part of the pivot row: r entries
+  __shared__ int s_p;
+  __shared__ double s_ip;
   const int ld = 2 * r;
-  for (int i = blockIdx.x; i < r; i += gridDim.x) {
-    const double f = fac[i];
-    if (f == 0.0) continue;
-    const double* prow = G + (size_t)k * ld;
-    double* row = G + (size_t)i * ld;
-    for (int j = k + threadIdx.x; j < ld; j += blockDim.x) row[j] -= f * __ldcg(prow + j);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  {
+    const double* cv = x.cval + (size_t)((k + 1) & 1) * kGjMaxBlocks;
+    const int* ci = x.cidx + (size_t)((k + 1) & 1) * kGjMaxBlocks;
+    double v = -1.0;
+    int i = 0x7fffffff;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) argmax_merge(v, i, cv[b], ci[b]);
+    block_argmax(v, i);
+    if (threadIdx.x == 0) {
+      if (!(v > 0.0) || i >= r) {  // singular: record it, keep the bookkeeping consistent
+        if (blockIdx.x == 0) atomicOr(x.err, 8);
+        i = 0;
+        while (i < r && x.used[i]) ++i;
+        if (i >= r) i = 0;
+      }
+      const double pv = G[(size_t)i * ld + k];
+      s_p = i;
+      s_ip = pv != 0.0 ? 1.0 / pv : 0.0;
+    }
+    __syncthreads();
   }
-  if (k + 1 >= r) return;
-  __threadfence();
+  const int p = s_p;
+  const double ip = s_ip;
+  const int nl = r - k - 1;  // active left columns k+1 .. r-1, then right columns r .. r+k
+  const double* prow = G + (size_t)p * ld;
+  for (int c = threadIdx.x; c < r; c += blockDim.x)
+    sprow[c] = c < nl ? prow[k + 1 + c] : (c - nl == k ? 1.0 : prow[r + (c - nl)]);
+  if (threadIdx.x == 0) {
+    if (blockIdx.x == 0) {
+      x.piv[k] = p;
+      x.pinv[k] = ip;
+      x.pscale[p] = ip;  // row p_k is normalised when it is next updated
+      x.slot[p] = k;
+      x.used[p] = 1;
+    }
+    if ((p / kGjRowsPerBlock) % (int)gridDim.x == (int)blockIdx.x) G[(size_t)p * ld + r + k] = 1.0;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  gj_pivot_block(r, k + 1, G, fac, err);
-  if (threadIdx.x == 0) *ticket = 0u;
+  double bv = -1.0;
+  int bi = 0x7fffffff;
+  for (int i = blockIdx.x * kGjRowsPerBlock + warp; i < r; i += gridDim.x * kGjRowsPerBlock) {
+    if (i == p) continue;
+    double* row = G + (size_t)i * ld;
+    const double ps = x.pscale[i];
+    const double f = ps * row[k] * ip;
+    const bool cand = k + 1 < r && !x.used[i];
+    for (int c0 = 0; c0 < r; c0 += 32 * 16) {
+      double v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int c = c0 + lane + 32 * u;
+        v[u] = c < r ? (c < nl ? row[k + 1 + c] : row[r + (c - nl)]) : 0.0;
+      }
+      if (ps != 1.0) {  // the previous pivot row: apply its pending scale (warp-uniform)
+#pragma unroll
+        for (int u = 0; u < 16; ++u) v[u] *= ps;
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int c = c0 + lane + 32 * u;
+        if (c < r) {
+          const double nv = fma(-f, sprow[c], v[u]);
+          if (c < nl) row[k + 1 + c] = nv;
+          else row[r + (c - nl)] = nv;
+          if (c == 0 && cand) argmax_merge(bv, bi, fabs(nv), i);
+        }
+      }
+    }
+    if (ps != 1.0) {
+      __syncwarp();  // every lane has read pscale[i] before it is reset
+      if (lane == 0) x.pscale[i] = 1.0;
+    }
+  }
+  block_argmax(bv, bi);
+  if (threadIdx.x == 0) {
+    x.cval[(size_t)(k & 1) * kGjMaxBlocks + blockIdx.x] = bv;
+    x.cidx[(size_t)(k & 1) * kGjMaxBlocks + blockIdx.x] = bi;
+  }
 }
 
-__global__ void k_gj_extract(int r, const double* __restrict__ G, double* __restrict__ Tinv,
-                             double* __restrict__ TinvT) {
+// T^-1[a][c] = s(p_a) G[p_a][r + slot(c)]  (and its transpose)
+__global__ void k_gj_extract(int r, const double* __restrict__ G, GjAux x,
+                             double* __restrict__ Tinv, double* __restrict__ TinvT) {
   const long long tot = (long long)r * r;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
        t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t / r), j = (int)(t % r);
-    const double v = G[(size_t)i * 2 * r + r + j];
+    const int a = (int)(t / r), c = (int)(t % r);
+    const int pa = x.piv[a];
+    const double v = x.pscale[pa] * G[(size_t)pa * 2 * r + r + x.slot[c]];
     Tinv[t] = v;
-    if (TinvT) TinvT[(size_t)j * r + i] = v;
+    if (TinvT) TinvT[(size_t)c * r + a] = v;
   }
 }
 
@@ -517,27 +616,45 @@ cudaError_t launch_coarse_T(int r, const int* rowptr, const int* col, const doub
   return cudaGetLastError();
 }
 
-cudaError_t launch_gauss_jordan(int r, const double* T, double* G /* r*2r */, double* fac,
+size_t gj_aux_bytes(int r) {
+  return sizeof(double) * (2 * (size_t)r + 2 * kGjMaxBlocks) +
+         sizeof(int) * (3 * (size_t)r + 2 * kGjMaxBlocks);
+}
+
+cudaError_t launch_gauss_jordan(int r, const double* T, double* G /* r*2r */, void* aux,
                                 double* Tinv, double* TinvT, int* err, cudaStream_t st) {
-  // one launch per column, captured into a CUDA graph (launch gaps of a plain loop of r
-  // kernels would dominate for r ~ 1000)
-  unsigned* ticket = reinterpret_cast<unsigned*>(fac + r);  // fac has r + 1 doubles
-  cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
-  if (e != cudaSuccess) return e;
-  k_gj_init<<<grid_for(2LL * r * r, 256, 152 * 8), 256, 0, st>>>(r, T, G);
-  k_gj_pivot0<<<1, 1024, 0, st>>>(r, G, fac, err);
+  GjAux x;
+  double* d = static_cast<double*>(aux);
+  x.pinv = d;
+  x.pscale = d + r;
+  x.cval = d + 2 * (size_t)r;
+  int* q = reinterpret_cast<int*>(d + 2 * (size_t)r + 2 * kGjMaxBlocks);
+  x.piv = q;
+  x.slot = q + r;
+  x.used = q + 2 * (size_t)r;
+  x.cidx = q + 3 * (size_t)r;
+  x.err = err;
+  cudaError_t e;
+  const size_t sm = sizeof(double) * (size_t)r;
+  if (sm > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_gj_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  int gs = (r + kGjRowsPerBlock - 1) / kGjRowsPerBlock;
+  if (gs > kGjMaxBlocks) gs = kGjMaxBlocks;
+  k_gj_init<<<grid_for(2LL * r * r, 256, 152 * 8), 256, 0, st>>>(r, T, G, x);
+  k_gj_first<<<1, 1024, 0, st>>>(r, G, x, gs);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  int dev = 0, sms = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = r < 2 * sms ? r : 2 * sms;
+  // one launch per column, captured into a CUDA graph (launch gaps of a plain loop of r
+  // kernels would dominate)
   cudaStream_t cap;
   if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ex = nullptr;
   e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
   if (e == cudaSuccess) {
-    for (int k = 0; k < r; ++k) k_gj_step<<<grid, 256, 0, cap>>>(r, k, G, fac, ticket, err);
+    for (int k = 0; k < r; ++k)
+      k_gj_step<<<gs, 32 * kGjRowsPerBlock, sm, cap>>>(r, k, G, x);
     const cudaError_t le = cudaGetLastError();
     e = cudaStreamEndCapture(cap, &g);
     if (e == cudaSuccess) e = le;
@@ -549,7 +666,7 @@ cudaError_t launch_gauss_jordan(int r, const double* T, double* G /* r*2r */, do
   if (g) cudaGraphDestroy(g);
   cudaStreamDestroy(cap);
   if (e != cudaSuccess) return e;
-  k_gj_extract<<<grid_for((long long)r * r, 256, 152 * 8), 256, 0, st>>>(r, G, Tinv, TinvT);
+  k_gj_extract<<<grid_for((long long)r * r, 256, 152 * 8), 256, 0, st>>>(r, G, x, Tinv, TinvT);
   return cudaGetLastError();
 }
 

@@ -440,13 +440,13 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
                         h->piece_start.as<int>(), h->uscale.as<double>(), err.as<int>(), st));
     CKC(T.ensure(sizeof(double) * (size_t)r * r));
     CKC(G.ensure(sizeof(double) * 2 * (size_t)r * r));
-    CKC(fac.ensure(sizeof(double) * (size_t)(r + 1)));
+    CKC(fac.ensure(gj_aux_bytes(r)));
     CKC(h->fwd.tinv.ensure(sizeof(double) * (size_t)r * r));
     CKC(h->adj.tinv.ensure(sizeof(double) * (size_t)r * r));
     CKC(launch_coarse_T(r, h->fwd.rowptr.as<int>(), h->fwd.col.as<int>(),
                         h->fwd.val.as<double>(), h->agg.as<int>(), h->perm.as<int>(),
                         aggptr.as<int>(), h->uscale.as<double>(), T.as<double>(), st));
-    CKC(launch_gauss_jordan(r, T.as<double>(), G.as<double>(), fac.as<double>(),
+    CKC(launch_gauss_jordan(r, T.as<double>(), G.as<double>(), fac.p,
                             h->fwd.tinv.as<double>(), h->adj.tinv.as<double>(), err.as<int>(), st));
     int np = 0;
     CKC(cudaMemcpyAsync(&np, h->agg_piece.as<int>() + r, sizeof(int), cudaMemcpyDeviceToHost, st));
