@@ -201,6 +201,19 @@ gmres_status gmres_batch_solve(int32_t count, gmres_t const* hs, const double* c
 gmres_status gmres_profile(gmres_t h, int32_t enable, int32_t reset, double* ms,
                            int64_t* launches);
 
+/* Device data layout chosen at create (host-only, never blocks).  No counterpart in the
+ * paper: it reports how the operator and the deflation space are stored. */
+typedef struct gmres_layout {
+  int64_t n, nnz;     /* order and stored entries of A */
+  int32_t r;          /* deflation vectors (aggregates); 0 without deflation */
+  int32_t npieces;    /* runs of at most 1024 nodes in which U^T x is summed */
+  int32_t ndiag;      /* diagonals of A in diagonal storage; 0: A is kept in CSR only */
+  int32_t reserved;
+  int64_t nau;        /* entries of A W (coarse part of the deflated SpMV) */
+  int64_t ldv;        /* rows per basis column in device memory (n rounded up) */
+} gmres_layout;
+gmres_status gmres_layout_query(gmres_t h, gmres_layout* out);
+
 gmres_status gmres_set_stream(gmres_t h, void* stream);
 /* Message of the last error on this handle (or of the last failed create when h is
  * NULL).  Owned by the library, valid until the next call on the handle. */

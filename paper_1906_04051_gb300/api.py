@@ -123,6 +123,12 @@ class Solver:
         _check(N.load().gmres_profile(self._h, int(enable), 1 if reset else 0, ms, nl), self._h)
         return {name: (ms[i], nl[i]) for i, name in enumerate(N.PHASES)}
 
+    def layout(self) -> dict:
+        """Device data layout chosen at create (gmres_layout_query)."""
+        out = N.gmres_layout()
+        _check(N.load().gmres_layout_query(self._h, C.byref(out)), self._h)
+        return out.as_dict()
+
     def close(self):
         h = getattr(self, "_h", None)
         if h:

@@ -50,6 +50,7 @@ struct OpHost {
   DevMem aurp, aucol, auval, auval32;  // A W in CSR (projector, residual)
   DevMem xrp, xcol, xval, xval32;      // [A | A W] rows (deflated SpMV of a step)
   DevMem dval, dval32;                 // diagonal storage (banded operators)
+  long long nau = 0;                   // entries of A W
   DiaOffsets dia{};
   long long ldd = 0;
   bool ready = false;
@@ -227,6 +228,7 @@ inline gmres_status build_au(gmres_s* h, OpHost& o) {
   int nau = 0;
   CK(h, cudaMemcpyAsync(&nau, o.aurp.as<int>() + n, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(h, cudaStreamSynchronize(st));
+  o.nau = nau;
   const size_t cap = nau > 0 ? (size_t)nau : 1;
   CK(h, o.aucol.ensure(sizeof(int) * cap));
   CK(h, o.auval.ensure(sizeof(double) * cap));

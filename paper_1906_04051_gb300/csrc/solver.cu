@@ -562,6 +562,20 @@ gmres_status gmres_profile(gmres_t h, int32_t enable, int32_t reset, double* ms,
   return GMRES_OK;
 }
 
+gmres_status gmres_layout_query(gmres_t h, gmres_layout* out) {
+  if (!h) return fail(nullptr, GMRES_ERR_INVALID_ARG, "null handle");
+  if (!out) return fail(h, GMRES_ERR_INVALID_ARG, "gmres_layout_query: null output");
+  std::memset(out, 0, sizeof(*out));
+  out->n = h->n;
+  out->nnz = h->nnz;
+  out->r = h->r;
+  out->npieces = h->npieces;
+  out->ndiag = h->fwd.dia.nd;
+  out->nau = h->fwd.nau;
+  out->ldv = h->ldv;
+  return GMRES_OK;
+}
+
 gmres_status gmres_set_stream(gmres_t h, void* stream) {
   if (!h) return fail(nullptr, GMRES_ERR_INVALID_ARG, "null handle");
   h->stream = static_cast<cudaStream_t>(stream);

@@ -137,6 +137,11 @@ def test_general_csr_path_permuted(G, orc, mode, prec):
                                 deflation_mode=dm, precision=pr)
     x2, i2 = s2.solve(to_dev(b), m=30, tol=1e-11, maxit=20000)
     assert relerr(xg.cpu().numpy(), x2.cpu().numpy()[perm]) <= 1e-8
+    # the banded system is held in diagonal storage (9 diagonals), the renumbered one not
+    lay, lay2 = s.layout(), s2.layout()
+    assert lay["ndiag"] == 0 and lay2["ndiag"] == 9
+    assert lay["nnz"] == lay2["nnz"] == A.nnz and lay["n"] == A.n
+    assert lay["r"] == (p.r if defl else 0)
     if prec == "fp64":
         assert abs(ig["iters"] - i2["iters"]) <= 3
 
