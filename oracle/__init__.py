@@ -33,7 +33,7 @@ _lock = threading.Lock()
 _lib = None
 
 CGS2, MGS = 0, 1
-DEFL_NONE, DEFL_EBP, DEFL_PROJECTOR = 0, 1, 2
+DEFL_NONE, DEFL_EBP, DEFL_PROJECTOR, DEFL_ADAPTIVE = 0, 1, 2, 3
 MU_RITZ_FIRST_CYCLE, MU_USER, MU_NORM_INF = 0, 1, 2
 
 
@@ -61,6 +61,9 @@ class Opts(C.Structure):
         ("mu_user", C.c_double),
         ("fixed_iterations", C.c_int32),
         ("r0_norm_ref", C.c_double),
+        ("rmax", C.c_int32),
+        ("ninv", C.c_int32),
+        ("u_out", C.c_void_p),
     ]
 
 
@@ -72,6 +75,7 @@ class Info(C.Structure):
         ("rel_res_est", C.c_double),
         ("rel_res_true", C.c_double),
         ("mu", C.c_double),
+        ("q", C.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -97,6 +101,7 @@ def lib():
             L.orc_lu_factor.argtypes = [C.c_int32, _P, _P]
             L.orc_lu_solve.argtypes = [C.c_int32, _P, _P, _P]
             L.orc_hessenberg_eigs.argtypes = [C.c_int32, _P, _P, _P]
+            L.orc_hess_invvec.argtypes = [C.c_int32, _P, C.c_int32, _P, _P]
             L.orc_defl_create.restype = _P
             L.orc_defl_create.argtypes = [C.c_int32, _P, _P, _P, C.c_int32, _P,
                                           C.POINTER(C.c_int)]
@@ -253,13 +258,22 @@ class Deflation:
 
 def gmres(A: CSR, b, x0=None, *, m=30, tol=1e-8, maxit=10000, defl: Deflation | None = None,
           defl_mode=DEFL_EBP, mu_mode=MU_RITZ_FIRST_CYCLE, mu_user=0.0, ortho=CGS2,
-          fixed_iterations=False, r0_norm_ref=0.0, history=False):
-    """Deflated restarted GMRES(m); returns (x, info dict[, history (steps x 2)])."""
+          fixed_iterations=False, r0_norm_ref=0.0, history=False, rmax=20, ninv=20,
+          return_u=False):
+    """Deflated restarted GMRES(m); returns (x, info dict[, history (steps x 2)][, U]).
+
+    defl_mode=DEFL_ADAPTIVE needs no Deflation object: U starts empty and grows after
+    every cycle (Sec. 3.3, Eq. 19), at most rmax columns; return_u appends the final U
+    (N x q)."""
     b = _f64(b)
     x0a = None if x0 is None else _f64(x0)
     x = np.empty(A.n)
-    o = Opts(m, tol, maxit, ortho, defl_mode if defl is not None else DEFL_NONE, mu_mode,
-             mu_user, 1 if fixed_iterations else 0, r0_norm_ref)
+    adaptive = defl_mode == DEFL_ADAPTIVE
+    uo = np.zeros(A.n * rmax) if (adaptive and return_u) else None
+    o = Opts(m, tol, maxit, ortho,
+             defl_mode if (defl is not None or adaptive) else DEFL_NONE, mu_mode,
+             mu_user, 1 if fixed_iterations else 0, r0_norm_ref, rmax, ninv,
+             None if uo is None else uo.ctypes.data)
     info = Info()
     hist = np.zeros(2 * maxit) if history else None
     lib().orc_gmres(A.n, _p(A.rowptr), _p(A.col), _p(A.val),
@@ -269,7 +283,19 @@ def gmres(A: CSR, b, x0=None, *, m=30, tol=1e-8, maxit=10000, defl: Deflation | 
     if history:
         hs = hist.reshape(-1, 2)[: info.iters]
         out = out + (hs,)
+    if uo is not None:
+        out = out + (uo[: A.n * info.q].reshape(info.q, A.n).T.copy(),)
     return out
+
+
+def hess_invvec(H, ninv=20):
+    """Inverse power method on an upper Hessenberg H (Sec. 3.3): one vector, or two
+    spanning a complex pair's invariant subspace."""
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    k = H.shape[0]
+    z = np.zeros(2 * k)
+    nv = lib().orc_hess_invvec(k, _p(H), ninv, _p(z), _p(z[k:]))
+    return [z[i * k:(i + 1) * k].copy() for i in range(nv)]
 
 
 def arnoldi(A: CSR, v0, k: int, *, defl: Deflation | None = None, defl_mode=DEFL_NONE,

@@ -450,6 +450,191 @@ void orc_defl_apply_P(const orc_defl* d, const double* w, double* out) {
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* Adaptive deflation (Sec. 3.3, Eq. 19): U grows by eigenvectors of H_m mapped through V */
+/* ------------------------------------------------------------------------------------ */
+
+/* LU of a k x k upper Hessenberg matrix (row-major, in place): column j only has rows j
+ * and j+1 below the diagonal, so partial pivoting compares those two rows. */
+static void hess_lu(int32_t k, double* a, int32_t* sw, double* l, double eps) {
+  for (int32_t j = 0; j < k; ++j) {
+    sw[j] = 0;
+    l[j] = 0.0;
+    if (j + 1 < k && fabs(a[(size_t)(j + 1) * k + j]) > fabs(a[(size_t)j * k + j])) {
+      for (int32_t c = j; c < k; ++c) {
+        double t = a[(size_t)j * k + c];
+        a[(size_t)j * k + c] = a[(size_t)(j + 1) * k + c];
+        a[(size_t)(j + 1) * k + c] = t;
+      }
+      sw[j] = 1;
+    }
+    if (a[(size_t)j * k + j] == 0.0) a[(size_t)j * k + j] = eps;
+    if (j + 1 < k) {
+      l[j] = a[(size_t)(j + 1) * k + j] / a[(size_t)j * k + j];
+      for (int32_t c = j + 1; c < k; ++c) a[(size_t)(j + 1) * k + c] -= l[j] * a[(size_t)j * k + c];
+      a[(size_t)(j + 1) * k + j] = 0.0;
+    }
+  }
+}
+
+static void hess_solve(int32_t k, const double* a, const int32_t* sw, const double* l, double* z) {
+  for (int32_t j = 0; j + 1 < k; ++j) {
+    if (sw[j]) {
+      double t = z[j];
+      z[j] = z[j + 1];
+      z[j + 1] = t;
+    }
+    z[j + 1] -= l[j] * z[j];
+  }
+  for (int32_t i = k - 1; i >= 0; --i) {
+    double s = z[i];
+    for (int32_t c = i + 1; c < k; ++c) s -= a[(size_t)i * k + c] * z[c];
+    z[i] = s / a[(size_t)i * k + i];
+  }
+}
+
+static void normalise_sign(int32_t k, double* z) {
+  double nz = nrm2(z, k);
+  for (int32_t i = 0; i < k; ++i) z[i] /= nz;
+  int32_t im = 0;
+  for (int32_t i = 1; i < k; ++i)
+    if (fabs(z[i]) > fabs(z[im])) im = i;
+  if (z[im] < 0.0)
+    for (int32_t i = 0; i < k; ++i) z[i] = -z[i];
+}
+
+int orc_hess_invvec(int32_t k, const double* H, int32_t ninv, double* z1, double* z2) {
+  if (k < 1) return 0;
+  double* a = (double*)malloc(sizeof(double) * (size_t)k * k);
+  double* l = (double*)malloc(sizeof(double) * (size_t)k);
+  int32_t* sw = (int32_t*)malloc(sizeof(int32_t) * (size_t)k);
+  double* hz = (double*)malloc(sizeof(double) * (size_t)k);
+  double hmax = 0.0;
+  for (int32_t i = 0; i < k * k; ++i) hmax = fabs(H[i]) > hmax ? fabs(H[i]) : hmax;
+  memcpy(a, H, sizeof(double) * (size_t)k * k);
+  hess_lu(k, a, sw, l, hmax > 0.0 ? 1e-14 * hmax : 1e-300);
+  for (int32_t i = 0; i < k; ++i) z1[i] = 1.0 / sqrt((double)k);
+  for (int32_t it = 0; it < ninv; ++it) {
+    hess_solve(k, a, sw, l, z1);
+    normalise_sign(k, z1);
+  }
+  /* eigenvector test with the Rayleigh quotient rho = z^T H z */
+  double rho = 0.0, nhz = 0.0, res = 0.0;
+  for (int32_t i = 0; i < k; ++i) {
+    double s = 0.0;
+    for (int32_t c = 0; c < k; ++c) s += H[(size_t)i * k + c] * z1[c];
+    hz[i] = s;
+    rho += z1[i] * s;
+    nhz += s * s;
+  }
+  for (int32_t i = 0; i < k; ++i) res += (hz[i] - rho * z1[i]) * (hz[i] - rho * z1[i]);
+  int nvec = 1;
+  if (sqrt(res) > 1e-3 * sqrt(nhz)) {
+    /* a complex pair: the next iterate completes a basis of its invariant subspace */
+    memcpy(z2, z1, sizeof(double) * (size_t)k);
+    hess_solve(k, a, sw, l, z2);
+    double c = dot(z1, z2, k);
+    for (int32_t i = 0; i < k; ++i) z2[i] -= c * z1[i];
+    normalise_sign(k, z2);
+    nvec = 2;
+  }
+  free(a);
+  free(l);
+  free(sw);
+  free(hz);
+  return nvec;
+}
+
+/* Dense deflation space of the adaptive variant: U (N x q, orthonormal), A U, T = U^T A U
+ * and its LU; at most rmax columns. */
+typedef struct {
+  int32_t N, rmax, q;
+  double *U, *AU, *T, *lu;
+  int32_t* piv;
+} adapt_space;
+
+static void adapt_apply_Minv(const adapt_space* s, double mu, const double* v, double* z) {
+  /* z = v + U (|mu| T^-1 - I) U^T v  (Eq. 17 with the current U) */
+  double* c = (double*)malloc(sizeof(double) * (size_t)(s->q + 1));
+  double* y = (double*)malloc(sizeof(double) * (size_t)(s->q + 1));
+  for (int32_t t = 0; t < s->q; ++t) c[t] = dot(s->U + (size_t)t * s->N, v, s->N);
+  memcpy(y, c, sizeof(double) * (size_t)s->q);
+  orc_lu_solve(s->q, s->lu, s->piv, y);
+  for (int32_t t = 0; t < s->q; ++t) y[t] = fabs(mu) * y[t] - c[t];
+  memcpy(z, v, sizeof(double) * (size_t)s->N);
+  for (int32_t t = 0; t < s->q; ++t)
+    for (int32_t i = 0; i < s->N; ++i) z[i] += y[t] * s->U[(size_t)t * s->N + i];
+  free(c);
+  free(y);
+}
+
+/* After a cycle of k steps: the inverse-power eigenvector(s) z of H_k give u = V_k z
+ * (Eq. 19), orthonormalised against U (two classical Gram-Schmidt passes) and appended;
+ * at rmax columns the column whose Rayleigh quotient T_jj is largest in modulus is
+ * dropped first (the last column takes its place).  T and its LU follow U. */
+static int adapt_update(adapt_space* s, int32_t N, const int32_t* rowptr, const int32_t* col,
+                        const double* val, const double* V, const double* Hr, int32_t m,
+                        int32_t k, int32_t ninv) {
+  if (k < 1) return 0;
+  double* hk = (double*)malloc(sizeof(double) * (size_t)k * k);
+  double* z = (double*)malloc(sizeof(double) * 2 * (size_t)k);
+  double* u = (double*)malloc(sizeof(double) * (size_t)N);
+  double* c = (double*)malloc(sizeof(double) * (size_t)(s->rmax + 1));
+  for (int32_t i = 0; i < k; ++i)
+    for (int32_t l = 0; l < k; ++l) hk[(size_t)i * k + l] = Hr[(size_t)i * m + l];
+  const int nz = orc_hess_invvec(k, hk, ninv, z, z + k);
+  const int32_t R = s->rmax;
+  for (int v = 0; v < nz; ++v) {
+    const double* zv = z + (size_t)v * k;
+    for (int32_t i = 0; i < N; ++i) u[i] = 0.0;
+    for (int32_t l = 0; l < k; ++l)
+      for (int32_t i = 0; i < N; ++i) u[i] += zv[l] * V[(size_t)l * N + i];
+    const double n0 = nrm2(u, N);
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int32_t t = 0; t < s->q; ++t) c[t] = dot(s->U + (size_t)t * N, u, N);
+      for (int32_t t = 0; t < s->q; ++t)
+        for (int32_t i = 0; i < N; ++i) u[i] -= c[t] * s->U[(size_t)t * N + i];
+    }
+    const double n1 = nrm2(u, N);
+    if (!(n1 > 1e-10 * n0)) continue; /* already in span(U) */
+    for (int32_t i = 0; i < N; ++i) u[i] /= n1;
+    if (s->q == R) { /* r > rmax: deflate the column with the largest |T_jj| */
+      int32_t jd = 0;
+      for (int32_t j = 1; j < s->q; ++j)
+        if (fabs(s->T[(size_t)j * R + j]) > fabs(s->T[(size_t)jd * R + jd])) jd = j;
+      const int32_t last = s->q - 1;
+      if (jd != last) {
+        memcpy(s->U + (size_t)jd * N, s->U + (size_t)last * N, sizeof(double) * (size_t)N);
+        memcpy(s->AU + (size_t)jd * N, s->AU + (size_t)last * N, sizeof(double) * (size_t)N);
+        for (int32_t j = 0; j < s->q; ++j) s->T[(size_t)jd * R + j] = s->T[(size_t)last * R + j];
+        for (int32_t i = 0; i < s->q; ++i) s->T[(size_t)i * R + jd] = s->T[(size_t)i * R + last];
+        s->T[(size_t)jd * R + jd] = s->T[(size_t)last * R + last];
+      }
+      s->q = last;
+    }
+    const int32_t q = s->q;
+    memcpy(s->U + (size_t)q * N, u, sizeof(double) * (size_t)N);
+    orc_spmv(N, rowptr, col, val, u, s->AU + (size_t)q * N);
+    for (int32_t i = 0; i < q; ++i) {
+      s->T[(size_t)i * R + q] = dot(s->U + (size_t)i * N, s->AU + (size_t)q * N, N);
+      s->T[(size_t)q * R + i] = dot(s->U + (size_t)q * N, s->AU + (size_t)i * N, N);
+    }
+    s->T[(size_t)q * R + q] = dot(s->U + (size_t)q * N, s->AU + (size_t)q * N, N);
+    s->q = q + 1;
+  }
+  int err = 0;
+  if (s->q > 0) {
+    for (int32_t i = 0; i < s->q; ++i)
+      for (int32_t j = 0; j < s->q; ++j) s->lu[(size_t)i * s->q + j] = s->T[(size_t)i * R + j];
+    err = orc_lu_factor(s->q, s->lu, s->piv);
+  }
+  free(hk);
+  free(z);
+  free(u);
+  free(c);
+  return err;
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* GMRES(m) (Sec. 3.2, Eqs. 10-15) with right deflation preconditioning (Eq. 16)         */
 /* ------------------------------------------------------------------------------------ */
 
@@ -525,8 +710,19 @@ int orc_gmres(int32_t N, const int32_t* rowptr, const int32_t* col, const double
               const orc_defl* d, const double* b, const double* x0, const orc_opts* o,
               double* x, orc_info* info, double* hist) {
   const int32_t m = o->m;
-  const int mode = d ? o->defl_mode : ORC_DEFL_NONE;
+  const int adaptive = o->defl_mode == ORC_DEFL_ADAPTIVE;
+  const int mode = adaptive ? ORC_DEFL_ADAPTIVE : (d ? o->defl_mode : ORC_DEFL_NONE);
   memset(info, 0, sizeof(*info));
+  adapt_space as = {0};
+  if (adaptive) {
+    as.N = N;
+    as.rmax = o->rmax > 0 ? o->rmax : 20;
+    as.U = (double*)malloc(sizeof(double) * (size_t)N * as.rmax);
+    as.AU = (double*)malloc(sizeof(double) * (size_t)N * as.rmax);
+    as.T = (double*)calloc((size_t)as.rmax * as.rmax, sizeof(double));
+    as.lu = (double*)malloc(sizeof(double) * (size_t)as.rmax * as.rmax);
+    as.piv = (int32_t*)malloc(sizeof(int32_t) * (size_t)as.rmax);
+  }
   double* V = (double*)malloc(sizeof(double) * (size_t)N * (m + 1));
   double* H = (double*)calloc((size_t)(m + 1) * m, sizeof(double));  /* rotated */
   double* Hr = (double*)calloc((size_t)(m + 1) * m, sizeof(double)); /* as built */
@@ -545,7 +741,7 @@ int orc_gmres(int32_t N, const int32_t* rowptr, const int32_t* col, const double
    * first cycle, which runs with M = I; or given; or bounded by the infinity norm. */
   double mu = 0.0;
   int defl_on = (mode == ORC_DEFL_PROJECTOR);
-  if (mode == ORC_DEFL_EBP) {
+  if (mode == ORC_DEFL_EBP || mode == ORC_DEFL_ADAPTIVE) {
     if (o->mu_mode == ORC_MU_USER) {
       mu = o->mu_user;
       defl_on = 1;
@@ -609,8 +805,18 @@ int orc_gmres(int32_t N, const int32_t* rowptr, const int32_t* col, const double
     g[0] = beta;
     int32_t k = 0;
     int use_defl = defl_on ? mode : ORC_DEFL_NONE;
+    const int dense = adaptive && defl_on && as.q > 0; /* M^-1 with the current U */
     for (int32_t j = 0; j < m && steps < o->maxit; ++j) {
-      apply_op(N, rowptr, col, val, d, use_defl, mu, V + (size_t)j * N, w, tmp);
+      if (adaptive) {
+        if (dense) {
+          adapt_apply_Minv(&as, mu, V + (size_t)j * N, tmp);
+          orc_spmv(N, rowptr, col, val, tmp, w);
+        } else {
+          orc_spmv(N, rowptr, col, val, V + (size_t)j * N, w);
+        }
+      } else {
+        apply_op(N, rowptr, col, val, d, use_defl, mu, V + (size_t)j * N, w, tmp);
+      }
       orthogonalise(N, V, j, o->ortho, w, hcol);
       double hnext = hcol[j + 1];
       double hn2 = 0.0;
@@ -667,11 +873,14 @@ int orc_gmres(int32_t N, const int32_t* rowptr, const int32_t* col, const double
     if (use_defl == ORC_DEFL_EBP) {
       orc_defl_apply_Minv(d, mu, w, tmp);
       for (int32_t i = 0; i < N; ++i) x[i] += tmp[i];
+    } else if (dense) {
+      adapt_apply_Minv(&as, mu, w, tmp);
+      for (int32_t i = 0; i < N; ++i) x[i] += tmp[i];
     } else {
       for (int32_t i = 0; i < N; ++i) x[i] += w[i];
     }
     ++cycles;
-    if (mode == ORC_DEFL_EBP && !defl_on) {
+    if ((mode == ORC_DEFL_EBP || mode == ORC_DEFL_ADAPTIVE) && !defl_on) {
       /* Ritz values of H_k from the first cycle give |mu| */
       double* hk = (double*)malloc(sizeof(double) * (size_t)k * k);
       double* wr = (double*)malloc(sizeof(double) * (size_t)k);
@@ -692,6 +901,11 @@ int orc_gmres(int32_t N, const int32_t* rowptr, const int32_t* col, const double
         break;
       }
       defl_on = 1;
+    }
+    /* grow U from this cycle's Hessenberg matrix and basis (Sec. 3.3, Eq. 19) */
+    if (adaptive && adapt_update(&as, N, rowptr, col, val, V, Hr, m, k, o->ninv > 0 ? o->ninv : 20)) {
+      status = -4;
+      break;
     }
     TRUE_RESIDUAL();
   }
@@ -719,6 +933,15 @@ done:
   info->rel_res_est = est;
   info->rel_res_true = truerel;
   info->mu = mu;
+  if (adaptive) {
+    info->q = as.q;
+    if (o->u_out) memcpy(o->u_out, as.U, sizeof(double) * (size_t)N * as.q);
+    free(as.U);
+    free(as.AU);
+    free(as.T);
+    free(as.lu);
+    free(as.piv);
+  }
   free(V);
   free(H);
   free(Hr);

@@ -63,7 +63,7 @@ void orc_defl_apply_P(const orc_defl* d, const double* w, double* out); /* (I - 
 
 /* ---- GMRES(m) ---- */
 enum { ORC_CGS2 = 0, ORC_MGS = 1 };
-enum { ORC_DEFL_NONE = 0, ORC_DEFL_EBP = 1, ORC_DEFL_PROJECTOR = 2 };
+enum { ORC_DEFL_NONE = 0, ORC_DEFL_EBP = 1, ORC_DEFL_PROJECTOR = 2, ORC_DEFL_ADAPTIVE = 3 };
 enum { ORC_MU_RITZ_FIRST_CYCLE = 0, ORC_MU_USER = 1, ORC_MU_NORM_INF = 2 };
 
 typedef struct {
@@ -76,13 +76,29 @@ typedef struct {
   double mu_user;
   int32_t fixed_iterations; /* 1: no convergence test, exactly maxit steps */
   double r0_norm_ref;       /* > 0: reference norm for the relative tolerance */
+  /* ORC_DEFL_ADAPTIVE (Sec. 3.3, Eq. 19): U starts empty and grows by the inverse-power
+   * eigenvectors of each cycle's H_k mapped through V_k, at most rmax columns */
+  int32_t rmax;             /* upper limit on the columns of U (paper: 20) */
+  int32_t ninv;             /* inverse power iterations per restart */
+  double* u_out;            /* N x rmax column-major (may be NULL): the final U */
 } orc_opts;
 
 typedef struct {
   int64_t iters, cycles;
   int32_t status;           /* 0 converged, 1 not converged, <0 error */
   double rel_res_est, rel_res_true, mu;
+  int32_t q;                /* columns of U at the end (ORC_DEFL_ADAPTIVE) */
 } orc_info;
+
+/* Inverse power method on a k x k upper Hessenberg H (row-major; Sec. 3.3): iterates
+ * z <- H^-1 z / ||H^-1 z|| ninv times from the normalised all-ones vector (LU with
+ * partial pivoting between the two rows each column touches; a zero pivot is replaced
+ * by 1e-14 max|H|), then sign-normalises z (its largest-magnitude entry positive, the
+ * first one on ties).  If z is not an eigenvector to within ||Hz - (z^T H z) z|| <=
+ * 1e-3 ||Hz|| (the smallest eigenvalues form a complex pair), one more iterate is
+ * orthonormalised against z and returned as z2: the pair spans the pair's invariant
+ * subspace.  Returns the number of vectors (1 or 2), 0 if k < 1. */
+int orc_hess_invvec(int32_t k, const double* H, int32_t ninv, double* z1, double* z2);
 
 /* Solves A x = b.  d may be NULL (no deflation).  hist (2*maxit doubles, may be NULL)
  * receives, per Arnoldi step, (step index j within its cycle, |gamma_{j+1}| / rho0). */
