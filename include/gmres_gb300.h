@@ -86,7 +86,15 @@ typedef enum {
                                x = xh + U T^-1 U^T (b - A xh); P A W = 0.  The true
                                residual of x equals P (b - A xh), which the stopping test
                                uses (single-system solves; not in gmres_batch_solve) */
-  GMRES_DEFL_NONE = 2
+  GMRES_DEFL_NONE = 2,
+  GMRES_DEFL_ADAPTIVE = 3   /* the paper's adaptive EBP (Sec. 3.3, Eq. 19): U starts empty;
+                               after every restart cycle the eigenvector of the cycle's
+                               H_k for its smallest-modulus eigenvalue (inverse power
+                               method; a complex pair gives two vectors) is mapped through
+                               the basis, u = V_k z, orthonormalised against U and
+                               appended; beyond rmax columns the column with the largest
+                               |T_jj| is dropped first.  W (gmres_defl) must be empty;
+                               FP64 only; single-system solves */
 } gmres_deflation_mode;
 
 typedef enum {
@@ -109,6 +117,8 @@ typedef struct {
   double inner_tol;         /* mixed precision: a cycle ends once its own residual
                                estimate falls by this factor (0 = 1e-4 FP32, 1e-2 BF16) */
   int32_t profile;          /* 1: bracket every phase with CUDA events (gmres_profile) */
+  int32_t rmax;             /* GMRES_DEFL_ADAPTIVE: most columns of U, 1..32 (paper: 20) */
+  int32_t ninv;             /* GMRES_DEFL_ADAPTIVE: inverse power iterations per restart */
 } gmres_opts;
 
 /* Phases reported by gmres_profile (kernel groups of one solve). */
@@ -123,7 +133,8 @@ typedef enum {
   GMRES_PH_CYCLE_END = 7, /* back substitution and x += M^-1 V y (Eq. 11) */
   GMRES_PH_RITZ = 8,      /* |mu| from the Ritz values of H_k */
   GMRES_PH_PROJ_FINAL = 9,/* projector: x = xh + U T^-1 U^T (b - A xh) */
-  GMRES_PH_COUNT = 10
+  GMRES_PH_ADAPT = 10,    /* adaptive deflation: the update of U, A U, T, T^-1 */
+  GMRES_PH_COUNT = 11
 } gmres_phase;
 
 typedef struct {

@@ -5,13 +5,14 @@ The solver lives in a C-ABI CUDA library (include/gmres_gb300.h,
 package does not load the library; the first call does, and fails loudly if the library
 has not been built (``python -m paper_1906_04051_gb300.build``).
 """
-from ._native import (BF16_BASIS, DEFL_EBP, DEFL_NONE, DEFL_PROJECTOR, FP32_INNER, FP64,
-                      MU_NORM_INF, MU_RITZ_FIRST_CYCLE, MU_USER, GmresError)
+from ._native import (BF16_BASIS, DEFL_ADAPTIVE, DEFL_EBP, DEFL_NONE, DEFL_PROJECTOR,
+                      FP32_INNER, FP64, MU_NORM_INF, MU_RITZ_FIRST_CYCLE, MU_USER, GmresError)
 from .api import Solver, batch_solve, q1_assemble, q1_kappa_grad, q1_nnz
 
 __all__ = [
     "Solver", "batch_solve", "q1_assemble", "q1_kappa_grad", "q1_nnz", "GmresError",
     "FP64", "FP32_INNER", "BF16_BASIS", "DEFL_EBP", "DEFL_PROJECTOR", "DEFL_NONE",
+    "DEFL_ADAPTIVE",
     "MU_RITZ_FIRST_CYCLE", "MU_USER", "MU_NORM_INF",
 ]
 from .autograd import GmresSolve, Q1Setup, q1_solve  # noqa: E402

@@ -44,7 +44,7 @@ class Solver:
                  agg: torch.Tensor | None = None, r: int = 0, *, precision=N.FP64,
                  deflation_mode=N.DEFL_EBP, mu_mode=N.MU_RITZ_FIRST_CYCLE, mu_user=0.0,
                  fixed_iterations=False, r0_norm_ref=0.0, timeout_ms=0, inner_tol=0.0,
-                 profile=False, stream=None):
+                 profile=False, rmax=20, ninv=20, stream=None):
         L = N.load()
         n = rowptr.numel() - 1
         _dev(rowptr, torch.int32, "rowptr")
@@ -68,6 +68,8 @@ class Solver:
         opts.timeout_ms = int(timeout_ms)
         opts.inner_tol = float(inner_tol)
         opts.profile = 1 if profile else 0
+        opts.rmax = int(rmax)
+        opts.ninv = int(ninv)
         self._stream = stream
         h = C.c_void_p()
         st = L.gmres_create(C.byref(h), C.byref(csr), C.byref(defl) if defl else None,

@@ -36,7 +36,7 @@ template <typename TA, typename TV, typename TACC, bool DEFL>
 __global__ void __launch_bounds__(kThreads)
     k_spmv_step(int N, const int* __restrict__ rowptr, const int* __restrict__ col,
                 const TA* __restrict__ val, const TV* __restrict__ x, int j,
-                const TACC* __restrict__ sdefl, TACC* __restrict__ w, Ctl ctl) {
+                const TACC* __restrict__ sdefl, TACC* __restrict__ w, Ctl ctl, Defl d) {
   pdl_wait();
   pdl_trigger();
   if (ctl.flags[F_CYCLE_DONE]) return;
@@ -65,6 +65,8 @@ __global__ void __launch_bounds__(kThreads)
       acc1 += v[3] * xv[3];
     }
     for (; k < re; ++k) acc0 += (TACC)__ldg(val + k) * g(__ldg(col + k));
+    if (DEFL && d.qd > 0)  // adaptive deflation: A U dense (the rows are plain A)
+      for (int t = 0; t < d.qd; ++t) acc1 += (TACC)d.aud[(size_t)t * d.ldu + i] * sdefl[t];
     w[i] = sigma * (acc0 + acc1);
   }
 }
@@ -138,17 +140,25 @@ __global__ void __launch_bounds__(kThreads)
     const int i = i0 + u * blockDim.x;
     if (i < N) {
       TACC v = acc[u];
-      if constexpr (DEFL) v += au_row<TA, TACC>(i, d.aurp, d.aucol, auval, sdefl);
+      if constexpr (DEFL) {
+        if (d.qd > 0) {  // adaptive deflation: A U dense
+          for (int t = 0; t < d.qd; ++t) v += (TACC)d.aud[(size_t)t * d.ldu + i] * sdefl[t];
+        } else {
+          v += au_row<TA, TACC>(i, d.aurp, d.aucol, auval, sdefl);
+        }
+      }
       w[i] = sigma * v;
     }
   }
 }
 
-// CGS2 pass 1 (pipelined): h_c = sigma_c (u_c . w), coef_c = sigma_c h_c.
+// CGS2 pass 1 (pipelined): h_c = sigma_c (u_c . w), coef_c = sigma_c h_c.  The same
+// multi-dot c = M^T x serves the adaptive deflation space (columns of U or A U) with
+// another epilogue (DotEpi).
 template <typename TV, typename TACC>
 __global__ void __launch_bounds__(kThreads)
     k_pass1(int N, const TV* __restrict__ V, long long ldv, int k, int TR,
-            const TACC* __restrict__ w, Ctl ctl) {
+            const TACC* __restrict__ w, Ctl ctl, DotEpi epi) {
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ uint64_t bars[kMaxStages];
   __shared__ double swarp[kSlices * kSliceCols];
@@ -166,10 +176,25 @@ __global__ void __launch_bounds__(kThreads)
 #define GG_P1(NW) tile_dot<NW, TV, TACC>(acc, R.vt(st), R.wt(st), TR, warp, lane)
     GG_SLICE_SWITCH(nw, GG_P1)
 #undef GG_P1
-  });
+  }, epi.skip_slot);
   if (!ok) return;
   reduce_slices(acc, nw, k, kSlices, reinterpret_cast<double*>(smraw), swarp, sred);
   if (!last_block_reduce(sred, k, ctl.part, ctl.part2, ctl.ldp, ctl.ticket, tot)) return;
+  if (epi.mode == kEpiCoarse) {  // s = |mu| T^-1 c - c (adaptive deflation, Eq. 17)
+    const double mu = fabs(ctl.scal[S_MU]);
+    for (int t = threadIdx.x; t < k; t += blockDim.x) {
+      double y = 0.0;
+      for (int u = 0; u < k; ++u) y += epi.tinv[(size_t)t * epi.ldt + u] * tot[u];
+      const double sv = mu * y - tot[t];
+      ctl.sdefl[t] = sv;
+      ctl.sdefl32[t] = (float)sv;
+    }
+    return;
+  }
+  if (epi.mode == kEpiRaw) {
+    for (int t = threadIdx.x; t < k; t += blockDim.x) epi.out[t] = tot[t];
+    return;
+  }
   for (int c = threadIdx.x; c < k; c += blockDim.x) {
     const double hc = ctl.sigma[c] * tot[c];
     ctl.h[c] = hc;
@@ -518,6 +543,17 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// x += t + U s with the dense adaptive U (s in ctl.sdefl)
+__global__ void __launch_bounds__(kThreads)
+    k_xapply_dense(int N, double* __restrict__ x, const double* __restrict__ t, Defl d, Ctl ctl) {
+  if (ctl.flags[F_STOP]) return;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < N; row += gridDim.x * blockDim.x) {
+    double v = t[row];
+    for (int q = 0; q < d.qd; ++q) v += d.ud[(size_t)q * d.ldu + row] * ctl.sdefl[q];
+    x[row] += v;
+  }
+}
+
 // True residual in FP64 (Eq. 15): r = b - A x, u_0 = r stored in the basis precision,
 // rho0 on the first call, convergence / maxit decision, and the start of a new cycle.
 // With proj_t != null (deflation projector) the unprojected residual goes to proj_t, its
@@ -713,6 +749,19 @@ struct Kern {
              (const double*)a.ctl.cpart, scale, a.ctl, skip, proj);
   }
 
+  // c = M^T x over ncols columns of M (leading dimension ldm) with the pipelined multi-dot
+  // (FP64), finished by epi
+  static void udots(const CycleArgs& a, const double* M, long long ldm, int ncols,
+                    const double* x, DotEpi epi, bool pdl, cudaStream_t st) {
+    if constexpr (sizeof(TV) == sizeof(double) && sizeof(TACC) == sizeof(double)) {
+      const Grids& g = grids(a.sms);
+      const int tr = g.tr[ncols];
+      launch_k(pdl, k_pass1<TV, TACC>, grid_for((a.op.n + tr - 1) / tr, 1, g.p1[ncols]),
+               kThreads, ring_smem(ncols), st, a.op.n, (const TV*)M, ldm, ncols, tr,
+               (const TACC*)x, a.ctl, epi);
+    }
+  }
+
   static cudaError_t phase(const CycleArgs& a, int ph, int j, bool defl, double* x,
                            const double* b, cudaStream_t st, int* launches) {
     const int N = a.op.n;
@@ -737,12 +786,15 @@ struct Kern {
           else
             launch_k(pdl, k_spmv_dia<TA, TV, TACC, false>, gdd, kThreads, 0, st, N, a.op.dia,
                      a.op.ldd, dvals(a), xj, j, d, auvals(a), sdefl(a), w, a.ctl);
+        } else if (defl && !a.proj && d.qd > 0) {  // adaptive: plain rows + A U dense
+          launch_k(pdl, k_spmv_step<TA, TV, TACC, true>, gd, kThreads, 0, st, N, a.op.rowptr,
+                   a.op.col, vals(a), xj, j, sdefl(a), w, a.ctl, d);
         } else if (defl && !a.proj) {
           launch_k(pdl, k_spmv_step<TA, TV, TACC, true>, gd, kThreads, 0, st, N, a.op.xrp,
-                   a.op.xcol, xvals(a), xj, j, sdefl(a), w, a.ctl);
+                   a.op.xcol, xvals(a), xj, j, sdefl(a), w, a.ctl, d);
         } else {
           launch_k(pdl, k_spmv_step<TA, TV, TACC, false>, gd, kThreads, 0, st, N, a.op.rowptr,
-                   a.op.col, vals(a), xj, j, sdefl(a), w, a.ctl);
+                   a.op.col, vals(a), xj, j, sdefl(a), w, a.ctl, d);
         }
         nl = 1;
         if (a.proj) {  // w = P A v_j = A v_j - A U T^-1 U^T A v_j
@@ -756,7 +808,8 @@ struct Kern {
       case PH_DOT1: {
         const int tr = g.tr[k];
         launch_k(a.pdl != 0, k_pass1<TV, TACC>, grid_for((N + tr - 1) / tr, 1, g.p1[k]),
-                 kThreads, ring_smem(k), st, N, V, a.ldv, k, tr, (const TACC*)w, a.ctl);
+                 kThreads, ring_smem(k), st, N, V, a.ldv, k, tr, (const TACC*)w, a.ctl,
+                 DotEpi{kEpiArnoldi, nullptr, 0, nullptr, F_CYCLE_DONE});
         nl = 1;
         break;
       }
@@ -776,14 +829,28 @@ struct Kern {
       }
       case PH_DEFL: {  // U^T v_j and the correction for column j
         const TV* xj = V + (size_t)j * a.ldv;
-        coarse(a, xj, nullptr, F_CYCLE_DONE, 0, st, a.pdl != 0);  // s' = s / sigma_j
-        nl = 2;
+        if (d.qd > 0) {  // adaptive: one multi-dot over the dense U, then s' = |mu| T^-1 c - c
+          if constexpr (sizeof(TV) == sizeof(double))
+            udots(a, d.ud, d.ldu, d.qd, (const double*)xj,
+                  DotEpi{kEpiCoarse, d.tinv_a, d.qd, nullptr, F_CYCLE_DONE}, a.pdl != 0, st);
+          nl = 1;
+        } else {
+          coarse(a, xj, nullptr, F_CYCLE_DONE, 0, st, a.pdl != 0);  // s' = s / sigma_j
+          nl = 2;
+        }
         break;
       }
       case PH_CYCLE_END: {
         k_backsolve<<<1, 128, 0, st>>>(a.ctl);
         const int tiles = (N + kThreads - 1) / kThreads;
-        if (defl) {
+        if (defl && d.qd > 0) {  // adaptive: x += t + U s, s = |mu| T^-1 U^T t - U^T t
+          k_xupdate<TV, true><<<grid_for(tiles, 1, g.xupd_d), kThreads, 0, st>>>(N, V, a.ldv, x,
+                                                                                a.t, a.ctl);
+          udots(a, d.ud, d.ldu, d.qd, a.t,
+                DotEpi{kEpiCoarse, d.tinv_a, d.qd, nullptr, F_STOP}, false, st);
+          k_xapply_dense<<<grid_for(tiles, 1, g.xapply), kThreads, 0, st>>>(N, x, a.t, d, a.ctl);
+          nl = 4;
+        } else if (defl) {
           k_xupdate<TV, true><<<grid_for(tiles, 1, g.xupd_d), kThreads, 0, st>>>(N, V, a.ldv, x,
                                                                                 a.t, a.ctl);
           coarse(a, (const double*)a.t, nullptr, F_STOP, 0, st);
@@ -868,6 +935,14 @@ cudaError_t launch_init(const CycleArgs& a, double tol, double inner_tol, double
   cudaError_t e = prepare_all();
   if (e != cudaSuccess) return e;
   k_init<<<1, 32, 0, st>>>(a.ctl, tol, inner_tol, r0ref, mu, fixed, mixed, maxit);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_udots(const CycleArgs& a, const double* M, long long ldm, int ncols,
+                         const double* x, DotEpi epi, cudaStream_t st) {
+  cudaError_t e = prepare_all();
+  if (e != cudaSuccess) return e;
+  K64::udots(a, M, ldm, ncols, x, epi, false, st);
   return cudaGetLastError();
 }
 

@@ -815,6 +815,9 @@ gmres_status batch_solve_impl(int count, gmres_t const* hs, const double* const*
       return fail(nullptr, GMRES_ERR_INVALID_ARG, "all handles of a batch must use one precision");
     if (hs[i]->r > 0 && hs[i]->opts.deflation_mode == GMRES_DEFL_PROJECTOR)
       return fail(nullptr, GMRES_ERR_INVALID_ARG, "deflation_mode PROJECTOR is not available");
+    if (hs[i]->opts.deflation_mode == GMRES_DEFL_ADAPTIVE)
+      return fail(nullptr, GMRES_ERR_INVALID_ARG,
+                  "deflation_mode ADAPTIVE is for single-system solves");
   }
   int sms = hs[0]->sms;
   // workspaces of the handles serve the batch (allocated on the batch stream)

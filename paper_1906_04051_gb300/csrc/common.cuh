@@ -16,6 +16,7 @@ namespace gg {
 constexpr int kWarp = 32;
 constexpr int kMaxM = 64;               // largest restart length m
 constexpr int kMaxK = kMaxM + 1;        // basis columns held in a cycle
+constexpr int kMaxAdapt = 32;           // most columns of the adaptive deflation space
 constexpr int kMaxR = 6144;             // largest number of deflation aggregates
 constexpr int kThreads = 256;           // threads of the streaming kernels
 constexpr int kSlices = 8;              // column slices of a multi-dot (one per warp)
@@ -48,7 +49,7 @@ enum FlagSlot {
   F_DEFL_ON,         // the EBP correction is active (batched driver; set by the Ritz step)
   F_NFLAGS = 16
 };
-enum CountSlot { C_STEPS = 0, C_CYCLES, C_REFINE, C_MAXIT, C_NCOUNT = 8 };
+enum CountSlot { C_STEPS = 0, C_CYCLES, C_REFINE, C_MAXIT, C_QDEF, C_NCOUNT = 8 };  // C_QDEF: columns of the adaptive U
 
 // Device control block: all pointers into library-owned device memory.
 struct Ctl {
@@ -74,6 +75,17 @@ struct Ctl {
   int ldp;        // leading dimension of part (>= kMaxK + 1)
 };
 
+// Epilogue of a multi-dot kernel: the Arnoldi coefficients, the adaptive deflation's
+// coarse correction s = |mu| T^-1 c - c (into ctl.sdefl), or the raw dots (into out).
+enum { kEpiArnoldi = 0, kEpiCoarse = 1, kEpiRaw = 2 };
+struct DotEpi {
+  int mode;
+  const double* tinv;  // kEpiCoarse: k x k, row stride ldt
+  int ldt;
+  double* out;         // kEpiRaw
+  int skip_slot;       // flag that ends the launch at once (F_CYCLE_DONE, F_STOP, -1)
+};
+
 // Deflation data of one operator (A or A^T).
 // Diagonal storage of a banded operator: a_{i, i + off[d]} = dval[d * ldd + i].
 constexpr int kMaxDiag = 32;
@@ -97,6 +109,13 @@ struct Defl {
   const int* aucol;       // aggregate ids
   const double* auval;
   const float* auval32;   // FP32 copy (FP32 inner), may be null
+  // adaptive deflation: U and A U dense (qd columns of ldu rows), T^-1 (qd x qd); the
+  // step's coarse term is sum_t aud[t][i] s'_t instead of the A W row
+  const double* ud;
+  const double* aud;
+  const double* tinv_a;
+  long long ldu;
+  int qd;
 };
 
 // ---- element-type helpers ----

@@ -72,6 +72,10 @@ struct gmres_s {
   int ldh = 0, prec_ws = -1;
   long long ldv = 0;
   DevMem V, w, t, dctl, meta, part, part2, tickets, cpart, sdefl;
+  // adaptive deflation (GMRES_DEFL_ADAPTIVE): U, A U (ldv x rmax), T (rmax x rmax),
+  // T^-1 (q x q), a work vector, small scratch; aq columns in use
+  DevMem aU, aAU, aT, aTinv, au, asmall;
+  int aq = 0;
   Meta* hmeta = nullptr;  // pinned
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // per-phase profiling: events bracket each phase when enabled; launches always counted
@@ -111,6 +115,10 @@ inline size_t basis_elem(int prec) { return prec == P_FP64 ? 8 : (prec == P_FP32
 
 constexpr int kLdp = 80;  // >= kMaxK + 1, multiple of 16
 
+// Entries of the coarse correction s' (FP64, then its FP32 copy right after): one per
+// aggregate, or per column of the adaptive space (at most kMaxAdapt), plus one.
+inline int sdefl_len(const gmres_s* h) { return (h->r > kMaxAdapt ? h->r : kMaxAdapt) + 1; }
+
 // Lays out the control block for restart length ldh and returns the Ctl view.
 inline gmres_status ensure_workspace(gmres_s* h, int m, int prec) {
   const int ldh = m > h->ldh ? m : h->ldh;
@@ -140,7 +148,20 @@ inline gmres_status ensure_workspace(gmres_s* h, int m, int prec) {
     CK(h, cudaMemsetAsync(h->tickets.p, 0, sizeof(unsigned) * (1 + kMaxGroups), h->stream));
   }
   CK(h, h->cpart.ensure(sizeof(double) * (size_t)(h->npieces + 1)));
-  CK(h, h->sdefl.ensure(12 * (size_t)(h->r + 1)));
+  CK(h, h->sdefl.ensure(12 * (size_t)sdefl_len(h)));
+  if (h->opts.deflation_mode == GMRES_DEFL_ADAPTIVE && !h->aU.p) {
+    const size_t col = sizeof(double) * (size_t)ldv;
+    const size_t R = (size_t)h->opts.rmax;
+    CK(h, h->aU.ensure(col * R));
+    CK(h, h->aAU.ensure(col * R));
+    CK(h, h->au.ensure(col));
+    CK(h, cudaMemsetAsync(h->aU.p, 0, col * R, h->stream));
+    CK(h, cudaMemsetAsync(h->aAU.p, 0, col * R, h->stream));
+    CK(h, cudaMemsetAsync(h->au.p, 0, col, h->stream));
+    CK(h, h->aT.ensure(sizeof(double) * R * R));
+    CK(h, h->aTinv.ensure(sizeof(double) * R * R));
+    CK(h, h->asmall.ensure(sizeof(double) * (2 * kMaxK + 2 * (kMaxAdapt + 1) + 2) + 4 * sizeof(int)));
+  }
   CK(h, h->meta.ensure(sizeof(Meta)));
   if (!h->hmeta) CK(h, cudaMallocHost(&h->hmeta, sizeof(Meta)));
   if (!h->ev0) CK(h, cudaEventCreate(&h->ev0));
@@ -172,7 +193,7 @@ inline Ctl make_ctl(gmres_s* h) {
   c.part2 = h->part2.as<double>();
   c.cpart = h->cpart.as<double>();
   c.sdefl = h->sdefl.as<double>();
-  c.sdefl32 = reinterpret_cast<float*>(h->sdefl.as<double>() + (h->r + 1));
+  c.sdefl32 = reinterpret_cast<float*>(h->sdefl.as<double>() + sdefl_len(h));
   c.ldh = ldh;
   c.ldp = kLdp;
   return c;
@@ -299,4 +320,7 @@ gmres_status batch_solve_impl(int count, gmres_t const* hs, const double* const*
                               double* const* x, gmres_info* infos, cudaStream_t st,
                               long long* launches);
 void batch_forget(gmres_t h);
+// after a restart cycle: grows the adaptive deflation space (adaptive.cu)
+gmres_status adapt_update(gmres_s* h, CycleArgs& a);
+
 }  // namespace gg

@@ -101,8 +101,13 @@ enum Phase {
   PH_CYCLE_END,     // back substitution and x update
   PH_RITZ,          // |mu| from the Ritz values
   PH_PROJ_FINAL,    // projector: x = xh + U T^-1 U^T (b - A xh)
+  PH_ADAPT,         // adaptive deflation: update of U, A U, T, T^-1 after a cycle
   PH_COUNT
 };
+// c = M^T x over ncols FP64 columns of M (leading dimension ldm), pipelined multi-dot with
+// the given epilogue (adaptive deflation)
+cudaError_t launch_udots(const CycleArgs& a, const double* M, long long ldm, int ncols,
+                         const double* x, DotEpi epi, cudaStream_t st);
 cudaError_t launch_phase(const CycleArgs& a, int ph, int j, bool defl, double* x,
                          const double* b, cudaStream_t st, int* launches);
 // Control-block initialisation for a new solve.

@@ -354,12 +354,13 @@ __host__ __device__ inline int ring_stages(size_t stage_bytes) {
 // issued before pdl_wait() (the columns 0..k-1 are final by then); the slice of w joins
 // them before the wait too when w_early (w is not written by the predecessor), after it
 // otherwise.  After the wait, post_wait() runs on all threads (loads of the
-// predecessor's outputs); when the cycle has ended the copies in flight are drained and
-// false is returned, as it is (after recording GMRES_ERR_TIMEOUT and draining, with a
+// predecessor's outputs); when flags[skip_slot] is set (by default the cycle has ended)
+// the copies in flight are drained and false is returned, as it is (after recording GMRES_ERR_TIMEOUT and draining, with a
 // bound) when a copy never completes.
 template <typename TV, typename TACC, typename F, typename PW>
 __device__ bool ring_run(const Ring<TV, TACC>& R, int N, const TV* V, long long ldv,
-                         const TACC* w, Ctl& ctl, bool w_early, PW&& post_wait, F&& body) {
+                         const TACC* w, Ctl& ctl, bool w_early, PW&& post_wait, F&& body,
+                         int skip_slot = F_CYCLE_DONE) {
   __shared__ int s_pre;
   const int tiles = (N + R.TR - 1) / R.TR;
   const int nt = (int)blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -370,7 +371,7 @@ __device__ bool ring_run(const Ring<TV, TACC>& R, int N, const TV* V, long long 
     mbar_fence_init();
     // a cycle that has visibly ended already needs no prefetch (a stale read only costs
     // a wasted prefetch; the decision below is taken after the wait)
-    s_pre = *(volatile const int*)&ctl.flags[F_CYCLE_DONE] ? 0 : 1;
+    s_pre = (skip_slot >= 0 && *(volatile const int*)&ctl.flags[skip_slot]) ? 0 : 1;
   }
   __syncthreads();
   const bool pre = s_pre != 0;
@@ -378,7 +379,7 @@ __device__ bool ring_run(const Ring<TV, TACC>& R, int N, const TV* V, long long 
     for (int i = 0; i < first; ++i) R.issue_v(i, r0_of(i), V, ldv, w, w_early);
   pdl_wait();
   pdl_trigger();
-  const bool done = ctl.flags[F_CYCLE_DONE] != 0;
+  const bool done = skip_slot >= 0 && ctl.flags[skip_slot] != 0;
   if (pre && !w_early && threadIdx.x < 32)
     for (int i = 0; i < first; ++i) R.issue_w(i, r0_of(i), w);
   if (done) {

@@ -91,6 +91,8 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
   a.proj = (h->r > 0 && h->opts.deflation_mode == GMRES_DEFL_PROJECTOR) ? 1 : 0;
 
   const bool ebp = h->r > 0 && h->opts.deflation_mode == GMRES_DEFL_EBP;
+  const bool ada = h->opts.deflation_mode == GMRES_DEFL_ADAPTIVE;  // U grows from empty
+  if (ada) h->aq = 0;
   const int mu_mode = h->opts.mu_mode;
   double mu = 0.0;
   if (mu_mode == GMRES_MU_USER) mu = std::fabs(h->opts.mu_user);
@@ -111,7 +113,15 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
   int cycle = 0;
   gmres_status status = GMRES_OK;
   while (!h->hmeta->flags[F_STOP]) {
-    const bool defl_cycle = ebp && (mu_mode != GMRES_MU_RITZ_FIRST_CYCLE || cycle > 0);
+    const bool mu_known = mu_mode != GMRES_MU_RITZ_FIRST_CYCLE || cycle > 0;
+    const bool defl_cycle = (ebp || (ada && h->aq > 0)) && mu_known;
+    if (ada) {  // this cycle's dense deflation space (empty until the first update)
+      a.op.defl.ud = h->aU.as<double>();
+      a.op.defl.aud = h->aAU.as<double>();
+      a.op.defl.tinv_a = h->aTinv.as<double>();
+      a.op.defl.ldu = h->ldv;
+      a.op.defl.qd = defl_cycle ? h->aq : 0;
+    }
     if (defl_cycle) CK(h, phase(h, a, PH_DEFL, 0, true, x, b));
     const long long left = maxit - h->hmeta->counts[C_STEPS];
     const int jmax = (int)(left < m ? left : m);
@@ -123,8 +133,13 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
       if (defl_cycle) CK(h, phase(h, a, PH_DEFL, j + 1, true, x, b));
     }
     CK(h, phase(h, a, PH_CYCLE_END, 0, defl_cycle, x, b));
-    if (ebp && mu_mode == GMRES_MU_RITZ_FIRST_CYCLE && cycle == 0)
+    if ((ebp || ada) && mu_mode == GMRES_MU_RITZ_FIRST_CYCLE && cycle == 0)
       CK(h, phase(h, a, PH_RITZ, 0, false, x, b));
+    if (ada) {  // grow U from this cycle's H_k and basis (Sec. 3.3, Eq. 19)
+      CK(h, prof_mark(h, PH_ADAPT));
+      s = adapt_update(h, a);
+      if (s != GMRES_OK) return s;
+    }
     CK(h, phase(h, a, PH_RESIDUAL, 0, false, x, b));
     s = read_meta(h);
     if (s != GMRES_OK) return s;
@@ -156,7 +171,7 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
     info->refinements = h->hmeta->counts[C_REFINE];
     info->rel_res_est = h->hmeta->scal[S_EST];
     info->rel_res_true = h->hmeta->scal[S_TRUE];
-    info->mu = ebp ? h->hmeta->scal[S_MU] : 0.0;
+    info->mu = (ebp || ada) ? h->hmeta->scal[S_MU] : 0.0;
     info->ms_total = ms;
     info->status = status;
   }
@@ -201,6 +216,8 @@ cudaError_t noalloc_scratch(unsigned char** out) {
 gmres_status run_noalloc(gmres_s* h, OpHost& o, const double* b, const double* x0, int m,
                          double tol, long long maxit, double* x, gmres_info* info) {
   if (!b || !x) return fail(h, GMRES_ERR_INVALID_ARG, "b and x must be device pointers");
+  if (h->opts.deflation_mode == GMRES_DEFL_ADAPTIVE)
+    return fail(h, GMRES_ERR_INVALID_ARG, "gmres_solve_noalloc: GMRES_DEFL_ADAPTIVE allocates its space");
   if (m < 1 || m > kMaxM) return fail(h, GMRES_ERR_INVALID_ARG, "m must be in [1, 64]");
   if (!(tol >= 0.0) || maxit < 0) return fail(h, GMRES_ERR_INVALID_ARG, "tol >= 0, maxit >= 0");
   const int prec = prec_of(h->opts.precision);
@@ -222,7 +239,7 @@ gmres_status run_noalloc(gmres_s* h, OpHost& o, const double* b, const double* x
   const size_t oPart2 = take(sizeof(double) * (size_t)kMaxGroups * kLdp);
   const size_t oTick = take(sizeof(unsigned) * (1 + kMaxGroups));
   const size_t oCpart = take(sizeof(double) * (size_t)(h->npieces + 1));
-  const size_t oSdefl = take(12 * (size_t)(h->r + 1));
+  const size_t oSdefl = take(12 * (size_t)sdefl_len(h));
   if (off > kNoAllocBytes)
     return fail(h, GMRES_ERR_INVALID_ARG,
                 "gmres_solve_noalloc: workspace of " + std::to_string(off) +
@@ -262,7 +279,7 @@ gmres_status run_noalloc(gmres_s* h, OpHost& o, const double* b, const double* x
   c.part2 = reinterpret_cast<double*>(base + oPart2);
   c.cpart = reinterpret_cast<double*>(base + oCpart);
   c.sdefl = reinterpret_cast<double*>(base + oSdefl);
-  c.sdefl32 = reinterpret_cast<float*>(c.sdefl + (h->r + 1));
+  c.sdefl32 = reinterpret_cast<float*>(c.sdefl + sdefl_len(h));
   c.ldh = m;
   c.ldp = kLdp;
   a.V = base + oV;
@@ -357,6 +374,8 @@ void gmres_opts_default(gmres_opts* o) {
   o->precision = GMRES_FP64;
   o->deflation_mode = GMRES_DEFL_EBP;
   o->mu_mode = GMRES_MU_RITZ_FIRST_CYCLE;
+  o->rmax = 20;
+  o->ninv = 20;
 }
 
 gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
@@ -372,8 +391,17 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
   if (o) opts = *o;
   else gmres_opts_default(&opts);
   if (opts.precision < 0 || opts.precision > 2 || opts.deflation_mode < 0 ||
-      opts.deflation_mode > 2 || opts.mu_mode < 0 || opts.mu_mode > 2)
+      opts.deflation_mode > 3 || opts.mu_mode < 0 || opts.mu_mode > 2)
     return fail(nullptr, GMRES_ERR_INVALID_ARG, "invalid option value");
+  if (opts.deflation_mode == GMRES_DEFL_ADAPTIVE) {
+    if (r > 0)
+      return fail(nullptr, GMRES_ERR_INVALID_ARG,
+                  "GMRES_DEFL_ADAPTIVE builds U itself: pass no aggregates");
+    if (opts.precision != GMRES_FP64)
+      return fail(nullptr, GMRES_ERR_INVALID_ARG, "GMRES_DEFL_ADAPTIVE is FP64 only");
+    if (opts.rmax < 1 || opts.rmax > kMaxAdapt || opts.ninv < 1 || opts.ninv > 1000)
+      return fail(nullptr, GMRES_ERR_INVALID_ARG, "rmax must be in [1, 32], ninv in [1, 1000]");
+  }
 
   gmres_s* h = new gmres_s();
   const auto t_setup = std::chrono::steady_clock::now();
