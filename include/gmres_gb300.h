@@ -92,9 +92,12 @@ typedef enum {
                                H_k for its smallest-modulus eigenvalue (inverse power
                                method; a complex pair gives two vectors) is mapped through
                                the basis, u = V_k z, orthonormalised against U and
-                               appended; beyond rmax columns the column with the largest
-                               |T_jj| is dropped first.  W (gmres_defl) must be empty;
-                               FP64 only; single-system solves */
+                               appended; with rmax columns in U, the direction of the
+                               largest-modulus eigenvalue of T = U^T A U (two for a
+                               complex pair) leaves first: U keeps the complement of
+                               that eigenvalue's left eigenvector, a T-invariant
+                               subspace.  W (gmres_defl) must be empty; FP64 only;
+                               single-system solves */
 } gmres_deflation_mode;
 
 typedef enum {
@@ -219,11 +222,20 @@ typedef struct gmres_layout {
   int32_t r;          /* deflation vectors (aggregates); 0 without deflation */
   int32_t npieces;    /* runs of at most 1024 nodes in which U^T x is summed */
   int32_t ndiag;      /* diagonals of A in diagonal storage; 0: A is kept in CSR only */
-  int32_t reserved;
+  int32_t adapt_q;    /* GMRES_DEFL_ADAPTIVE: columns of U after the last solve, else 0 */
   int64_t nau;        /* entries of A W (coarse part of the deflated SpMV) */
   int64_t ldv;        /* rows per basis column in device memory (n rounded up) */
 } gmres_layout;
 gmres_status gmres_layout_query(gmres_t h, gmres_layout* out);
+
+/* The adaptive deflation space left by the last solve of a GMRES_DEFL_ADAPTIVE handle
+ * (Sec. 3.3, Eqs. 17-19): U (orthonormal, n x q) and T = U^T A U (q x q).  q (host,
+ * required) receives the column count, at most opts.rmax.  U (device, may be NULL)
+ * receives column c at U + c * ldu (ldu >= n); T (device, may be NULL) receives
+ * T[i * q + j] = u_i^T A u_j.  Call with both NULL to learn q first.  Synchronises the
+ * handle's stream.  The space belongs to the handle and is rebuilt (from empty) by the
+ * next solve.  Errors: INVALID_ARG (other deflation mode, null q, ldu < n), CUDA. */
+gmres_status gmres_adaptive_space(gmres_t h, int32_t* q, double* U, int64_t ldu, double* T);
 
 gmres_status gmres_set_stream(gmres_t h, void* stream);
 /* Message of the last error on this handle (or of the last failed create when h is

@@ -15,6 +15,9 @@ Parity status of each routine (what pins it, see tests/test_oracle_*.py):
                    estimate = true residual, MGS/CGS2 agreement
   arnoldi          Arnoldi relation and orthonormality checked with dense numpy algebra
   defl (EBP, P)    U^T (A M^-1) U = |mu| I, invariant-subspace eigenvalue shift, P A W = 0
+  adaptive         hess_invvec vs numpy eigenvectors (real and complex smallest pairs);
+                   adapt_drop vs scipy left eigenvectors and the remaining spectrum;
+                   the adaptive solve vs a direct solve, U orthonormal, T = U^T A U
   kappa_grad       dense adjoint (numpy) and central finite differences
 """
 from __future__ import annotations
@@ -102,6 +105,7 @@ def lib():
             L.orc_lu_solve.argtypes = [C.c_int32, _P, _P, _P]
             L.orc_hessenberg_eigs.argtypes = [C.c_int32, _P, _P, _P]
             L.orc_hess_invvec.argtypes = [C.c_int32, _P, C.c_int32, _P, _P]
+            L.orc_adapt_drop.argtypes = [C.c_int32, _P, C.c_int32, _P, _P]
             L.orc_defl_create.restype = _P
             L.orc_defl_create.argtypes = [C.c_int32, _P, _P, _P, C.c_int32, _P,
                                           C.POINTER(C.c_int)]
@@ -309,3 +313,18 @@ def arnoldi(A: CSR, v0, k: int, *, defl: Deflation | None = None, defl_mode=DEFL
                              defl_mode if defl is not None else DEFL_NONE, float(mu), ortho,
                              _p(v0), k, _p(V), _p(H))
     return V.reshape(k + 1, A.n).T.copy(), H.reshape(k + 1, k), done
+
+
+def adapt_drop(T):
+    """Drop step of the adaptive deflation (Sec. 3.3) on a full space: returns (Qc, Tn,
+    p) with Qc (q x (q-p)) an orthonormal basis of the complement of the left
+    eigenvector(s) of T's largest-modulus eigenvalue and Tn = Qc^T T Qc."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    q = T.shape[0]
+    Qc = np.zeros(q * q)
+    Tn = np.zeros(q * q)
+    p = lib().orc_adapt_drop(q, _p(T), q, _p(Qc), _p(Tn))
+    if p < 0:
+        raise RuntimeError("orc_adapt_drop: QR iteration failed")
+    nc = q - p
+    return Qc[: q * nc].reshape(q, nc).copy(), Tn[: nc * nc].reshape(nc, nc).copy(), p

@@ -544,6 +544,171 @@ int orc_hess_invvec(int32_t k, const double* H, int32_t ninv, double* z1, double
   return nvec;
 }
 
+/* Reduction of a general n x n matrix (row-major, in place) to upper Hessenberg form by
+ * Householder similarity transformations; the eigenvalues are unchanged. */
+static void hessenberg_reduce(int32_t n, double* a) {
+  double* v = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  for (int32_t k = 0; k + 2 < n; ++k) {
+    const int32_t len = n - k - 1;
+    double nx = 0.0;
+    for (int32_t i = 0; i < len; ++i) nx += a[(size_t)(k + 1 + i) * n + k] * a[(size_t)(k + 1 + i) * n + k];
+    nx = sqrt(nx);
+    if (nx == 0.0) continue;
+    const double x0 = a[(size_t)(k + 1) * n + k];
+    const double alpha = x0 >= 0.0 ? -nx : nx;
+    double vv = 0.0;
+    for (int32_t i = 0; i < len; ++i) {
+      v[i] = a[(size_t)(k + 1 + i) * n + k] - (i == 0 ? alpha : 0.0);
+      vv += v[i] * v[i];
+    }
+    if (vv == 0.0) continue;
+    const double beta = 2.0 / vv;
+    for (int32_t j = 0; j < n; ++j) { /* rows k+1.. : (I - beta v v^T) A */
+      double s = 0.0;
+      for (int32_t i = 0; i < len; ++i) s += v[i] * a[(size_t)(k + 1 + i) * n + j];
+      for (int32_t i = 0; i < len; ++i) a[(size_t)(k + 1 + i) * n + j] -= beta * s * v[i];
+    }
+    for (int32_t i = 0; i < n; ++i) { /* columns k+1.. : A (I - beta v v^T) */
+      double s = 0.0;
+      for (int32_t j = 0; j < len; ++j) s += a[(size_t)i * n + k + 1 + j] * v[j];
+      for (int32_t j = 0; j < len; ++j) a[(size_t)i * n + k + 1 + j] -= beta * s * v[j];
+    }
+    a[(size_t)(k + 1) * n + k] = alpha;
+    for (int32_t i = k + 2; i < n; ++i) a[(size_t)i * n + k] = 0.0;
+  }
+  free(v);
+}
+
+int orc_adapt_drop(int32_t q, const double* T, int32_t ldt, double* Qc, double* Tn) {
+  if (q < 1) return -1;
+  double* h = (double*)malloc(sizeof(double) * (size_t)q * q);
+  double* wr = (double*)malloc(sizeof(double) * (size_t)q);
+  double* wi = (double*)malloc(sizeof(double) * (size_t)q);
+  for (int32_t i = 0; i < q; ++i)
+    for (int32_t j = 0; j < q; ++j) h[(size_t)i * q + j] = T[(size_t)i * ldt + j];
+  hessenberg_reduce(q, h);
+  const int e = orc_hessenberg_eigs(q, h, wr, wi);
+  free(h);
+  if (e != 0) {
+    free(wr);
+    free(wi);
+    return -1;
+  }
+  /* the eigenvalue of largest modulus (the first one on ties), a + i b with b >= 0 */
+  int32_t best = 0;
+  double bmod = -1.0;
+  for (int32_t i = 0; i < q; ++i) {
+    const double md = hypot(wr[i], wi[i]);
+    if (md > bmod) {
+      bmod = md;
+      best = i;
+    }
+  }
+  const double la = wr[best], lb = fabs(wi[best]);
+  free(wr);
+  free(wi);
+  const int32_t p = lb != 0.0 ? 2 : 1;
+  /* left eigenvector y (T^T y = lambda y) by inverse iteration on the real form of
+   * T^T - lambda I: [[T^T - a I, b I], [-b I, T^T - a I]] [y_r; y_i] = rhs */
+  const int32_t n2 = p * q;
+  double* M = (double*)calloc((size_t)n2 * n2, sizeof(double));
+  for (int32_t i = 0; i < q; ++i)
+    for (int32_t j = 0; j < q; ++j) {
+      const double tv = T[(size_t)j * ldt + i] - (i == j ? la : 0.0);
+      M[(size_t)i * n2 + j] = tv;
+      if (p == 2) M[(size_t)(q + i) * n2 + q + j] = tv;
+    }
+  if (p == 2)
+    for (int32_t i = 0; i < q; ++i) {
+      M[(size_t)i * n2 + q + i] = lb;
+      M[(size_t)(q + i) * n2 + i] = -lb;
+    }
+  double mmax = 0.0;
+  for (int32_t i = 0; i < n2 * n2; ++i) mmax = fabs(M[i]) > mmax ? fabs(M[i]) : mmax;
+  const double eps = mmax > 0.0 ? 1e-14 * mmax : 1e-300;
+  int32_t* piv = (int32_t*)malloc(sizeof(int32_t) * (size_t)n2);
+  for (int32_t k = 0; k < n2; ++k) { /* LU, partial pivoting; a tiny pivot becomes eps */
+    int32_t pr = k;
+    for (int32_t i = k + 1; i < n2; ++i)
+      if (fabs(M[(size_t)i * n2 + k]) > fabs(M[(size_t)pr * n2 + k])) pr = i;
+    piv[k] = pr;
+    if (pr != k)
+      for (int32_t j = 0; j < n2; ++j) {
+        const double t = M[(size_t)k * n2 + j];
+        M[(size_t)k * n2 + j] = M[(size_t)pr * n2 + j];
+        M[(size_t)pr * n2 + j] = t;
+      }
+    if (fabs(M[(size_t)k * n2 + k]) <= eps) M[(size_t)k * n2 + k] = eps;
+    for (int32_t i = k + 1; i < n2; ++i) {
+      const double l = M[(size_t)i * n2 + k] / M[(size_t)k * n2 + k];
+      M[(size_t)i * n2 + k] = l;
+      for (int32_t j = k + 1; j < n2; ++j) M[(size_t)i * n2 + j] -= l * M[(size_t)k * n2 + j];
+    }
+  }
+  double* y = (double*)malloc(sizeof(double) * (size_t)n2);
+  for (int32_t i = 0; i < n2; ++i) y[i] = 1.0;
+  for (int it = 0; it < 3; ++it) {
+    orc_lu_solve(n2, M, piv, y);
+    const double ny = nrm2(y, n2);
+    for (int32_t i = 0; i < n2; ++i) y[i] /= ny;
+  }
+  free(M);
+  free(piv);
+  /* Householder QR of Y = [y_r (, y_i)]: Q = H_0 ... H_{p-1}; the last q - p columns of
+   * Q are an orthonormal basis of the vectors c with y^T c = 0 */
+  double* Y = (double*)malloc(sizeof(double) * (size_t)q * p);
+  double* hv = (double*)calloc((size_t)q * p, sizeof(double));
+  double hb[2] = {0.0, 0.0};
+  for (int32_t i = 0; i < q; ++i)
+    for (int32_t c = 0; c < p; ++c) Y[(size_t)i * p + c] = y[(size_t)c * q + i];
+  for (int32_t c = 0; c < p; ++c) {
+    double nx = 0.0;
+    for (int32_t i = c; i < q; ++i) nx += Y[(size_t)i * p + c] * Y[(size_t)i * p + c];
+    nx = sqrt(nx);
+    const double x0 = Y[(size_t)c * p + c];
+    const double alpha = x0 >= 0.0 ? -nx : nx;
+    double vv = 0.0;
+    for (int32_t i = c; i < q; ++i) {
+      hv[(size_t)c * q + i] = Y[(size_t)i * p + c] - (i == c ? alpha : 0.0);
+      vv += hv[(size_t)c * q + i] * hv[(size_t)c * q + i];
+    }
+    hb[c] = vv > 0.0 ? 2.0 / vv : 0.0;
+    for (int32_t c2 = c + 1; c2 < p; ++c2) {
+      double sd = 0.0;
+      for (int32_t i = c; i < q; ++i) sd += hv[(size_t)c * q + i] * Y[(size_t)i * p + c2];
+      for (int32_t i = c; i < q; ++i) Y[(size_t)i * p + c2] -= hb[c] * sd * hv[(size_t)c * q + i];
+    }
+  }
+  const int32_t nc = q - p;
+  for (int32_t i = 0; i < q; ++i)
+    for (int32_t c = 0; c < nc; ++c) Qc[(size_t)i * nc + c] = (i == p + c) ? 1.0 : 0.0;
+  for (int32_t c = p - 1; c >= 0; --c)
+    for (int32_t j = 0; j < nc; ++j) {
+      double sd = 0.0;
+      for (int32_t i = c; i < q; ++i) sd += hv[(size_t)c * q + i] * Qc[(size_t)i * nc + j];
+      for (int32_t i = c; i < q; ++i) Qc[(size_t)i * nc + j] -= hb[c] * sd * hv[(size_t)c * q + i];
+    }
+  free(Y);
+  free(hv);
+  free(y);
+  /* Tn = Qc^T T Qc */
+  double* W = (double*)malloc(sizeof(double) * (size_t)q * (nc > 0 ? nc : 1));
+  for (int32_t i = 0; i < q; ++i)
+    for (int32_t j = 0; j < nc; ++j) {
+      double sd = 0.0;
+      for (int32_t l = 0; l < q; ++l) sd += T[(size_t)i * ldt + l] * Qc[(size_t)l * nc + j];
+      W[(size_t)i * nc + j] = sd;
+    }
+  for (int32_t i = 0; i < nc; ++i)
+    for (int32_t j = 0; j < nc; ++j) {
+      double sd = 0.0;
+      for (int32_t l = 0; l < q; ++l) sd += Qc[(size_t)l * nc + i] * W[(size_t)l * nc + j];
+      Tn[(size_t)i * nc + j] = sd;
+    }
+  free(W);
+  return p;
+}
+
 /* Dense deflation space of the adaptive variant: U (N x q, orthonormal), A U, T = U^T A U
  * and its LU; at most rmax columns. */
 typedef struct {
@@ -569,8 +734,9 @@ static void adapt_apply_Minv(const adapt_space* s, double mu, const double* v, d
 
 /* After a cycle of k steps: the inverse-power eigenvector(s) z of H_k give u = V_k z
  * (Eq. 19), orthonormalised against U (two classical Gram-Schmidt passes) and appended;
- * at rmax columns the column whose Rayleigh quotient T_jj is largest in modulus is
- * dropped first (the last column takes its place).  T and its LU follow U. */
+ * at rmax columns the direction of T's largest-modulus eigenvalue (two for a complex
+ * pair) is deflated first: U <- U Qc with Qc spanning the complement of its left
+ * eigenvector (orc_adapt_drop).  T and its LU follow U. */
 static int adapt_update(adapt_space* s, int32_t N, const int32_t* rowptr, const int32_t* col,
                         const double* val, const double* V, const double* Hr, int32_t m,
                         int32_t k, int32_t ninv) {
@@ -597,19 +763,39 @@ static int adapt_update(adapt_space* s, int32_t N, const int32_t* rowptr, const 
     const double n1 = nrm2(u, N);
     if (!(n1 > 1e-10 * n0)) continue; /* already in span(U) */
     for (int32_t i = 0; i < N; ++i) u[i] /= n1;
-    if (s->q == R) { /* r > rmax: deflate the column with the largest |T_jj| */
-      int32_t jd = 0;
-      for (int32_t j = 1; j < s->q; ++j)
-        if (fabs(s->T[(size_t)j * R + j]) > fabs(s->T[(size_t)jd * R + jd])) jd = j;
-      const int32_t last = s->q - 1;
-      if (jd != last) {
-        memcpy(s->U + (size_t)jd * N, s->U + (size_t)last * N, sizeof(double) * (size_t)N);
-        memcpy(s->AU + (size_t)jd * N, s->AU + (size_t)last * N, sizeof(double) * (size_t)N);
-        for (int32_t j = 0; j < s->q; ++j) s->T[(size_t)jd * R + j] = s->T[(size_t)last * R + j];
-        for (int32_t i = 0; i < s->q; ++i) s->T[(size_t)i * R + jd] = s->T[(size_t)i * R + last];
-        s->T[(size_t)jd * R + jd] = s->T[(size_t)last * R + last];
+    if (s->q == R) { /* r > rmax: deflate the direction of T's largest eigenvalue */
+      const int32_t q0 = s->q;
+      double* Qc = (double*)malloc(sizeof(double) * (size_t)q0 * q0);
+      double* Tn = (double*)malloc(sizeof(double) * (size_t)q0 * q0);
+      const int p = orc_adapt_drop(q0, s->T, R, Qc, Tn);
+      if (p < 0) {
+        free(Qc);
+        free(Tn);
+        free(hk);
+        free(z);
+        free(u);
+        free(c);
+        return 1;
       }
-      s->q = last;
+      const int32_t nc = q0 - p;
+      double* row = (double*)malloc(sizeof(double) * (size_t)q0);
+      for (int pass = 0; pass < 2; ++pass) { /* U <- U Qc, then A U <- A U Qc */
+        double* X = pass == 0 ? s->U : s->AU;
+        for (int32_t i = 0; i < N; ++i) {
+          for (int32_t t = 0; t < q0; ++t) row[t] = X[(size_t)t * N + i];
+          for (int32_t cc = 0; cc < nc; ++cc) {
+            double sd = 0.0;
+            for (int32_t t = 0; t < q0; ++t) sd += row[t] * Qc[(size_t)t * nc + cc];
+            X[(size_t)cc * N + i] = sd;
+          }
+        }
+      }
+      for (int32_t i = 0; i < nc; ++i)
+        for (int32_t j = 0; j < nc; ++j) s->T[(size_t)i * R + j] = Tn[(size_t)i * nc + j];
+      free(row);
+      free(Qc);
+      free(Tn);
+      s->q = nc;
     }
     const int32_t q = s->q;
     memcpy(s->U + (size_t)q * N, u, sizeof(double) * (size_t)N);

@@ -100,6 +100,18 @@ typedef struct {
  * subspace.  Returns the number of vectors (1 or 2), 0 if k < 1. */
 int orc_hess_invvec(int32_t k, const double* H, int32_t ninv, double* z1, double* z2);
 
+/* The drop step of the adaptive deflation when U is full (Sec. 3.3: the vectors that
+ * correspond to the largest eigenvalues of T_r leave the space).  T: q x q (row stride
+ * ldt).  Its eigenvalue lambda of largest modulus (Householder reduction to Hessenberg
+ * form, then orc_hessenberg_eigs; the first on ties) has a left eigenvector y (T^T y =
+ * lambda y; inverse iteration, three solves from all ones, on the real 2q x 2q form when
+ * lambda is complex).  The real vectors c with y^T c = 0 form a T-invariant subspace
+ * that carries the other eigenvalues; Qc (q x (q-p), row-major, orthonormal columns) is
+ * a basis of it (the last q - p columns of the Householder QR factor of [Re y, Im y]) and
+ * Tn = Qc^T T Qc ((q-p) x (q-p)).  Returns p (1, or 2 for a complex pair) or -1 when
+ * the QR iteration fails. */
+int orc_adapt_drop(int32_t q, const double* T, int32_t ldt, double* Qc, double* Tn);
+
 /* Solves A x = b.  d may be NULL (no deflation).  hist (2*maxit doubles, may be NULL)
  * receives, per Arnoldi step, (step index j within its cycle, |gamma_{j+1}| / rho0). */
 int orc_gmres(int32_t N, const int32_t* rowptr, const int32_t* col, const double* val,

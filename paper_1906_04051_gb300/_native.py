@@ -60,11 +60,11 @@ class gmres_info(C.Structure):
 
 class gmres_layout(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("r", C.c_int32), ("npieces", C.c_int32),
-                ("ndiag", C.c_int32), ("reserved", C.c_int32), ("nau", C.c_int64),
+                ("ndiag", C.c_int32), ("adapt_q", C.c_int32), ("nau", C.c_int64),
                 ("ldv", C.c_int64)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 # name -> (restype, argtypes); every symbol declared in include/gmres_gb300.h
@@ -83,6 +83,7 @@ SIGNATURES = {
                                     C.c_int32, C.c_double, C.c_int64, C.POINTER(_P),
                                     C.POINTER(gmres_info), _P]),
     "gmres_layout_query": (C.c_int, [_P, C.POINTER(gmres_layout)]),
+    "gmres_adaptive_space": (C.c_int, [_P, C.POINTER(C.c_int32), _P, C.c_int64, _P]),
     "gmres_set_stream": (C.c_int, [_P, _P]),
     "gmres_profile": (C.c_int, [_P, C.c_int32, C.c_int32, C.POINTER(C.c_double),
                                 C.POINTER(C.c_int64)]),

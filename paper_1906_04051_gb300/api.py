@@ -52,6 +52,7 @@ class Solver:
         _dev(val, torch.float64, "val", col.numel())
         self.n = n
         self.nnz = col.numel()
+        self.device = rowptr.device
         csr = N.gmres_csr(n, self.nnz, rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
         defl = None
         if agg is not None and r > 0:
@@ -130,6 +131,20 @@ class Solver:
         out = N.gmres_layout()
         _check(N.load().gmres_layout_query(self._h, C.byref(out)), self._h)
         return out.as_dict()
+
+    def adaptive_space(self):
+        """(U, T) of the adaptive deflation space left by the last solve: U (n x q,
+        orthonormal columns), T = U^T A U (q x q); gmres_adaptive_space."""
+        lib = N.load()
+        q = C.c_int32()
+        _check(lib.gmres_adaptive_space(self._h, C.byref(q), None, 0, None), self._h)
+        U = torch.empty((q.value, self.n), dtype=torch.float64, device=self.device)
+        T = torch.empty((q.value, q.value), dtype=torch.float64, device=self.device)
+        if q.value:
+            self._set_stream()
+            _check(lib.gmres_adaptive_space(self._h, C.byref(q), U.data_ptr(), self.n,
+                                            T.data_ptr()), self._h)
+        return U.t(), T
 
     def close(self):
         h = getattr(self, "_h", None)

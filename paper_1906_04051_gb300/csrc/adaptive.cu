@@ -4,11 +4,14 @@
 // matrix H_k for its smallest-modulus eigenvalue (inverse power method; a complex pair of
 // smallest eigenvalues gives two vectors spanning its invariant subspace), u = V_k z,
 // orthonormalised against U (two classical Gram-Schmidt passes) and appended to U; A u is
-// appended to A U and T = U^T A U grows by a row and a column; beyond rmax columns the
-// column with the largest |T_jj| is dropped first (the last column takes its place).
-// T^-1 follows.  Arithmetic runs in the kernels below and in the pipelined multi-dot of
-// arnoldi.cu; the host only sequences them and reads the few scalars that decide the
-// branches (vector count, norms, T's diagonal).
+// appended to A U and T = U^T A U grows by a row and a column.  With rmax columns already
+// in U, the direction of T's largest-modulus eigenvalue leaves first (two directions for
+// a complex pair): U <- U Qc, A U <- A U Qc, T <- Qc^T T Qc, where Qc is an orthonormal
+// basis of the complement of that eigenvalue's left eigenvector(s), a T-invariant
+// subspace carrying the other eigenvalues.  T^-1 follows.  Arithmetic runs in the
+// kernels below and in the pipelined multi-dot of arnoldi.cu; the host only sequences
+// them and reads the few scalars that decide the branches (vector count, norms, the
+// number of dropped directions).
 #include <cmath>
 #include <cstring>
 
@@ -242,20 +245,219 @@ __global__ void k_adapt_tset(double* __restrict__ T, int ldt, int q, const doubl
   for (int i = threadIdx.x; i < q; i += blockDim.x) T[(size_t)q * ldt + i] = c2[i];
 }
 
-// T: row and column last move to jd (the dropped column's place)
-__global__ void k_adapt_tmove(double* __restrict__ T, int ldt, int last, int jd) {
-  __shared__ double row[kMaxAdapt], colv[kMaxAdapt];
-  for (int j = threadIdx.x; j <= last; j += blockDim.x) {
-    row[j] = T[(size_t)last * ldt + j];
-    colv[j] = T[(size_t)j * ldt + last];
+// ---- drop step at rmax, one warp --------------------------------------------------
+// T (q x q, row stride ldt): Householder reduction of a copy to Hessenberg form, Francis
+// QR (hqr_warp) for the eigenvalue lambda = a + i b of largest modulus, its left
+// eigenvector y (T^T y = lambda y) by three inverse iterations from all ones on the real
+// form [[T^T - a I, b I], [-b I, T^T - a I]] (LU with partial pivoting, first index on
+// ties; a pivot of modulus <= 1e-14 max|entry| becomes that bound), Householder QR of
+// Y = [Re y (, Im y)] and Qc = (H_0 ... H_{p-1})[:, p:] (row stride kMaxAdapt), the
+// orthonormal basis of {c : y^T c = 0}; T's leading (q-p) x (q-p) block becomes
+// Qc^T T Qc.  out[0] = p (1, or 2 for a complex pair), out[1] = 1 if the QR iteration
+// did not converge.
+__global__ void __launch_bounds__(32)
+    k_adapt_drop(double* __restrict__ T, int ldt, int q, double* __restrict__ Qc,
+                 int* __restrict__ out) {
+  constexpr int Q = kMaxAdapt;
+  __shared__ double M[4 * Q * Q];  // Hessenberg copy, then the shifted system, then Qc | T Qc
+  __shared__ double T0[Q * Q];
+  __shared__ double y[2 * Q], hv[2][Q], hb[2], sv[Q];
+  __shared__ int piv[2 * Q];
+  __shared__ double sre, sim, smod;
+  __shared__ int sfail;
+  const int lane = threadIdx.x;
+  for (int t = lane; t < q * q; t += 32) {
+    const double v = T[(size_t)(t / q) * ldt + t % q];
+    T0[t] = v;
+    M[t] = v;
   }
-  __syncthreads();
-  for (int j = threadIdx.x; j <= last; j += blockDim.x) {
-    T[(size_t)jd * ldt + j] = row[j];
-    T[(size_t)j * ldt + jd] = colv[j];
+  __syncwarp();
+  // Householder reduction of M (row stride q) to upper Hessenberg form
+  for (int k = 0; k + 2 < q; ++k) {
+    const int len = q - k - 1;
+    const double x = lane < len ? M[(k + 1 + lane) * q + k] : 0.0;
+    const double nx = sqrt(warp_sum(x * x));
+    if (nx == 0.0) continue;
+    const double x0 = __shfl_sync(0xffffffffu, x, 0);
+    const double alpha = x0 >= 0.0 ? -nx : nx;
+    const double v = lane < len ? x - (lane == 0 ? alpha : 0.0) : 0.0;
+    const double vv = warp_sum(v * v);
+    if (vv == 0.0) continue;
+    const double beta = 2.0 / vv;
+    sv[lane] = v;
+    __syncwarp();
+    if (lane < q) {  // (I - beta v v^T) on rows k+1.., column lane
+      double sd = 0.0;
+      for (int i = 0; i < len; ++i) sd += sv[i] * M[(k + 1 + i) * q + lane];
+      for (int i = 0; i < len; ++i) M[(k + 1 + i) * q + lane] -= beta * sd * sv[i];
+    }
+    __syncwarp();
+    if (lane < q) {  // on columns k+1.., row lane
+      double sd = 0.0;
+      for (int j = 0; j < len; ++j) sd += M[lane * q + k + 1 + j] * sv[j];
+      for (int j = 0; j < len; ++j) M[lane * q + k + 1 + j] -= beta * sd * sv[j];
+    }
+    __syncwarp();
+    if (lane == 0) M[(k + 1) * q + k] = alpha;
+    if (lane >= 1 && lane < len) M[(k + 1 + lane) * q + k] = 0.0;
+    __syncwarp();
   }
+  hqr_warp(M, q, sre, sim, smod, sfail);
+  if (sfail) {
+    if (lane == 0) {
+      out[0] = 0;
+      out[1] = 1;
+    }
+    return;
+  }
+  const double la = sre, lb = sim;
+  const int p = lb != 0.0 ? 2 : 1, n2 = p * q;
+  // the shifted real system (row stride n2)
+  double mx = 0.0;
+  for (int t = lane; t < n2 * n2; t += 32) {
+    const int i = t / n2, j = t % n2, bi = i / q, ii = i % q, bj = j / q, jj = j % q;
+    double v;
+    if (bi == bj) v = T0[jj * q + ii] - (ii == jj ? la : 0.0);
+    else if (bi == 0) v = ii == jj ? lb : 0.0;
+    else v = ii == jj ? -lb : 0.0;
+    M[t] = v;
+    mx = fmax(mx, fabs(v));
+  }
+  mx = warp_max(mx);
+  const double eps = mx > 0.0 ? 1e-14 * mx : 1e-300;
+  __syncwarp();
+  for (int k = 0; k < n2; ++k) {
+    double bv = -1.0;
+    int bi = n2;
+    for (int i = k + lane; i < n2; i += 32) {
+      const double a = fabs(M[i * n2 + k]);
+      if (a > bv) { bv = a; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (bi >= n2) bi = k;  // no comparable entry (NaN column): keep the row order
+    if (lane == 0) piv[k] = bi;
+    if (bi != k)
+      for (int j = lane; j < n2; j += 32) {
+        const double t = M[k * n2 + j];
+        M[k * n2 + j] = M[bi * n2 + j];
+        M[bi * n2 + j] = t;
+      }
+    __syncwarp();
+    if (lane == 0 && fabs(M[k * n2 + k]) <= eps) M[k * n2 + k] = eps;
+    __syncwarp();
+    const double pv = M[k * n2 + k];
+    for (int i = k + 1 + lane; i < n2; i += 32) {
+      const double l = M[i * n2 + k] / pv;
+      M[i * n2 + k] = l;
+      for (int j = k + 1; j < n2; ++j) M[i * n2 + j] -= l * M[k * n2 + j];
+    }
+    __syncwarp();
+  }
+  for (int i = lane; i < n2; i += 32) y[i] = 1.0;
+  __syncwarp();
+  for (int it = 0; it < 3; ++it) {
+    if (lane == 0)
+      for (int k = 0; k < n2; ++k)
+        if (piv[k] != k) {
+          const double t = y[k];
+          y[k] = y[piv[k]];
+          y[piv[k]] = t;
+        }
+    __syncwarp();
+    for (int j = 0; j < n2; ++j) {  // L (unit diagonal), by columns
+      const double yj = y[j];
+      for (int i = j + 1 + lane; i < n2; i += 32) y[i] -= M[i * n2 + j] * yj;
+      __syncwarp();
+    }
+    for (int i = n2 - 1; i >= 0; --i) {  // U, by columns
+      if (lane == 0) y[i] /= M[i * n2 + i];
+      __syncwarp();
+      const double yi = y[i];
+      for (int r = lane; r < i; r += 32) y[r] -= M[r * n2 + i] * yi;
+      __syncwarp();
+    }
+    double ss = 0.0;
+    for (int i = lane; i < n2; i += 32) ss += y[i] * y[i];
+    const double inv = 1.0 / sqrt(warp_sum(ss));
+    for (int i = lane; i < n2; i += 32) y[i] *= inv;
+    __syncwarp();
+  }
+  // Householder QR of Y = [y[0..q) (, y[q..2q))]; lane i holds row i
+  double yc[2];
+  yc[0] = lane < q ? y[lane] : 0.0;
+  yc[1] = (p == 2 && lane < q) ? y[q + lane] : 0.0;
+  for (int c = 0; c < p; ++c) {
+    const double x = (lane >= c && lane < q) ? yc[c] : 0.0;
+    const double nx = sqrt(warp_sum(x * x));
+    const double x0 = __shfl_sync(0xffffffffu, yc[c], c);
+    const double alpha = x0 >= 0.0 ? -nx : nx;
+    const double v = (lane >= c && lane < q) ? x - (lane == c ? alpha : 0.0) : 0.0;
+    const double vv = warp_sum(v * v);
+    const double beta = vv > 0.0 ? 2.0 / vv : 0.0;
+    hv[c][lane] = v;
+    if (lane == 0) hb[c] = beta;
+    if (c + 1 < p) {
+      const double sd = warp_sum(v * yc[c + 1]);
+      if (lane >= c && lane < q) yc[c + 1] -= beta * sd * v;
+    }
+  }
+  __syncwarp();
+  const int nc = q - p;
+  double* Qs = M;          // q x nc, row stride Q
+  double* Ws = M + Q * Q;  // T Qc, row stride Q
+  if (lane < nc) {         // column lane of (H_0 ... H_{p-1}) E, E = I[:, p:]
+    for (int i = 0; i < q; ++i) Qs[i * Q + lane] = i == p + lane ? 1.0 : 0.0;
+    for (int c = p - 1; c >= 0; --c) {
+      double sd = 0.0;
+      for (int i = c; i < q; ++i) sd += hv[c][i] * Qs[i * Q + lane];
+      for (int i = c; i < q; ++i) Qs[i * Q + lane] -= hb[c] * sd * hv[c][i];
+    }
+    for (int i = 0; i < q; ++i) {
+      double sd = 0.0;
+      for (int l = 0; l < q; ++l) sd += T0[i * q + l] * Qs[l * Q + lane];
+      Ws[i * Q + lane] = sd;
+    }
+  }
+  __syncwarp();
+  if (lane < nc) {
+    for (int i = 0; i < nc; ++i) {
+      double sd = 0.0;
+      for (int l = 0; l < q; ++l) sd += Qs[l * Q + i] * Ws[l * Q + lane];
+      T[(size_t)i * ldt + lane] = sd;
+    }
+    for (int i = 0; i < q; ++i) Qc[i * Q + lane] = Qs[i * Q + lane];
+  }
+  if (lane == 0) {
+    out[0] = p;
+    out[1] = 0;
+  }
+}
+
+// U <- U Qc and A U <- A U Qc in place (q columns to nc), thread per row
+__global__ void __launch_bounds__(kThreads)
+    k_adapt_rotate(int N, double* __restrict__ U, double* __restrict__ AU, long long ld, int q,
+                   int nc, const double* __restrict__ Qc) {
+  __shared__ double sq[kMaxAdapt * kMaxAdapt];
+  for (int t = threadIdx.x; t < q * kMaxAdapt; t += blockDim.x) sq[t] = Qc[t];
   __syncthreads();
-  if (threadIdx.x == 0) T[(size_t)jd * ldt + jd] = T[(size_t)last * ldt + last];
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < N; row += gridDim.x * blockDim.x)
+    for (int pass = 0; pass < 2; ++pass) {
+      double* X = pass == 0 ? U : AU;
+      double u[kMaxAdapt];
+#pragma unroll
+      for (int t = 0; t < kMaxAdapt; ++t) u[t] = t < q ? X[(size_t)t * ld + row] : 0.0;
+      for (int c = 0; c < nc; ++c) {
+        double sd = 0.0;
+#pragma unroll
+        for (int t = 0; t < kMaxAdapt; ++t)
+          if (t < q) sd += u[t] * sq[t * kMaxAdapt + c];
+        X[(size_t)c * ld + row] = sd;
+      }
+    }
 }
 
 // Tinv (q x q, row stride q) = T^-1 by Gauss-Jordan with partial pivoting, one block;
@@ -320,7 +522,8 @@ gmres_status adapt_update(gmres_s* h, CycleArgs& a) {
   double* c1 = z + 2 * kMaxK;            // kMaxAdapt + 1
   double* c2 = c1 + kMaxAdapt + 1;       // kMaxAdapt + 1
   double* nrm = c2 + kMaxAdapt + 1;      // 2
-  int* iv = reinterpret_cast<int*>(nrm + 2);  // nvec, bad
+  double* qc = nrm + 2;                  // kMaxAdapt x kMaxAdapt
+  int* iv = reinterpret_cast<int*>(qc + kMaxAdapt * kMaxAdapt);  // nvec, bad, p, fail
   const int tiles = (N + kThreads - 1) / kThreads;
   const int grid = grid_for(tiles, 1, 8 * h->sms);
   const Ctl& ctl = a.ctl;
@@ -351,25 +554,19 @@ gmres_status adapt_update(gmres_s* h, CycleArgs& a) {
     CK(h, cudaMemcpyAsync(hn, nrm, sizeof(hn), cudaMemcpyDeviceToHost, st));
     CK(h, cudaStreamSynchronize(st));
     if (!(hn[1] > 1e-10 * hn[0])) continue;  // already in span(U)
-    if (q == R) {  // r > rmax: deflate the column whose |T_jj| is largest
-      double d[kMaxAdapt];
-      for (int j = 0; j < q; ++j)
-        CK(h, cudaMemcpyAsync(d + j, T + (size_t)j * R + j, sizeof(double), cudaMemcpyDeviceToHost,
-                              st));
+    if (q == R) {  // U is full: the direction(s) of T's largest eigenvalue leave first
+      k_adapt_drop<<<1, 32, 0, st>>>(T, R, q, qc, iv + 2);
+      CK(h, cudaGetLastError());
+      int hd[2] = {0, 0};
+      CK(h, cudaMemcpyAsync(hd, iv + 2, sizeof(hd), cudaMemcpyDeviceToHost, st));
       CK(h, cudaStreamSynchronize(st));
-      int jd = 0;
-      for (int j = 1; j < q; ++j)
-        if (std::fabs(d[j]) > std::fabs(d[jd])) jd = j;
-      const int last = q - 1;
-      if (jd != last) {
-        CK(h, cudaMemcpyAsync(U + (size_t)jd * ld, U + (size_t)last * ld, sizeof(double) * N,
-                              cudaMemcpyDeviceToDevice, st));
-        CK(h, cudaMemcpyAsync(AU + (size_t)jd * ld, AU + (size_t)last * ld, sizeof(double) * N,
-                              cudaMemcpyDeviceToDevice, st));
-        k_adapt_tmove<<<1, 32, 0, st>>>(T, R, last, jd);
-        ++nl;
-      }
-      q = last;
+      if (hd[1] || hd[0] < 1 || hd[0] > q)
+        return fail(h, GMRES_ERR_SINGULAR_COARSE,
+                    "adaptive deflation: the QR iteration on T = U^T A U did not converge");
+      const int nc = q - hd[0];
+      k_adapt_rotate<<<grid, kThreads, 0, st>>>(N, U, AU, ld, q, nc, qc);
+      nl += 2;
+      q = nc;
     }
     k_adapt_scale<<<grid, kThreads, 0, st>>>(N, u, nrm + 1, U + (size_t)q * ld);
     k_adapt_spmv<<<grid, kThreads, 0, st>>>(N, a.op.rowptr, a.op.col, a.op.val,

@@ -612,16 +612,23 @@ __device__ void backsolve_block(Ctl& ctl, double* R, double* sg, double* sy) {
   }
 }
 
-// One warp (lanes 0..31 of the calling warp); A is kMaxM^2 doubles of shared scratch.
-__device__ void ritz_warp(Ctl& ctl, double* A, double& smod, int& sfail) {
-  const int n = ctl.flags[F_K];
+// Eigenvalues of the n x n upper Hessenberg matrix A in shared memory (row stride n,
+// overwritten) by the Francis double-shift QR iteration, run by one warp (lanes 0..31 of
+// the calling warp).  On return (after a __syncwarp) smod holds the largest eigenvalue
+// modulus and (sre, sim) that eigenvalue (sim >= 0 for a complex pair; among equal
+// moduli the one of lowest position on the diagonal); sfail = 1 if the iteration did not
+// converge within 60 n sweeps.
+__device__ void hqr_warp(double* A, int n, double& sre, double& sim, double& smod, int& sfail) {
   const int lane = threadIdx.x & 31;
-  if (n <= 0) return;
-  const int ldh = ctl.ldh;
 #define AA(i, j) A[(i) * n + (j)]
-  for (int t = lane; t < n * n; t += 32) AA(t / n, t % n) = ctl.Hr[(size_t)(t / n) * ldh + t % n];
-  if (lane == 0) { smod = 0.0; sfail = 0; }
+  if (lane == 0) { smod = 0.0; sre = 0.0; sim = 0.0; sfail = 0; }
   __syncwarp();
+  // eigenvalues are found from the bottom of the diagonal upwards, so ">=" keeps the
+  // lowest-positioned one among equal moduli
+  auto take = [&](double re, double im) {
+    const double md = im == 0.0 ? fabs(re) : hypot(re, im);
+    if (md >= smod) { smod = md; sre = re; sim = fabs(im); }
+  };
   double an = 0.0;
   for (int t = lane; t < n * n; t += 32)
     if (t % n >= t / n - 1) an += fabs(A[t]);
@@ -638,7 +645,7 @@ __device__ void ritz_warp(Ctl& ctl, double* A, double& smod, int& sfail) {
     if (l > 0 && lane == 0) AA(l, l - 1) = 0.0;
     __syncwarp();
     if (l == hi) {
-      if (lane == 0) smod = fmax(smod, fabs(AA(hi, hi)));
+      if (lane == 0) take(AA(hi, hi), 0.0);
       __syncwarp();
       --hi;
       its = 0;
@@ -647,16 +654,17 @@ __device__ void ritz_warp(Ctl& ctl, double* A, double& smod, int& sfail) {
     if (l == hi - 1) {
       const double a = AA(hi - 1, hi - 1), b = AA(hi - 1, hi), c = AA(hi, hi - 1), d = AA(hi, hi);
       const double p = 0.5 * (a - d), disc = p * p + b * c, mid = 0.5 * (a + d);
-      double m2;
-      if (disc >= 0.0) {
-        const double q = sqrt(disc);
-        const double l1 = mid + (p >= 0.0 ? q : -q);
-        const double l2 = (l1 != 0.0) ? (a * d - b * c) / l1 : mid - (p >= 0.0 ? q : -q);
-        m2 = fmax(fabs(l1), fabs(l2));
-      } else {
-        m2 = hypot(mid, sqrt(-disc));
+      if (lane == 0) {
+        if (disc >= 0.0) {
+          const double q = sqrt(disc);
+          const double l1 = mid + (p >= 0.0 ? q : -q);
+          const double l2 = (l1 != 0.0) ? (a * d - b * c) / l1 : mid - (p >= 0.0 ? q : -q);
+          take(l2, 0.0);  // position hi
+          take(l1, 0.0);  // position hi - 1
+        } else {
+          take(mid, sqrt(-disc));
+        }
       }
-      if (lane == 0) smod = fmax(smod, m2);
       __syncwarp();
       hi -= 2;
       its = 0;
@@ -739,6 +747,19 @@ __device__ void ritz_warp(Ctl& ctl, double* A, double& smod, int& sfail) {
   }
 #undef AA
   __syncwarp();
+}
+
+// |mu| from the Ritz values of the cycle's H_k (one warp; A is kMaxM^2 doubles of shared
+// scratch): the largest eigenvalue modulus.
+__device__ void ritz_warp(Ctl& ctl, double* A, double& smod, int& sfail) {
+  const int n = ctl.flags[F_K];
+  const int lane = threadIdx.x & 31;
+  if (n <= 0) return;
+  const int ldh = ctl.ldh;
+  for (int t = lane; t < n * n; t += 32) A[t] = ctl.Hr[(size_t)(t / n) * ldh + t % n];
+  __syncwarp();
+  __shared__ double sre, sim;
+  hqr_warp(A, n, sre, sim, smod, sfail);
   if (lane == 0) {
     if (sfail || !(smod > 0.0) || !isfinite(smod)) {
       ctl.flags[F_STATUS] = GMRES_ERR_SINGULAR_COARSE;
@@ -748,6 +769,7 @@ __device__ void ritz_warp(Ctl& ctl, double* A, double& smod, int& sfail) {
     }
   }
 }
+
 
 __device__ void init_ctl(Ctl& ctl, double tol, double inner_tol, double r0ref, double mu,
                        int fixed, int mixed, long long maxit) {

@@ -601,6 +601,28 @@ gmres_status gmres_layout_query(gmres_t h, gmres_layout* out) {
   out->ndiag = h->fwd.dia.nd;
   out->nau = h->fwd.nau;
   out->ldv = h->ldv;
+  out->adapt_q = h->opts.deflation_mode == GMRES_DEFL_ADAPTIVE ? h->aq : 0;
+  return GMRES_OK;
+}
+
+gmres_status gmres_adaptive_space(gmres_t h, int32_t* q, double* U, int64_t ldu, double* T) {
+  if (!h) return fail(nullptr, GMRES_ERR_INVALID_ARG, "null handle");
+  if (h->opts.deflation_mode != GMRES_DEFL_ADAPTIVE)
+    return fail(h, GMRES_ERR_INVALID_ARG, "gmres_adaptive_space: not an adaptive-deflation handle");
+  if (!q) return fail(h, GMRES_ERR_INVALID_ARG, "gmres_adaptive_space: null q");
+  if (U && ldu < h->n) return fail(h, GMRES_ERR_INVALID_ARG, "gmres_adaptive_space: ldu < n");
+  const int nq = h->aU.p ? h->aq : 0;
+  *q = nq;
+  if (nq == 0) return GMRES_OK;
+  cudaStream_t st = h->stream;
+  const size_t d = sizeof(double);
+  if (U)
+    CK(h, cudaMemcpy2DAsync(U, d * (size_t)ldu, h->aU.p, d * (size_t)h->ldv, d * (size_t)h->n, nq,
+                            cudaMemcpyDeviceToDevice, st));
+  if (T)
+    CK(h, cudaMemcpy2DAsync(T, d * (size_t)nq, h->aT.p, d * (size_t)h->opts.rmax, d * (size_t)nq,
+                            nq, cudaMemcpyDeviceToDevice, st));
+  CK(h, cudaStreamSynchronize(st));
   return GMRES_OK;
 }
 

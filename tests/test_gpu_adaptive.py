@@ -76,3 +76,70 @@ def test_adaptive_options_rejected(G, orc):
                                precision=G.FP32_INNER)
     with pytest.raises(G.GmresError):
         gpu_solver_from_oracle(G, A, None, 0, deflation_mode=G.DEFL_ADAPTIVE, rmax=0)
+
+
+def test_adaptive_space_matches_oracle(G, orc):
+    # the space itself: U (up to rounding, same signs) and T = U^T A U after 6 cycles
+    p = W.convdiff(40, pe=25.0, sigma=0.5, seed=140, px=2, py=3)
+    A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f, p.u)
+    s = gpu_solver_from_oracle(G, A, None, 0, deflation_mode=G.DEFL_ADAPTIVE, rmax=20,
+                               mu_mode=1, mu_user=5.0, fixed_iterations=True)
+    _, ig = s.solve(to_dev(b), m=15, tol=0.0, maxit=90)
+    Ug, Tg = (t.cpu().numpy() for t in s.adaptive_space())
+    _, io, Uo = orc.gmres(A, b, m=15, tol=0.0, maxit=90, defl_mode=orc.DEFL_ADAPTIVE, rmax=20,
+                          mu_mode=1, mu_user=5.0, fixed_iterations=True, return_u=True)
+    assert Ug.shape == Uo.shape and Ug.shape[1] == io["q"] >= 3
+    assert s.layout()["adapt_q"] == Ug.shape[1]
+    assert np.abs(Ug - Uo).max() <= 1e-8
+    As = A.to_scipy()
+    assert np.abs(Tg - Uo.T @ (As @ Uo)).max() <= 1e-10 * np.abs(Tg).max()
+
+
+def test_adaptive_space_invariants(G, orc):
+    # Eq. 17 on the returned space: U orthonormal, T = U^T A U, U^T (A M^-1) U = |mu| I
+    p = W.workload1()
+    A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f, p.u)
+    s = gpu_solver_from_oracle(G, A, None, 0, deflation_mode=G.DEFL_ADAPTIVE, rmax=4)
+    _, ig = s.solve(to_dev(b), m=20, tol=1e-10, maxit=20000)
+    assert ig["status"] == 0 and ig["cycles"] > 4
+    Ug, Tg = (t.cpu().numpy() for t in s.adaptive_space())
+    q = Ug.shape[1]
+    assert q == 4  # the space filled up and was truncated, never beyond rmax
+    assert np.abs(Ug.T @ Ug - np.eye(q)).max() <= 1e-12
+    As = A.to_scipy()
+    AU = As @ Ug
+    assert np.abs(Tg - Ug.T @ AU).max() <= 1e-12 * np.abs(Tg).max()
+    mu = abs(ig["mu"])
+    AMU = AU + AU @ (mu * np.linalg.solve(Tg, np.eye(q)) - np.eye(q))  # A M^-1 U
+    assert np.abs(Ug.T @ AMU - mu * np.eye(q)).max() <= 1e-9 * mu
+
+
+def test_adaptive_space_rejected_for_other_modes(G, orc):
+    p = W.workload1()
+    A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f, p.u)
+    s = gpu_solver_from_oracle(G, A, p.agg, p.r)
+    with pytest.raises(G.GmresError):
+        s.adaptive_space()
+
+
+@pytest.mark.parametrize("rmax", [1, 3, 6])
+def test_adaptive_drop_fixed_iterations_parity(G, orc, rmax):
+    # many cycles at a full space: every update drops the direction(s) of T's largest
+    # eigenvalue first; the solution and the space (as a projector U U^T, which does not
+    # depend on the basis chosen inside it) agree with the oracle's
+    p = W.convdiff(40, pe=25.0, sigma=0.5, seed=140, px=2, py=3)
+    A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f, p.u)
+    s = gpu_solver_from_oracle(G, A, None, 0, deflation_mode=G.DEFL_ADAPTIVE, rmax=rmax,
+                               mu_mode=1, mu_user=5.0, fixed_iterations=True)
+    xg, ig = s.solve(to_dev(b), m=10, tol=0.0, maxit=160)
+    xg = xg.cpu().numpy()
+    Ug, _ = s.adaptive_space()
+    Ug = Ug.cpu().numpy()
+    xo, io, Uo = orc.gmres(A, b, m=10, tol=0.0, maxit=160, defl_mode=orc.DEFL_ADAPTIVE,
+                           rmax=rmax, mu_mode=1, mu_user=5.0, fixed_iterations=True,
+                           return_u=True)
+    assert ig["iters"] == io["iters"] == 160 and ig["cycles"] == io["cycles"] == 16
+    assert Ug.shape == Uo.shape and 1 <= Ug.shape[1] <= rmax
+    assert relerr(xg, xo) <= 1e-9
+    Pg, Po = Ug @ Ug.T, Uo @ Uo.T
+    assert np.abs(Pg - Po).max() <= 1e-8
