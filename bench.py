@@ -172,6 +172,8 @@ def main():
                     help="skip the time-to-1e-10 comparison on q1-n2048")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched (one graph launch) vs sequential comparison")
+    ap.add_argument("--no-adaptive", action="store_true",
+                    help="skip the adaptive-deflation time-to-tol on the bench system")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -322,6 +324,27 @@ def main():
         e2e = {"value": world * args.steps / (e_tot / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # ---- the paper's adaptive deflation (U grown from H_m eigenvectors after every
+    # restart, rmax 20) and plain GMRES(50) on the same system, time to tol 1e-8
+    adaptive = None
+    if rank == 0 and not args.no_adaptive:
+        adaptive = {"workload": "q1-n1024 GMRES(50) tol 1e-8 (the system above), U grown "
+                                "from the eigenvectors of H_m after every restart"}
+        for name, kw in (("adaptive_rmax20", dict(deflation_mode=G.DEFL_ADAPTIVE, rmax=20)),
+                         ("no_deflation", dict(deflation_mode=G.DEFL_NONE))):
+            sa = G.Solver(rowptr, col, val, None, 0, **kw)
+            ev0.record(stream)
+            _, ia = sa.solve(b, m=M, tol=TOL, maxit=20000)
+            ev1.record(stream)
+            ev1.synchronize()
+            adaptive[name] = {"ms": ev0.elapsed_time(ev1), "iters": ia["iters"],
+                              "cycles": ia["cycles"], "status": ia["status"],
+                              "rel_res_true": ia["rel_res_true"]}
+            if kw["deflation_mode"] == G.DEFL_ADAPTIVE:
+                adaptive[name]["q"] = sa.layout()["adapt_q"]
+            sa.close()
+        adaptive["ebp_r1024"] = {"ms": statistics.median(step_ms), "iters": it}
+
     # ---- time to a true relative residual of 1e-10 on q1-n2048: FP64 vs FP32 / BF16 inner
     mixed = None
     if rank == 0 and not args.no_mixed:
@@ -413,6 +436,7 @@ def main():
             "e2e": e2e,
             "mixed_precision": mixed,
             "batched": batched,
+            "adaptive": adaptive,
             "cpu_baseline": cb,
         }
         print(json.dumps(out), flush=True)
