@@ -8,6 +8,10 @@ compiled with gcc at ``-O2`` and loaded through ctypes.
 
 Parity status of each routine (what pins it, see tests/test_oracle_*.py):
   q1_assemble      closed-form Q1 stencils, nnz counts, manufactured-solution order 2
+  q2_bratu         the paper's Table 1 nnz and CSR bytes, element matrices vs exact 1-D
+                   Kronecker forms (sympy), Jacobian vs finite differences of the
+                   residual, Newton's quadratic convergence, the z-independence and
+                   x/y symmetries of the discrete Bratu solution
   spmv, transpose  scipy.sparse products, <Ax,y> = <x,A^T y>
   lu               numpy.linalg.solve
   hessenberg_eigs  numpy.linalg.eigvals, companion matrices with known roots
@@ -106,6 +110,10 @@ def lib():
             L.orc_hessenberg_eigs.argtypes = [C.c_int32, _P, _P, _P]
             L.orc_hess_invvec.argtypes = [C.c_int32, _P, C.c_int32, _P, _P]
             L.orc_adapt_drop.argtypes = [C.c_int32, _P, C.c_int32, _P, _P]
+            L.orc_q2_nnz.restype = C.c_int64
+            L.orc_q2_nnz.argtypes = [C.c_int32]
+            L.orc_q2_element.argtypes = [C.c_double, C.c_double, _P, _P, _P]
+            L.orc_q2_bratu_assemble.argtypes = [C.c_int32, C.c_double, _P, _P, _P, _P, _P]
             L.orc_defl_create.restype = _P
             L.orc_defl_create.argtypes = [C.c_int32, _P, _P, _P, C.c_int32, _P,
                                           C.POINTER(C.c_int)]
@@ -189,6 +197,33 @@ def q1_assemble(n: int, kappa, beta, f, u=None):
     b = np.empty(N)
     lib().orc_q1_assemble(n, _p(kappa), float(beta[0]), float(beta[1]), _p(f), _p(uu),
                           _p(rowptr), _p(col), _p(val), _p(b))
+    return CSR(rowptr, col, val), b
+
+
+def q2_nnz(n: int) -> int:
+    return int(lib().orc_q2_nnz(n))
+
+
+def q2_element(h: float, lam: float, ue=None):
+    """Element Jacobian (27 x 27) and residual (27) of the Q2 Bratu element."""
+    Je = np.empty(27 * 27)
+    Re = np.empty(27)
+    uu = None if ue is None else _f64(ue).reshape(-1)
+    lib().orc_q2_element(float(h), float(lam), _p(uu), _p(Je), _p(Re))
+    return Je.reshape(27, 27), Re
+
+
+def q2_bratu_assemble(n: int, lam: float, u=None):
+    """Newton system of the 3-D Bratu problem on n^3 Q2 elements at u: (CSR J, b = -R)."""
+    N = (2 * n + 1) ** 3
+    uu = None if u is None else _f64(u).reshape(-1)
+    assert uu is None or uu.size == N
+    nnz = q2_nnz(n)
+    rowptr = np.empty(N + 1, np.int32)
+    col = np.empty(nnz, np.int32)
+    val = np.empty(nnz)
+    b = np.empty(N)
+    lib().orc_q2_bratu_assemble(n, float(lam), _p(uu), _p(rowptr), _p(col), _p(val), _p(b))
     return CSR(rowptr, col, val), b
 
 

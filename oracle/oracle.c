@@ -129,6 +129,163 @@ void orc_q1_kappa_grad(int32_t n, const double* lam, const double* x, double* gr
 /* Sparse and dense building blocks                                                      */
 /* ------------------------------------------------------------------------------------ */
 
+/* ------------------------------------------------------------------------------------ */
+/* 3-D Bratu problem on 27-node triquadratic hexahedra (Sec. 3.1, Eqs. 2-9)              */
+/* ------------------------------------------------------------------------------------ */
+
+/* Nodes per direction M = 2n + 1; node (I, J, K) -> (K M + J) M + I.  Along one
+ * direction a vertex node (even index) shares elements with the nodes within 2 of it,
+ * a mid-edge node (odd index) only with those within 1. */
+static void q2_range(int32_t M, int32_t I, int32_t* lo, int32_t* hi) {
+  const int32_t r = (I % 2 == 0) ? 2 : 1;
+  *lo = I - r < 0 ? 0 : I - r;
+  *hi = I + r > M - 1 ? M - 1 : I + r;
+}
+
+static int q2_dirichlet(int32_t M, int32_t I, int32_t J) {
+  return I == 0 || J == 0 || I == M - 1 || J == M - 1; /* x- and y-faces (Eqs. 3-4) */
+}
+
+int64_t orc_q2_nnz(int32_t n) {
+  const int32_t M = 2 * n + 1;
+  int64_t nnz = 0;
+  for (int32_t K = 0; K < M; ++K)
+    for (int32_t J = 0; J < M; ++J)
+      for (int32_t I = 0; I < M; ++I) {
+        if (q2_dirichlet(M, I, J)) {
+          nnz += 1;
+          continue;
+        }
+        int32_t a0, a1, b0, b1, c0, c1;
+        q2_range(M, I, &a0, &a1);
+        q2_range(M, J, &b0, &b1);
+        q2_range(M, K, &c0, &c1);
+        nnz += (int64_t)(a1 - a0 + 1) * (b1 - b0 + 1) * (c1 - c0 + 1);
+      }
+  return nnz;
+}
+
+void orc_q2_element(double h, double lambda, const double* ue, double* Je, double* Re) {
+  /* Element of side h, local node l = a + 3 b + 9 c (a, b, c in {0, 1, 2} along x, y, z).
+   * 1-D quadratic Lagrange functions on [0,1] with nodes 0, 1/2, 1:
+   *   p0 = (1 - s)(1 - 2 s), p1 = 4 s (1 - s), p2 = s (2 s - 1).
+   * R_e[l] = - int grad(u_h) . grad(phi_l) + lambda int exp(u_h) phi_l        (Eq. 7)
+   * J_e[l][m] = dR_e[l]/du_m = - int grad(phi_m) . grad(phi_l)
+   *                            + lambda int exp(u_h) phi_m phi_l               (Eq. 9)
+   * integrated by the 3 x 3 x 3 Gauss-Legendre rule (exact for the polynomial parts). */
+  const double gs = sqrt(0.6);
+  const double xg[3] = {0.5 * (1.0 - gs), 0.5, 0.5 * (1.0 + gs)};
+  const double wg[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+  double P[3][3], D[3][3]; /* P[g][a] = p_a(x_g), D[g][a] = p_a'(x_g) */
+  for (int g = 0; g < 3; ++g) {
+    const double t = xg[g];
+    P[g][0] = (1.0 - t) * (1.0 - 2.0 * t);
+    P[g][1] = 4.0 * t * (1.0 - t);
+    P[g][2] = t * (2.0 * t - 1.0);
+    D[g][0] = 4.0 * t - 3.0;
+    D[g][1] = 4.0 - 8.0 * t;
+    D[g][2] = 4.0 * t - 1.0;
+  }
+  for (int l = 0; l < 27 * 27; ++l) Je[l] = 0.0;
+  for (int l = 0; l < 27; ++l) Re[l] = 0.0;
+  for (int gz = 0; gz < 3; ++gz)
+    for (int gy = 0; gy < 3; ++gy)
+      for (int gx = 0; gx < 3; ++gx) {
+        const double w = wg[gx] * wg[gy] * wg[gz] * h * h * h;
+        double phi[27], dx[27], dy[27], dz[27];
+        for (int c = 0; c < 3; ++c)
+          for (int b = 0; b < 3; ++b)
+            for (int a = 0; a < 3; ++a) {
+              const int l = a + 3 * b + 9 * c;
+              phi[l] = P[gx][a] * P[gy][b] * P[gz][c];
+              dx[l] = D[gx][a] * P[gy][b] * P[gz][c] / h;
+              dy[l] = P[gx][a] * D[gy][b] * P[gz][c] / h;
+              dz[l] = P[gx][a] * P[gy][b] * D[gz][c] / h;
+            }
+        double ug = 0.0, ux = 0.0, uy = 0.0, uz = 0.0;
+        for (int l = 0; l < 27; ++l) {
+          const double v = ue ? ue[l] : 0.0;
+          ug += v * phi[l];
+          ux += v * dx[l];
+          uy += v * dy[l];
+          uz += v * dz[l];
+        }
+        const double eg = exp(ug);
+        for (int l = 0; l < 27; ++l) {
+          Re[l] += w * (-(ux * dx[l] + uy * dy[l] + uz * dz[l]) + lambda * eg * phi[l]);
+          for (int m = 0; m < 27; ++m)
+            Je[l * 27 + m] += w * (-(dx[m] * dx[l] + dy[m] * dy[l] + dz[m] * dz[l]) +
+                                   lambda * eg * phi[m] * phi[l]);
+        }
+      }
+}
+
+int orc_q2_bratu_assemble(int32_t n, double lambda, const double* u, int32_t* rowptr,
+                          int32_t* col, double* val, double* b) {
+  const int32_t M = 2 * n + 1;
+  const int32_t N = M * M * M;
+  /* pattern: mesh connectivity, columns ascending; Dirichlet rows hold du_i = 0 (Sec. 3.1) */
+  int64_t pos = 0;
+  for (int32_t K = 0; K < M; ++K)
+    for (int32_t J = 0; J < M; ++J)
+      for (int32_t I = 0; I < M; ++I) {
+        const int32_t row = (K * M + J) * M + I;
+        rowptr[row] = (int32_t)pos;
+        if (q2_dirichlet(M, I, J)) {
+          col[pos] = row;
+          val[pos] = 1.0;
+          ++pos;
+          continue;
+        }
+        int32_t a0, a1, b0, b1, c0, c1;
+        q2_range(M, I, &a0, &a1);
+        q2_range(M, J, &b0, &b1);
+        q2_range(M, K, &c0, &c1);
+        for (int32_t k = c0; k <= c1; ++k)
+          for (int32_t j = b0; j <= b1; ++j)
+            for (int32_t i = a0; i <= a1; ++i) {
+              col[pos] = (k * M + j) * M + i;
+              val[pos] = 0.0;
+              ++pos;
+            }
+      }
+  rowptr[N] = (int32_t)pos;
+  for (int32_t r = 0; r < N; ++r) b[r] = 0.0;
+  /* element loop: J = sum_e J_e, b = -R = -sum_e R_e on the rows that are not Dirichlet */
+  double Je[27 * 27], Re[27], ue[27];
+  int32_t gid[27];
+  int dir[27];
+  for (int32_t ez = 0; ez < n; ++ez)
+    for (int32_t ey = 0; ey < n; ++ey)
+      for (int32_t ex = 0; ex < n; ++ex) {
+        for (int c = 0; c < 3; ++c)
+          for (int bb = 0; bb < 3; ++bb)
+            for (int a = 0; a < 3; ++a) {
+              const int l = a + 3 * bb + 9 * c;
+              const int32_t I = 2 * ex + a, J = 2 * ey + bb, K = 2 * ez + c;
+              gid[l] = (K * M + J) * M + I;
+              dir[l] = q2_dirichlet(M, I, J);
+              ue[l] = u ? u[gid[l]] : 0.0;
+            }
+        orc_q2_element(1.0 / n, lambda, ue, Je, Re);
+        for (int l = 0; l < 27; ++l) {
+          if (dir[l]) continue;
+          const int32_t row = gid[l];
+          b[row] -= Re[l];
+          for (int m = 0; m < 27; ++m) {
+            int32_t lo = rowptr[row], hi = rowptr[row + 1] - 1; /* binary search */
+            while (lo < hi) {
+              const int32_t mid = (lo + hi) / 2;
+              if (col[mid] < gid[m]) lo = mid + 1;
+              else hi = mid;
+            }
+            val[lo] += Je[l * 27 + m];
+          }
+        }
+      }
+  return 0;
+}
+
 void orc_spmv(int32_t N, const int32_t* rowptr, const int32_t* col, const double* val,
               const double* x, double* y) {
   for (int32_t i = 0; i < N; ++i) {

@@ -8,6 +8,7 @@
  * Every routine follows the paper (Ioannidis et al., arXiv:1906.04051) step by step,
  * in FP64, with no blocking, fusion or reordering:
  *   - Q1 Galerkin assembly with Dirichlet row replacement      (Sec. 3.1, Eqs. 6-8)
+ *   - the paper's 3-D Bratu Newton system on Q2 hexahedra       (Sec. 3.1, Eqs. 2-9)
  *   - restarted GMRES(m), Arnoldi + Givens least squares       (Sec. 3.2, Eqs. 10-15)
  *   - right preconditioning by deflation M^-1 = I + U(|mu|T^-1 - I)U^T, T = U^T A U
  *                                                              (Sec. 3.3, Eqs. 16-18)
@@ -36,6 +37,21 @@ int orc_q1_assemble(int32_t n, const double* kappa, double bx, double by, const 
                     const double* u, int32_t* rowptr, int32_t* col, double* val, double* b);
 /* dL/dkappa_e = - sum_{i in e, i interior} lam_i (K1 x_e)_i  (adjoint of the assembly). */
 void orc_q1_kappa_grad(int32_t n, const double* lam, const double* x, double* grad);
+
+/* ---- 3-D Bratu problem (Sec. 3.1, Eqs. 2-9): lap u + lambda exp(u) = 0 on the unit
+ * cube, u = 0 on the x- and y-faces, du/dz = 0 on the z-faces; n x n x n elements with
+ * 27 nodes (triquadratic), M = 2n + 1 nodes per direction, node (I, J, K) ->
+ * (K M + J) M + I ---- */
+int64_t orc_q2_nnz(int32_t n);
+/* Element Jacobian J_e (27x27 row-major) and residual R_e (27) for nodal values ue
+ * (NULL: zero), local node l = a + 3b + 9c, by 3x3x3 Gauss-Legendre quadrature. */
+void orc_q2_element(double h, double lambda, const double* ue, double* Je, double* Re);
+/* The Newton system J(u) du = -R(u) (Eq. 9): A = J (CSR, ascending columns, the mesh
+ * connectivity pattern), b = -R.  Rows of x- and y-face nodes are replaced by du_i = 0
+ * (one stored 1.0, b_i = 0); the other rows keep their couplings to those columns.
+ * u may be NULL (u = 0).  Returns 0. */
+int orc_q2_bratu_assemble(int32_t n, double lambda, const double* u, int32_t* rowptr,
+                          int32_t* col, double* val, double* b);
 
 /* ---- sparse / dense kernels ---- */
 void orc_spmv(int32_t N, const int32_t* rowptr, const int32_t* col, const double* val,
