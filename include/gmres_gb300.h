@@ -225,6 +225,9 @@ typedef struct gmres_layout {
   int32_t adapt_q;    /* GMRES_DEFL_ADAPTIVE: columns of U after the last solve, else 0 */
   int64_t nau;        /* entries of A W (coarse part of the deflated SpMV) */
   int64_t ldv;        /* rows per basis column in device memory (n rounded up) */
+  int32_t spmv_lanes; /* CSR SpMV: lanes per row (8 for rows of 16+ entries on average;
+                         0: a thread per row, or diagonal storage) */
+  int32_t reserved;
 } gmres_layout;
 gmres_status gmres_layout_query(gmres_t h, gmres_layout* out);
 
@@ -267,6 +270,53 @@ gmres_status q1_assemble(int32_t n, const double* kappa, double bx, double by,
  * stiffness.  lam, x (device, (n+1)^2), grad (device, n*n). */
 gmres_status q1_kappa_grad(int32_t n, const double* lam, const double* x, double* grad,
                            void* stream);
+
+/* ---- The paper's benchmark: 3-D Bratu problem (Sec. 3.1, Eqs. 2-9) -------------------
+ * lap u + lambda exp(u) = 0 on the unit cube, u = 0 on the x- and y-faces, du/dz = 0 on
+ * the z-faces; Galerkin method with n^3 cubic 27-node (triquadratic) elements,
+ * M = 2n + 1 nodes per direction, node (I, J, K) -> (K M + J) M + I, N = M^3.  Newton's
+ * method solves J(u) du = -R(u) (Eq. 9) with this library's GMRES(m).  Rows of x- and
+ * y-face nodes are replaced by du_i = 0 (one entry 1.0, b_i = 0); the other rows keep
+ * their couplings to those columns (the pattern is the mesh connectivity, as counted by
+ * the paper's Table 1).  The element integrals use 3 x 3 x 3 Gauss-Legendre points. */
+
+/* nnz of the Newton matrix: M (4M - 4) + S^2 (S + 6), S = 8n - 5 (Table 1: 1,603,945 at
+ * n = 15, 108,583,705 at n = 60). */
+int64_t q2_nnz(int32_t n);
+
+/* The Newton system at u (device, N entries; NULL: u = 0): rowptr (N + 1), col and val
+ * (q2_nnz(n) entries; columns ascending), b = -R(u) (N).  All device, caller-owned.
+ * Deterministic.  Errors: INVALID_ARG (n < 1, null output, non-finite lambda, nnz or
+ * N >= 2^31), CUDA. */
+gmres_status q2_bratu_assemble(int32_t n, double lambda, const double* u, int32_t* rowptr,
+                               int32_t* col, double* val, double* b, void* stream);
+
+typedef struct {
+  int32_t newton_iters;   /* Newton steps taken */
+  int32_t status;         /* GMRES_OK when ||du||_inf <= newton_tol, else why it stopped */
+  int64_t gmres_iters;    /* Arnoldi steps over all linear solves */
+  double du_inf;          /* max |du_i| of the last step */
+  double last_rel_res;    /* true relative residual of the last linear solve */
+  float ms_total;         /* device time of the whole Newton iteration */
+  float ms_assemble;      /* of which assembly */
+  float ms_solve;         /* of which GMRES solves (setup excluded) */
+  int32_t reserved;
+  int64_t step_iters[32]; /* GMRES steps of Newton steps 1..32 */
+  double step_du[32];     /* ||du||_inf of Newton steps 1..32 */
+} q2_newton_info;
+
+/* Newton's method for the Bratu problem from u (device, N entries, updated in place):
+ * per step the system is assembled, a handle is created with opts and W (W may be NULL;
+ * its aggregates index the N nodes), GMRES(m) solves J du = -R from du = 0 to tol
+ * (relative; a step whose solve stops at maxit is still taken: inexact Newton), and
+ * u += du.  Stops when max |du_i| <= newton_tol (status GMRES_OK) or after max_newton
+ * steps (GMRES_NOT_CONVERGED).  Allocates its CSR and vectors for the call.  Errors:
+ * INVALID_ARG, the errors of gmres_create and gmres_solve (message in
+ * gmres_last_error(NULL)), NAN, CUDA. */
+gmres_status q2_bratu_newton(int32_t n, double lambda, const gmres_opts* opts,
+                             const gmres_defl* W, int32_t m, double tol, int64_t maxit,
+                             double newton_tol, int32_t max_newton, double* u,
+                             q2_newton_info* info, void* stream);
 
 #ifdef __cplusplus
 }

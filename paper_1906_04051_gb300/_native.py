@@ -61,10 +61,26 @@ class gmres_info(C.Structure):
 class gmres_layout(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("r", C.c_int32), ("npieces", C.c_int32),
                 ("ndiag", C.c_int32), ("adapt_q", C.c_int32), ("nau", C.c_int64),
-                ("ldv", C.c_int64)]
+                ("ldv", C.c_int64), ("spmv_lanes", C.c_int32), ("reserved", C.c_int32)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class q2_newton_info(C.Structure):
+    _fields_ = [("newton_iters", C.c_int32), ("status", C.c_int32),
+                ("gmres_iters", C.c_int64), ("du_inf", C.c_double),
+                ("last_rel_res", C.c_double), ("ms_total", C.c_float),
+                ("ms_assemble", C.c_float), ("ms_solve", C.c_float), ("reserved", C.c_int32),
+                ("step_iters", C.c_int64 * 32), ("step_du", C.c_double * 32)]
+
+    def as_dict(self) -> dict:
+        k = min(self.newton_iters, 32)
+        out = {f: getattr(self, f) for f, _ in self._fields_
+               if f not in ("reserved", "step_iters", "step_du")}
+        out["step_iters"] = list(self.step_iters[:k])
+        out["step_du"] = list(self.step_du[:k])
+        return out
 
 
 # name -> (restype, argtypes); every symbol declared in include/gmres_gb300.h
@@ -93,6 +109,11 @@ SIGNATURES = {
     "q1_assemble": (C.c_int, [C.c_int32, _P, C.c_double, C.c_double, _P, _P, _P, _P, _P, _P,
                               _P]),
     "q1_kappa_grad": (C.c_int, [C.c_int32, _P, _P, _P, _P]),
+    "q2_nnz": (C.c_int64, [C.c_int32]),
+    "q2_bratu_assemble": (C.c_int, [C.c_int32, C.c_double, _P, _P, _P, _P, _P, _P]),
+    "q2_bratu_newton": (C.c_int, [C.c_int32, C.c_double, C.POINTER(gmres_opts),
+                                  C.POINTER(gmres_defl), C.c_int32, C.c_double, C.c_int64,
+                                  C.c_double, C.c_int32, _P, C.POINTER(q2_newton_info), _P]),
 }
 
 _lock = threading.Lock()

@@ -214,3 +214,62 @@ def q1_kappa_grad(n: int, lam: torch.Tensor, x: torch.Tensor, stream=None) -> to
                          _stream_ptr(stream))
     _check(st, None)
     return grad
+
+
+def q2_nnz(n: int) -> int:
+    return int(N.load().q2_nnz(int(n)))
+
+
+def q2_bratu_assemble(n: int, lam: float, u: torch.Tensor | None = None, *, device=None,
+                      stream=None):
+    """Newton system J(u) du = -R(u) of the 3-D Bratu problem on n^3 27-node hexahedra
+    (Sec. 3.1) on the device: returns (rowptr, col, val, b)."""
+    L = N.load()
+    NN = (2 * n + 1) ** 3
+    if u is not None:
+        _dev(u, torch.float64, "u", NN)
+        device = u.device
+    dev = torch.device(device) if device is not None else torch.device("cuda")
+    nnz = q2_nnz(n)
+    rowptr = torch.empty(NN + 1, dtype=torch.int32, device=dev)
+    col = torch.empty(nnz, dtype=torch.int32, device=dev)
+    val = torch.empty(nnz, dtype=torch.float64, device=dev)
+    b = torch.empty(NN, dtype=torch.float64, device=dev)
+    st = L.q2_bratu_assemble(int(n), float(lam), u.data_ptr() if u is not None else None,
+                             rowptr.data_ptr(), col.data_ptr(), val.data_ptr(), b.data_ptr(),
+                             _stream_ptr(stream))
+    _check(st, None)
+    return rowptr, col, val, b
+
+
+def bratu_newton(n: int, lam: float, u: torch.Tensor | None = None, *, m=50, tol=1e-8,
+                 maxit=20000, newton_tol=1e-10, max_newton=30, agg: torch.Tensor | None = None,
+                 r: int = 0, precision=N.FP64, deflation_mode=N.DEFL_ADAPTIVE,
+                 mu_mode=N.MU_RITZ_FIRST_CYCLE, mu_user=0.0, rmax=20, ninv=20, device=None,
+                 stream=None):
+    """Newton's method for the 3-D Bratu problem (q2_bratu_newton); u (device, updated in
+    place; zeros when None).  Returns (u, info dict)."""
+    L = N.load()
+    NN = (2 * n + 1) ** 3
+    if u is None:
+        u = torch.zeros(NN, dtype=torch.float64,
+                        device=torch.device(device) if device is not None else "cuda")
+    _dev(u, torch.float64, "u", NN)
+    opts = N.gmres_opts()
+    L.gmres_opts_default(C.byref(opts))
+    opts.precision = int(precision)
+    opts.deflation_mode = int(deflation_mode)
+    opts.mu_mode = int(mu_mode)
+    opts.mu_user = float(mu_user)
+    opts.rmax = int(rmax)
+    opts.ninv = int(ninv)
+    defl = None
+    if agg is not None and r > 0:
+        _dev(agg, torch.int32, "agg", NN)
+        defl = N.gmres_defl(int(r), agg.data_ptr())
+    info = N.q2_newton_info()
+    st = L.q2_bratu_newton(int(n), float(lam), C.byref(opts), C.byref(defl) if defl else None,
+                           int(m), float(tol), int(maxit), float(newton_tol), int(max_newton),
+                           u.data_ptr(), C.byref(info), _stream_ptr(stream))
+    _check(st, None)  # negative: an error; GMRES_NOT_CONVERGED is reported in info
+    return u, info.as_dict()

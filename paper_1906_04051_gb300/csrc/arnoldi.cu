@@ -71,6 +71,45 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// The same product for long rows (finite elements of higher order: the 27-node hexahedra
+// of the paper's benchmark couple a node with 27 to 125 others): kVecLanes consecutive
+// lanes share a row and stride through its entries, so a warp reads four rows'
+// contiguous runs coalesced, and the lanes' partial sums meet by shuffles.  The loop
+// bound is the warp's first row group, so every lane takes part in every shuffle.
+template <typename TA, typename TV, typename TACC, bool DEFL>
+__global__ void __launch_bounds__(kThreads)
+    k_spmv_vec(int N, const int* __restrict__ rowptr, const int* __restrict__ col,
+               const TA* __restrict__ val, const TV* __restrict__ x, int j,
+               const TACC* __restrict__ sdefl, TACC* __restrict__ w, Ctl ctl, Defl d) {
+  constexpr int G = kVecLanes;
+  constexpr int RPW = 32 / G;  // rows per warp and pass
+  pdl_wait();
+  pdl_trigger();
+  if (ctl.flags[F_CYCLE_DONE]) return;
+  const TACC sigma = (TACC)ctl.sigma[j];
+  auto g = [&](int c) -> TACC {
+    if constexpr (DEFL) return c < N ? ld_as<TACC, TV>(x + c) : sdefl[c - N];
+    else return ld_as<TACC, TV>(x + c);
+  };
+  const int sub = threadIdx.x & (G - 1);
+  const long long gid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / G;
+  const long long groups = (long long)gridDim.x * blockDim.x / G;
+  for (long long base = gid & ~(long long)(RPW - 1); base < N; base += groups) {
+    const long long row = base + (gid & (RPW - 1));
+    TACC acc = 0;
+    if (row < N) {
+      const int rs = __ldg(rowptr + row), re = __ldg(rowptr + row + 1);
+      for (int k = rs + sub; k < re; k += G) acc += (TACC)__ldg(val + k) * g(__ldg(col + k));
+      if (DEFL && d.qd > 0)  // adaptive deflation: A U dense, split over the row's lanes
+        for (int t = sub; t < d.qd; t += G)
+          acc += (TACC)d.aud[(size_t)t * d.ldu + row] * sdefl[t];
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (row < N && sub == 0) w[row] = sigma * acc;
+  }
+}
+
 // The same product with A in diagonal storage: row i sums dval[q][i] x[i + off_q] over the
 // nd diagonals (coalesced loads of the values and of the shifted x; an index past either
 // end is clamped to a valid row, where the stored value is 0), plus the A W row.  Each
@@ -786,6 +825,17 @@ struct Kern {
           else
             launch_k(pdl, k_spmv_dia<TA, TV, TACC, false>, gdd, kThreads, 0, st, N, a.op.dia,
                      a.op.ldd, dvals(a), xj, j, d, auvals(a), sdefl(a), w, a.ctl);
+        } else if (a.op.vec) {  // long rows: kVecLanes lanes per row
+          const int gv = grid_for((long long)N * kVecLanes, kThreads, 8 * sms);
+          if (defl && !a.proj && d.qd > 0)
+            launch_k(pdl, k_spmv_vec<TA, TV, TACC, true>, gv, kThreads, 0, st, N, a.op.rowptr,
+                     a.op.col, vals(a), xj, j, sdefl(a), w, a.ctl, d);
+          else if (defl && !a.proj)
+            launch_k(pdl, k_spmv_vec<TA, TV, TACC, true>, gv, kThreads, 0, st, N, a.op.xrp,
+                     a.op.xcol, xvals(a), xj, j, sdefl(a), w, a.ctl, d);
+          else
+            launch_k(pdl, k_spmv_vec<TA, TV, TACC, false>, gv, kThreads, 0, st, N,
+                     a.op.rowptr, a.op.col, vals(a), xj, j, sdefl(a), w, a.ctl, d);
         } else if (defl && !a.proj && d.qd > 0) {  // adaptive: plain rows + A U dense
           launch_k(pdl, k_spmv_step<TA, TV, TACC, true>, gd, kThreads, 0, st, N, a.op.rowptr,
                    a.op.col, vals(a), xj, j, sdefl(a), w, a.ctl, d);

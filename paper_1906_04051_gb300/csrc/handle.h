@@ -304,6 +304,7 @@ inline OpDev make_op(gmres_s* h, OpHost& o) {
   op.xcol = o.xcol.as<int>();
   op.xval = o.xval.as<double>();
   op.xval32 = o.xval32.as<float>();
+  op.vec = (o.dia.nd == 0 && h->nnz >= (long long)kVecMinRowLen * h->n) ? kVecLanes : 0;
   return op;
 }
 

@@ -72,6 +72,8 @@ struct OpDev {           // one operator (A or A^T) as the kernels see it
   const int* xcol;
   const double* xval;
   const float* xval32;
+  // lanes per row of the CSR SpMV (0: a thread per row); set for long rows
+  int vec;
 };
 
 struct CycleArgs {

@@ -602,6 +602,7 @@ gmres_status gmres_layout_query(gmres_t h, gmres_layout* out) {
   out->nau = h->fwd.nau;
   out->ldv = h->ldv;
   out->adapt_q = h->opts.deflation_mode == GMRES_DEFL_ADAPTIVE ? h->aq : 0;
+  out->spmv_lanes = (h->fwd.dia.nd == 0 && h->nnz >= (long long)kVecMinRowLen * h->n) ? kVecLanes : 0;
   return GMRES_OK;
 }
 
