@@ -225,7 +225,7 @@ typedef struct gmres_layout {
   int32_t adapt_q;    /* GMRES_DEFL_ADAPTIVE: columns of U after the last solve, else 0 */
   int64_t nau;        /* entries of A W (coarse part of the deflated SpMV) */
   int64_t ldv;        /* rows per basis column in device memory (n rounded up) */
-  int32_t spmv_lanes; /* CSR SpMV: lanes per row (8 for rows of 16+ entries on average;
+  int32_t spmv_lanes; /* CSR SpMV: lanes per row (4 for rows of 16+ entries on average;
                          0: a thread per row, or diagonal storage) */
   int32_t reserved;
 } gmres_layout;

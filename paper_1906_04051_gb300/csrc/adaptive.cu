@@ -6,9 +6,11 @@
 // orthonormalised against U (two classical Gram-Schmidt passes) and appended to U; A u is
 // appended to A U and T = U^T A U grows by a row and a column.  With rmax columns already
 // in U, the direction of T's largest-modulus eigenvalue leaves first (two directions for
-// a complex pair): U <- U Qc, A U <- A U Qc, T <- Qc^T T Qc, where Qc is an orthonormal
-// basis of the complement of that eigenvalue's left eigenvector(s), a T-invariant
-// subspace carrying the other eigenvalues.  T^-1 follows.  Arithmetic runs in the
+// a complex pair): U keeps the complement of that eigenvalue's left eigenvector(s), a
+// T-invariant subspace carrying the other eigenvalues, in the basis U H_0 (H_1) given by
+// Householder reflectors that map the dropped directions onto single coordinates (rank-1
+// updates of U and A U instead of a dense rotation), T <- H T H without those rows and
+// columns.  T^-1 follows.  Arithmetic runs in the
 // kernels below and in the pipelined multi-dot of arnoldi.cu; the host only sequences
 // them and reads the few scalars that decide the branches (vector count, norms, the
 // number of dropped directions).
@@ -28,45 +30,70 @@ namespace {
 // z <- H^-1 z / ||H^-1 z|| from the normalised all-ones vector, the sign making the
 // largest-magnitude entry positive (the first on ties); if ||Hz - (z^T H z) z|| >
 // 1e-3 ||Hz|| one more iterate, orthonormalised against z, is the second vector.
-__device__ void warp_hess_solve(int k, const double* a, const int* sw, const double* l,
-                                double* z, int lane) {
-  // forward: the row operations of the factorisation, in order (lane 0)
-  if (lane == 0)
-    for (int j = 0; j + 1 < k; ++j) {
-      if (sw[j]) {
-        const double t = z[j];
-        z[j] = z[j + 1];
-        z[j + 1] = t;
-      }
-      z[j + 1] -= l[j] * z[j];
-    }
-  __syncwarp();
-  // backward, by columns: z_i /= a_ii, then the rows above drop a_ri z_i
-  for (int i = k - 1; i >= 0; --i) {
-    if (lane == 0) z[i] /= a[i * k + i];
-    __syncwarp();
-    const double zi = z[i];
-    for (int r = lane; r < i; r += 32) z[r] -= a[r * k + i] * zi;
-    __syncwarp();
-  }
+// z lives in registers, entry i in lane i % 32 (z0: i < 32, z1: i >= 32); the two
+// triangular solves are chains of k dependent steps, so each step is a shuffle and an
+// FMA, with the factors read from shared memory off the chain.
+
+struct WZ {  // a vector of k <= 64 entries spread over the warp
+  double z0, z1;
+};
+
+__device__ __forceinline__ double wz_get(const WZ& v, int i) {
+  return __shfl_sync(0xffffffffu, i < 32 ? v.z0 : v.z1, i & 31);
 }
 
-__device__ void warp_normalise_sign(int k, double* z, int lane) {
-  double s = 0.0;
-  for (int i = lane; i < k; i += 32) s += z[i] * z[i];
-  s = warp_sum(s);
+// z <- U^-1 L^-1 P z for the factors of the Hessenberg LU: sw[j] (rows j and j+1
+// exchanged at step j), l[j] (multiplier of step j), Ut (U transposed: Ut[c * 64 + r] =
+// U[r][c]) and rd (1 / U[i][i]).
+__device__ void warp_hess_solve(int k, const double* Ut, const int* sw, const double* l,
+                                const double* rd, WZ& z, int lane) {
+  // forward: the row operations of the factorisation in order; c carries the current
+  // entry j, which step j finalises
+  double c = wz_get(z, 0);
+  WZ f{0.0, 0.0};
+  for (int j = 0; j + 1 < k; ++j) {
+    const double o = wz_get(z, j + 1);  // not yet touched by the chain
+    const double lj = l[j];
+    double fin, nxt;
+    if (sw[j]) {
+      fin = o;
+      nxt = c - lj * o;
+    } else {
+      fin = c;
+      nxt = o - lj * c;
+    }
+    if (lane == (j & 31)) (j < 32 ? f.z0 : f.z1) = fin;
+    c = nxt;
+  }
+  if (lane == ((k - 1) & 31)) (k - 1 < 32 ? f.z0 : f.z1) = c;
+  // backward, by columns: x_i = y_i / u_ii, then the rows above drop u_ri x_i
+  for (int i = k - 1; i >= 0; --i) {
+    const double xi = wz_get(f, i) * rd[i];
+    if (lane == (i & 31)) (i < 32 ? f.z0 : f.z1) = xi;
+    const double* col = Ut + i * 64;
+    if (lane < i) f.z0 -= col[lane] * xi;
+    if (lane + 32 < i) f.z1 -= col[lane + 32] * xi;
+  }
+  z = f;
+}
+
+__device__ void warp_normalise_sign(int k, WZ& z, int lane) {
+  const double a0 = lane < k ? z.z0 : 0.0, a1 = lane + 32 < k ? z.z1 : 0.0;
+  const double s = warp_sum(a0 * a0 + a1 * a1);
   const double inv = 1.0 / sqrt(s);
-  __syncwarp();
-  for (int i = lane; i < k; i += 32) z[i] *= inv;
-  __syncwarp();
+  z.z0 = a0 * inv;
+  z.z1 = a1 * inv;
   // largest magnitude, first index on ties
   double bv = -1.0;
   int bi = 0x7fffffff;
-  for (int i = lane; i < k; i += 32)
-    if (fabs(z[i]) > bv) {
-      bv = fabs(z[i]);
-      bi = i;
-    }
+  if (lane < k) {
+    bv = fabs(z.z0);
+    bi = lane;
+  }
+  if (lane + 32 < k && fabs(z.z1) > bv) {
+    bv = fabs(z.z1);
+    bi = lane + 32;
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
@@ -76,16 +103,16 @@ __device__ void warp_normalise_sign(int k, double* z, int lane) {
       bi = oi;
     }
   }
-  const bool neg = z[bi] < 0.0;
-  __syncwarp();
-  if (neg)
-    for (int i = lane; i < k; i += 32) z[i] = -z[i];
-  __syncwarp();
+  if (wz_get(z, bi) < 0.0) {
+    z.z0 = -z.z0;
+    z.z1 = -z.z1;
+  }
 }
 
 __global__ void k_adapt_z(Ctl ctl, int ninv, double* __restrict__ zout, int* __restrict__ iv) {
-  __shared__ double a[kMaxM * kMaxM];  // the LU factors (H itself is read from ctl.Hr)
-  __shared__ double l[kMaxM], z[kMaxM], z2[kMaxM], hz[kMaxM];
+  static_assert(kMaxM <= 64, "the register layout holds 64 entries");
+  __shared__ double a[kMaxM * kMaxM];  // the LU factors in place, U transposed afterwards
+  __shared__ double l[kMaxM], rd[kMaxM];
   __shared__ int sw[kMaxM];
   const int lane = threadIdx.x;
   const int k = ctl.flags[F_K];
@@ -129,44 +156,51 @@ __global__ void k_adapt_z(Ctl ctl, int ninv, double* __restrict__ zout, int* __r
     }
     __syncwarp();
   }
-  for (int i = lane; i < k; i += 32) z[i] = 1.0 / sqrt((double)k);
+  // U transposed into registers' order of access (column i contiguous), reciprocal pivots
+  double ut[kMaxM * kMaxM / 32];
+  int nt = 0;
+  for (int t = lane; t < k * k; t += 32) ut[nt++] = a[t];
   __syncwarp();
+  nt = 0;
+  for (int t = lane; t < k * k; t += 32) {
+    const int r = t / k, c = t % k;
+    a[c * 64 + r] = r <= c ? ut[nt] : 0.0;
+    ++nt;
+  }
+  __syncwarp();
+  for (int i = lane; i < k; i += 32) rd[i] = 1.0 / a[i * 64 + i];
+  __syncwarp();
+  WZ z{lane < k ? 1.0 / sqrt((double)k) : 0.0, lane + 32 < k ? 1.0 / sqrt((double)k) : 0.0};
   for (int it = 0; it < ninv; ++it) {
-    warp_hess_solve(k, a, sw, l, z, lane);
+    warp_hess_solve(k, a, sw, l, rd, z, lane);
     warp_normalise_sign(k, z, lane);
   }
-  // eigenvector test with the Rayleigh quotient
-  double rho = 0.0, nhz = 0.0;
-  for (int i = lane; i < k; i += 32) {
-    double s = 0.0;
-    for (int c = 0; c < k; ++c) s += ctl.Hr[(size_t)i * ldh + c] * z[c];
-    hz[i] = s;
-    rho += z[i] * s;
-    nhz += s * s;
+  // eigenvector test with the Rayleigh quotient rho = z^T H z
+  double rho = 0.0, nhz = 0.0, hz0 = 0.0, hz1 = 0.0;
+  for (int c = 0; c < k; ++c) {
+    const double zc = wz_get(z, c);
+    if (lane < k) hz0 += ctl.Hr[(size_t)lane * ldh + c] * zc;
+    if (lane + 32 < k) hz1 += ctl.Hr[(size_t)(lane + 32) * ldh + c] * zc;
   }
-  rho = warp_sum(rho);
-  nhz = warp_sum(nhz);
-  __syncwarp();
-  double res = 0.0;
-  for (int i = lane; i < k; i += 32) res += (hz[i] - rho * z[i]) * (hz[i] - rho * z[i]);
-  res = warp_sum(res);
+  rho = warp_sum(z.z0 * hz0 + z.z1 * hz1);
+  nhz = warp_sum(hz0 * hz0 + hz1 * hz1);
+  const double r0 = hz0 - rho * z.z0, r1 = hz1 - rho * z.z1;
+  const double res = warp_sum(r0 * r0 + r1 * r1);
   int nvec = 1;
+  WZ z2{0.0, 0.0};
   if (sqrt(res) > 1e-3 * sqrt(nhz)) {
-    for (int i = lane; i < k; i += 32) z2[i] = z[i];
-    __syncwarp();
-    warp_hess_solve(k, a, sw, l, z2, lane);
-    double c = 0.0;
-    for (int i = lane; i < k; i += 32) c += z[i] * z2[i];
-    c = warp_sum(c);
-    __syncwarp();
-    for (int i = lane; i < k; i += 32) z2[i] -= c * z[i];
-    __syncwarp();
+    z2 = z;
+    warp_hess_solve(k, a, sw, l, rd, z2, lane);
+    const double c = warp_sum(z.z0 * z2.z0 + z.z1 * z2.z1);
+    z2.z0 -= c * z.z0;
+    z2.z1 -= c * z.z1;
     warp_normalise_sign(k, z2, lane);
     nvec = 2;
   }
   for (int i = lane; i < kMaxK; i += 32) {
-    zout[i] = i < k ? z[i] : 0.0;
-    zout[kMaxK + i] = (nvec == 2 && i < k) ? z2[i] : 0.0;
+    const bool lo = i < 32;
+    zout[i] = i < k ? (lo ? z.z0 : z.z1) : 0.0;
+    zout[kMaxK + i] = (nvec == 2 && i < k) ? (lo ? z2.z0 : z2.z1) : 0.0;
   }
   if (lane == 0) iv[0] = nvec;
 }
@@ -225,16 +259,39 @@ __global__ void __launch_bounds__(kThreads)
     dst[i] = u[i] * inv;
 }
 
-// y = A x in FP64 (CSR, thread per row)
+// y = A x in FP64 (CSR): kVecLanes lanes per row, kVecRows consecutive rows per lane
+// group (the layout of the step's SpMV for long rows; short rows lose little by it)
 __global__ void __launch_bounds__(kThreads)
     k_adapt_spmv(int N, const int* __restrict__ rowptr, const int* __restrict__ col,
                  const double* __restrict__ val, const double* __restrict__ x,
                  double* __restrict__ y) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int e = __ldg(rowptr + i); e < __ldg(rowptr + i + 1); ++e)
-      s += __ldg(val + e) * x[__ldg(col + e)];
-    y[i] = s;
+  constexpr int G = kVecLanes, R = kVecRows, GPW = 32 / G;
+  const int sub = threadIdx.x & (G - 1);
+  const long long gid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / G;
+  const long long groups = (long long)gridDim.x * blockDim.x / G;
+  const long long nb = (N + R - 1) / R;
+  for (long long base = gid & ~(long long)(GPW - 1); base < nb; base += groups) {
+    const long long bund = base + (gid & (GPW - 1));
+    double acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      acc[r] = 0.0;
+      const long long row = bund * R + r;
+      if (bund < nb && row < N)
+        for (int e = __ldg(rowptr + row) + sub; e < __ldg(rowptr + row + 1); e += G)
+          acc[r] += __ldg(val + e) * x[__ldg(col + e)];
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    if (bund < nb && sub < R) {
+      double v = acc[0];
+#pragma unroll
+      for (int r = 1; r < R; ++r)
+        if (sub == r) v = acc[r];
+      if (bund * R + sub < N) y[bund * R + sub] = v;
+    }
   }
 }
 
@@ -386,77 +443,125 @@ __global__ void __launch_bounds__(32)
     for (int i = lane; i < n2; i += 32) y[i] *= inv;
     __syncwarp();
   }
-  // Householder QR of Y = [y[0..q) (, y[q..2q))]; lane i holds row i
+  // Householder reflectors H_c = I - beta_c v_c v_c^T, c < p, each mapping column c of
+  // Y = [Re y (, Im y)] (after the earlier reflectors) onto a coordinate jd_c, chosen as
+  // its largest entry among the coordinates not yet taken; v_c vanishes on those, so
+  // Q = H_0 ... H_{p-1} has Q e_{jd_c} spanning span(Y) and its other columns spanning
+  // the complement {c : y^T c = 0}.  U Q is then U with p rank-1 updates, and T's
+  // new coordinates are Q^T T Q with rows and columns jd_c removed.
   double yc[2];
   yc[0] = lane < q ? y[lane] : 0.0;
   yc[1] = (p == 2 && lane < q) ? y[q + lane] : 0.0;
+  int used = -1;
   for (int c = 0; c < p; ++c) {
-    const double x = (lane >= c && lane < q) ? yc[c] : 0.0;
+    const double x = (lane < q && lane != used) ? yc[c] : 0.0;
+    double bv = fabs(x);
+    int bi = lane < q && lane != used ? lane : 64;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    const int jc = bi < q ? bi : 0;
     const double nx = sqrt(warp_sum(x * x));
-    const double x0 = __shfl_sync(0xffffffffu, yc[c], c);
-    const double alpha = x0 >= 0.0 ? -nx : nx;
-    const double v = (lane >= c && lane < q) ? x - (lane == c ? alpha : 0.0) : 0.0;
+    const double xj = __shfl_sync(0xffffffffu, x, jc);
+    const double alpha = xj >= 0.0 ? -nx : nx;
+    const double v = x - (lane == jc ? alpha : 0.0);
     const double vv = warp_sum(v * v);
     const double beta = vv > 0.0 ? 2.0 / vv : 0.0;
     hv[c][lane] = v;
-    if (lane == 0) hb[c] = beta;
+    if (lane == 0) {
+      hb[c] = beta;
+      piv[c] = jc;
+    }
     if (c + 1 < p) {
       const double sd = warp_sum(v * yc[c + 1]);
-      if (lane >= c && lane < q) yc[c + 1] -= beta * sd * v;
+      yc[c + 1] -= beta * sd * v;
     }
+    used = jc;
   }
   __syncwarp();
+  // T <- H_c T H_c for c = 0..p-1 (T0, row stride q)
+  for (int c = 0; c < p; ++c) {
+    const double bt = hb[c];
+    if (lane < q) {  // left: column lane
+      double sd = 0.0;
+      for (int i = 0; i < q; ++i) sd += hv[c][i] * T0[i * q + lane];
+      for (int i = 0; i < q; ++i) T0[i * q + lane] -= bt * sd * hv[c][i];
+    }
+    __syncwarp();
+    if (lane < q) {  // right: row lane
+      double sd = 0.0;
+      for (int jj = 0; jj < q; ++jj) sd += T0[lane * q + jj] * hv[c][jj];
+      for (int jj = 0; jj < q; ++jj) T0[lane * q + jj] -= bt * sd * hv[c][jj];
+    }
+    __syncwarp();
+  }
+  // slots of the kept coordinates: a dropped slot below nc takes the next kept
+  // coordinate at or above nc; map[s] = source coordinate of slot s
   const int nc = q - p;
-  double* Qs = M;          // q x nc, row stride Q
-  double* Ws = M + Q * Q;  // T Qc, row stride Q
-  if (lane < nc) {         // column lane of (H_0 ... H_{p-1}) E, E = I[:, p:]
-    for (int i = 0; i < q; ++i) Qs[i * Q + lane] = i == p + lane ? 1.0 : 0.0;
-    for (int c = p - 1; c >= 0; --c) {
-      double sd = 0.0;
-      for (int i = c; i < q; ++i) sd += hv[c][i] * Qs[i * Q + lane];
-      for (int i = c; i < q; ++i) Qs[i * Q + lane] -= hb[c] * sd * hv[c][i];
-    }
-    for (int i = 0; i < q; ++i) {
-      double sd = 0.0;
-      for (int l = 0; l < q; ++l) sd += T0[i * q + l] * Qs[l * Q + lane];
-      Ws[i * Q + lane] = sd;
+  if (lane == 0) {
+    int src = nc;
+    for (int sl = 0; sl < nc; ++sl) {
+      bool drop = false;
+      for (int c = 0; c < p; ++c) drop = drop || piv[c] == sl;
+      if (!drop) {
+        piv[8 + sl] = sl;
+        continue;
+      }
+      for (;; ++src) {
+        bool dsrc = false;
+        for (int c = 0; c < p; ++c) dsrc = dsrc || piv[c] == src;
+        if (!dsrc) break;
+      }
+      piv[8 + sl] = src++;
     }
   }
   __syncwarp();
-  if (lane < nc) {
-    for (int i = 0; i < nc; ++i) {
-      double sd = 0.0;
-      for (int l = 0; l < q; ++l) sd += Qs[l * Q + i] * Ws[l * Q + lane];
-      T[(size_t)i * ldt + lane] = sd;
-    }
-    for (int i = 0; i < q; ++i) Qc[i * Q + lane] = Qs[i * Q + lane];
-  }
+  if (lane < nc)
+    for (int i = 0; i < nc; ++i) T[(size_t)i * ldt + lane] = T0[piv[8 + i] * q + piv[8 + lane]];
+  // reflectors and the slot map for k_adapt_reflect and the column moves
+  for (int c = 0; c < p; ++c) Qc[c * Q + lane] = hv[c][lane];
   if (lane == 0) {
+    Qc[2 * Q] = hb[0];
+    Qc[2 * Q + 1] = p == 2 ? hb[1] : 0.0;
     out[0] = p;
     out[1] = 0;
   }
+  if (lane < nc) out[2 + lane] = piv[8 + lane];
 }
 
-// U <- U Qc and A U <- A U Qc in place (q columns to nc), thread per row
+// U <- U H_0 ... H_{p-1} and A U <- A U H_0 ... H_{p-1} in place (q columns), thread per
+// row: w = X v_c, X -= beta_c w v_c^T.  QT >= q bounds the unrolled column loops.
+template <int QT>
 __global__ void __launch_bounds__(kThreads)
-    k_adapt_rotate(int N, double* __restrict__ U, double* __restrict__ AU, long long ld, int q,
-                   int nc, const double* __restrict__ Qc) {
-  __shared__ double sq[kMaxAdapt * kMaxAdapt];
-  for (int t = threadIdx.x; t < q * kMaxAdapt; t += blockDim.x) sq[t] = Qc[t];
+    k_adapt_reflect(int N, double* __restrict__ U, double* __restrict__ AU, long long ld, int q,
+                    int p, const double* __restrict__ hvec) {
+  __shared__ double sv[2][kMaxAdapt], sb[2];
+  for (int t = threadIdx.x; t < 2 * kMaxAdapt; t += blockDim.x)
+    sv[t / kMaxAdapt][t % kMaxAdapt] = (t / kMaxAdapt) < p ? hvec[t] : 0.0;
+  if (threadIdx.x < 2) sb[threadIdx.x] = hvec[2 * kMaxAdapt + threadIdx.x];
   __syncthreads();
   for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < N; row += gridDim.x * blockDim.x)
     for (int pass = 0; pass < 2; ++pass) {
       double* X = pass == 0 ? U : AU;
-      double u[kMaxAdapt];
+      double u[QT];
 #pragma unroll
-      for (int t = 0; t < kMaxAdapt; ++t) u[t] = t < q ? X[(size_t)t * ld + row] : 0.0;
-      for (int c = 0; c < nc; ++c) {
-        double sd = 0.0;
+      for (int t = 0; t < QT; ++t) u[t] = t < q ? X[(size_t)t * ld + row] : 0.0;
+      for (int c = 0; c < p; ++c) {
+        double w = 0.0;
 #pragma unroll
-        for (int t = 0; t < kMaxAdapt; ++t)
-          if (t < q) sd += u[t] * sq[t * kMaxAdapt + c];
-        X[(size_t)c * ld + row] = sd;
+        for (int t = 0; t < QT; ++t) w += u[t] * sv[c][t];
+        w *= sb[c];
+#pragma unroll
+        for (int t = 0; t < QT; ++t) u[t] -= w * sv[c][t];
       }
+#pragma unroll
+      for (int t = 0; t < QT; ++t)
+        if (t < q) X[(size_t)t * ld + row] = u[t];
     }
 }
 
@@ -522,8 +627,8 @@ gmres_status adapt_update(gmres_s* h, CycleArgs& a) {
   double* c1 = z + 2 * kMaxK;            // kMaxAdapt + 1
   double* c2 = c1 + kMaxAdapt + 1;       // kMaxAdapt + 1
   double* nrm = c2 + kMaxAdapt + 1;      // 2
-  double* qc = nrm + 2;                  // kMaxAdapt x kMaxAdapt
-  int* iv = reinterpret_cast<int*>(qc + kMaxAdapt * kMaxAdapt);  // nvec, bad, p, fail
+  double* qc = nrm + 2;                  // reflectors of the drop step (2 kMaxAdapt + 2)
+  int* iv = reinterpret_cast<int*>(qc + kMaxAdapt * kMaxAdapt);  // nvec, bad, p, fail, map
   const int tiles = (N + kThreads - 1) / kThreads;
   const int grid = grid_for(tiles, 1, 8 * h->sms);
   const Ctl& ctl = a.ctl;
@@ -557,20 +662,35 @@ gmres_status adapt_update(gmres_s* h, CycleArgs& a) {
     if (q == R) {  // U is full: the direction(s) of T's largest eigenvalue leave first
       k_adapt_drop<<<1, 32, 0, st>>>(T, R, q, qc, iv + 2);
       CK(h, cudaGetLastError());
-      int hd[2] = {0, 0};
+      int hd[2 + kMaxAdapt] = {0};
       CK(h, cudaMemcpyAsync(hd, iv + 2, sizeof(hd), cudaMemcpyDeviceToHost, st));
       CK(h, cudaStreamSynchronize(st));
       if (hd[1] || hd[0] < 1 || hd[0] > q)
         return fail(h, GMRES_ERR_SINGULAR_COARSE,
                     "adaptive deflation: the QR iteration on T = U^T A U did not converge");
-      const int nc = q - hd[0];
-      k_adapt_rotate<<<grid, kThreads, 0, st>>>(N, U, AU, ld, q, nc, qc);
+      const int p = hd[0], nc = q - p;
+      if (q <= 8)
+        k_adapt_reflect<8><<<grid, kThreads, 0, st>>>(N, U, AU, ld, q, p, qc);
+      else if (q <= 16)
+        k_adapt_reflect<16><<<grid, kThreads, 0, st>>>(N, U, AU, ld, q, p, qc);
+      else if (q <= 24)
+        k_adapt_reflect<24><<<grid, kThreads, 0, st>>>(N, U, AU, ld, q, p, qc);
+      else
+        k_adapt_reflect<32><<<grid, kThreads, 0, st>>>(N, U, AU, ld, q, p, qc);
       nl += 2;
+      for (int sl = 0; sl < nc; ++sl)  // the dropped slots below nc take kept columns
+        if (hd[2 + sl] != sl) {
+          CK(h, cudaMemcpyAsync(U + (size_t)sl * ld, U + (size_t)hd[2 + sl] * ld,
+                                sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+          CK(h, cudaMemcpyAsync(AU + (size_t)sl * ld, AU + (size_t)hd[2 + sl] * ld,
+                                sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+        }
       q = nc;
     }
     k_adapt_scale<<<grid, kThreads, 0, st>>>(N, u, nrm + 1, U + (size_t)q * ld);
-    k_adapt_spmv<<<grid, kThreads, 0, st>>>(N, a.op.rowptr, a.op.col, a.op.val,
-                                            U + (size_t)q * ld, AU + (size_t)q * ld);
+    k_adapt_spmv<<<grid_for((long long)N * kVecLanes / kVecRows, kThreads, 64 * h->sms), kThreads,
+                   0, st>>>(N, a.op.rowptr, a.op.col, a.op.val, U + (size_t)q * ld,
+                            AU + (size_t)q * ld);
     nl += 2;
     launch_udots(a, U, ld, q + 1, AU + (size_t)q * ld, DotEpi{kEpiRaw, nullptr, 0, c1, -1}, st);
     ++nl;

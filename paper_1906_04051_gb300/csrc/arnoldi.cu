@@ -72,17 +72,20 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // The same product for long rows (finite elements of higher order: the 27-node hexahedra
-// of the paper's benchmark couple a node with 27 to 125 others): kVecLanes consecutive
-// lanes share a row and stride through its entries, so a warp reads four rows'
-// contiguous runs coalesced, and the lanes' partial sums meet by shuffles.  The loop
-// bound is the warp's first row group, so every lane takes part in every shuffle.
+// of the paper's benchmark couple a node with 27 to 125 others).  A group of kVecLanes
+// consecutive lanes takes kVecRows consecutive rows in turn, striding through each row's
+// entries (two independent chains per lane), and the partial sums meet by shuffles.  The
+// FP64 pipe is nearly as tight as HBM here (12 bytes per FMA), so lanes must not idle:
+// few lanes per row keep the shuffle adds rare, and taking rows in pairs evens out the
+// alternating vertex / mid-edge row lengths between the groups of a warp.  The loop bound
+// is the warp's first group, so every lane takes part in every shuffle.
 template <typename TA, typename TV, typename TACC, bool DEFL>
 __global__ void __launch_bounds__(kThreads)
     k_spmv_vec(int N, const int* __restrict__ rowptr, const int* __restrict__ col,
                const TA* __restrict__ val, const TV* __restrict__ x, int j,
                const TACC* __restrict__ sdefl, TACC* __restrict__ w, Ctl ctl, Defl d) {
-  constexpr int G = kVecLanes;
-  constexpr int RPW = 32 / G;  // rows per warp and pass
+  constexpr int G = kVecLanes, R = kVecRows;
+  constexpr int GPW = 32 / G;  // groups per warp
   pdl_wait();
   pdl_trigger();
   if (ctl.flags[F_CYCLE_DONE]) return;
@@ -94,19 +97,45 @@ __global__ void __launch_bounds__(kThreads)
   const int sub = threadIdx.x & (G - 1);
   const long long gid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / G;
   const long long groups = (long long)gridDim.x * blockDim.x / G;
-  for (long long base = gid & ~(long long)(RPW - 1); base < N; base += groups) {
-    const long long row = base + (gid & (RPW - 1));
-    TACC acc = 0;
-    if (row < N) {
-      const int rs = __ldg(rowptr + row), re = __ldg(rowptr + row + 1);
-      for (int k = rs + sub; k < re; k += G) acc += (TACC)__ldg(val + k) * g(__ldg(col + k));
-      if (DEFL && d.qd > 0)  // adaptive deflation: A U dense, split over the row's lanes
-        for (int t = sub; t < d.qd; t += G)
-          acc += (TACC)d.aud[(size_t)t * d.ldu + row] * sdefl[t];
+  const long long nb = (N + R - 1) / R;
+  for (long long base = gid & ~(long long)(GPW - 1); base < nb; base += groups) {
+    const long long bund = base + (gid & (GPW - 1));
+    TACC acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0;
+    if (bund < nb) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const long long row = bund * R + r;
+        if (row < N) {
+          const int rs = __ldg(rowptr + row), re = __ldg(rowptr + row + 1);
+          TACC a2 = 0;
+          int k = rs + sub;
+          for (; k + G < re; k += 2 * G) {
+            const int c0 = __ldg(col + k), c1 = __ldg(col + k + G);
+            const TACC v0 = (TACC)__ldg(val + k), v1 = (TACC)__ldg(val + k + G);
+            acc[r] += v0 * g(c0);
+            a2 += v1 * g(c1);
+          }
+          if (k < re) acc[r] += (TACC)__ldg(val + k) * g(__ldg(col + k));
+          if (DEFL && d.qd > 0)  // adaptive deflation: A U dense, split over the lanes
+            for (int t = sub; t < d.qd; t += G) a2 += (TACC)d.aud[(size_t)t * d.ldu + row] * sdefl[t];
+          acc[r] += a2;
+        }
+      }
     }
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (row < N && sub == 0) w[row] = sigma * acc;
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    if (bund < nb && sub < R) {
+      TACC a = acc[0];
+#pragma unroll
+      for (int r = 1; r < R; ++r)
+        if (sub == r) a = acc[r];
+      const long long row = bund * R + sub;
+      if (row < N) w[row] = sigma * a;
+    }
   }
 }
 
@@ -816,6 +845,10 @@ struct Kern {
       case PH_SPMV: {
         const TV* xj = V + (size_t)j * a.ldv;
         const bool pdl = a.pdl != 0;
+        // The CSR kernels gather x and are launched in plain stream order: started early
+        // under programmatic dependent launch they made a GMRES(50) step 1.8x (lanes per
+        // row) to 2.7x (thread per row) slower on the 3-D Bratu matrices.
+        constexpr bool pdl_csr = false;
         const int gd = grid_for((N + kThreads - 1) / kThreads, 1, 8 * sms);
         if (a.op.dia.nd > 0) {  // banded A: diagonal storage
           const int gdd = (N + kThreads * kDiaRows - 1) / (kThreads * kDiaRows);
@@ -825,25 +858,25 @@ struct Kern {
           else
             launch_k(pdl, k_spmv_dia<TA, TV, TACC, false>, gdd, kThreads, 0, st, N, a.op.dia,
                      a.op.ldd, dvals(a), xj, j, d, auvals(a), sdefl(a), w, a.ctl);
-        } else if (a.op.vec) {  // long rows: kVecLanes lanes per row
-          const int gv = grid_for((long long)N * kVecLanes, kThreads, 8 * sms);
+        } else if (a.op.vec) {  // long rows: kVecLanes lanes per row, rows in pairs
+          const int gv = grid_for((long long)N * kVecLanes / kVecRows, kThreads, 64 * sms);
           if (defl && !a.proj && d.qd > 0)
-            launch_k(pdl, k_spmv_vec<TA, TV, TACC, true>, gv, kThreads, 0, st, N, a.op.rowptr,
+            launch_k(pdl_csr, k_spmv_vec<TA, TV, TACC, true>, gv, kThreads, 0, st, N, a.op.rowptr,
                      a.op.col, vals(a), xj, j, sdefl(a), w, a.ctl, d);
           else if (defl && !a.proj)
-            launch_k(pdl, k_spmv_vec<TA, TV, TACC, true>, gv, kThreads, 0, st, N, a.op.xrp,
+            launch_k(pdl_csr, k_spmv_vec<TA, TV, TACC, true>, gv, kThreads, 0, st, N, a.op.xrp,
                      a.op.xcol, xvals(a), xj, j, sdefl(a), w, a.ctl, d);
           else
-            launch_k(pdl, k_spmv_vec<TA, TV, TACC, false>, gv, kThreads, 0, st, N,
+            launch_k(pdl_csr, k_spmv_vec<TA, TV, TACC, false>, gv, kThreads, 0, st, N,
                      a.op.rowptr, a.op.col, vals(a), xj, j, sdefl(a), w, a.ctl, d);
         } else if (defl && !a.proj && d.qd > 0) {  // adaptive: plain rows + A U dense
-          launch_k(pdl, k_spmv_step<TA, TV, TACC, true>, gd, kThreads, 0, st, N, a.op.rowptr,
+          launch_k(pdl_csr, k_spmv_step<TA, TV, TACC, true>, gd, kThreads, 0, st, N, a.op.rowptr,
                    a.op.col, vals(a), xj, j, sdefl(a), w, a.ctl, d);
         } else if (defl && !a.proj) {
-          launch_k(pdl, k_spmv_step<TA, TV, TACC, true>, gd, kThreads, 0, st, N, a.op.xrp,
+          launch_k(pdl_csr, k_spmv_step<TA, TV, TACC, true>, gd, kThreads, 0, st, N, a.op.xrp,
                    a.op.xcol, xvals(a), xj, j, sdefl(a), w, a.ctl, d);
         } else {
-          launch_k(pdl, k_spmv_step<TA, TV, TACC, false>, gd, kThreads, 0, st, N, a.op.rowptr,
+          launch_k(pdl_csr, k_spmv_step<TA, TV, TACC, false>, gd, kThreads, 0, st, N, a.op.rowptr,
                    a.op.col, vals(a), xj, j, sdefl(a), w, a.ctl, d);
         }
         nl = 1;

@@ -17,7 +17,8 @@ constexpr int kWarp = 32;
 constexpr int kMaxM = 64;               // largest restart length m
 constexpr int kMaxK = kMaxM + 1;        // basis columns held in a cycle
 constexpr int kMaxAdapt = 32;           // most columns of the adaptive deflation space
-constexpr int kVecLanes = 8;          // lanes per row of the CSR SpMV for long rows
+constexpr int kVecLanes = 4;          // lanes per row of the CSR SpMV for long rows
+constexpr int kVecRows = 2;           // consecutive rows per lane group (taken in turn)
 constexpr int kVecMinRowLen = 16;     // mean row length from which it is used
 constexpr int kMaxR = 6144;             // largest number of deflation aggregates
 constexpr int kThreads = 256;           // threads of the streaming kernels

@@ -161,7 +161,8 @@ inline gmres_status ensure_workspace(gmres_s* h, int m, int prec) {
     CK(h, h->aT.ensure(sizeof(double) * R * R));
     CK(h, h->aTinv.ensure(sizeof(double) * R * R));
     CK(h, h->asmall.ensure(sizeof(double) * (2 * kMaxK + 2 * (kMaxAdapt + 1) + 2 +
-                                             kMaxAdapt * kMaxAdapt) + 4 * sizeof(int)));
+                                             kMaxAdapt * kMaxAdapt) +
+                           (4 + kMaxAdapt) * sizeof(int)));
   }
   CK(h, h->meta.ensure(sizeof(Meta)));
   if (!h->hmeta) CK(h, cudaMallocHost(&h->hmeta, sizeof(Meta)));

@@ -85,7 +85,7 @@ def test_gmres_on_newton_matrix_matches_oracle(G, orc, mode):
         kw.update(deflation_mode=G.DEFL_ADAPTIVE, rmax=4)
         okw.update(defl_mode=orc.DEFL_ADAPTIVE, rmax=4)
     s = gpu_solver_from_oracle(G, A, agg, r, mu_mode=1, mu_user=3.0, fixed_iterations=True, **kw)
-    assert s.layout()["spmv_lanes"] == 8  # 27..125 entries per row: lanes per row
+    assert s.layout()["spmv_lanes"] == 4  # 27..125 entries per row: lanes per row
     xg, ig = s.solve(to_dev(b), m=12, tol=0.0, maxit=60)
     d = orc.Deflation(A, agg, r) if r else None
     xo, io = orc.gmres(A, b, defl=d, m=12, tol=0.0, maxit=60, mu_mode=1, mu_user=3.0,
