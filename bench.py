@@ -135,6 +135,24 @@ def cpu_baseline(p, budget_steps=M):
             "projected_solve_s": projected, "setup_s": t1 - t0, "s_per_step": per_step}
 
 
+BRATU_N, BRATU_LAM = 60, 6.8  # Table 1's largest mesh: 121^3 nodes, 108,583,705 nnz
+
+
+def bratu_cpu_sample(n=30, steps=M):
+    """The oracle on the paper's own workload: Q2 Bratu Newton matrix J(0) on n^3
+    elements, one adaptive-deflation GMRES(50) cycle (the paper's protocol repeats 100)."""
+    import oracle
+    oracle.build()
+    A, b = oracle.q2_bratu_assemble(n, BRATU_LAM)
+    t0 = time.perf_counter()
+    _, info = oracle.gmres(A, b, m=M, tol=0.0, maxit=steps, defl_mode=oracle.DEFL_ADAPTIVE,
+                           rmax=20, fixed_iterations=True)
+    dt = time.perf_counter() - t0
+    return {"n": n, "dof": A.n, "nnz": A.nnz, "cores": 1, "kind": "oracle",
+            "us_per_step": dt * 1e6 / max(info["iters"], 1),
+            "sample": f"one GMRES(50) cycle ({info['iters']} steps, {dt:.1f} s)"}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -174,6 +192,8 @@ def main():
                     help="skip the batched (one graph launch) vs sequential comparison")
     ap.add_argument("--no-adaptive", action="store_true",
                     help="skip the adaptive-deflation time-to-tol on the bench system")
+    ap.add_argument("--no-bratu", action="store_true",
+                    help="skip the paper's own workload (3-D Bratu on Q2 hexahedra)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -199,9 +219,12 @@ def main():
 
     # CPU baseline first, before anything else touches the GPU from this process
     cb = None
+    bratu_cpu = None
     p = W.workload2()
     if rank == 0 and not args.no_cpu_baseline:
         cb = cpu_baseline(p)
+        if not args.no_bratu:
+            bratu_cpu = bratu_cpu_sample()
 
     t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
     rowptr, col, val, b = G.q1_assemble(p.n, t(p.kappa), p.beta, t(p.f))
@@ -345,6 +368,68 @@ def main():
             sa.close()
         adaptive["ebp_r1024"] = {"ms": statistics.median(step_ms), "iters": it}
 
+    # ---- the paper's own workload: 3-D Bratu, 27-node hexahedra, lambda 6.8 (Sec. 3.1) --
+    # its protocol (GMRES(50) with the adaptive deflation, exactly 100 restart cycles) on the
+    # first Newton matrix J(0), and Newton's method to max |du| <= 1e-9
+    bratu = None
+    if rank == 0 and not args.no_bratu:
+        torch.cuda.empty_cache()
+        nb = BRATU_N
+        ev0.record(stream)
+        br, bc, bv, bb = G.q2_bratu_assemble(nb, BRATU_LAM, device=dev)
+        ev1.record(stream)
+        ev1.synchronize()
+        nnz_b, N_b = int(br[-1].item()), br.numel() - 1
+        bratu = {"workload": f"3-D Bratu, {nb}^3 Q2 elements ({N_b} DOF, {nnz_b} nnz), "
+                             f"lambda {BRATU_LAM}, adaptive deflation rmax 20",
+                 "assemble_ms": ev0.elapsed_time(ev1)}
+        sb = G.Solver(br, bc, bv, None, 0, deflation_mode=G.DEFL_ADAPTIVE, rmax=20,
+                      fixed_iterations=True)
+        ev0.record(stream)
+        _, ib = sb.solve(bb, m=M, tol=0.0, maxit=100 * M)
+        ev1.record(stream)
+        ev1.synchronize()
+        sb.close()
+        pr_ms = ev0.elapsed_time(ev1)
+        bratu["protocol_100_cycles"] = {"ms": pr_ms, "iters": ib["iters"],
+                                        "us_per_step": pr_ms * 1e3 / ib["iters"]}
+        # SpMV rate of the lane-per-row CSR kernel from a profiled cycle
+        sp = G.Solver(br, bc, bv, None, 0, deflation_mode=G.DEFL_NONE, fixed_iterations=True,
+                      profile=True)
+        sp.solve(bb, m=M, tol=0.0, maxit=M)
+        ph_b = sp.profile()
+        sp.close()
+        sp_ms, sp_n = ph_b["spmv"]
+        spmv_bytes = 12.0 * nnz_b + 4.0 * (N_b + 1) + 16.0 * N_b
+        bratu["spmv"] = {"kernel": "k_spmv_vec (4 lanes x 2 rows)", "us": sp_ms * 1e3 / sp_n,
+                         "gbs": spmv_bytes / (sp_ms / sp_n / 1e3) / 1e9,
+                         "bytes_per_launch": spmv_bytes}
+        bratu["spmv"]["hbm_frac"] = bratu["spmv"]["gbs"] / hbm_peak
+        ev0.record(stream)
+        ub, inw = G.bratu_newton(nb, BRATU_LAM, m=M, tol=1e-8, maxit=100000, newton_tol=1e-9,
+                                 device=dev)
+        ev1.record(stream)
+        ev1.synchronize()
+        bratu["newton"] = {"ms": ev0.elapsed_time(ev1), "newton_iters": inw["newton_iters"],
+                           "gmres_iters": inw["gmres_iters"], "status": inw["status"],
+                           "du_inf": inw["du_inf"], "u_max": float(ub.max().item())}
+        del br, bc, bv, bb, ub
+        if bratu_cpu:  # the same cycle on the GPU, for the paper's GPU-vs-one-core ratio
+            r30, c30, v30, b30 = G.q2_bratu_assemble(bratu_cpu["n"], BRATU_LAM, device=dev)
+            s30 = G.Solver(r30, c30, v30, None, 0, deflation_mode=G.DEFL_ADAPTIVE, rmax=20,
+                           fixed_iterations=True)
+            s30.solve(b30, m=M, tol=0.0, maxit=M)  # warm-up
+            ev0.record(stream)
+            _, i30 = s30.solve(b30, m=M, tol=0.0, maxit=M)
+            ev1.record(stream)
+            ev1.synchronize()
+            s30.close()
+            g_us = ev0.elapsed_time(ev1) * 1e3 / i30["iters"]
+            bratu["one_cycle_vs_oracle"] = {"n": bratu_cpu["n"], "gpu_us_per_step": g_us,
+                                            "oracle": bratu_cpu,
+                                            "gpu_vs_one_core": bratu_cpu["us_per_step"] / g_us}
+            del r30, c30, v30, b30
+
     # ---- time to a true relative residual of 1e-10 on q1-n2048: FP64 vs FP32 / BF16 inner
     mixed = None
     if rank == 0 and not args.no_mixed:
@@ -437,6 +522,7 @@ def main():
             "mixed_precision": mixed,
             "batched": batched,
             "adaptive": adaptive,
+            "bratu": bratu,
             "cpu_baseline": cb,
         }
         print(json.dumps(out), flush=True)
