@@ -107,6 +107,15 @@ typedef enum {
   GMRES_MU_NORM_INF = 2          /* |mu| = max_i sum_j |a_ij| (an upper bound) */
 } gmres_mu_mode;
 
+typedef enum {
+  GMRES_ORTHO_CGS2 = 0,     /* classical Gram-Schmidt applied twice (three pipelined passes
+                               over the basis per Arnoldi step) */
+  GMRES_ORTHO_MGS = 1       /* the paper's modified Gram-Schmidt (Sec. 3.2, Eq. 13): one
+                               projection after the other, in one cooperative kernel per
+                               step that keeps w in shared memory; half the FMAs of CGS2.
+                               FP64 single-system solves with n <= 27,000 x the SM count */
+} gmres_ortho;
+
 typedef struct {
   int32_t precision;        /* gmres_precision */
   int32_t deflation_mode;   /* gmres_deflation_mode */
@@ -122,6 +131,7 @@ typedef struct {
   int32_t profile;          /* 1: bracket every phase with CUDA events (gmres_profile) */
   int32_t rmax;             /* GMRES_DEFL_ADAPTIVE: most columns of U, 1..32 (paper: 20) */
   int32_t ninv;             /* GMRES_DEFL_ADAPTIVE: inverse power iterations per restart */
+  int32_t ortho;            /* gmres_ortho (default CGS2) */
 } gmres_opts;
 
 /* Phases reported by gmres_profile (kernel groups of one solve). */
@@ -137,7 +147,8 @@ typedef enum {
   GMRES_PH_RITZ = 8,      /* |mu| from the Ritz values of H_k */
   GMRES_PH_PROJ_FINAL = 9,/* projector: x = xh + U T^-1 U^T (b - A xh) */
   GMRES_PH_ADAPT = 10,    /* adaptive deflation: the update of U, A U, T, T^-1 */
-  GMRES_PH_COUNT = 11
+  GMRES_PH_MGS = 11,      /* modified Gram-Schmidt step: projections, ||w||, rotations */
+  GMRES_PH_COUNT = 12
 } gmres_phase;
 
 typedef struct {

@@ -44,7 +44,7 @@ class Solver:
                  agg: torch.Tensor | None = None, r: int = 0, *, precision=N.FP64,
                  deflation_mode=N.DEFL_EBP, mu_mode=N.MU_RITZ_FIRST_CYCLE, mu_user=0.0,
                  fixed_iterations=False, r0_norm_ref=0.0, timeout_ms=0, inner_tol=0.0,
-                 profile=False, rmax=20, ninv=20, stream=None):
+                 profile=False, rmax=20, ninv=20, ortho=N.ORTHO_CGS2, stream=None):
         L = N.load()
         n = rowptr.numel() - 1
         _dev(rowptr, torch.int32, "rowptr")
@@ -71,6 +71,7 @@ class Solver:
         opts.profile = 1 if profile else 0
         opts.rmax = int(rmax)
         opts.ninv = int(ninv)
+        opts.ortho = int(ortho)
         self._stream = stream
         h = C.c_void_p()
         st = L.gmres_create(C.byref(h), C.byref(csr), C.byref(defl) if defl else None,
@@ -245,8 +246,8 @@ def q2_bratu_assemble(n: int, lam: float, u: torch.Tensor | None = None, *, devi
 def bratu_newton(n: int, lam: float, u: torch.Tensor | None = None, *, m=50, tol=1e-8,
                  maxit=20000, newton_tol=1e-10, max_newton=30, agg: torch.Tensor | None = None,
                  r: int = 0, precision=N.FP64, deflation_mode=N.DEFL_ADAPTIVE,
-                 mu_mode=N.MU_RITZ_FIRST_CYCLE, mu_user=0.0, rmax=20, ninv=20, device=None,
-                 stream=None):
+                 mu_mode=N.MU_RITZ_FIRST_CYCLE, mu_user=0.0, rmax=20, ninv=20,
+                 ortho=N.ORTHO_CGS2, device=None, stream=None):
     """Newton's method for the 3-D Bratu problem (q2_bratu_newton); u (device, updated in
     place; zeros when None).  Returns (u, info dict)."""
     L = N.load()
@@ -263,6 +264,7 @@ def bratu_newton(n: int, lam: float, u: torch.Tensor | None = None, *, m=50, tol
     opts.mu_user = float(mu_user)
     opts.rmax = int(rmax)
     opts.ninv = int(ninv)
+    opts.ortho = int(ortho)
     defl = None
     if agg is not None and r > 0:
         _dev(agg, torch.int32, "agg", NN)

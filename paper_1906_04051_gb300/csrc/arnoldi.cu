@@ -389,6 +389,147 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // --------------------------------------------------------------------------------------
+// Modified Gram-Schmidt (the paper's orthogonalisation, Sec. 3.2, Eq. 13): for c = 0..j,
+// h_c = v_c . w, then w -= h_c v_c, each projection on the w left by the previous one.
+// One cooperative kernel per Arnoldi step, one block per SM: each block keeps its
+// contiguous slice of w on chip (registers, or shared memory for large n) for the whole
+// step, so the basis is read once and w never leaves the chip; the only traffic is V
+// (k columns) plus w in and u_{j+1} out.  Each projection needs the full dot product before the update, so every column
+// ends with a grid barrier; the blocks' partial sums are then added by every block in
+// the same fixed order (bitwise identical h_c everywhere, deterministic runs).  The last
+// round is ||w||: u_{j+1} = w is stored (v_{j+1} = sigma_{j+1} u_{j+1}) and block 0 applies
+// the plane rotations (Eq. 12).  The barrier's waits are bounded: a block that waits
+// longer than about a second records GMRES_ERR_TIMEOUT and returns.
+// --------------------------------------------------------------------------------------
+constexpr int kMgsThreads = 512;
+constexpr long long kBarrierSpins = 1LL << 21;  // polls of an L2 word: about a second
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident): bar[0] counts
+// arrivals, bar[1] is the generation that the last arrival advances.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& gen) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&bar[0], 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicExch(&bar[1], gen + 1u);
+    } else {
+      long long spins = 0;
+      while (*(volatile unsigned*)&bar[1] == gen) {
+        if (++spins > kBarrierSpins) {
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  ++gen;
+  return s_ok != 0;
+}
+
+// After each barrier the update with column c and the dot with column c+1 share one
+// pass over the rows (w_r -= coef_c u_c[r]; part += w_r u_{c+1}[r]), so a column costs one
+// pass and one barrier.  RPT > 0: each thread keeps its RPT rows of w and of the current
+// column in registers (n <= SMs x threads x RPT); RPT = 0: w in shared memory and each
+// column read twice (the second time from L1/L2).
+template <int RPT>
+__global__ void __launch_bounds__(kMgsThreads, 1)
+    k_mgs(int N, double* __restrict__ V, long long ldv, int k, const double* __restrict__ w,
+          Ctl ctl, int m, unsigned* bar, int rows) {
+  extern __shared__ __align__(16) double sw[];  // RPT = 0: this block's rows of w
+  __shared__ double sred[kMgsThreads / 32];
+  __shared__ double stot;
+  if (ctl.flags[F_CYCLE_DONE]) return;  // set before the launch: the same in every block
+  unsigned gen = *(volatile unsigned*)&bar[1];  // nobody advances it before all arrive
+  const int b = blockIdx.x, G = gridDim.x, T = blockDim.x, t = threadIdx.x;
+  const long long r0 = (long long)b * rows;
+  const int nr = (int)max(0LL, min((long long)rows, (long long)N - r0));
+  double wr[RPT > 0 ? RPT : 1], ur[RPT > 0 ? RPT : 1];
+  double part = 0.0;
+  {  // w in, and the first dot (with u_0, or ||w||^2 when k = 0)
+    const double* u = V + r0;
+    if constexpr (RPT > 0) {
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        const int r = t + i * T;
+        wr[i] = r < nr ? w[r0 + r] : 0.0;
+        ur[i] = (r < nr && k > 0) ? u[r] : 0.0;
+        part += k > 0 ? wr[i] * ur[i] : wr[i] * wr[i];
+      }
+    } else {
+      for (int r = t; r < nr; r += T) {
+        const double x = w[r0 + r];
+        sw[r] = x;
+        part += k > 0 ? x * u[r] : x * x;
+      }
+    }
+  }
+  for (int c = 0; c <= k; ++c) {  // round c: the dot with u_c (c < k) or ||w||^2 (c = k)
+    const double bs = block_sum(part, sred);
+    if (t == 0) __stcg(&ctl.part[(size_t)b * ctl.ldp + c], bs);
+    if (!grid_barrier(bar, gen)) {
+      if (t == 0) {
+        ctl.flags[F_STATUS] = GMRES_ERR_TIMEOUT;
+        ctl.flags[F_STOP] = 1;
+        ctl.flags[F_CYCLE_DONE] = 1;
+      }
+      return;
+    }
+    if (t < 32) {  // every block: the same ordered sum of the G partials
+      double x = 0.0;
+      for (int i = t; i < G; i += 32) x += __ldcg(&ctl.part[(size_t)i * ctl.ldp + c]);
+      x = warp_sum(x);
+      if (t == 0) stot = x;
+    }
+    __syncthreads();
+    const double tot = stot;
+    if (c == k) {  // u_{j+1} = w is stored; v_{j+1} = sigma_{j+1} u_{j+1}
+      double* vout = V + (size_t)k * ldv + r0;
+      if constexpr (RPT > 0) {
+#pragma unroll
+        for (int i = 0; i < RPT; ++i)
+          if (t + i * T < nr) vout[t + i * T] = wr[i];
+      } else {
+        for (int r = t; r < nr; r += T) vout[r] = sw[r];
+      }
+      if (b == 0) givens_step(ctl, k - 1, m, sqrt(tot));
+      break;
+    }
+    const double sig = ctl.sigma[c];
+    const double hc = sig * tot;  // v_c . w with v_c = sigma_c u_c
+    if (b == 0 && t == 0) ctl.h[c] = hc;
+    const double coef = sig * hc;
+    const double* u = V + (size_t)c * ldv + r0;
+    const double* un = u + ldv;  // u_{c+1}
+    const bool last = c + 1 == k;
+    part = 0.0;
+    if constexpr (RPT > 0) {
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        const int r = t + i * T;
+        const double nu = (r < nr && !last) ? un[r] : 0.0;
+        wr[i] -= coef * ur[i];
+        part += last ? wr[i] * wr[i] : wr[i] * nu;
+        ur[i] = nu;
+      }
+    } else {
+      for (int r = t; r < nr; r += T) {
+        const double x = sw[r] - coef * u[r];
+        sw[r] = x;
+        part += last ? x * x : x * un[r];
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------------------------------
 // Deflation: c = scale U^T x by pieces (warp per piece), then s = U (|mu| T^-1 - I) c.
 // --------------------------------------------------------------------------------------
 // Piece sums: a warp per piece, up to 32 gathers in flight per lane (pieces hold at most
@@ -910,6 +1051,37 @@ struct Kern {
         nl = 1;
         break;
       }
+      case PH_MGS: {  // modified Gram-Schmidt step on w = A M^-1 v_j (FP64)
+        if constexpr (sizeof(TV) == sizeof(double) && sizeof(TACC) == sizeof(double)) {
+          int rows = mgs_rows(N, sms);
+          if (rows == 0) return cudaErrorInvalidValue;
+          const int rpt = (rows + kMgsThreads - 1) / kMgsThreads;
+          void (*kern)(int, double*, long long, int, const double*, Ctl, int, unsigned*, int) =
+              rpt <= 4 ? k_mgs<4> : rpt <= 8 ? k_mgs<8> : rpt <= 16 ? k_mgs<16> : k_mgs<0>;
+          const size_t smem = rpt <= 16 ? 0 : sizeof(double) * (size_t)rows;
+          static bool attr = false;
+          if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_mgs<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(220 * 1024));
+            if (e != cudaSuccess) return e;
+            attr = true;
+          }
+          int kk = k, Nn = N, m = a.m;
+          double* Vd = reinterpret_cast<double*>(Vm);
+          long long ldv = a.ldv;
+          const double* wd = reinterpret_cast<const double*>(w);
+          Ctl ctl = a.ctl;
+          unsigned* bar = a.gbar;
+          void* args[] = {&Nn, &Vd, &ldv, &kk, &wd, &ctl, &m, &bar, &rows};
+          cudaError_t e = cudaLaunchCooperativeKernel((const void*)kern, dim3(sms),
+                                                      dim3(kMgsThreads), args, smem, st);
+          if (e != cudaSuccess) return e;
+          nl = 1;
+        } else {
+          return cudaErrorInvalidValue;
+        }
+        break;
+      }
       case PH_DEFL: {  // U^T v_j and the correction for column j
         const TV* xj = V + (size_t)j * a.ldv;
         if (d.qd > 0) {  // adaptive: one multi-dot over the dense U, then s' = |mu| T^-1 c - c
@@ -1027,6 +1199,12 @@ cudaError_t launch_udots(const CycleArgs& a, const double* M, long long ldm, int
   if (e != cudaSuccess) return e;
   K64::udots(a, M, ldm, ncols, x, epi, false, st);
   return cudaGetLastError();
+}
+
+// rows of w per block of the modified Gram-Schmidt kernel, 0 if n does not fit
+int mgs_rows(int n, int sms) {
+  const long long rows = ((long long)n + sms - 1) / sms;
+  return rows * (long long)sizeof(double) <= 220 * 1024 ? (int)rows : 0;
 }
 
 cudaError_t launch_phase(const CycleArgs& a, int ph, int j, bool defl, double* x,

@@ -818,6 +818,8 @@ gmres_status batch_solve_impl(int count, gmres_t const* hs, const double* const*
     if (hs[i]->opts.deflation_mode == GMRES_DEFL_ADAPTIVE)
       return fail(nullptr, GMRES_ERR_INVALID_ARG,
                   "deflation_mode ADAPTIVE is for single-system solves");
+    if (hs[i]->opts.ortho != GMRES_ORTHO_CGS2)
+      return fail(nullptr, GMRES_ERR_INVALID_ARG, "the batched solve orthogonalises by CGS2");
   }
   int sms = hs[0]->sms;
   // workspaces of the handles serve the batch (allocated on the batch stream)

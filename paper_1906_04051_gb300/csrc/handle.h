@@ -75,6 +75,7 @@ struct gmres_s {
   // adaptive deflation (GMRES_DEFL_ADAPTIVE): U, A U (ldv x rmax), T (rmax x rmax),
   // T^-1 (q x q), a work vector, small scratch; aq columns in use
   DevMem aU, aAU, aT, aTinv, au, asmall;
+  DevMem gbar;  // grid barrier words of the modified Gram-Schmidt kernel
   int aq = 0;
   Meta* hmeta = nullptr;  // pinned
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -149,6 +150,7 @@ inline gmres_status ensure_workspace(gmres_s* h, int m, int prec) {
   }
   CK(h, h->cpart.ensure(sizeof(double) * (size_t)(h->npieces + 1)));
   CK(h, h->sdefl.ensure(12 * (size_t)sdefl_len(h)));
+  CK(h, h->gbar.ensure(2 * sizeof(unsigned)));
   if (h->opts.deflation_mode == GMRES_DEFL_ADAPTIVE && !h->aU.p) {
     const size_t col = sizeof(double) * (size_t)ldv;
     const size_t R = (size_t)h->opts.rmax;

@@ -8,6 +8,9 @@
 namespace gg {
 
 int grid_for(long long work, int threads, int max_blocks);
+// rows of w per block of the modified Gram-Schmidt kernel (one block per SM), 0 if n
+// does not fit in its shared memory
+int mgs_rows(int n, int sms);
 
 // fem.cu
 cudaError_t launch_q1_assemble(int n, const double* kappa, double bx, double by,
@@ -89,6 +92,8 @@ struct CycleArgs {
   int sms;               // multiprocessors of the device
   int grid_small;        // blocks of the coarse GEMV
   int pdl;               // step kernels with programmatic dependent launch
+  int ortho;             // gmres_ortho
+  unsigned* gbar;        // grid barrier of the modified Gram-Schmidt kernel (2 words)
 };
 
 // Phases of a solve; each launch_phase call enqueues the kernels of one phase.
@@ -104,6 +109,7 @@ enum Phase {
   PH_RITZ,          // |mu| from the Ritz values
   PH_PROJ_FINAL,    // projector: x = xh + U T^-1 U^T (b - A xh)
   PH_ADAPT,         // adaptive deflation: update of U, A U, T, T^-1 after a cycle
+  PH_MGS,           // modified Gram-Schmidt step (one cooperative kernel)
   PH_COUNT
 };
 // c = M^T x over ncols FP64 columns of M (leading dimension ldm), pipelined multi-dot with

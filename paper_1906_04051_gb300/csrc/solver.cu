@@ -89,6 +89,14 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
   a.grid_small = h->r > 0 ? grid_for(h->r, 8, h->sms) : 1;
   a.pdl = h->prof_on ? 0 : 1;  // per-phase events would serialise the launches anyway
   a.proj = (h->r > 0 && h->opts.deflation_mode == GMRES_DEFL_PROJECTOR) ? 1 : 0;
+  a.ortho = h->opts.ortho;
+  a.gbar = h->gbar.as<unsigned>();
+  const bool mgs = a.ortho == GMRES_ORTHO_MGS;
+  if (mgs) {
+    if (mgs_rows(h->n, h->sms) == 0)
+      return fail(h, GMRES_ERR_INVALID_ARG, "GMRES_ORTHO_MGS: n exceeds 220 KiB of w per SM");
+    CK(h, cudaMemsetAsync(h->gbar.p, 0, 2 * sizeof(unsigned), st));
+  }
 
   const bool ebp = h->r > 0 && h->opts.deflation_mode == GMRES_DEFL_EBP;
   const bool ada = h->opts.deflation_mode == GMRES_DEFL_ADAPTIVE;  // U grows from empty
@@ -127,9 +135,13 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
     const int jmax = (int)(left < m ? left : m);
     for (int j = 0; j < jmax; ++j) {
       CK(h, phase(h, a, PH_SPMV, j, defl_cycle, x, b));
-      CK(h, phase(h, a, PH_DOT1, j, defl_cycle, x, b));
-      CK(h, phase(h, a, PH_UPD1DOT2, j, defl_cycle, x, b));
-      CK(h, phase(h, a, PH_UPD2NORM, j, defl_cycle, x, b));
+      if (mgs) {
+        CK(h, phase(h, a, PH_MGS, j, defl_cycle, x, b));
+      } else {
+        CK(h, phase(h, a, PH_DOT1, j, defl_cycle, x, b));
+        CK(h, phase(h, a, PH_UPD1DOT2, j, defl_cycle, x, b));
+        CK(h, phase(h, a, PH_UPD2NORM, j, defl_cycle, x, b));
+      }
       if (defl_cycle) CK(h, phase(h, a, PH_DEFL, j + 1, true, x, b));
     }
     CK(h, phase(h, a, PH_CYCLE_END, 0, defl_cycle, x, b));
@@ -218,6 +230,8 @@ gmres_status run_noalloc(gmres_s* h, OpHost& o, const double* b, const double* x
   if (!b || !x) return fail(h, GMRES_ERR_INVALID_ARG, "b and x must be device pointers");
   if (h->opts.deflation_mode == GMRES_DEFL_ADAPTIVE)
     return fail(h, GMRES_ERR_INVALID_ARG, "gmres_solve_noalloc: GMRES_DEFL_ADAPTIVE allocates its space");
+  if (h->opts.ortho != GMRES_ORTHO_CGS2)
+    return fail(h, GMRES_ERR_INVALID_ARG, "gmres_solve_noalloc: CGS2 only");
   if (m < 1 || m > kMaxM) return fail(h, GMRES_ERR_INVALID_ARG, "m must be in [1, 64]");
   if (!(tol >= 0.0) || maxit < 0) return fail(h, GMRES_ERR_INVALID_ARG, "tol >= 0, maxit >= 0");
   const int prec = prec_of(h->opts.precision);
@@ -391,8 +405,11 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
   if (o) opts = *o;
   else gmres_opts_default(&opts);
   if (opts.precision < 0 || opts.precision > 2 || opts.deflation_mode < 0 ||
-      opts.deflation_mode > 3 || opts.mu_mode < 0 || opts.mu_mode > 2)
+      opts.deflation_mode > 3 || opts.mu_mode < 0 || opts.mu_mode > 2 || opts.ortho < 0 ||
+      opts.ortho > 1)
     return fail(nullptr, GMRES_ERR_INVALID_ARG, "invalid option value");
+  if (opts.ortho == GMRES_ORTHO_MGS && opts.precision != GMRES_FP64)
+    return fail(nullptr, GMRES_ERR_INVALID_ARG, "GMRES_ORTHO_MGS is FP64 only");
   if (opts.deflation_mode == GMRES_DEFL_ADAPTIVE) {
     if (r > 0)
       return fail(nullptr, GMRES_ERR_INVALID_ARG,
