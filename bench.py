@@ -4,7 +4,8 @@
 lognormal kappa, 1024 aggregate deflation vectors), FP64, on one GB300 per rank.
 
 One step = one pass of the whole hot path on one synthetic system: gmres_create (coarse
-matrix T = U^T A U and its inverse) + gmres_solve to tol.  The metric value is solves/s
+matrix T = U^T A U and its inverse) + gmres_solve to tol, orthogonalising by the paper's
+modified Gram-Schmidt in its one-reduction form.  The metric value is solves/s
 (whole job: all ranks' solves / slowest rank's time).  The system is assembled on the
 device once (untimed input generation); between timed steps L2 is flushed with a 256 MB
 write.  Multi-GPU runs are independent replicas (the single-system solve does not shard
@@ -31,11 +32,15 @@ if ROOT not in sys.path:
 METRIC = ("time-to-tol & SpMV+Arnoldi HBM GB/s vs peak; mixed/batched vs FP64 GMRES "
           "speedup")
 UNIT = "solves/s"
+# orthogonalisation of the timed solves: the paper's MGS projections in the one-reduction
+# (inverse compact WY) form; CGS2 and column-by-column MGS are timed beside it
+ORTHO = 2  # GMRES_ORTHO_MGS_LOWSYNC
 M, TOL, MAXIT = 50, 1e-8, 20000
 # FP64 FMA peak of GB300: 2 DFMA/clk/SM (ncu sm__sass_thread_inst_executed_op_dfma
 # peak_sustained) x 152 SMs x 2.07 GHz x 2 flop
 FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 PASS2_DRAM_BYTES_K26 = 235.34e6  # dram__bytes_read.sum + dram__bytes_write.sum, k = 26
+PASS1I_DRAM_BYTES_K26 = 230.41e6  # the same for the one-reduction MGS pass 1, k = 26
 # Arnoldi steps the deflated GMRES(50) takes to 1e-8 on this workload (deterministic;
 # the GPU arm prints its own count): used only to project the CPU sample to a full solve
 PROJECT_ITERS = 782
@@ -124,13 +129,13 @@ def cpu_baseline(p, budget_steps=M):
     d = oracle.Deflation(A, p.agg, p.r)
     t1 = time.perf_counter()
     x, info = oracle.gmres(A, b, m=M, tol=0.0, maxit=budget_steps, defl=d, mu_mode=1,
-                           mu_user=14.0, fixed_iterations=True)
+                           mu_user=14.0, fixed_iterations=True, ortho=oracle.MGS)
     t2 = time.perf_counter()
     per_step = (t2 - t1) / max(info["iters"], 1)
     projected = (t1 - t0) + per_step * PROJECT_ITERS
     del x, np
     return {"value": 1.0 / projected, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"oracle setup (T, LU of T) + {info['iters']} Arnoldi steps of the same "
+            "sample": (f"oracle setup (T, LU of T) + {info['iters']} MGS Arnoldi steps of the same "
                        f"workload ({t2 - t0:.1f} s), projected to {PROJECT_ITERS} steps"),
             "projected_solve_s": projected, "setup_s": t1 - t0, "s_per_step": per_step}
 
@@ -171,6 +176,7 @@ def run_reference(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
            "config": {"workload": "q1-n1024 deflated GMRES(50) tol 1e-8 (projected)",
+                      "ortho": "mgs",
                       "n": p.n, "dof": p.N, "nnz": p.nnz, "r": p.r, "m": M},
            "cpu_baseline": dict(vals[-1], value=v),
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -236,7 +242,7 @@ def main():
     layout = {}
 
     def one_step(profile=False):
-        s = G.Solver(rowptr, col, val, agg, p.r, profile=profile)
+        s = G.Solver(rowptr, col, val, agg, p.r, profile=profile, ortho=ORTHO)
         _, info = s.solve(b, m=M, tol=TOL, maxit=MAXIT, out=x)
         prof = s.profile() if profile else None
         if profile:
@@ -282,40 +288,44 @@ def main():
         total_ms = float(tt.item())
     value = world * args.steps / (total_ms / 1e3)
 
-    # ---- per-kernel roofline of the dominant kernel (CGS2 pass 2, FP64) -------------
+    # ---- per-kernel roofline of the dominant kernel: the one-reduction MGS pass 1 -------
+    # (g = V^T w and V^T u_j in one multi-dot, 2k FMA per row; its phase also holds the
+    # k x k triangular solve, a few us per step, so the rate is a slight underestimate)
     N, nnz = p.N, p.nnz
     it = infos[-1]["iters"]
     cyc = infos[-1]["cycles"]
     steps_per_cycle = [M] * (cyc - 1) + [it - M * (cyc - 1)]
     ks = [j + 1 for sc in steps_per_cycle for j in range(sc)]
-    flops_upd1 = sum(4.0 * k * N for k in ks)          # 2k FMA per row
-    bytes_upd1 = sum(8.0 * k * N + 16.0 * N for k in ks)
-    ms_upd1 = statistics.mean(pr["upd1dot2"][0] for pr in profs)
+    flops_p1 = sum(4.0 * k * N for k in ks)          # 2k FMA per row
+    bytes_p1 = sum(8.0 * k * N + 8.0 * N for k in ks)
+    ms_p1 = statistics.mean(pr["dot1"][0] for pr in profs)
     # every timed step runs the same deterministic solve, so each launches what the
     # profiled one did
     launches = args.steps * sum(v[1] for v in profs[-1].values())
-    achieved = flops_upd1 / (ms_upd1 / 1e3) / 1e12
+    achieved = flops_p1 / (ms_p1 / 1e3) / 1e12
     hbm_peak, peak_kind = _peaks()
-    # DRAM traffic of one pass-2 launch at k = 26 columns from an ncu capture of this build
-    # (profiles/k_pass2_q1-n1024_fp64.txt), scaled to each launch by its columns (the
-    # bytes grow as 8 k N + 16 N), averaged over the solve's launches
-    traffic = statistics.mean(PASS2_DRAM_BYTES_K26 * (8.0 * k + 16.0) / (8.0 * 26 + 16.0)
+    # DRAM traffic of one pass-1 launch at k = 26 columns from an ncu capture of this build
+    # (profiles/k_pass1_lowsync_q1-n1024_fp64.txt), scaled to each launch by its columns
+    # (the bytes grow as 8 k N + 8 N), averaged over the solve's launches
+    traffic = statistics.mean(PASS1I_DRAM_BYTES_K26 * (8.0 * k + 8.0) / (8.0 * 26 + 8.0)
                               for k in ks)
-    roofline = {"kernel": "k_pass2 (CGS2 pass 2)", "bound": "alu", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+    roofline = {"kernel": "k_pass1 (one-reduction MGS: V^T w and V^T u_j)", "bound": "alu",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": traffic, "traffic_unit": "bytes per launch",
-                "algorithmic_bytes_per_launch": bytes_upd1 / len(ks),
+                "algorithmic_bytes_per_launch": bytes_p1 / len(ks),
                 "peak_kind": "derived FP64 FMA rate",
-                "hbm_gbs_same_kernel": bytes_upd1 / (ms_upd1 / 1e3) / 1e9}
+                "hbm_gbs_same_kernel": bytes_p1 / (ms_p1 / 1e3) / 1e9}
     # SpMV + Arnoldi algorithmic bytes over the whole solve (metric part 2)
     ph = profs[-1]
-    arn_ms = sum(ph[k][0] for k in ("spmv", "dot1", "upd1dot2", "upd2norm"))
+    arn_ms = sum(ph[k][0] for k in ("spmv", "dot1", "upd1dot2", "upd2norm") if k in ph)
     # the SpMV streams A in the storage chosen at create: nd diagonals (values only) or CSR
     # (values + column indexes + row pointers), then the A W rows, x once, w written
     nd, nau = layout.get("ndiag", 0), layout.get("nau", 0)
     a_bytes = 8.0 * nd * N if nd else 12.0 * nnz + 4.0 * (N + 1)
     spmv_bytes = a_bytes + 4.0 * (N + 1) + 12.0 * nau + 8.0 * N * 2
-    arn_bytes = sum(spmv_bytes + 3 * 8.0 * k * N + 6 * 8.0 * N for k in ks)
+    # two passes over the basis: pass 1 reads V and w, pass 3 reads V and w, writes u_{j+1}
+    arn_bytes = sum(spmv_bytes + 2 * 8.0 * k * N + 4 * 8.0 * N for k in ks)
     arnoldi_gbs = arn_bytes / (arn_ms / 1e3) / 1e9
 
     # ---- end to end through the public API from pinned host buffers ------------------
@@ -332,7 +342,7 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             dv = {k: v.to(dev, non_blocking=True) for k, v in hb.items()}
-            s = G.Solver(dv["rowptr"], dv["col"], dv["val"], dv["agg"], p.r)
+            s = G.Solver(dv["rowptr"], dv["col"], dv["val"], dv["agg"], p.r, ortho=ORTHO)
             xd, _ = s.solve(dv["b"], m=M, tol=TOL, maxit=MAXIT)
             xh.copy_(xd, non_blocking=True)
             torch.cuda.synchronize()
@@ -368,21 +378,22 @@ def main():
             sa.close()
         adaptive["ebp_r1024"] = {"ms": statistics.median(step_ms), "iters": it}
 
-    # ---- the paper's modified Gram-Schmidt (one cooperative kernel per step) on the same
-    # system, against the CGS2 steps timed above
+    # ---- the other orthogonalisations on the same system (solve only, T set up) ---------
     ortho = None
     if rank == 0:
-        so = G.Solver(rowptr, col, val, agg, p.r, ortho=G.ORTHO_MGS)
-        so.solve(b, m=M, tol=TOL, maxit=MAXIT)  # warm-up
-        ev0.record(stream)
-        _, io = so.solve(b, m=M, tol=TOL, maxit=MAXIT)
-        ev1.record(stream)
-        ev1.synchronize()
-        so.close()
         ortho = {"workload": "q1-n1024 EBP GMRES(50) tol 1e-8, solve only (T set up)",
-                 "mgs": {"ms": ev0.elapsed_time(ev1), "iters": io["iters"],
-                         "rel_res_true": io["rel_res_true"]},
-                 "cgs2": {"ms": statistics.median(i["ms_total"] for i in infos), "iters": it}}
+                 "mgs_lowsync": {"ms": statistics.median(i["ms_total"] for i in infos),
+                                 "iters": it}}
+        for name, o in (("cgs2", G.ORTHO_CGS2), ("mgs_per_column", G.ORTHO_MGS)):
+            so = G.Solver(rowptr, col, val, agg, p.r, ortho=o)
+            so.solve(b, m=M, tol=TOL, maxit=MAXIT)  # warm-up
+            ev0.record(stream)
+            _, io = so.solve(b, m=M, tol=TOL, maxit=MAXIT)
+            ev1.record(stream)
+            ev1.synchronize()
+            so.close()
+            ortho[name] = {"ms": ev0.elapsed_time(ev1), "iters": io["iters"],
+                           "rel_res_true": io["rel_res_true"]}
 
     # ---- the paper's own workload: 3-D Bratu, 27-node hexahedra, lambda 6.8 (Sec. 3.1) --
     # its protocol (GMRES(50) with the adaptive deflation, exactly 100 restart cycles) on the
@@ -519,7 +530,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "q1-n1024 deflated GMRES(50) tol 1e-8", "n": p.n,
+            "config": {"workload": "q1-n1024 deflated GMRES(50) tol 1e-8",
+                       "ortho": "mgs_lowsync", "n": p.n,
                        "dof": N, "nnz": nnz, "r": p.r, "m": M, "tol": TOL,
                        "parallelism": f"replicas x{world}",
                        "l2": "flushed (256 MB write) between steps; V basis 430 MB > L2"},

@@ -110,10 +110,16 @@ typedef enum {
 typedef enum {
   GMRES_ORTHO_CGS2 = 0,     /* classical Gram-Schmidt applied twice (three pipelined passes
                                over the basis per Arnoldi step) */
-  GMRES_ORTHO_MGS = 1       /* the paper's modified Gram-Schmidt (Sec. 3.2, Eq. 13): one
+  GMRES_ORTHO_MGS = 1,      /* the paper's modified Gram-Schmidt (Sec. 3.2, Eq. 13): one
                                projection after the other, in one cooperative kernel per
                                step that keeps w in shared memory; half the FMAs of CGS2.
-                               FP64 single-system solves with n <= 27,000 x the SM count */
+                               FP64 single-system solves with n <= 28,000 x the SM count */
+  GMRES_ORTHO_MGS_LOWSYNC = 2 /* the same projections as MGS in the inverse compact WY
+                               form: one reduction gives V^T w and V^T v_j, h solves
+                               (I + L) h = V^T w with L the strictly lower part of V^T V,
+                               and w -= V h; two passes over the basis per step, 3k FMAs
+                               per row instead of CGS2's 4k.  FP64 and FP32 inner solves,
+                               single-system */
 } gmres_ortho;
 
 typedef struct {

@@ -7,7 +7,7 @@ has not been built (``python -m paper_1906_04051_gb300.build``).
 """
 from ._native import (BF16_BASIS, DEFL_ADAPTIVE, DEFL_EBP, DEFL_NONE, DEFL_PROJECTOR,
                       FP32_INNER, FP64, MU_NORM_INF, MU_RITZ_FIRST_CYCLE, MU_USER, ORTHO_CGS2,
-                      ORTHO_MGS, GmresError)
+                      ORTHO_MGS, ORTHO_MGS_LOWSYNC, GmresError)
 from .api import (Solver, batch_solve, bratu_newton, q1_assemble, q1_kappa_grad, q1_nnz,
                   q2_bratu_assemble, q2_nnz)
 
@@ -17,6 +17,7 @@ __all__ = [
     "FP64", "FP32_INNER", "BF16_BASIS", "DEFL_EBP", "DEFL_PROJECTOR", "DEFL_NONE",
     "DEFL_ADAPTIVE",
     "MU_RITZ_FIRST_CYCLE", "MU_USER", "MU_NORM_INF", "ORTHO_CGS2", "ORTHO_MGS",
+    "ORTHO_MGS_LOWSYNC",
 ]
 from .autograd import GmresSolve, Q1Setup, q1_solve  # noqa: E402
 

@@ -28,7 +28,7 @@ STATUS_NAMES = {
 FP64, FP32_INNER, BF16_BASIS = 0, 1, 2
 DEFL_EBP, DEFL_PROJECTOR, DEFL_NONE, DEFL_ADAPTIVE = 0, 1, 2, 3
 MU_RITZ_FIRST_CYCLE, MU_USER, MU_NORM_INF = 0, 1, 2
-ORTHO_CGS2, ORTHO_MGS = 0, 1
+ORTHO_CGS2, ORTHO_MGS, ORTHO_MGS_LOWSYNC = 0, 1, 2
 PHASES = ["setup", "residual", "spmv", "dot1", "upd1dot2", "upd2norm", "defl", "cycle_end",
           "ritz", "proj_final", "adapt", "mgs"]
 

@@ -23,6 +23,8 @@
 #include "internal.h"
 #include "kernels.cuh"
 
+#include <type_traits>
+
 namespace gg {
 
 namespace {
@@ -222,32 +224,56 @@ __global__ void __launch_bounds__(kThreads)
 
 // CGS2 pass 1 (pipelined): h_c = sigma_c (u_c . w), coef_c = sigma_c h_c.  The same
 // multi-dot c = M^T x serves the adaptive deflation space (columns of U or A U) with
-// another epilogue (DotEpi).
-template <typename TV, typename TACC>
+// another epilogue (DotEpi).  ICWY (one-reduction MGS): the same pass also forms the
+// dots of the newest basis column u_j with all columns from the tile already in shared
+// memory, so one reduction gives g = V^T w and the new row of L (v_j . v_c, c < j).
+template <typename TV, typename TACC, bool ICWY = false>
 __global__ void __launch_bounds__(kThreads)
     k_pass1(int N, const TV* __restrict__ V, long long ldv, int k, int TR,
             const TACC* __restrict__ w, Ctl ctl, DotEpi epi) {
+  constexpr int NR = ICWY ? 2 * kMaxK : kMaxK;
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ uint64_t bars[kMaxStages];
   __shared__ double swarp[kSlices * kSliceCols];
-  __shared__ double sred[kMaxK];
-  __shared__ double tot[kMaxK];
+  __shared__ double sred[NR];
+  __shared__ double tot[NR];
   const size_t sb = ring_stage_bytes(k, TR, sizeof(TV), sizeof(TACC));
   const Ring<TV, TACC> R{smraw, bars, k, TR, ring_stages(sb), sb};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = slice_cols(k, warp, kSlices);
-  TACC acc[kSliceCols];
+  TACC acc[kSliceCols], acc2[ICWY ? kSliceCols : 1];
 #pragma unroll
   for (int i = 0; i < kSliceCols; ++i) acc[i] = 0;
+#pragma unroll
+  for (int i = 0; i < (ICWY ? kSliceCols : 1); ++i) acc2[i] = 0;
   // w is the predecessor's (the SpMV's) output: its slices are copied after the wait
   const bool ok = ring_run(R, N, V, ldv, w, ctl, false, [] {}, [&](int st, long long) {
-#define GG_P1(NW) tile_dot<NW, TV, TACC>(acc, R.vt(st), R.wt(st), TR, warp, lane)
+#define GG_P1(NW)                                                                        \
+  {                                                                                      \
+    tile_dot<NW, TV, TACC>(acc, R.vt(st), R.wt(st), TR, warp, lane);                     \
+    if constexpr (ICWY)                                                                  \
+      tile_dot<NW, TV, TACC>(acc2, R.vt(st), (const TACC*)(R.vt(st) + (size_t)(k - 1) * TR), \
+                             TR, warp, lane);                                            \
+  }
     GG_SLICE_SWITCH(nw, GG_P1)
 #undef GG_P1
   }, epi.skip_slot);
   if (!ok) return;
   reduce_slices(acc, nw, k, kSlices, reinterpret_cast<double*>(smraw), swarp, sred);
-  if (!last_block_reduce(sred, k, ctl.part, ctl.part2, ctl.ldp, ctl.ticket, tot)) return;
+  if constexpr (ICWY) {
+    reduce_slices(acc2, nw, k, kSlices, reinterpret_cast<double*>(smraw), swarp, sred + k);
+    if (!last_block_reduce(sred, 2 * k, ctl.part, ctl.part2, ctl.ldp, ctl.ticket, tot)) return;
+    // g_c = v_c . w into h (the solve kernel turns it into the MGS coefficients) and the
+    // new row of L: v_j . v_c = sigma_j sigma_c (u_j . u_c), c < j
+    const double sj = ctl.sigma[k - 1];
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+      ctl.h[c] = ctl.sigma[c] * tot[c];
+      if (c < k - 1) ctl.L[(size_t)(k - 1) * kMaxK + c] = sj * ctl.sigma[c] * tot[k + c];
+    }
+    return;
+  } else {
+    if (!last_block_reduce(sred, k, ctl.part, ctl.part2, ctl.ldp, ctl.ticket, tot)) return;
+  }
   if (epi.mode == kEpiCoarse) {  // s = |mu| T^-1 c - c (adaptive deflation, Eq. 17)
     const double mu = fabs(ctl.scal[S_MU]);
     for (int t = threadIdx.x; t < k; t += blockDim.x) {
@@ -267,6 +293,44 @@ __global__ void __launch_bounds__(kThreads)
     const double hc = ctl.sigma[c] * tot[c];
     ctl.h[c] = hc;
     ctl.coef[c] = ctl.sigma[c] * hc;
+  }
+}
+
+// One-reduction MGS, the solve: (I + L) h = g with L strictly lower triangular (k x k of
+// the cycle's rows), by forward substitution in one warp (entries i, i+32, i+64 of h in
+// lane i's registers, column by column: h_c is final when reached, the rows below drop
+// L[i][c] h_c), L staged in shared memory by the whole block first; then h = the MGS
+// projection coefficients and coef_c = sigma_c h_c for the update pass.
+__global__ void __launch_bounds__(256) k_icwy_solve(Ctl ctl, int k) {
+  __shared__ double sL[kMaxK * kMaxK];
+  pdl_wait();
+  pdl_trigger();
+  if (ctl.flags[F_CYCLE_DONE]) return;
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    const int i = t / k, c = t % k;
+    sL[i * kMaxK + c] = c < i ? ctl.L[(size_t)i * kMaxK + c] : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  double g[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) g[q] = lane + 32 * q < k ? ctl.h[lane + 32 * q] : 0.0;
+  for (int c = 0; c < k; ++c) {
+    const double hc = __shfl_sync(0xffffffffu, c < 32 ? g[0] : (c < 64 ? g[1] : g[2]), c & 31);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int i = lane + 32 * q;
+      if (i > c && i < k) g[q] -= sL[i * kMaxK + c] * hc;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int i = lane + 32 * q;
+    if (i < k) {
+      ctl.h[i] = g[q];
+      ctl.coef[i] = ctl.sigma[i] * g[q];
+    }
   }
 }
 
@@ -885,7 +949,7 @@ struct Kern {
   struct Grids {
     int spmv_d = 0, spmv_n = 0, resid = 0, xupd_d = 0, xupd_n = 0, xapply = 0;
     int tr[kMaxK + 1] = {0};
-    int p1[kMaxK + 1] = {0}, p2[kMaxK + 1] = {0}, p3[kMaxK + 1] = {0};
+    int p1[kMaxK + 1] = {0}, p2[kMaxK + 1] = {0}, p3[kMaxK + 1] = {0}, p1i[kMaxK + 1] = {0};
   };
   // Tile height of the pipelined passes (256/128/64 rows, at least 32 16-byte vectors):
   // the largest whose stage fits 40 KB, so that a double-buffered ring leaves room for
@@ -915,6 +979,8 @@ struct Kern {
       for (int k = 1; k <= kMaxK; ++k) {
         g.tr[k] = tile_rows(k);
         g.p1[k] = resident_grid(k_pass1<TV, TACC>, kThreads, ring_smem(k), sms);
+        if constexpr (std::is_same<TV, TACC>::value)
+          g.p1i[k] = resident_grid(k_pass1<TV, TACC, true>, kThreads, ring_smem(k), sms);
         g.p2[k] = resident_grid(k_pass2<TV, TACC>, kThreads, ring_smem(k), sms);
         g.p3[k] = resident_grid(k_pass3<TV, TACC>, kThreads, ring_smem(k), sms);
       }
@@ -1031,6 +1097,18 @@ struct Kern {
       }
       case PH_DOT1: {
         const int tr = g.tr[k];
+        if (a.ortho == GMRES_ORTHO_MGS_LOWSYNC) {  // one reduction, then the triangular solve
+          if constexpr (std::is_same<TV, TACC>::value) {
+            launch_k(a.pdl != 0, k_pass1<TV, TACC, true>, grid_for((N + tr - 1) / tr, 1, g.p1i[k]),
+                     kThreads, ring_smem(k), st, N, V, a.ldv, k, tr, (const TACC*)w, a.ctl,
+                     DotEpi{kEpiIcwy, nullptr, 0, nullptr, F_CYCLE_DONE});
+            launch_k(a.pdl != 0, k_icwy_solve, 1, 256, 0, st, a.ctl, k);
+            nl = 2;
+          } else {
+            return cudaErrorInvalidValue;
+          }
+          break;
+        }
         launch_k(a.pdl != 0, k_pass1<TV, TACC>, grid_for((N + tr - 1) / tr, 1, g.p1[k]),
                  kThreads, ring_smem(k), st, N, V, a.ldv, k, tr, (const TACC*)w, a.ctl,
                  DotEpi{kEpiArnoldi, nullptr, 0, nullptr, F_CYCLE_DONE});
@@ -1161,6 +1239,10 @@ struct Kern {
     for (int k = 1; k <= kMaxK; ++k) mx = ring_smem(k) > mx ? ring_smem(k) : mx;
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_pass1<TV, TACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+    if constexpr (std::is_same<TV, TACC>::value)
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pass1<TV, TACC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)mx);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_pass2<TV, TACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     if (e == cudaSuccess)

@@ -75,12 +75,13 @@ struct Ctl {
   unsigned* ticket;         // 1 + kMaxGroups last-block counters (zero between kernels)
   long long* counts;        // C_NCOUNT
   int ldh;        // m of the workspace
-  int ldp;        // leading dimension of part (>= kMaxK + 1)
+  int ldp;        // leading dimension of part (>= 2 kMaxK + 1)
+  double* L;      // one-reduction MGS: kMaxK x kMaxK, L[i][c] = v_i . v_c (c < i) of the cycle
 };
 
 // Epilogue of a multi-dot kernel: the Arnoldi coefficients, the adaptive deflation's
 // coarse correction s = |mu| T^-1 c - c (into ctl.sdefl), or the raw dots (into out).
-enum { kEpiArnoldi = 0, kEpiCoarse = 1, kEpiRaw = 2 };
+enum { kEpiArnoldi = 0, kEpiCoarse = 1, kEpiRaw = 2, kEpiIcwy = 3 };
 struct DotEpi {
   int mode;
   const double* tinv;  // kEpiCoarse: k x k, row stride ldt

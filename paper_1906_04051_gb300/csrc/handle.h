@@ -76,6 +76,7 @@ struct gmres_s {
   // T^-1 (q x q), a work vector, small scratch; aq columns in use
   DevMem aU, aAU, aT, aTinv, au, asmall;
   DevMem gbar;  // grid barrier words of the modified Gram-Schmidt kernel
+  DevMem lmat;  // strictly lower part of V^T V (one-reduction MGS)
   int aq = 0;
   Meta* hmeta = nullptr;  // pinned
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -114,7 +115,7 @@ inline int prec_of(int precision) {
 
 inline size_t basis_elem(int prec) { return prec == P_FP64 ? 8 : (prec == P_FP32 ? 4 : 2); }
 
-constexpr int kLdp = 80;  // >= kMaxK + 1, multiple of 16
+constexpr int kLdp = 144;  // >= 2 kMaxK + 1 (two dot sets), multiple of 16
 
 // Entries of the coarse correction s' (FP64, then its FP32 copy right after): one per
 // aggregate, or per column of the adaptive space (at most kMaxAdapt), plus one.
@@ -151,6 +152,8 @@ inline gmres_status ensure_workspace(gmres_s* h, int m, int prec) {
   CK(h, h->cpart.ensure(sizeof(double) * (size_t)(h->npieces + 1)));
   CK(h, h->sdefl.ensure(12 * (size_t)sdefl_len(h)));
   CK(h, h->gbar.ensure(2 * sizeof(unsigned)));
+  if (h->opts.ortho == GMRES_ORTHO_MGS_LOWSYNC)
+    CK(h, h->lmat.ensure(sizeof(double) * (size_t)kMaxK * kMaxK));
   if (h->opts.deflation_mode == GMRES_DEFL_ADAPTIVE && !h->aU.p) {
     const size_t col = sizeof(double) * (size_t)ldv;
     const size_t R = (size_t)h->opts.rmax;
@@ -200,6 +203,7 @@ inline Ctl make_ctl(gmres_s* h) {
   c.sdefl32 = reinterpret_cast<float*>(h->sdefl.as<double>() + sdefl_len(h));
   c.ldh = ldh;
   c.ldp = kLdp;
+  c.L = h->lmat.as<double>();
   return c;
 }
 

@@ -137,6 +137,9 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
       CK(h, phase(h, a, PH_SPMV, j, defl_cycle, x, b));
       if (mgs) {
         CK(h, phase(h, a, PH_MGS, j, defl_cycle, x, b));
+      } else if (a.ortho == GMRES_ORTHO_MGS_LOWSYNC) {  // pass 1 + solve, then pass 3
+        CK(h, phase(h, a, PH_DOT1, j, defl_cycle, x, b));
+        CK(h, phase(h, a, PH_UPD2NORM, j, defl_cycle, x, b));
       } else {
         CK(h, phase(h, a, PH_DOT1, j, defl_cycle, x, b));
         CK(h, phase(h, a, PH_UPD1DOT2, j, defl_cycle, x, b));
@@ -296,6 +299,7 @@ gmres_status run_noalloc(gmres_s* h, OpHost& o, const double* b, const double* x
   c.sdefl32 = reinterpret_cast<float*>(c.sdefl + sdefl_len(h));
   c.ldh = m;
   c.ldp = kLdp;
+  c.L = nullptr;
   a.V = base + oV;
   a.ldv = ldv;
   a.w = base + oW;
@@ -406,10 +410,12 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
   else gmres_opts_default(&opts);
   if (opts.precision < 0 || opts.precision > 2 || opts.deflation_mode < 0 ||
       opts.deflation_mode > 3 || opts.mu_mode < 0 || opts.mu_mode > 2 || opts.ortho < 0 ||
-      opts.ortho > 1)
+      opts.ortho > 2)
     return fail(nullptr, GMRES_ERR_INVALID_ARG, "invalid option value");
   if (opts.ortho == GMRES_ORTHO_MGS && opts.precision != GMRES_FP64)
     return fail(nullptr, GMRES_ERR_INVALID_ARG, "GMRES_ORTHO_MGS is FP64 only");
+  if (opts.ortho == GMRES_ORTHO_MGS_LOWSYNC && opts.precision == GMRES_BF16_BASIS)
+    return fail(nullptr, GMRES_ERR_INVALID_ARG, "GMRES_ORTHO_MGS_LOWSYNC: FP64 or FP32 inner");
   if (opts.deflation_mode == GMRES_DEFL_ADAPTIVE) {
     if (r > 0)
       return fail(nullptr, GMRES_ERR_INVALID_ARG,

@@ -21,6 +21,7 @@ from . import Solver, q1_assemble
 from . import _native as N
 
 PRECISIONS = {"fp64": N.FP64, "fp32": N.FP32_INNER, "bf16": N.BF16_BASIS}
+ORTHOS = {"cgs2": N.ORTHO_CGS2, "mgs": N.ORTHO_MGS, "lowsync": N.ORTHO_MGS_LOWSYNC}
 
 
 def load_workload(num: int, n: int | None = None):
@@ -41,6 +42,7 @@ def main(argv=None):
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--maxit", type=int, default=50000)
     ap.add_argument("--repeat", type=int, default=2)
+    ap.add_argument("--ortho", default="cgs2", choices=sorted(ORTHOS))
     args = ap.parse_args(argv)
     dev = torch.device("cuda")
     p = load_workload(args.workload, args.n)
@@ -48,7 +50,7 @@ def main(argv=None):
                                                     device=dev)
     rowptr, col, val, b = q1_assemble(p.n, t(p.kappa), p.beta, t(p.f))
     fixed = args.steps is not None
-    kw = dict(precision=PRECISIONS[args.precision], profile=True)
+    kw = dict(precision=PRECISIONS[args.precision], profile=True, ortho=ORTHOS[args.ortho])
     if fixed:
         kw.update(mu_mode=N.MU_USER, mu_user=50.0, fixed_iterations=True)
     s = Solver(rowptr, col, val, t(p.agg, torch.int32), p.r, **kw)
@@ -57,7 +59,8 @@ def main(argv=None):
         x, info = s.solve(b, m=p.m, tol=0.0 if fixed else (args.tol or p.tol),
                           maxit=args.steps if fixed else args.maxit)
     prof = s.profile()
-    out = {"workload": p.name, "precision": args.precision, "m": p.m, "info": info,
+    out = {"workload": p.name, "precision": args.precision, "ortho": args.ortho, "m": p.m,
+           "info": info,
            "us_per_step": 1e3 * info["ms_total"] / max(info["iters"], 1),
            "phases": {k: {"ms": round(v[0], 4), "launches": v[1],
                           "us_per_launch": round(1e3 * v[0] / v[1], 2) if v[1] else None}

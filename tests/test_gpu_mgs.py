@@ -1,7 +1,8 @@
 """GPU parity of the modified Gram-Schmidt orthogonalisation (the paper's, Sec. 3.2,
-Eq. 13), one cooperative kernel per Arnoldi step, against the oracle's MGS GMRES: the
-same steps and solutions in every deflation mode, bitwise repeatable runs, the same
-step counts as CGS2, and the option's limits."""
+Eq. 13) against the oracle's MGS GMRES, in both GPU forms: one cooperative kernel per
+Arnoldi step (column by column), and the one-reduction inverse compact WY form (the
+same projections: (I + L) h = V^T w).  The same steps and solutions in every deflation
+mode, bitwise repeatable runs, the same step counts as CGS2, and the options' limits."""
 import numpy as np
 import pytest
 
@@ -22,8 +23,9 @@ def G():
     return G
 
 
+@pytest.mark.parametrize("lowsync", [False, True])
 @pytest.mark.parametrize("mode", ["ebp", "proj", "none", "adaptive"])
-def test_mgs_fixed_iterations_match_oracle(G, orc, mode):
+def test_mgs_fixed_iterations_match_oracle(G, orc, mode, lowsync):
     p = W.convdiff(40, pe=25.0, sigma=0.5, seed=140, px=2, py=3)
     A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f)
     gm = {"ebp": G.DEFL_EBP, "proj": G.DEFL_PROJECTOR, "none": G.DEFL_NONE,
@@ -33,7 +35,8 @@ def test_mgs_fixed_iterations_match_oracle(G, orc, mode):
     defl = mode in ("ebp", "proj")
     s = gpu_solver_from_oracle(G, A, p.agg if defl else None, p.r if defl else 0,
                                deflation_mode=gm, mu_mode=1, mu_user=5.0,
-                               fixed_iterations=True, ortho=G.ORTHO_MGS)
+                               fixed_iterations=True,
+                               ortho=G.ORTHO_MGS_LOWSYNC if lowsync else G.ORTHO_MGS)
     xg, ig = s.solve(to_dev(b), m=15, tol=0.0, maxit=47)
     d = orc.Deflation(A, p.agg, p.r) if defl else None
     xo, io = orc.gmres(A, b, defl=d, defl_mode=om, m=15, tol=0.0, maxit=47, mu_mode=1,
@@ -44,10 +47,12 @@ def test_mgs_fixed_iterations_match_oracle(G, orc, mode):
     assert ig["rel_res_est"] == pytest.approx(io["rel_res_est"], rel=1e-6, abs=1e-13)
 
 
-def test_mgs_to_tolerance_matches_oracle_and_repeats(G, orc):
+@pytest.mark.parametrize("lowsync", [False, True])
+def test_mgs_to_tolerance_matches_oracle_and_repeats(G, orc, lowsync):
     p = W.workload1()
     A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f, p.u)
-    s = gpu_solver_from_oracle(G, A, p.agg, p.r, ortho=G.ORTHO_MGS)
+    s = gpu_solver_from_oracle(G, A, p.agg, p.r,
+                               ortho=G.ORTHO_MGS_LOWSYNC if lowsync else G.ORTHO_MGS)
     xg, ig = s.solve(to_dev(b), m=30, tol=1e-11, maxit=20000)
     xg2, ig2 = s.solve(to_dev(b), m=30, tol=1e-11, maxit=20000)
     d = orc.Deflation(A, p.agg, p.r)
@@ -64,13 +69,15 @@ def test_mgs_and_cgs2_take_the_same_steps(G, orc):
     p = W.workload2(256)
     A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f)
     its = {}
-    for name, o in (("cgs2", G.ORTHO_CGS2), ("mgs", G.ORTHO_MGS)):
+    for name, o in (("cgs2", G.ORTHO_CGS2), ("mgs", G.ORTHO_MGS),
+                    ("lowsync", G.ORTHO_MGS_LOWSYNC)):
         s = gpu_solver_from_oracle(G, A, p.agg, p.r, ortho=o)
         x, info = s.solve(to_dev(b), m=50, tol=1e-10, maxit=50000)
         assert info["status"] == 0 and info["rel_res_true"] <= 1e-10
         its[name] = (info["iters"], x.cpu().numpy())
-    assert abs(its["mgs"][0] - its["cgs2"][0]) <= max(3, 0.02 * its["cgs2"][0])
-    assert relerr(its["mgs"][1], its["cgs2"][1]) <= 1e-7
+    for name in ("mgs", "lowsync"):
+        assert abs(its[name][0] - its["cgs2"][0]) <= max(3, 0.02 * its["cgs2"][0])
+        assert relerr(its[name][1], its["cgs2"][1]) <= 1e-7
 
 
 def test_mgs_bratu_newton(G, orc):
@@ -89,6 +96,18 @@ def test_mgs_bratu_newton(G, orc):
     assert np.abs(ug.cpu().numpy() - u).max() <= 1e-8
 
 
+def test_lowsync_fp32_inner_refines_to_fp64(G, orc):
+    p = W.convdiff(96, pe=50.0, sigma=0.5, seed=150, px=4, py=4)
+    A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f)
+    s = gpu_solver_from_oracle(G, A, p.agg, p.r, precision=G.FP32_INNER,
+                               ortho=G.ORTHO_MGS_LOWSYNC)
+    xg, ig = s.solve(to_dev(b), m=40, tol=1e-10, maxit=50000)
+    assert ig["status"] == 0 and ig["rel_res_true"] <= 1e-10
+    d = orc.Deflation(A, p.agg, p.r)
+    xo, io = orc.gmres(A, b, defl=d, m=40, tol=1e-12, maxit=50000)
+    assert relerr(xg.cpu().numpy(), xo) <= 1e-7
+
+
 def test_mgs_limits(G, orc):
     p = W.workload1()
     A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f, p.u)
@@ -96,6 +115,9 @@ def test_mgs_limits(G, orc):
         gpu_solver_from_oracle(G, A, p.agg, p.r, ortho=G.ORTHO_MGS, precision=G.FP32_INNER)
     with pytest.raises(G.GmresError):
         gpu_solver_from_oracle(G, A, p.agg, p.r, ortho=7)
+    with pytest.raises(G.GmresError):  # not with a BF16 basis
+        gpu_solver_from_oracle(G, A, p.agg, p.r, ortho=G.ORTHO_MGS_LOWSYNC,
+                               precision=G.BF16_BASIS)
     s = gpu_solver_from_oracle(G, A, p.agg, p.r, ortho=G.ORTHO_MGS)
     with pytest.raises(G.GmresError):  # the batched solve orthogonalises by CGS2
         G.batch_solve([s], [to_dev(b)], m=30, tol=1e-8, maxit=1000)
