@@ -109,6 +109,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, pg=None, device="cpu") -> float:
+    """The slowest rank's value (MAX all-reduce over the process group; x itself when
+    there is no group)."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, steps: int, slowest_ms: float) -> float:
+    """Whole-job throughput: every rank's steps over the slowest rank's time (per s)."""
+    return world * steps / (slowest_ms / 1e3)
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -281,12 +297,8 @@ def main():
     if pg:
         pg.barrier()
     clocks = sampler.stop()
-    total_ms = sum(step_ms)
-    if pg:
-        tt = torch.tensor([total_ms], device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), pg, dev)
+    value = job_rate(world, args.steps, total_ms)
 
     # ---- per-kernel roofline of the dominant kernel: the one-reduction MGS pass 1 -------
     # (g = V^T w and V^T u_j in one multi-dot, 2k FMA per row; its phase also holds the
@@ -349,12 +361,8 @@ def main():
             s.close()
             if i >= args.warmup:
                 e_ms.append((time.perf_counter() - t0) * 1e3)
-        e_tot = sum(e_ms)
-        if pg:
-            tt = torch.tensor([e_tot], device=dev)
-            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-            e_tot = float(tt.item())
-        e2e = {"value": world * args.steps / (e_tot / 1e3), "unit": UNIT,
+        e_tot = max_over_ranks(sum(e_ms), pg, dev)
+        e2e = {"value": job_rate(world, args.steps, e_tot), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # ---- the paper's adaptive deflation (U grown from H_m eigenvectors after every
