@@ -1136,14 +1136,7 @@ struct Kern {
           const int rpt = (rows + kMgsThreads - 1) / kMgsThreads;
           void (*kern)(int, double*, long long, int, const double*, Ctl, int, unsigned*, int) =
               rpt <= 4 ? k_mgs<4> : rpt <= 8 ? k_mgs<8> : rpt <= 16 ? k_mgs<16> : k_mgs<0>;
-          const size_t smem = rpt <= 16 ? 0 : sizeof(double) * (size_t)rows;
-          static bool attr = false;
-          if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(k_mgs<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)(220 * 1024));
-            if (e != cudaSuccess) return e;
-            attr = true;
-          }
+          const size_t smem = rpt <= 16 ? 0 : sizeof(double) * (size_t)rows;  // see prepare()
           int kk = k, Nn = N, m = a.m;
           double* Vd = reinterpret_cast<double*>(Vm);
           long long ldv = a.ldv;
@@ -1243,6 +1236,10 @@ struct Kern {
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_pass1<TV, TACC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)mx);
+    if constexpr (sizeof(TV) == sizeof(double))  // w of the MGS kernel, large n
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mgs<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(220 * 1024));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_pass2<TV, TACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     if (e == cudaSuccess)
