@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kThreads)
 // dots of the newest basis column u_j with all columns from the tile already in shared
 // memory, so one reduction gives g = V^T w and the new row of L (v_j . v_c, c < j).
 template <typename TV, typename TACC, bool ICWY = false>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, ICWY ? (sizeof(TV) == 8 ? 3 : 2) : 1)
     k_pass1(int N, const TV* __restrict__ V, long long ldv, int k, int TR,
             const TACC* __restrict__ w, Ctl ctl, DotEpi epi) {
   constexpr int NR = ICWY ? 2 * kMaxK : kMaxK;
@@ -236,7 +236,10 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ uint64_t bars[kMaxStages];
   __shared__ double swarp[kSlices * kSliceCols];
   __shared__ double sred[NR];
-  __shared__ double tot[NR];
+  // the grid totals: ICWY keeps them in the ring's memory, free once the block's slices
+  // are reduced, so that its static shared memory still allows three blocks per SM
+  __shared__ double tot_s[ICWY ? 1 : kMaxK];
+  double* tot = ICWY ? reinterpret_cast<double*>(smraw) : tot_s;
   const size_t sb = ring_stage_bytes(k, TR, sizeof(TV), sizeof(TACC));
   const Ring<TV, TACC> R{smraw, bars, k, TR, ring_stages(sb), sb};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
