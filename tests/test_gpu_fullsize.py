@@ -1,0 +1,55 @@
+"""Parity at the full size of the headline system, in the configuration bench.py times:
+q1-n1024 (1,050,625 DOF, 9,422,857 nnz), 1024 aggregate deflation vectors, GMRES(50),
+the paper's MGS projections in their one-reduction form.  Two restart cycles in the
+fixed-iteration protocol against the oracle's MGS GMRES (every entry of x), and the solve
+to 1e-8 checked with the oracle's own SpMV (the true residual of the returned x)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from helpers import gpu_solver_from_oracle, relerr, to_dev
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1906_04051_gb300 as G
+    from paper_1906_04051_gb300 import build as B
+    B.build()
+    return G
+
+
+@pytest.fixture(scope="module")
+def system(orc):
+    p = W.workload2()
+    A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f)
+    return p, A, b
+
+
+def test_full_size_fixed_iterations_match_oracle_mgs(G, orc, system):
+    p, A, b = system
+    s = gpu_solver_from_oracle(G, A, p.agg, p.r, ortho=G.ORTHO_MGS_LOWSYNC, mu_mode=1,
+                               mu_user=14.0, fixed_iterations=True)
+    xg, ig = s.solve(to_dev(b), m=50, tol=0.0, maxit=100)
+    d = orc.Deflation(A, p.agg, p.r)
+    xo, io = orc.gmres(A, b, defl=d, m=50, tol=0.0, maxit=100, mu_mode=1, mu_user=14.0,
+                       fixed_iterations=True, ortho=orc.MGS)
+    assert ig["iters"] == io["iters"] == 100
+    assert relerr(xg.cpu().numpy(), xo) <= 1e-9
+    assert ig["rel_res_true"] == pytest.approx(io["rel_res_true"], rel=1e-7)
+
+
+def test_full_size_solve_true_residual(G, orc, system):
+    p, A, b = system
+    s = gpu_solver_from_oracle(G, A, p.agg, p.r, ortho=G.ORTHO_MGS_LOWSYNC)
+    xg, ig = s.solve(to_dev(b), m=50, tol=1e-8, maxit=20000)
+    assert ig["status"] == 0
+    x = xg.cpu().numpy()
+    r = b - A.matvec(x)  # the oracle's SpMV, in FP64 on the host
+    rel = np.linalg.norm(r) / np.linalg.norm(b)
+    assert rel <= 1e-8
+    assert rel == pytest.approx(ig["rel_res_true"], rel=1e-6)
