@@ -224,59 +224,32 @@ __global__ void __launch_bounds__(kThreads)
 
 // CGS2 pass 1 (pipelined): h_c = sigma_c (u_c . w), coef_c = sigma_c h_c.  The same
 // multi-dot c = M^T x serves the adaptive deflation space (columns of U or A U) with
-// another epilogue (DotEpi).  ICWY (one-reduction MGS): the same pass also forms the
-// dots of the newest basis column u_j with all columns from the tile already in shared
-// memory, so one reduction gives g = V^T w and the new row of L (v_j . v_c, c < j).
-template <typename TV, typename TACC, bool ICWY = false>
-__global__ void __launch_bounds__(kThreads, ICWY ? (sizeof(TV) == 8 ? 3 : 2) : 1)
+// another epilogue (DotEpi).
+template <typename TV, typename TACC>
+__global__ void __launch_bounds__(kThreads)
     k_pass1(int N, const TV* __restrict__ V, long long ldv, int k, int TR,
             const TACC* __restrict__ w, Ctl ctl, DotEpi epi) {
-  constexpr int NR = ICWY ? 2 * kMaxK : kMaxK;
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ uint64_t bars[kMaxStages];
   __shared__ double swarp[kSlices * kSliceCols];
-  __shared__ double sred[NR];
-  // the grid totals: ICWY keeps them in the ring's memory, free once the block's slices
-  // are reduced, so that its static shared memory still allows three blocks per SM
-  __shared__ double tot_s[ICWY ? 1 : kMaxK];
-  double* tot = ICWY ? reinterpret_cast<double*>(smraw) : tot_s;
+  __shared__ double sred[kMaxK];
+  __shared__ double tot[kMaxK];
   const size_t sb = ring_stage_bytes(k, TR, sizeof(TV), sizeof(TACC));
   const Ring<TV, TACC> R{smraw, bars, k, TR, ring_stages(sb), sb};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = slice_cols(k, warp, kSlices);
-  TACC acc[kSliceCols], acc2[ICWY ? kSliceCols : 1];
+  TACC acc[kSliceCols];
 #pragma unroll
   for (int i = 0; i < kSliceCols; ++i) acc[i] = 0;
-#pragma unroll
-  for (int i = 0; i < (ICWY ? kSliceCols : 1); ++i) acc2[i] = 0;
   // w is the predecessor's (the SpMV's) output: its slices are copied after the wait
   const bool ok = ring_run(R, N, V, ldv, w, ctl, false, [] {}, [&](int st, long long) {
-#define GG_P1(NW)                                                                        \
-  {                                                                                      \
-    tile_dot<NW, TV, TACC>(acc, R.vt(st), R.wt(st), TR, warp, lane);                     \
-    if constexpr (ICWY)                                                                  \
-      tile_dot<NW, TV, TACC>(acc2, R.vt(st), (const TACC*)(R.vt(st) + (size_t)(k - 1) * TR), \
-                             TR, warp, lane);                                            \
-  }
+#define GG_P1(NW) tile_dot<NW, TV, TACC>(acc, R.vt(st), R.wt(st), TR, warp, lane)
     GG_SLICE_SWITCH(nw, GG_P1)
 #undef GG_P1
   }, epi.skip_slot);
   if (!ok) return;
   reduce_slices(acc, nw, k, kSlices, reinterpret_cast<double*>(smraw), swarp, sred);
-  if constexpr (ICWY) {
-    reduce_slices(acc2, nw, k, kSlices, reinterpret_cast<double*>(smraw), swarp, sred + k);
-    if (!last_block_reduce(sred, 2 * k, ctl.part, ctl.part2, ctl.ldp, ctl.ticket, tot)) return;
-    // g_c = v_c . w into h (the solve kernel turns it into the MGS coefficients) and the
-    // new row of L: v_j . v_c = sigma_j sigma_c (u_j . u_c), c < j
-    const double sj = ctl.sigma[k - 1];
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-      ctl.h[c] = ctl.sigma[c] * tot[c];
-      if (c < k - 1) ctl.L[(size_t)(k - 1) * kMaxK + c] = sj * ctl.sigma[c] * tot[k + c];
-    }
-    return;
-  } else {
-    if (!last_block_reduce(sred, k, ctl.part, ctl.part2, ctl.ldp, ctl.ticket, tot)) return;
-  }
+  if (!last_block_reduce(sred, k, ctl.part, ctl.part2, ctl.ldp, ctl.ticket, tot)) return;
   if (epi.mode == kEpiCoarse) {  // s = |mu| T^-1 c - c (adaptive deflation, Eq. 17)
     const double mu = fabs(ctl.scal[S_MU]);
     for (int t = threadIdx.x; t < k; t += blockDim.x) {
@@ -296,6 +269,55 @@ __global__ void __launch_bounds__(kThreads, ICWY ? (sizeof(TV) == 8 ? 3 : 2) : 1
     const double hc = ctl.sigma[c] * tot[c];
     ctl.h[c] = hc;
     ctl.coef[c] = ctl.sigma[c] * hc;
+  }
+}
+
+// One-reduction MGS, pass 1: the multi-dot of pass 1 that also forms the dots of the
+// newest basis column u_j with all columns from the tile already in shared memory, so
+// one reduction gives g = V^T w and the new row of L (v_j . v_c, c < j).  (A separate
+// kernel from k_pass1 so that CGS2's pass keeps its own register allocation.)
+template <typename TV, typename TACC>
+__global__ void __launch_bounds__(kThreads, sizeof(TV) == 8 ? 3 : 2)
+    k_pass1_icwy(int N, const TV* __restrict__ V, long long ldv, int k, int TR,
+                 const TACC* __restrict__ w, Ctl ctl, DotEpi epi) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ uint64_t bars[kMaxStages];
+  __shared__ double swarp[kSlices * kSliceCols];
+  __shared__ double sred[2 * kMaxK];  // the block's sums: g (k), then the L row (k)
+  // the grid totals live in the ring's memory, free once the block's slices are reduced,
+  // so that the static shared memory still allows three blocks per SM
+  double* tot = reinterpret_cast<double*>(smraw);
+  const size_t sb = ring_stage_bytes(k, TR, sizeof(TV), sizeof(TACC));
+  const Ring<TV, TACC> R{smraw, bars, k, TR, ring_stages(sb), sb};
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = slice_cols(k, warp, kSlices);
+  TACC acc[kSliceCols], acc2[kSliceCols];
+#pragma unroll
+  for (int i = 0; i < kSliceCols; ++i) acc[i] = 0;
+#pragma unroll
+  for (int i = 0; i < kSliceCols; ++i) acc2[i] = 0;
+  // w is the predecessor's (the SpMV's) output: its slices are copied after the wait;
+  // the second multi-dot takes the tile's newest column u_j in the place of w
+  const bool ok = ring_run(R, N, V, ldv, w, ctl, false, [] {}, [&](int st, long long) {
+#define GG_P1(NW)                                                                        \
+  {                                                                                      \
+    tile_dot<NW, TV, TACC>(acc, R.vt(st), R.wt(st), TR, warp, lane);                     \
+    tile_dot<NW, TV, TACC>(acc2, R.vt(st), (const TACC*)(R.vt(st) + (size_t)(k - 1) * TR), \
+                           TR, warp, lane);                                              \
+  }
+    GG_SLICE_SWITCH(nw, GG_P1)
+#undef GG_P1
+  }, epi.skip_slot);
+  if (!ok) return;
+  reduce_slices(acc, nw, k, kSlices, reinterpret_cast<double*>(smraw), swarp, sred);
+  reduce_slices(acc2, nw, k, kSlices, reinterpret_cast<double*>(smraw), swarp, sred + k);
+  if (!last_block_reduce(sred, 2 * k, ctl.part, ctl.part2, ctl.ldp, ctl.ticket, tot)) return;
+  // g_c = v_c . w into h (the solve kernel turns it into the MGS coefficients) and the
+  // new row of L: v_j . v_c = sigma_j sigma_c (u_j . u_c), c < j
+  const double sj = ctl.sigma[k - 1];
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    ctl.h[c] = ctl.sigma[c] * tot[c];
+    if (c < k - 1) ctl.L[(size_t)(k - 1) * kMaxK + c] = sj * ctl.sigma[c] * tot[k + c];
   }
 }
 
@@ -983,7 +1005,7 @@ struct Kern {
         g.tr[k] = tile_rows(k);
         g.p1[k] = resident_grid(k_pass1<TV, TACC>, kThreads, ring_smem(k), sms);
         if constexpr (std::is_same<TV, TACC>::value)
-          g.p1i[k] = resident_grid(k_pass1<TV, TACC, true>, kThreads, ring_smem(k), sms);
+          g.p1i[k] = resident_grid(k_pass1_icwy<TV, TACC>, kThreads, ring_smem(k), sms);
         g.p2[k] = resident_grid(k_pass2<TV, TACC>, kThreads, ring_smem(k), sms);
         g.p3[k] = resident_grid(k_pass3<TV, TACC>, kThreads, ring_smem(k), sms);
       }
@@ -1102,7 +1124,7 @@ struct Kern {
         const int tr = g.tr[k];
         if (a.ortho == GMRES_ORTHO_MGS_LOWSYNC) {  // one reduction, then the triangular solve
           if constexpr (std::is_same<TV, TACC>::value) {
-            launch_k(a.pdl != 0, k_pass1<TV, TACC, true>, grid_for((N + tr - 1) / tr, 1, g.p1i[k]),
+            launch_k(a.pdl != 0, k_pass1_icwy<TV, TACC>, grid_for((N + tr - 1) / tr, 1, g.p1i[k]),
                      kThreads, ring_smem(k), st, N, V, a.ldv, k, tr, (const TACC*)w, a.ctl,
                      DotEpi{kEpiIcwy, nullptr, 0, nullptr, F_CYCLE_DONE});
             launch_k(a.pdl != 0, k_icwy_solve, 1, 256, 0, st, a.ctl, k);
@@ -1237,7 +1259,7 @@ struct Kern {
       e = cudaFuncSetAttribute(k_pass1<TV, TACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     if constexpr (std::is_same<TV, TACC>::value)
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_pass1<TV, TACC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_pass1_icwy<TV, TACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)mx);
     if constexpr (sizeof(TV) == sizeof(double))  // w of the MGS kernel, large n
       if (e == cudaSuccess)
