@@ -321,7 +321,7 @@ def main():
     # (the bytes grow as 8 k N + 8 N), averaged over the solve's launches
     traffic = statistics.mean(PASS1I_DRAM_BYTES_K26 * (8.0 * k + 8.0) / (8.0 * 26 + 8.0)
                               for k in ks)
-    roofline = {"kernel": "k_pass1 (one-reduction MGS: V^T w and V^T u_j)", "bound": "alu",
+    roofline = {"kernel": "k_pass1_icwy (one-reduction MGS: V^T w and V^T u_j)", "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": traffic, "traffic_unit": "bytes per launch",
