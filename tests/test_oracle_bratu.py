@@ -141,3 +141,65 @@ def test_discrete_solution_symmetries():
     # with lambda = 0 the problem is linear and u = 0 is its solution
     A, b = orc.q2_bratu_assemble(n, 0.0)
     assert np.abs(b).max() == 0.0
+
+
+def _bratu_2d_q2(n, lam, tol=1e-13):
+    """Independent 2-D reference: the Bratu problem on the unit square with 9-node
+    biquadratic elements, u = 0 on the boundary, Newton with direct solves (numpy / scipy,
+    element integrals by 3 x 3 Gauss points).  With the Neumann z-faces the 3-D discrete
+    solution is this one on every z-layer."""
+    import scipy.sparse as sp
+    M = 2 * n + 1
+    h = 1.0 / n
+    gs = np.sqrt(0.6)
+    xg = np.array([0.5 * (1 - gs), 0.5, 0.5 * (1 + gs)])
+    wg = np.array([5.0, 8.0, 5.0]) / 18.0
+    P = np.stack([(1 - xg) * (1 - 2 * xg), 4 * xg * (1 - xg), xg * (2 * xg - 1)], axis=1)
+    D = np.stack([4 * xg - 3, 4 - 8 * xg, 4 * xg - 1], axis=1) / h
+    # phi[g, l] with g = (gx, gy), l = a + 3 b
+    phi = np.einsum("xa,yb->xyba", P, P).reshape(9, 9)
+    dx = np.einsum("xa,yb->xyba", D, P).reshape(9, 9)
+    dy = np.einsum("xa,yb->xyba", P, D).reshape(9, 9)
+    w = (np.outer(wg, wg) * h * h).reshape(9)  # w[g], g = gx * 3 + gy
+    K = np.einsum("g,gl,gm->lm", w, dx, dx) + np.einsum("g,gl,gm->lm", w, dy, dy)
+    N2 = M * M
+    bnd = np.zeros(N2, bool)
+    for j in range(M):
+        for i in range(M):
+            bnd[j * M + i] = i in (0, M - 1) or j in (0, M - 1)
+    u = np.zeros(N2)
+    for _ in range(30):
+        rows, cols, vals = [], [], []
+        R = np.zeros(N2)
+        for ey in range(n):
+            for ex in range(n):
+                gid = np.array([(2 * ey + b) * M + 2 * ex + a for b in range(3) for a in range(3)])
+                ue = u[gid]
+                eg = np.exp(phi @ ue)
+                Re = -K @ ue + lam * np.einsum("g,g,gl->l", w, eg, phi)
+                Je = -K + lam * np.einsum("g,g,gl,gm->lm", w, eg, phi, phi)
+                R[gid] += Re
+                rows.append(np.repeat(gid, 9))
+                cols.append(np.tile(gid, 9))
+                vals.append(Je.reshape(-1))
+        J = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                          shape=(N2, N2)).tolil()
+        for r in np.nonzero(bnd)[0]:
+            J.rows[r] = [r]
+            J.data[r] = [1.0]
+        R[bnd] = 0.0
+        du = spla.spsolve(J.tocsc(), -R)
+        u += du
+        if np.abs(du).max() <= tol:
+            break
+    return u.reshape(M, M)
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_3d_solution_equals_independent_2d_reference(n):
+    u3, _ = _newton(n, 6.8)
+    M = 2 * n + 1
+    U = u3.reshape(M, M, M)  # [K, J, I]
+    u2 = _bratu_2d_q2(n, 6.8)  # [J, I]
+    for k in range(M):
+        assert np.abs(U[k] - u2).max() <= 1e-10
