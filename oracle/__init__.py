@@ -71,6 +71,8 @@ class Opts(C.Structure):
         ("rmax", C.c_int32),
         ("ninv", C.c_int32),
         ("u_out", C.c_void_p),
+        ("w_dense", C.c_void_p),
+        ("w_cols", C.c_int32),
     ]
 
 
@@ -298,26 +300,35 @@ class Deflation:
 def gmres(A: CSR, b, x0=None, *, m=30, tol=1e-8, maxit=10000, defl: Deflation | None = None,
           defl_mode=DEFL_EBP, mu_mode=MU_RITZ_FIRST_CYCLE, mu_user=0.0, ortho=CGS2,
           fixed_iterations=False, r0_norm_ref=0.0, history=False, rmax=20, ninv=20,
-          return_u=False):
+          return_u=False, w_dense=None):
     """Deflated restarted GMRES(m); returns (x, info dict[, history (steps x 2)][, U]).
 
     defl_mode=DEFL_ADAPTIVE needs no Deflation object: U starts empty and grows after
     every cycle (Sec. 3.3, Eq. 19), at most rmax columns; return_u appends the final U
-    (N x q)."""
+    (N x q).  w_dense (N x r): the deflation space as dense columns instead of aggregates
+    (U = their orthonormalisation, the EBP preconditioner); a ValueError if a column lies
+    in the span of the previous ones."""
     b = _f64(b)
     x0a = None if x0 is None else _f64(x0)
     x = np.empty(A.n)
     adaptive = defl_mode == DEFL_ADAPTIVE
-    uo = np.zeros(A.n * rmax) if (adaptive and return_u) else None
+    wd = None
+    if w_dense is not None:
+        wd = np.asfortranarray(np.asarray(w_dense, dtype=np.float64).reshape(A.n, -1))
+    given = wd is not None and not adaptive
+    uo = np.zeros(A.n * (wd.shape[1] if given else rmax)) if ((adaptive or given) and return_u) else None
     o = Opts(m, tol, maxit, ortho,
-             defl_mode if (defl is not None or adaptive) else DEFL_NONE, mu_mode,
+             defl_mode if (defl is not None or adaptive or given) else DEFL_NONE, mu_mode,
              mu_user, 1 if fixed_iterations else 0, r0_norm_ref, rmax, ninv,
-             None if uo is None else uo.ctypes.data)
+             None if uo is None else uo.ctypes.data,
+             None if wd is None else wd.ctypes.data, 0 if wd is None else wd.shape[1])
     info = Info()
     hist = np.zeros(2 * maxit) if history else None
-    lib().orc_gmres(A.n, _p(A.rowptr), _p(A.col), _p(A.val),
-                    None if defl is None else defl._h, _p(b), _p(x0a), C.byref(o), _p(x),
-                    C.byref(info), _p(hist))
+    rc = lib().orc_gmres(A.n, _p(A.rowptr), _p(A.col), _p(A.val),
+                         None if defl is None else defl._h, _p(b), _p(x0a), C.byref(o), _p(x),
+                         C.byref(info), _p(hist))
+    if given and rc == -1:
+        raise ValueError("w_dense: a column lies in the span of the previous ones")
     out = (x, info.as_dict())
     if history:
         hs = hist.reshape(-1, 2)[: info.iters]

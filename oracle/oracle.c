@@ -977,6 +977,49 @@ static int adapt_update(adapt_space* s, int32_t N, const int32_t* rowptr, const 
   return err;
 }
 
+/* U from the caller's columns W (N x nw): each column orthonormalised against the
+ * previous ones by two classical Gram-Schmidt passes and appended with A u and T's new
+ * row and column; then the LU of T.  Returns 1 if a column lies in the span of the
+ * previous ones (||u|| <= 1e-10 ||w_c|| after the passes) or T is singular. */
+static int adapt_fill(adapt_space* s, int32_t N, const int32_t* rowptr, const int32_t* col,
+                      const double* val, const double* W, int32_t nw) {
+  const int32_t R = s->rmax;
+  double* u = (double*)malloc(sizeof(double) * (size_t)N);
+  double* c = (double*)malloc(sizeof(double) * (size_t)(R + 1));
+  int err = 0;
+  for (int32_t cc = 0; cc < nw && !err; ++cc) {
+    memcpy(u, W + (size_t)cc * N, sizeof(double) * (size_t)N);
+    const double n0 = nrm2(u, N);
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int32_t t = 0; t < s->q; ++t) c[t] = dot(s->U + (size_t)t * N, u, N);
+      for (int32_t t = 0; t < s->q; ++t)
+        for (int32_t i = 0; i < N; ++i) u[i] -= c[t] * s->U[(size_t)t * N + i];
+    }
+    const double n1 = nrm2(u, N);
+    if (!(n1 > 1e-10 * n0)) {
+      err = 1;
+      break;
+    }
+    const int32_t q = s->q;
+    for (int32_t i = 0; i < N; ++i) s->U[(size_t)q * N + i] = u[i] / n1;
+    orc_spmv(N, rowptr, col, val, s->U + (size_t)q * N, s->AU + (size_t)q * N);
+    for (int32_t i = 0; i < q; ++i) {
+      s->T[(size_t)i * R + q] = dot(s->U + (size_t)i * N, s->AU + (size_t)q * N, N);
+      s->T[(size_t)q * R + i] = dot(s->U + (size_t)q * N, s->AU + (size_t)i * N, N);
+    }
+    s->T[(size_t)q * R + q] = dot(s->U + (size_t)q * N, s->AU + (size_t)q * N, N);
+    s->q = q + 1;
+  }
+  if (!err) {
+    for (int32_t i = 0; i < s->q; ++i)
+      for (int32_t j = 0; j < s->q; ++j) s->lu[(size_t)i * s->q + j] = s->T[(size_t)i * R + j];
+    err = orc_lu_factor(s->q, s->lu, s->piv) != 0;
+  }
+  free(u);
+  free(c);
+  return err;
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* GMRES(m) (Sec. 3.2, Eqs. 10-15) with right deflation preconditioning (Eq. 16)         */
 /* ------------------------------------------------------------------------------------ */
@@ -1053,13 +1096,15 @@ int orc_gmres(int32_t N, const int32_t* rowptr, const int32_t* col, const double
               const orc_defl* d, const double* b, const double* x0, const orc_opts* o,
               double* x, orc_info* info, double* hist) {
   const int32_t m = o->m;
-  const int adaptive = o->defl_mode == ORC_DEFL_ADAPTIVE;
+  const int growing = o->defl_mode == ORC_DEFL_ADAPTIVE;  /* U grows after every cycle */
+  const int given = !growing && o->w_dense && o->w_cols > 0; /* U from the caller's W */
+  const int adaptive = growing || given;                    /* a dense U, A U, T */
   const int mode = adaptive ? ORC_DEFL_ADAPTIVE : (d ? o->defl_mode : ORC_DEFL_NONE);
   memset(info, 0, sizeof(*info));
   adapt_space as = {0};
   if (adaptive) {
     as.N = N;
-    as.rmax = o->rmax > 0 ? o->rmax : 20;
+    as.rmax = given ? o->w_cols : (o->rmax > 0 ? o->rmax : 20);
     as.U = (double*)malloc(sizeof(double) * (size_t)N * as.rmax);
     as.AU = (double*)malloc(sizeof(double) * (size_t)N * as.rmax);
     as.T = (double*)calloc((size_t)as.rmax * as.rmax, sizeof(double));
@@ -1079,6 +1124,28 @@ int orc_gmres(int32_t N, const int32_t* rowptr, const int32_t* col, const double
   double* r = (double*)malloc(sizeof(double) * (size_t)N);
 
   for (int32_t i = 0; i < N; ++i) x[i] = x0 ? x0[i] : 0.0;
+
+  if (given && adapt_fill(&as, N, rowptr, col, val, o->w_dense, o->w_cols)) {
+    /* a column of W lies in the span of the previous ones (or U^T A U is singular) */
+    free(as.U);
+    free(as.AU);
+    free(as.T);
+    free(as.lu);
+    free(as.piv);
+    free(V);
+    free(H);
+    free(Hr);
+    free(cs);
+    free(sn);
+    free(g);
+    free(y);
+    free(hcol);
+    free(w);
+    free(tmp);
+    free(r);
+    info->status = -1;
+    return -1;
+  }
 
   /* mu (Sec. 3.3): the largest eigenvalue, estimated from the Ritz values of H_m of the
    * first cycle, which runs with M = I; or given; or bounded by the infinity norm. */
@@ -1246,7 +1313,7 @@ int orc_gmres(int32_t N, const int32_t* rowptr, const int32_t* col, const double
       defl_on = 1;
     }
     /* grow U from this cycle's Hessenberg matrix and basis (Sec. 3.3, Eq. 19) */
-    if (adaptive && adapt_update(&as, N, rowptr, col, val, V, Hr, m, k, o->ninv > 0 ? o->ninv : 20)) {
+    if (growing && adapt_update(&as, N, rowptr, col, val, V, Hr, m, k, o->ninv > 0 ? o->ninv : 20)) {
       status = -4;
       break;
     }

@@ -97,6 +97,12 @@ typedef struct {
   int32_t rmax;             /* upper limit on the columns of U (paper: 20) */
   int32_t ninv;             /* inverse power iterations per restart */
   double* u_out;            /* N x rmax column-major (may be NULL): the final U */
+  /* a deflation space given as dense columns instead of aggregates (Eqs. 16-18 with this
+   * U): W is N x w_cols column-major, U its orthonormalisation (two classical
+   * Gram-Schmidt passes per column, in order), fixed for the whole solve; the
+   * preconditioner and mu are those of ORC_DEFL_EBP.  w_cols = 0: none. */
+  const double* w_dense;
+  int32_t w_cols;
 } orc_opts;
 
 typedef struct {

@@ -239,3 +239,54 @@ def test_maxit_reports_not_converged(orc):
     p, A, b = _system(orc, 16)
     x, info = orc.gmres(A, b, m=5, tol=1e-14, maxit=12)
     assert info["status"] == 1 and info["iters"] == 12
+
+
+# ---- a deflation space given as dense columns (Eqs. 16-18 with U = orth(W)) -----------
+def _dense_problem(orc):
+    p = W.workload1()
+    A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f, p.u)
+    return p, A, b
+
+
+def test_dense_w_of_aggregate_indicators_equals_ebp(orc):
+    p, A, b = _dense_problem(orc)
+    Wd = np.zeros((A.n, p.r))
+    Wd[np.arange(A.n), p.agg] = 1.0  # indicator columns (unnormalised: the oracle orthonormalises)
+    d = orc.Deflation(A, p.agg, p.r)
+    x1, i1 = orc.gmres(A, b, m=30, tol=1e-10, maxit=20000, defl=d)
+    x2, i2 = orc.gmres(A, b, m=30, tol=1e-10, maxit=20000, w_dense=Wd)
+    assert i1["status"] == 0 and i2["status"] == 0
+    assert i1["iters"] == i2["iters"]
+    assert np.linalg.norm(x1 - x2) <= 1e-10 * np.linalg.norm(x1)
+    assert i2["mu"] == pytest.approx(i1["mu"], rel=1e-12)
+
+
+def test_dense_w_result_depends_only_on_its_span(orc):
+    # W and W R (R invertible) span the same space: the same M^-1, the same iterates
+    p, A, b = _dense_problem(orc)
+    rng = np.random.default_rng(12)
+    Wd = rng.standard_normal((A.n, 6))
+    R = rng.standard_normal((6, 6)) + 3 * np.eye(6)
+    kw = dict(m=20, tol=0.0, maxit=60, fixed_iterations=True, mu_mode=orc.MU_USER, mu_user=4.0)
+    x1, i1 = orc.gmres(A, b, w_dense=Wd, **kw)
+    x2, i2 = orc.gmres(A, b, w_dense=Wd @ R, **kw)
+    assert np.linalg.norm(x1 - x2) <= 1e-9 * np.linalg.norm(x1)
+    xd = spla.spsolve(A.to_scipy().tocsc(), b)
+    x3, i3 = orc.gmres(A, b, m=30, tol=1e-11, maxit=20000, w_dense=Wd)
+    assert i3["status"] == 0 and np.linalg.norm(x3 - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+def test_dense_w_identity_and_dependent_columns(orc):
+    p, A, b = _dense_problem(orc)
+    rng = np.random.default_rng(13)
+    Wd = rng.standard_normal((A.n, 4))
+    x, info, U = orc.gmres(A, b, m=20, tol=1e-9, maxit=5000, w_dense=Wd, return_u=True)
+    assert U.shape == (A.n, 4) and np.abs(U.T @ U - np.eye(4)).max() <= 1e-12
+    # U^T (A M^-1) U = |mu| I with M^-1 = I + U (|mu| T^-1 - I) U^T, T = U^T A U (Eq. 17)
+    Ad = A.to_scipy().toarray()
+    T = U.T @ Ad @ U
+    mu = abs(info["mu"])
+    Minv = np.eye(A.n) + U @ (mu * np.linalg.inv(T) - np.eye(4)) @ U.T
+    assert np.abs(U.T @ Ad @ Minv @ U - mu * np.eye(4)).max() <= 1e-9 * mu
+    with pytest.raises(ValueError):
+        orc.gmres(A, b, w_dense=np.column_stack([Wd, Wd[:, 0] + 2 * Wd[:, 1]]))
