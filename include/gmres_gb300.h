@@ -60,14 +60,22 @@ typedef struct {
   const double* val;     /* nnz entries */
 } gmres_csr;
 
-/* Deflation space W (Eq. 17): r indicator columns of disjoint aggregates.
- * agg (device, n entries): aggregate of each row in [0, r), or -1 for none.  The
- * library forms U = W diag(1/sqrt|agg_p|), which has orthonormal columns, and
- * T = U^T A U.  r = 0 (agg may be NULL) disables deflation.  1 <= r <= 6144
- * otherwise; every aggregate must be non-empty. */
+/* Deflation space W (Eq. 17), in one of two forms.
+ * Aggregates: agg (device, n entries) gives the aggregate of each row in [0, r), or -1
+ * for none; W holds their r indicator columns and the library forms
+ * U = W diag(1/sqrt|agg_p|), which has orthonormal columns, and T = U^T A U.
+ * 1 <= r <= 6144; every aggregate must be non-empty.
+ * Dense columns: dense (device, n x r column-major, column c at dense + c n), agg NULL,
+ * 1 <= r <= 32 (approximate eigenvectors, say): the library keeps a copy and, at the
+ * first solve, orthonormalises the columns in order into U (two classical Gram-Schmidt
+ * passes each; GMRES_ERR_INVALID_ARG if a column lies in the span of the previous ones)
+ * and forms A U, T = U^T A U and T^-1.  GMRES_DEFL_EBP, FP64, forward single-system
+ * solves.
+ * r = 0 (agg and dense may be NULL) disables deflation. */
 typedef struct {
   int32_t r;
   const int32_t* agg;
+  const double* dense;
 } gmres_defl;
 
 typedef enum {
@@ -248,13 +256,14 @@ typedef struct gmres_layout {
 } gmres_layout;
 gmres_status gmres_layout_query(gmres_t h, gmres_layout* out);
 
-/* The adaptive deflation space left by the last solve of a GMRES_DEFL_ADAPTIVE handle
- * (Sec. 3.3, Eqs. 17-19): U (orthonormal, n x q) and T = U^T A U (q x q).  q (host,
+/* The dense deflation space of a handle: the adaptive one left by the last solve of a
+ * GMRES_DEFL_ADAPTIVE handle (Sec. 3.3, Eqs. 17-19), or the orthonormalised dense W given
+ * at create (after the first solve): U (orthonormal, n x q) and T = U^T A U (q x q).  q (host,
  * required) receives the column count, at most opts.rmax.  U (device, may be NULL)
  * receives column c at U + c * ldu (ldu >= n); T (device, may be NULL) receives
  * T[i * q + j] = u_i^T A u_j.  Call with both NULL to learn q first.  Synchronises the
  * handle's stream.  The space belongs to the handle and is rebuilt (from empty) by the
- * next solve.  Errors: INVALID_ARG (other deflation mode, null q, ldu < n), CUDA. */
+ * next solve (adaptive).  Errors: INVALID_ARG (no dense space, null q, ldu < n), CUDA. */
 gmres_status gmres_adaptive_space(gmres_t h, int32_t* q, double* U, int64_t ldu, double* T);
 
 gmres_status gmres_set_stream(gmres_t h, void* stream);

@@ -39,7 +39,7 @@ class gmres_csr(C.Structure):
 
 
 class gmres_defl(C.Structure):
-    _fields_ = [("r", C.c_int32), ("agg", C.c_void_p)]
+    _fields_ = [("r", C.c_int32), ("agg", C.c_void_p), ("dense", C.c_void_p)]
 
 
 class gmres_opts(C.Structure):

@@ -44,7 +44,8 @@ class Solver:
                  agg: torch.Tensor | None = None, r: int = 0, *, precision=N.FP64,
                  deflation_mode=N.DEFL_EBP, mu_mode=N.MU_RITZ_FIRST_CYCLE, mu_user=0.0,
                  fixed_iterations=False, r0_norm_ref=0.0, timeout_ms=0, inner_tol=0.0,
-                 profile=False, rmax=20, ninv=20, ortho=N.ORTHO_CGS2, stream=None):
+                 profile=False, rmax=20, ninv=20, ortho=N.ORTHO_CGS2, w_dense=None,
+                 stream=None):
         L = N.load()
         n = rowptr.numel() - 1
         _dev(rowptr, torch.int32, "rowptr")
@@ -57,7 +58,15 @@ class Solver:
         defl = None
         if agg is not None and r > 0:
             _dev(agg, torch.int32, "agg", n)
-            defl = N.gmres_defl(int(r), agg.data_ptr())
+            defl = N.gmres_defl(int(r), agg.data_ptr(), None)
+        if w_dense is not None:  # W as dense columns (n x r, any strides): a column-major copy
+            if agg is not None and r > 0:
+                raise ValueError("give W as aggregates or as dense columns, not both")
+            if w_dense.dim() != 2 or w_dense.shape[0] != n:
+                raise ValueError(f"w_dense must be n x r, n = {n}")
+            self._wd = w_dense.to(torch.float64).t().contiguous()  # row c = column c of W
+            _dev(self._wd, torch.float64, "w_dense")
+            defl = N.gmres_defl(int(w_dense.shape[1]), None, self._wd.data_ptr())
         opts = N.gmres_opts()
         L.gmres_opts_default(C.byref(opts))
         opts.precision = int(precision)
@@ -78,7 +87,7 @@ class Solver:
                             C.byref(opts), _stream_ptr(stream))
         _check(st, None)
         self._h = h
-        self.r = int(r) if defl else 0
+        self.r = int(r) if (defl and w_dense is None) else 0
         self.precision = int(precision)
 
     @property
@@ -268,7 +277,7 @@ def bratu_newton(n: int, lam: float, u: torch.Tensor | None = None, *, m=50, tol
     defl = None
     if agg is not None and r > 0:
         _dev(agg, torch.int32, "agg", NN)
-        defl = N.gmres_defl(int(r), agg.data_ptr())
+        defl = N.gmres_defl(int(r), agg.data_ptr(), None)
     info = N.q2_newton_info()
     st = L.q2_bratu_newton(int(n), float(lam), C.byref(opts), C.byref(defl) if defl else None,
                            int(m), float(tol), int(maxit), float(newton_tol), int(max_newton),

@@ -611,6 +611,67 @@ __global__ void k_adapt_tinv(const double* __restrict__ T, int ldt, int q,
 
 }  // namespace
 
+// The dense space from the caller's columns W (the same steps as an update of the
+// adaptive space, without the eigenvector and the drop): each column orthonormalised
+// against the previous ones by two multi-dot passes, appended with A u and T's new row
+// and column; then T^-1.
+gmres_status dense_build(gmres_s* h, CycleArgs& a) {
+  cudaStream_t st = h->stream;
+  const int N = h->n;
+  const long long ld = h->ldv;
+  const int R = h->opts.rmax;  // = the number of columns of W
+  double* U = h->aU.as<double>();
+  double* AU = h->aAU.as<double>();
+  double* T = h->aT.as<double>();
+  double* Tinv = h->aTinv.as<double>();
+  double* u = h->au.as<double>();
+  double* sm = h->asmall.as<double>();
+  double* c1 = sm + 2 * kMaxK;
+  double* c2 = c1 + kMaxAdapt + 1;
+  double* nrm = c2 + kMaxAdapt + 1;
+  double* qc = nrm + 2;
+  int* iv = reinterpret_cast<int*>(qc + kMaxAdapt * kMaxAdapt);
+  const int tiles = (N + kThreads - 1) / kThreads;
+  const int grid = grid_for(tiles, 1, 8 * h->sms);
+  const Ctl& ctl = a.ctl;
+  const double* W = h->wdense.as<double>();
+  int q = 0;
+  for (int c = 0; c < h->dense_r; ++c) {
+    CK(h, cudaMemcpyAsync(u, W + (size_t)c * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    k_adapt_norm<<<grid, kThreads, 0, st>>>(N, u, ctl, nrm);
+    for (int pass = 0; pass < 2 && q > 0; ++pass) {
+      CK(h, launch_udots(a, U, ld, q, u, DotEpi{kEpiRaw, nullptr, 0, c1, -1}, st));
+      k_adapt_axpy<<<grid, kThreads, 0, st>>>(N, u, U, ld, q, c1);
+    }
+    k_adapt_norm<<<grid, kThreads, 0, st>>>(N, u, ctl, nrm + 1);
+    CK(h, cudaGetLastError());
+    double hn[2];
+    CK(h, cudaMemcpyAsync(hn, nrm, sizeof(hn), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    if (!(hn[1] > 1e-10 * hn[0]))
+      return fail(h, GMRES_ERR_INVALID_ARG,
+                  "dense W: column " + std::to_string(c) + " lies in the span of the previous ones");
+    k_adapt_scale<<<grid, kThreads, 0, st>>>(N, u, nrm + 1, U + (size_t)q * ld);
+    k_adapt_spmv<<<grid_for((long long)N * kVecLanes / kVecRows, kThreads, 64 * h->sms), kThreads,
+                   0, st>>>(N, a.op.rowptr, a.op.col, a.op.val, U + (size_t)q * ld,
+                            AU + (size_t)q * ld);
+    CK(h, launch_udots(a, U, ld, q + 1, AU + (size_t)q * ld, DotEpi{kEpiRaw, nullptr, 0, c1, -1}, st));
+    if (q > 0)
+      CK(h, launch_udots(a, AU, ld, q, U + (size_t)q * ld, DotEpi{kEpiRaw, nullptr, 0, c2, -1}, st));
+    k_adapt_tset<<<1, 64, 0, st>>>(T, R, q, c1, c2);
+    CK(h, cudaGetLastError());
+    ++q;
+  }
+  CK(h, cudaMemsetAsync(iv + 1, 0, sizeof(int), st));
+  k_adapt_tinv<<<1, 256, 0, st>>>(T, R, q, Tinv, iv + 1);
+  int bad = 0;
+  CK(h, cudaMemcpyAsync(&bad, iv + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  if (bad) return fail(h, GMRES_ERR_SINGULAR_COARSE, "dense W: T = U^T A U is singular");
+  h->aq = q;
+  return GMRES_OK;
+}
+
 // One update of the adaptive deflation space after a cycle (see the file comment).
 gmres_status adapt_update(gmres_s* h, CycleArgs& a) {
   cudaStream_t st = h->stream;

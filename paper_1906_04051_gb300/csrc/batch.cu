@@ -820,6 +820,8 @@ gmres_status batch_solve_impl(int count, gmres_t const* hs, const double* const*
                   "deflation_mode ADAPTIVE is for single-system solves");
     if (hs[i]->opts.ortho != GMRES_ORTHO_CGS2)
       return fail(nullptr, GMRES_ERR_INVALID_ARG, "the batched solve orthogonalises by CGS2");
+    if (hs[i]->dense_r > 0)
+      return fail(nullptr, GMRES_ERR_INVALID_ARG, "dense W is for single-system solves");
   }
   int sms = hs[0]->sms;
   // workspaces of the handles serve the batch (allocated on the batch stream)

@@ -77,6 +77,11 @@ struct gmres_s {
   DevMem aU, aAU, aT, aTinv, au, asmall;
   DevMem gbar;  // grid barrier words of the modified Gram-Schmidt kernel
   DevMem lmat;  // strictly lower part of V^T V (one-reduction MGS)
+  // a deflation space given as dense columns W (n x dense_r), orthonormalised into the
+  // dense-space buffers above (aU, aAU, aT, aTinv) at the first solve
+  DevMem wdense;
+  int dense_r = 0;
+  bool dense_built = false;
   int aq = 0;
   Meta* hmeta = nullptr;  // pinned
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -154,7 +159,7 @@ inline gmres_status ensure_workspace(gmres_s* h, int m, int prec) {
   CK(h, h->gbar.ensure(2 * sizeof(unsigned)));
   if (h->opts.ortho == GMRES_ORTHO_MGS_LOWSYNC)
     CK(h, h->lmat.ensure(sizeof(double) * (size_t)kMaxK * kMaxK));
-  if (h->opts.deflation_mode == GMRES_DEFL_ADAPTIVE && !h->aU.p) {
+  if ((h->opts.deflation_mode == GMRES_DEFL_ADAPTIVE || h->dense_r > 0) && !h->aU.p) {
     const size_t col = sizeof(double) * (size_t)ldv;
     const size_t R = (size_t)h->opts.rmax;
     CK(h, h->aU.ensure(col * R));
@@ -330,6 +335,8 @@ gmres_status batch_solve_impl(int count, gmres_t const* hs, const double* const*
                               long long* launches);
 void batch_forget(gmres_t h);
 // after a restart cycle: grows the adaptive deflation space (adaptive.cu)
+// U, A U, T and T^-1 of a handle from its dense columns W (first solve only)
+gmres_status dense_build(gmres_s* h, CycleArgs& a);
 gmres_status adapt_update(gmres_s* h, CycleArgs& a);
 
 }  // namespace gg

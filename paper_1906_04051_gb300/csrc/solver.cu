@@ -100,6 +100,7 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
 
   const bool ebp = h->r > 0 && h->opts.deflation_mode == GMRES_DEFL_EBP;
   const bool ada = h->opts.deflation_mode == GMRES_DEFL_ADAPTIVE;  // U grows from empty
+  const bool dw = h->dense_r > 0;  // U from the caller's dense columns, fixed
   if (ada) h->aq = 0;
   const int mu_mode = h->opts.mu_mode;
   double mu = 0.0;
@@ -114,6 +115,11 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
   CK(h, launch_init(a, tol, inner_tol, h->opts.r0_norm_ref, mu, h->opts.fixed_iterations ? 1 : 0,
                     mixed ? 1 : 0, maxit, st));
   h->plaunch[PH_RESIDUAL] += 1;  // the init kernel is counted with the first residual
+  if (dw && !h->dense_built) {  // U, A U, T, T^-1 from W, once per handle
+    s = dense_build(h, a);
+    if (s != GMRES_OK) return s;
+    h->dense_built = true;
+  }
   CK(h, phase(h, a, PH_RESIDUAL, 0, false, x, b));
   s = read_meta(h);
   if (s != GMRES_OK) return s;
@@ -122,8 +128,8 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
   gmres_status status = GMRES_OK;
   while (!h->hmeta->flags[F_STOP]) {
     const bool mu_known = mu_mode != GMRES_MU_RITZ_FIRST_CYCLE || cycle > 0;
-    const bool defl_cycle = (ebp || (ada && h->aq > 0)) && mu_known;
-    if (ada) {  // this cycle's dense deflation space (empty until the first update)
+    const bool defl_cycle = (ebp || ((ada || dw) && h->aq > 0)) && mu_known;
+    if (ada || dw) {  // this cycle's dense deflation space (adaptive: empty at first)
       a.op.defl.ud = h->aU.as<double>();
       a.op.defl.aud = h->aAU.as<double>();
       a.op.defl.tinv_a = h->aTinv.as<double>();
@@ -148,7 +154,7 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
       if (defl_cycle) CK(h, phase(h, a, PH_DEFL, j + 1, true, x, b));
     }
     CK(h, phase(h, a, PH_CYCLE_END, 0, defl_cycle, x, b));
-    if ((ebp || ada) && mu_mode == GMRES_MU_RITZ_FIRST_CYCLE && cycle == 0)
+    if ((ebp || ada || dw) && mu_mode == GMRES_MU_RITZ_FIRST_CYCLE && cycle == 0)
       CK(h, phase(h, a, PH_RITZ, 0, false, x, b));
     if (ada) {  // grow U from this cycle's H_k and basis (Sec. 3.3, Eq. 19)
       CK(h, prof_mark(h, PH_ADAPT));
@@ -186,7 +192,7 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
     info->refinements = h->hmeta->counts[C_REFINE];
     info->rel_res_est = h->hmeta->scal[S_EST];
     info->rel_res_true = h->hmeta->scal[S_TRUE];
-    info->mu = (ebp || ada) ? h->hmeta->scal[S_MU] : 0.0;
+    info->mu = (ebp || ada || dw) ? h->hmeta->scal[S_MU] : 0.0;
     info->ms_total = ms;
     info->status = status;
   }
@@ -235,6 +241,8 @@ gmres_status run_noalloc(gmres_s* h, OpHost& o, const double* b, const double* x
     return fail(h, GMRES_ERR_INVALID_ARG, "gmres_solve_noalloc: GMRES_DEFL_ADAPTIVE allocates its space");
   if (h->opts.ortho != GMRES_ORTHO_CGS2)
     return fail(h, GMRES_ERR_INVALID_ARG, "gmres_solve_noalloc: CGS2 only");
+  if (h->dense_r > 0)
+    return fail(h, GMRES_ERR_INVALID_ARG, "gmres_solve_noalloc: dense W allocates its space");
   if (m < 1 || m > kMaxM) return fail(h, GMRES_ERR_INVALID_ARG, "m must be in [1, 64]");
   if (!(tol >= 0.0) || maxit < 0) return fail(h, GMRES_ERR_INVALID_ARG, "tol >= 0, maxit >= 0");
   const int prec = prec_of(h->opts.precision);
@@ -402,9 +410,14 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
   *out = nullptr;
   if (A->n <= 0 || !A->rowptr || !A->col || !A->val || A->nnz < 0 || A->nnz >= (1LL << 31))
     return fail(nullptr, GMRES_ERR_INVALID_ARG, "invalid CSR description");
-  const int r = (W && W->r > 0) ? W->r : 0;
+  const bool dense_w = W && W->r > 0 && W->dense;  // W as dense columns
+  const int r = (W && W->r > 0 && !dense_w) ? W->r : 0;  // aggregates
+  const int dr = dense_w ? W->r : 0;
   if (r > kMaxR) return fail(nullptr, GMRES_ERR_INVALID_ARG, "r exceeds 6144");
   if (r > 0 && !W->agg) return fail(nullptr, GMRES_ERR_INVALID_ARG, "agg is null");
+  if (dense_w && W->agg)
+    return fail(nullptr, GMRES_ERR_INVALID_ARG, "give W as aggregates or as dense columns, not both");
+  if (dr > kMaxAdapt) return fail(nullptr, GMRES_ERR_INVALID_ARG, "dense W: r exceeds 32");
   gmres_opts opts;
   if (o) opts = *o;
   else gmres_opts_default(&opts);
@@ -416,8 +429,11 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
     return fail(nullptr, GMRES_ERR_INVALID_ARG, "GMRES_ORTHO_MGS is FP64 only");
   if (opts.ortho == GMRES_ORTHO_MGS_LOWSYNC && opts.precision == GMRES_BF16_BASIS)
     return fail(nullptr, GMRES_ERR_INVALID_ARG, "GMRES_ORTHO_MGS_LOWSYNC: FP64 or FP32 inner");
+  if (dense_w && (opts.deflation_mode != GMRES_DEFL_EBP || opts.precision != GMRES_FP64))
+    return fail(nullptr, GMRES_ERR_INVALID_ARG, "dense W: GMRES_DEFL_EBP and FP64 only");
+  if (dense_w) opts.rmax = dr;  // the dense-space buffers hold exactly its columns
   if (opts.deflation_mode == GMRES_DEFL_ADAPTIVE) {
-    if (r > 0)
+    if (r > 0 || dense_w)
       return fail(nullptr, GMRES_ERR_INVALID_ARG,
                   "GMRES_DEFL_ADAPTIVE builds U itself: pass no aggregates");
     if (opts.precision != GMRES_FP64)
@@ -460,6 +476,12 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
   if (r > 0) {
     CKC(h->agg.ensure(sizeof(int) * (size_t)n));
     CKC(cudaMemcpyAsync(h->agg.p, W->agg, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+  }
+  if (dense_w) {
+    h->dense_r = dr;
+    CKC(h->wdense.ensure(sizeof(double) * (size_t)n * dr));
+    CKC(cudaMemcpyAsync(h->wdense.p, W->dense, sizeof(double) * (size_t)n * dr,
+                        cudaMemcpyDeviceToDevice, st));
   }
   DevMem err;
   CKC(err.ensure(sizeof(int) * 4));
@@ -560,6 +582,8 @@ gmres_status gmres_solve_noalloc(gmres_t h, const double* b, const double* x0, i
 gmres_status gmres_adjoint_solve(gmres_t h, const double* g, const double* lam0, int32_t m,
                                  double tol, int64_t maxit, double* lam, gmres_info* info) {
   if (!h) return fail(nullptr, GMRES_ERR_INVALID_ARG, "null handle");
+  if (h->dense_r > 0)
+    return fail(h, GMRES_ERR_INVALID_ARG, "gmres_adjoint_solve: not with a dense W");
   if (!h->adj.ready) {
     cudaStream_t st = h->stream;
     const int n = h->n;
@@ -624,15 +648,15 @@ gmres_status gmres_layout_query(gmres_t h, gmres_layout* out) {
   out->ndiag = h->fwd.dia.nd;
   out->nau = h->fwd.nau;
   out->ldv = h->ldv;
-  out->adapt_q = h->opts.deflation_mode == GMRES_DEFL_ADAPTIVE ? h->aq : 0;
+  out->adapt_q = (h->opts.deflation_mode == GMRES_DEFL_ADAPTIVE || h->dense_r > 0) ? h->aq : 0;
   out->spmv_lanes = (h->fwd.dia.nd == 0 && h->nnz >= (long long)kVecMinRowLen * h->n) ? kVecLanes : 0;
   return GMRES_OK;
 }
 
 gmres_status gmres_adaptive_space(gmres_t h, int32_t* q, double* U, int64_t ldu, double* T) {
   if (!h) return fail(nullptr, GMRES_ERR_INVALID_ARG, "null handle");
-  if (h->opts.deflation_mode != GMRES_DEFL_ADAPTIVE)
-    return fail(h, GMRES_ERR_INVALID_ARG, "gmres_adaptive_space: not an adaptive-deflation handle");
+  if (h->opts.deflation_mode != GMRES_DEFL_ADAPTIVE && h->dense_r == 0)
+    return fail(h, GMRES_ERR_INVALID_ARG, "gmres_adaptive_space: the handle has no dense space");
   if (!q) return fail(h, GMRES_ERR_INVALID_ARG, "gmres_adaptive_space: null q");
   if (U && ldu < h->n) return fail(h, GMRES_ERR_INVALID_ARG, "gmres_adaptive_space: ldu < n");
   const int nq = h->aU.p ? h->aq : 0;
