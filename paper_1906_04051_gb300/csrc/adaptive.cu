@@ -10,10 +10,10 @@
 // T-invariant subspace carrying the other eigenvalues, in the basis U H_0 (H_1) given by
 // Householder reflectors that map the dropped directions onto single coordinates (rank-1
 // updates of U and A U instead of a dense rotation), T <- H T H without those rows and
-// columns.  T^-1 follows.  Arithmetic runs in the
-// kernels below and in the pipelined multi-dot of arnoldi.cu; the host only sequences
-// them and reads the few scalars that decide the branches (vector count, norms, the
-// number of dropped directions).
+// columns.  T^-1 follows.  Arithmetic runs in the kernels below and in the pipelined
+// multi-dot of arnoldi.cu; the host only sequences them and reads the few scalars that
+// decide the branches (vector count, norms, the number of dropped directions).  A
+// deflation space given as dense columns W is built by the same steps (dense_build).
 #include <cmath>
 #include <cstring>
 
@@ -307,11 +307,13 @@ __global__ void k_adapt_tset(double* __restrict__ T, int ldt, int q, const doubl
 // QR (hqr_warp) for the eigenvalue lambda = a + i b of largest modulus, its left
 // eigenvector y (T^T y = lambda y) by three inverse iterations from all ones on the real
 // form [[T^T - a I, b I], [-b I, T^T - a I]] (LU with partial pivoting, first index on
-// ties; a pivot of modulus <= 1e-14 max|entry| becomes that bound), Householder QR of
-// Y = [Re y (, Im y)] and Qc = (H_0 ... H_{p-1})[:, p:] (row stride kMaxAdapt), the
-// orthonormal basis of {c : y^T c = 0}; T's leading (q-p) x (q-p) block becomes
-// Qc^T T Qc.  out[0] = p (1, or 2 for a complex pair), out[1] = 1 if the QR iteration
-// did not converge.
+// ties; a pivot of modulus <= 1e-14 max|entry| becomes that bound), then p Householder
+// reflectors H_c = I - beta_c v_c v_c^T mapping the columns of Y = [Re y (, Im y)] onto
+// single coordinates jd_c (the columns of Q = H_0 ... H_{p-1} other than jd_c span
+// {c : y^T c = 0}); T <- Q^T T Q with rows and columns jd_c removed, the dropped slots
+// below q - p refilled from the kept coordinates above.  Qc receives v_0 (, v_1) and
+// beta_0, beta_1 for k_adapt_reflect; out[0] = p (1, or 2 for a complex pair), out[1] = 1
+// if the QR iteration did not converge, out[2 + s] = the coordinate that slot s keeps.
 __global__ void __launch_bounds__(32)
     k_adapt_drop(double* __restrict__ T, int ldt, int q, double* __restrict__ Qc,
                  int* __restrict__ out) {
