@@ -59,3 +59,47 @@ def test_host_only_calls(lib):
     assert L.gmres_create(ctypes.byref(h), None, None, None, None) == N.GMRES_ERR_INVALID_ARG
     assert b"null" in L.gmres_last_error(None)
     assert L.gmres_solve(None, None, None, 30, 1e-8, 10, None, None) == N.GMRES_ERR_INVALID_ARG
+
+
+def test_q2_nnz_closed_form_matches_the_oracle_count(lib, orc):
+    # the library's closed form (also the row pointer of the device assembly) against the
+    # oracle's row-by-row count, including Table 1's sizes
+    from paper_1906_04051_gb300 import _native as N
+    L = N.load()
+    assert L.q2_nnz(0) == 0
+    for n in list(range(1, 41)) + [45, 50, 55, 60]:
+        assert L.q2_nnz(n) == orc.q2_nnz(n), n
+    for n in (1, 2, 7, 64, 255, 1024, 2048):
+        assert L.q1_nnz(n) == orc.q1_nnz(n), n
+
+
+def test_option_validation_before_device_work(lib):
+    from paper_1906_04051_gb300 import _native as N
+    L = N.load()
+    o = N.gmres_opts()
+    L.gmres_opts_default(ctypes.byref(o))
+    assert (o.rmax, o.ninv, o.ortho) == (20, 20, N.ORTHO_CGS2)
+    csr = N.gmres_csr(4, 4, 1, 1, 1)  # non-null placeholders: never dereferenced here
+    h = ctypes.c_void_p()
+
+    def create(**kw):
+        oo = N.gmres_opts()
+        L.gmres_opts_default(ctypes.byref(oo))
+        for k, v in kw.items():
+            setattr(oo, k, v)
+        return L.gmres_create(ctypes.byref(h), ctypes.byref(csr), None, ctypes.byref(oo), None)
+
+    bad = [dict(precision=3), dict(deflation_mode=4), dict(mu_mode=3), dict(ortho=3),
+           dict(ortho=N.ORTHO_MGS, precision=N.FP32_INNER),
+           dict(ortho=N.ORTHO_MGS_LOWSYNC, precision=N.BF16_BASIS),
+           dict(deflation_mode=N.DEFL_ADAPTIVE, precision=N.FP32_INNER),
+           dict(deflation_mode=N.DEFL_ADAPTIVE, rmax=0),
+           dict(deflation_mode=N.DEFL_ADAPTIVE, rmax=33),
+           dict(deflation_mode=N.DEFL_ADAPTIVE, ninv=0)]
+    for kw in bad:
+        assert create(**kw) == N.GMRES_ERR_INVALID_ARG, kw
+        assert L.gmres_last_error(None), kw
+    # W given both as aggregates and as dense columns, or with too many dense columns
+    for defl in (N.gmres_defl(2, 1, 1), N.gmres_defl(33, None, 1)):
+        assert L.gmres_create(ctypes.byref(h), ctypes.byref(csr), ctypes.byref(defl), None,
+                              None) == N.GMRES_ERR_INVALID_ARG
