@@ -11,8 +11,10 @@
  *                         deflation preconditioner M^-1 = I + U (|mu| T^-1 - I) U^T,
  *                         T = U^T A U, mu the largest eigenvalue of A estimated from the
  *                         Ritz values of H_m.
- *   Sec. 3.1, Eqs. 6-8    Galerkin finite-element assembly with Dirichlet rows replaced
- *                         by u_i = 0 (here: bilinear Q1 elements on the unit square).
+ *   Sec. 3.1, Eqs. 2-9    Galerkin finite-element assembly with Dirichlet rows replaced
+ *                         by u_i = 0: bilinear Q1 elements on the unit square
+ *                         (convection-diffusion), and the paper's 3-D Bratu problem on
+ *                         27-node hexahedra solved by Newton's method.
  *
  * Conventions shared by every entry point
  *   - Pointers named "device" must point to memory of the current CUDA device; the
@@ -47,7 +49,9 @@ typedef enum {
   GMRES_ERR_SINGULAR_COARSE = -4, /* empty aggregate (zero column of W), singular T, or
                                      no usable Ritz estimate of mu */
   GMRES_ERR_NAN = -5,             /* NaN/Inf met in a residual or Hessenberg entry */
-  GMRES_ERR_TIMEOUT = -6          /* opts.timeout_ms elapsed (checked at restarts) */
+  GMRES_ERR_TIMEOUT = -6          /* opts.timeout_ms elapsed (checked at restarts), or a
+                                     bounded device wait ran out (a basis copy, or the
+                                     grid barrier of GMRES_ORTHO_MGS) */
 } gmres_status;
 
 /* Matrix A (Eq. 1), n x n.  All arrays device, read during gmres_create only: the
@@ -213,20 +217,25 @@ gmres_status gmres_solve(gmres_t h, const double* b, const double* x0, int32_t m
  * array and it keeps the previous call's contents (the call clears what must start at
  * zero): calls that overlap on the GPU, in any stream, race and give wrong results, so
  * serialise them.  ms_total in info is host wall time.  Arguments, outputs and errors as
- * gmres_solve; the per-phase profile of gmres_profile is not updated. */
+ * gmres_solve; the per-phase profile of gmres_profile is not updated.  Handles with
+ * GMRES_DEFL_ADAPTIVE, a dense W or an orthogonalisation other than GMRES_ORTHO_CGS2 are
+ * refused with GMRES_ERR_INVALID_ARG (their workspace does not fit the fixed array). */
 gmres_status gmres_solve_noalloc(gmres_t h, const double* b, const double* x0, int32_t m,
                                  double tol, int64_t maxit, double* x, gmres_info* info);
 
 /* Adjoint solve A^T lam = g with the transposed preconditioner
  * M^-T = I + U (|mu| T^-T - I) U^T (same U; T^T = U^T A^T U).  The transpose of A is
- * built on the first call and kept.  Arguments as gmres_solve. */
+ * built on the first call and kept.  Arguments as gmres_solve.  A handle with a dense W
+ * is refused with GMRES_ERR_INVALID_ARG. */
 gmres_status gmres_adjoint_solve(gmres_t h, const double* g, const double* lam0, int32_t m,
                                  double tol, int64_t maxit, double* lam, gmres_info* info);
 
 /* Solves count independent systems, system i with handle hs[i] (host array), in one
  * persistent launch on `stream`.  b, x0, x: host arrays of count device pointers (x0
  * may be NULL, or contain NULLs).  infos: host array of count entries, may be NULL.
- * All handles must use the same precision.  Returns the worst status. */
+ * All handles must use the same precision, GMRES_ORTHO_CGS2, and W as aggregates (or no
+ * W) with deflation_mode EBP or NONE; otherwise GMRES_ERR_INVALID_ARG before any launch.
+ * Returns the worst status. */
 gmres_status gmres_batch_solve(int32_t count, gmres_t const* hs, const double* const* b,
                                const double* const* x0, int32_t m, double tol,
                                int64_t maxit, double* const* x, gmres_info* infos,
