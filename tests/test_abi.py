@@ -103,3 +103,43 @@ def test_option_validation_before_device_work(lib):
     for defl in (N.gmres_defl(2, 1, 1), N.gmres_defl(33, None, 1)):
         assert L.gmres_create(ctypes.byref(h), ctypes.byref(csr), ctypes.byref(defl), None,
                               None) == N.GMRES_ERR_INVALID_ARG
+
+
+def test_assembly_and_batch_validation_before_device_work(lib):
+    # every call here is refused on the host, before any CUDA call: the placeholder
+    # pointers (1) are never dereferenced
+    from paper_1906_04051_gb300 import _native as N
+    L = N.load()
+    E = N.GMRES_ERR_INVALID_ARG
+    nan = float("nan")
+    assert L.q1_assemble(0, 1, 0.0, 0.0, 1, None, 1, 1, 1, 1, None) == E
+    assert L.q1_assemble(8, None, 0.0, 0.0, 1, None, 1, 1, 1, 1, None) == E
+    assert L.q1_assemble(50000, 1, 0.0, 0.0, 1, None, 1, 1, 1, 1, None) == E  # nnz >= 2^31
+    assert b"int32" in L.gmres_last_error(None)
+    assert L.q1_kappa_grad(0, 1, 1, 1, None) == E
+    assert L.q2_bratu_assemble(0, 6.8, None, 1, 1, 1, 1, None) == E
+    assert L.q2_bratu_assemble(2, 6.8, None, None, 1, 1, 1, None) == E
+    assert L.q2_bratu_assemble(2, nan, None, 1, 1, 1, 1, None) == E
+    assert b"lambda" in L.gmres_last_error(None)
+    # n = 162 is the first mesh whose nnz overflows int32 (N = 325^3 still fits)
+    assert L.q2_nnz(161) < 2 ** 31 <= L.q2_nnz(162)
+    assert L.q2_bratu_assemble(162, 6.8, None, 1, 1, 1, 1, None) == E
+    info = N.q2_newton_info()
+    assert L.q2_bratu_newton(0, 6.8, None, None, 50, 1e-8, 100, 1e-9, 10, 1,
+                             ctypes.byref(info), None) == E
+    assert L.q2_bratu_newton(4, 6.8, None, None, 50, 1e-8, 100, 1e-9, 0, 1,
+                             ctypes.byref(info), None) == E
+    assert L.q2_bratu_newton(4, 6.8, None, None, 50, 1e-8, 100, nan, 10, 1,
+                             ctypes.byref(info), None) == E
+    assert L.q2_bratu_newton(162, 6.8, None, None, 50, 1e-8, 100, 1e-9, 10, 1,
+                             ctypes.byref(info), None) == E
+    # batched solve: an empty batch is a no-op; a negative count or null arrays are refused
+    assert L.gmres_batch_solve(0, None, None, None, 30, 1e-8, 10, None, None, None) == N.GMRES_OK
+    assert L.gmres_batch_solve(-1, None, None, None, 30, 1e-8, 10, None, None, None) == E
+    assert L.gmres_batch_solve(2, None, None, None, 30, 1e-8, 10, None, None, None) == E
+    # handle-less queries
+    lay = N.gmres_layout()
+    assert L.gmres_layout_query(None, ctypes.byref(lay)) == E
+    q = ctypes.c_int32()
+    assert L.gmres_adaptive_space(None, ctypes.byref(q), None, 0, None) == E
+    assert L.gmres_profile(None, 1, 0, None, None) == E
