@@ -94,19 +94,25 @@ class ClockSampler:
                 self._p.kill()
         if self._t:
             self._t.join(timeout=2)
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for s in self.samples:
-            try:
-                sm.append(float(s[0]))
-                mx = float(s[1])
-            except ValueError:
-                continue
-            for n, v in zip(names, s[3:7]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return summarise_clocks(self.samples)
+
+
+def summarise_clocks(samples):
+    """Median SM clock, the maximum clock and the throttle reasons seen Active in rows of
+    ClockSampler.FIELDS (rows that do not parse are skipped)."""
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for s in samples:
+        try:
+            sm.append(float(s[0]))
+            mx = float(s[1])
+        except ValueError:
+            continue
+        for n, v in zip(names, s[3:7]):
+            if v.lower().startswith("active"):
+                reasons.add(n)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+            "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def max_over_ranks(x: float, pg=None, device="cpu") -> float:

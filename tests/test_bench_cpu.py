@@ -41,3 +41,22 @@ def test_reference_arm_prints_one_line(monkeypatch, capsys):
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == bench.UNIT
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["higher_is_better"] is True
+
+
+def test_clock_summary():
+    import bench
+    rows = [["1965", "2070", "900.1", "Not Active", "Not Active", "Not Active", "Active"],
+            ["2010", "2070", "910.0", "Not Active", "Not Active", "Not Active", "Not Active"],
+            ["[N/A]", "2070", "0", "Not Active", "Active", "Not Active", "Not Active"],
+            ["1980", "2070", "905.5", "Not Active", "Not Active", "Not Active", "Not Active"]]
+    c = bench.summarise_clocks(rows)
+    # the unparsable row is skipped whole, its reasons included
+    assert c == {"sm_mhz": 1980.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                 "samples": 3}
+    assert bench.summarise_clocks([])["sm_mhz"] is None
+
+
+def test_job_rate_counts_every_rank():
+    import bench
+    assert bench.job_rate(1, 10, 1000.0) == 10.0
+    assert bench.job_rate(4, 10, 2000.0) == 20.0
