@@ -3,9 +3,9 @@
 gmres_solve_noalloc serves callers that must not allocate once set up (a real-time loop
 with a frozen memory budget, or a process whose device memory is owned by a framework's
 caching allocator): its workspace lives in a static 32 MiB device array of the library
-instead of handle-owned allocations.  This file is collected last on purpose, so that a
-run stopping at the first failure has already run every other test; it also passes on
-its own in a fresh process.
+instead of handle-owned allocations.  This file is collected after the parity files on
+purpose, so that a run stopping at the first failure has already run them; it also passes
+on its own in a fresh process.
 """
 import ctypes as C
 
