@@ -290,3 +290,44 @@ def test_dense_w_identity_and_dependent_columns(orc):
     assert np.abs(U.T @ Ad @ Minv @ U - mu * np.eye(4)).max() <= 1e-9 * mu
     with pytest.raises(ValueError):
         orc.gmres(A, b, w_dense=np.column_stack([Wd, Wd[:, 0] + 2 * Wd[:, 1]]))
+
+
+def _random_sparse(seed, N, density):
+    """Nonsymmetric sparse matrix with irregular row lengths (including rows holding only
+    the diagonal) whose symmetric part is positive definite (diagonal above the mean of
+    each row's and column's off-diagonal absolute sums): restarted GMRES(m) then converges
+    for every m >= 1 (Elman's bound), while an indefinite matrix may stagnate at small m."""
+    rng = np.random.default_rng(seed)
+    M = sp.random(N, N, density=density, random_state=rng, format="csr")
+    M.data = rng.standard_normal(M.nnz)
+    M = (M - sp.diags(M.diagonal())).tocsr()
+    absM = abs(M)
+    off = 0.5 * (np.asarray(absM.sum(axis=1)).ravel() + np.asarray(absM.sum(axis=0)).ravel())
+    M = (M + sp.diags(off + 1.0 + rng.random(N))).tocsr()
+    M.sort_indices()
+    return M, rng
+
+
+@pytest.mark.parametrize("N,density,m", [(1, 1.0, 1), (2, 0.5, 1), (5, 0.4, 2), (17, 0.2, 3),
+                                         (40, 0.1, 7), (97, 0.05, 10)])
+@pytest.mark.parametrize("ortho", [0, 1])
+def test_random_sparse_systems_against_dense_solve(orc, N, density, m, ortho):
+    # brute force on small irregular systems: short restart lengths force many cycles, and
+    # the solution must be numpy's dense solve; an aggregate map with a random assignment
+    # (every aggregate non-empty) exercises the EBP path on the same systems
+    M, rng = _random_sparse(1000 + N, N, density)
+    A = orc.CSR(M.indptr, M.indices, M.data)
+    xt = rng.standard_normal(N)
+    b = M @ xt
+    xd = np.linalg.solve(M.toarray(), b)
+    x, info = orc.gmres(A, b, m=m, tol=1e-13, maxit=20000, ortho=ortho)
+    assert info["status"] == 0, info
+    assert np.linalg.norm(x - xd) <= 1e-10 * np.linalg.norm(xd)
+    r = max(1, N // 4)
+    agg = np.concatenate([np.arange(r), rng.integers(0, r, N - r)]).astype(np.int32)
+    rng.shuffle(agg)
+    d = orc.Deflation(A, agg, r)
+    x2, info2 = orc.gmres(A, b, m=m, tol=1e-13, maxit=20000, defl=d, ortho=ortho,
+                          mu_mode=orc.MU_USER, mu_user=3.0)
+    assert info2["status"] == 0, info2
+    assert np.linalg.norm(x2 - xd) <= 1e-10 * np.linalg.norm(xd)
