@@ -314,7 +314,7 @@ def _random_sparse(seed, N, density):
 def test_random_sparse_systems_against_dense_solve(orc, N, density, m, ortho):
     # brute force on small irregular systems: short restart lengths force many cycles, and
     # the solution must be numpy's dense solve; an aggregate map with a random assignment
-    # (every aggregate non-empty) exercises the EBP path on the same systems
+    # (every aggregate non-empty) exercises the EBP and projector paths on the same systems
     M, rng = _random_sparse(1000 + N, N, density)
     A = orc.CSR(M.indptr, M.indices, M.data)
     xt = rng.standard_normal(N)
@@ -331,3 +331,7 @@ def test_random_sparse_systems_against_dense_solve(orc, N, density, m, ortho):
                           mu_mode=orc.MU_USER, mu_user=3.0)
     assert info2["status"] == 0, info2
     assert np.linalg.norm(x2 - xd) <= 1e-10 * np.linalg.norm(xd)
+    x3, info3 = orc.gmres(A, b, m=m, tol=1e-13, maxit=20000, defl=d, ortho=ortho,
+                          defl_mode=orc.DEFL_PROJECTOR)
+    assert info3["status"] == 0, info3
+    assert np.linalg.norm(x3 - xd) <= 1e-10 * np.linalg.norm(xd)
