@@ -209,11 +209,15 @@ gmres_status gmres_solve(gmres_t h, const double* b, const double* x0, int32_t m
  * budget, or processes where a framework's caching allocator owns the device memory and
  * an extra cudaMalloc could fail or fragment it.  The handle (from gmres_create, which
  * does allocate) provides A and the deflation data.  The paper has no counterpart.
- * Limits: the workspace, about 8 (m+1) round_up(n, 64) bytes for FP64 (half / a quarter
- * of that basis for FP32 / BF16) plus about 1 MB, must fit in 32 MiB, otherwise
- * GMRES_ERR_INVALID_ARG with a message naming the size.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress) with that device current: make
- * that first call before any stream capture.  Every call on every handle shares the one
+ * Limits: the workspace must fit in 32 MiB, otherwise GMRES_ERR_INVALID_ARG with a
+ * message naming the size.  It is the basis, (m+1) round_up(n, 256) elements of 8 bytes
+ * (FP64), 4 (FP32) or 2 (BF16), plus two FP64 vectors of round_up(n, 256) entries, plus
+ * the reduction partials, 8 x 144 x 8 x (number of SMs) bytes (1.4 MB on a 152-SM GPU),
+ * plus a few kilobytes (control block, aggregate sums).  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device current and
+ * caches it (thread-safe): make that first call before any stream capture.  A
+ * cudaDeviceReset after that first call is not supported (the cached address would be
+ * stale).  Every call on every handle shares the one
  * array and it keeps the previous call's contents (the call clears what must start at
  * zero): calls that overlap on the GPU, in any stream, race and give wrong results, so
  * serialise them.  ms_total in info is host wall time.  Arguments, outputs and errors as

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -214,16 +215,19 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kNoAllocMaxDevices = 64;
 unsigned char* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+std::mutex g_noalloc_mu;  // guards g_noalloc_ptr (first calls from several host threads)
 
 // Device address of the scratch array for the current device.  In host code the array's
 // name is only a host-side stand-in, so the address is looked up once per device (with
 // that device current) and cached.  This first lookup on a device is the only set-up
-// step; make the first call on each device before any stream capture.
+// step; make the first call on each device before any stream capture.  The cache is not
+// invalidated by cudaDeviceReset, which is therefore not supported after that first call.
 cudaError_t noalloc_scratch(unsigned char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
     void* ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);

@@ -1,8 +1,9 @@
-"""Parity at the full size of the headline system, in the configuration bench.py times:
+"""Parity at full size.  The headline system, in the configuration bench.py times:
 q1-n1024 (1,050,625 DOF, 9,422,857 nnz), 1024 aggregate deflation vectors, GMRES(50),
 the paper's MGS projections in their one-reduction form.  Two restart cycles in the
 fixed-iteration protocol against the oracle's MGS GMRES (every entry of x), and the solve
-to 1e-8 checked with the oracle's own SpMV (the true residual of the returned x)."""
+to 1e-8 checked with the oracle's own SpMV (the true residual of the returned x).  The
+differentiable-solve system q1-n512: two adjoint GMRES(50) cycles against the oracle."""
 import numpy as np
 import pytest
 
@@ -53,3 +54,22 @@ def test_full_size_solve_true_residual(G, orc, system):
     rel = np.linalg.norm(r) / np.linalg.norm(b)
     assert rel <= 1e-8
     assert rel == pytest.approx(ig["rel_res_true"], rel=1e-6)
+
+
+def test_full_size_adjoint_fixed_iterations_q1_n512(G, orc):
+    # the differentiable-solve workload at its full size (q1-n512: 263,169 DOF,
+    # 2,352,137 nnz, 16 x 16 aggregates): two GMRES(50) cycles of the adjoint solve
+    # A^T lam = g (transpose built on the device, T^-T) in the fixed-iteration protocol of
+    # Sec. 4, every entry of lam against the oracle's GMRES on the explicit transpose
+    p, _ = W.workload5(512)
+    A, _ = orc.q1_assemble(p.n, p.kappa, p.beta, p.f)
+    g = W.uniform(5120, 1, A.n, -1, 1)
+    s = gpu_solver_from_oracle(G, A, p.agg, p.r, mu_mode=1, mu_user=8.0,
+                               fixed_iterations=True)
+    lam, il = s.adjoint_solve(to_dev(g), m=50, tol=0.0, maxit=100)
+    At = A.transpose()
+    lo, io = orc.gmres(At, g, m=50, tol=0.0, maxit=100, defl=orc.Deflation(At, p.agg, p.r),
+                       mu_mode=1, mu_user=8.0, fixed_iterations=True)
+    assert il["iters"] == io["iters"] == 100
+    assert relerr(lam.cpu().numpy(), lo) <= 1e-9
+    assert il["rel_res_true"] == pytest.approx(io["rel_res_true"], rel=1e-7)

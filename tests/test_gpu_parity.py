@@ -145,6 +145,34 @@ def test_general_csr_path_permuted(G, orc, mode, prec):
         assert abs(ig["iters"] - i2["iters"]) <= 3
 
 
+@pytest.mark.parametrize("maxit", [7, 45])
+@pytest.mark.parametrize("mode", ["ebp", "proj", "none"])
+@pytest.mark.parametrize("ortho", ["cgs2", "mgs_lowsync"])
+def test_general_csr_fixed_iterations(G, orc, mode, maxit, ortho):
+    # the thread-per-row CSR SpMV (a renumbered, non-banded system) in the fixed-iteration
+    # protocol of Sec. 4: the same step count and mu on both sides, every entry of x
+    p = W.convdiff(40, pe=25.0, sigma=0.5, seed=78, px=2, py=3)
+    A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f)
+    Ap, bp, aggp, _ = _permuted(orc, A, b, p.agg, seed=6)
+    defl = mode != "none"
+    dm = {"ebp": G.DEFL_EBP, "none": G.DEFL_NONE, "proj": G.DEFL_PROJECTOR}[mode]
+    go = {"cgs2": G.ORTHO_CGS2, "mgs_lowsync": G.ORTHO_MGS_LOWSYNC}[ortho]
+    s = gpu_solver_from_oracle(G, Ap, aggp if defl else None, p.r if defl else 0,
+                               deflation_mode=dm, mu_mode=1, mu_user=5.0,
+                               fixed_iterations=True, ortho=go)
+    lay = s.layout()
+    assert lay["ndiag"] == 0 and lay["spmv_lanes"] == 0  # CSR, a thread per row
+    xg, ig = s.solve(to_dev(bp), m=10, tol=0.0, maxit=maxit)
+    d = orc.Deflation(Ap, aggp, p.r) if defl else None
+    odm = {"ebp": orc.DEFL_EBP, "none": orc.DEFL_NONE, "proj": orc.DEFL_PROJECTOR}[mode]
+    oo = orc.CGS2 if ortho == "cgs2" else orc.MGS
+    xo, io = orc.gmres(Ap, bp, None, m=10, tol=0.0, maxit=maxit, defl=d, defl_mode=odm,
+                       mu_mode=1, mu_user=5.0, fixed_iterations=True, ortho=oo)
+    assert ig["iters"] == io["iters"] == maxit
+    assert relerr(xg.cpu().numpy(), xo) <= 1e-9
+    assert ig["rel_res_true"] == pytest.approx(io["rel_res_true"], rel=1e-7, abs=1e-13)
+
+
 @pytest.mark.parametrize("n", [3, 17, 40])
 @pytest.mark.parametrize("maxit", [1, 7, 45])
 @pytest.mark.parametrize("mode", ["ebp", "proj"])

@@ -37,8 +37,8 @@ def _handle(N, orc, p, **opts):
     return s, to_dev(b)
 
 
-def _call(N, fn, s, b, m, tol, maxit):
-    x = torch.empty_like(b)
+def _call(N, fn, s, b, m, tol, maxit, x=None):
+    x = torch.empty_like(b) if x is None else x
     info = N.gmres_info()
     st = getattr(N.load(), fn)(s.handle, b.data_ptr(), None, m, tol, maxit, x.data_ptr(),
                                C.byref(info))
@@ -46,20 +46,27 @@ def _call(N, fn, s, b, m, tol, maxit):
     return st, x.cpu().numpy(), info.as_dict()
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_noalloc_matches_gmres_solve_twice(lib, orc, prec):
+@pytest.mark.parametrize("prec,dmode", [(0, 0), (1, 0), (2, 0), (0, 1)])
+def test_noalloc_matches_gmres_solve_twice(lib, orc, prec, dmode):
+    # precision 0/1/2: FP64, FP32 inner, BF16 basis; deflation 0/1: EBP, projector
     N = lib
     p = W.workload1()
-    s, b = _handle(N, orc, p, precision=prec)
+    s, b = _handle(N, orc, p, precision=prec, deflation_mode=dmode)
     tol = 1e-12 if prec == 0 else 1e-10
     st_ref, x_ref, i_ref = _call(N, "gmres_solve", s, b, 30, tol, 20000)
     assert st_ref == 0
-    for _ in range(2):  # two calls in a row share (and reuse) the static scratch
-        st, x, info = _call(N, "gmres_solve_noalloc", s, b, 30, tol, 20000)
+    xd = torch.empty_like(b)
+    torch.cuda.synchronize()
+    for call in range(2):  # two calls in a row share (and reuse) the static scratch
+        free0 = torch.cuda.mem_get_info()[0]
+        st, x, info = _call(N, "gmres_solve_noalloc", s, b, 30, tol, 20000, xd)
+        free1 = torch.cuda.mem_get_info()[0]
         assert st == 0, N.load().gmres_last_error(s.handle)
         assert info["iters"] == i_ref["iters"]
         assert relerr(x, x_ref) <= 1e-9
         assert info["rel_res_true"] <= tol
+        if call == 1:  # the call itself took no device memory (x is allocated before it)
+            assert free1 == free0
     s.close()
 
 
