@@ -166,7 +166,9 @@ typedef enum {
   GMRES_PH_PROJ_FINAL = 9,/* projector: x = xh + U T^-1 U^T (b - A xh) */
   GMRES_PH_ADAPT = 10,    /* adaptive deflation: the update of U, A U, T, T^-1 */
   GMRES_PH_MGS = 11,      /* modified Gram-Schmidt step: projections, ||w||, rotations */
-  GMRES_PH_COUNT = 12
+  GMRES_PH_ARNOLDI = 12,  /* a whole step in one kernel: SpMV, one-reduction MGS, ||w||,
+                             rotations (Eqs. 10, 12-14) */
+  GMRES_PH_COUNT = 13
 } gmres_phase;
 
 typedef struct {

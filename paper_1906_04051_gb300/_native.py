@@ -30,7 +30,7 @@ DEFL_EBP, DEFL_PROJECTOR, DEFL_NONE, DEFL_ADAPTIVE = 0, 1, 2, 3
 MU_RITZ_FIRST_CYCLE, MU_USER, MU_NORM_INF = 0, 1, 2
 ORTHO_CGS2, ORTHO_MGS, ORTHO_MGS_LOWSYNC = 0, 1, 2
 PHASES = ["setup", "residual", "spmv", "dot1", "upd1dot2", "upd2norm", "defl", "cycle_end",
-          "ritz", "proj_final", "adapt", "mgs"]
+          "ritz", "proj_final", "adapt", "mgs", "arnoldi"]
 
 
 class gmres_csr(C.Structure):

@@ -1243,6 +1243,12 @@ struct Kern {
         k_ritz<<<1, 32, 0, st>>>(a.ctl);
         nl = 1;
         break;
+      case PH_ARNOLDI: {  // the whole step in one persistent kernel (fused.cu)
+        const cudaError_t e = launch_arnoldi(a, j, defl, st);
+        if (e != cudaSuccess) return e;
+        nl = 1;
+        break;
+      }
       default:
         return cudaErrorInvalidValue;
     }

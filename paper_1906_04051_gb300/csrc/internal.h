@@ -110,6 +110,7 @@ enum Phase {
   PH_PROJ_FINAL,    // projector: x = xh + U T^-1 U^T (b - A xh)
   PH_ADAPT,         // adaptive deflation: update of U, A U, T, T^-1 after a cycle
   PH_MGS,           // modified Gram-Schmidt step (one cooperative kernel)
+  PH_ARNOLDI,       // a whole Arnoldi step in one persistent kernel (fused.cu)
   PH_COUNT
 };
 // c = M^T x over ncols FP64 columns of M (leading dimension ldm), pipelined multi-dot with
@@ -118,6 +119,10 @@ cudaError_t launch_udots(const CycleArgs& a, const double* M, long long ldm, int
                          const double* x, DotEpi epi, cudaStream_t st);
 cudaError_t launch_phase(const CycleArgs& a, int ph, int j, bool defl, double* x,
                          const double* b, cudaStream_t st, int* launches);
+// fused.cu: SpMV, one-reduction MGS projections, ||w|| and the rotations of step j in one
+// cooperative kernel (diagonal storage, EBP deflation or none, FP64 or FP32)
+bool arnoldi_fusable(const CycleArgs& a);
+cudaError_t launch_arnoldi(const CycleArgs& a, int j, bool defl, cudaStream_t st);
 // Control-block initialisation for a new solve.
 cudaError_t launch_init(const CycleArgs& a, double tol, double inner_tol, double r0ref,
                         double mu, int fixed, int mixed, long long maxit, cudaStream_t st);

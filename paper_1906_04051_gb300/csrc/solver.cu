@@ -103,6 +103,9 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
   const bool ada = h->opts.deflation_mode == GMRES_DEFL_ADAPTIVE;  // U grows from empty
   const bool dw = h->dense_r > 0;  // U from the caller's dense columns, fixed
   if (ada) h->aq = 0;
+  // the whole step in one persistent kernel where it applies (fused.cu)
+  const bool fused = !mgs && !ada && !dw && arnoldi_fusable(a);
+  if (fused) CK(h, cudaMemsetAsync(h->gbar.p, 0, 2 * sizeof(unsigned), st));
   const int mu_mode = h->opts.mu_mode;
   double mu = 0.0;
   if (mu_mode == GMRES_MU_USER) mu = std::fabs(h->opts.mu_user);
@@ -141,6 +144,11 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
     const long long left = maxit - h->hmeta->counts[C_STEPS];
     const int jmax = (int)(left < m ? left : m);
     for (int j = 0; j < jmax; ++j) {
+      if (fused) {
+        CK(h, phase(h, a, PH_ARNOLDI, j, defl_cycle, x, b));
+        if (defl_cycle) CK(h, phase(h, a, PH_DEFL, j + 1, true, x, b));
+        continue;
+      }
       CK(h, phase(h, a, PH_SPMV, j, defl_cycle, x, b));
       if (mgs) {
         CK(h, phase(h, a, PH_MGS, j, defl_cycle, x, b));

@@ -39,6 +39,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                : "memory");
 }
 
+// a plain arrival (consumer release of a stage)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // bytes (multiple of 16) from global src (16-byte aligned) to shared dst (16-byte
 // aligned); completion is counted on bar
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
