@@ -36,7 +36,10 @@ constexpr int kArnSliceCols = (kMaxK + kArnCW - 1) / kArnCW;  // 5 accumulators 
 constexpr int kArnMaxStages = 8;
 constexpr int kArnUnit = 256;                    // rows per unit of the row partition
 constexpr size_t kArnRing = 200 * 1024;          // the ring (dynamic shared memory)
-constexpr size_t kArnStageCap = 28 * 1024;       // preferred stage size (FP64 tiles)
+// preferred stage size: FP64 (bound by its FMA pipe) keeps 128-row tiles longer, so that a
+// tile's SpMV rows occupy four warps (one per scheduler); FP32 (bound by HBM) keeps stages
+// small enough for six or more in the ring
+template <typename TV> constexpr size_t arn_stage_cap() { return sizeof(TV) == 8 ? 48 * 1024 : 28 * 1024; }
 constexpr long long kArnSpins = 1LL << 21;       // polls of the barrier word: about a second
 constexpr int kArnNormCol = 2 * kMaxK;           // column of ctl.part holding the norm partials
 
@@ -46,10 +49,19 @@ struct ArnArgs {
   int units;      // ldv / kArnUnit
   int j, k, m;    // step, basis columns in use (j + 1), restart length
   int TR, S;      // tile rows, ring stages
-  int pre;        // the predecessor is the coarse solve: the SpMV's diagonal part and the
-                  // basis prefetch may run before the wait
+  int pre;        // the predecessor is the coarse solve: the basis and operator tiles may be
+                  // prefetched before the wait
   int defl;       // add the coarse correction A W s'
   unsigned stage_bytes;
+  // byte offsets of a stage's parts: basis tile (k columns), diagonals (nd), x windows,
+  // A W row pointers, A W columns, A W values, and w (computed in place)
+  unsigned offD, offX, offP, offC, offA, offW;
+  int awcap;      // A W entries reserved per stage (a multiple of 4)
+  int ng;         // x windows: groups of diagonals whose offsets lie close together
+  int wlo[kMaxDiag];   // window g starts at row r0 + wlo[g] (elements, 16-byte aligned)
+  int wlen[kMaxDiag];  // its length (elements, 16-byte multiple)
+  int woff[kMaxDiag];  // its place in the stage's window part (elements)
+  int gq[kMaxDiag + 1];  // diagonals gq[g] .. gq[g+1]-1 (sorted offsets) use window g
   long long ldv, ldd;
   const TV* V;    // basis, column-major (ldv)
   TACC* w;        // working vector
@@ -96,44 +108,53 @@ __device__ __forceinline__ bool arn_grid_sync(unsigned* bar, unsigned gen) {
   return s_ok != 0;
 }
 
-// Diagonal part of SpMV row i: sum_q dval[q][i] x[i + off_q] (index clamped to a valid
-// row, where the stored value is 0).
-template <typename TA, typename TV, typename TACC>
-__device__ __forceinline__ TACC arn_dia_row(long long i, int N, const int* soff, int nd,
-                                            long long ldd, const TA* __restrict__ dval,
-                                            const TV* __restrict__ x) {
-  TACC acc0 = 0, acc1 = 0;
-  int q = 0;
-  for (; q + 3 < nd; q += 4) {
-    TACC av[4], xv[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const long long c = min(max(i + soff[q + u], 0LL), (long long)N - 1);
-      av[u] = (TACC)__ldg(dval + (size_t)(q + u) * ldd + i);
-      xv[u] = ld_as<TACC, TV>(x + c);
-    }
-    acc0 += av[0] * xv[0];
-    acc1 += av[1] * xv[1];
-    acc0 += av[2] * xv[2];
-    acc1 += av[3] * xv[3];
+// Barrier of the first nthreads threads on named barrier id, returning the AND of v.
+__device__ __forceinline__ bool bar_and(int id, int nthreads, bool v) {
+  int r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred p, %2, %3, q;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"((int)v), "r"(id), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+
+// Copy range of x window g for the tile at row r0: [cs, ce) clamped into [0, ldv) and
+// never shorter than one 16-byte chunk (E elements), placed at element dpos of the window's
+// part of the stage.  Element i of x is then read at  xb + clamp(i, cs, ce - 1), with
+// xb = woff + dpos - cs: outside [0, n) the diagonal entries are 0, so the clamped (finite)
+// value they meet contributes nothing.
+struct ArnWin {
+  long long cs, ce;
+  long long xb;
+};
+
+__host__ __device__ __forceinline__ ArnWin arn_win(int wlo, int wlen, int woff, long long r0,
+                                                   long long ldv, int E) {
+  const long long start = r0 + wlo, end = start + wlen;
+  ArnWin w;
+  w.cs = start < 0 ? 0 : start;
+  w.ce = end > ldv ? ldv : end;
+  long long dpos = w.cs - start;
+  if (w.ce - w.cs < E) {  // (almost) outside [0, ldv): one chunk at the window's start
+    w.cs = start < 0 ? 0 : ldv - E;
+    w.ce = w.cs + E;
+    dpos = 0;
   }
-  for (; q < nd; ++q) {
-    const long long c = min(max(i + soff[q], 0LL), (long long)N - 1);
-    acc0 += (TACC)__ldg(dval + (size_t)q * ldd + i) * ld_as<TACC, TV>(x + c);
-  }
-  return acc0 + acc1;
+  w.xb = woff + dpos - w.cs;
+  return w;
 }
 
 // Multi-dot of one stage by consumer warp `sl` (columns sl, sl + 16, ...; NW of them):
 // acc += V_c . w and acc2 += V_c . u_j over the stage's TR rows.
 template <int NW, typename TV, typename TACC>
 __device__ __forceinline__ void arn_dots(TACC (&acc)[kArnSliceCols], TACC (&acc2)[kArnSliceCols],
-                                         const unsigned char* st, int k, int TR, int sl,
-                                         int lane) {
+                                         const unsigned char* st, const TACC* sw, int k, int TR,
+                                         int sl, int lane) {
   constexpr int VN = ArnVec<TV>::n;
   const TV* sV = reinterpret_cast<const TV*>(st);
   const TV* su = sV + (size_t)(k - 1) * TR;
-  const TACC* sw = reinterpret_cast<const TACC*>(st + (size_t)k * TR * sizeof(TV));
   for (int r = lane * VN; r < TR; r += 32 * VN) {
     TACC wv[VN], uv[VN];
     ld_acc<VN>(sw + r, wv);
@@ -220,13 +241,13 @@ template <typename TV, typename TACC>
 __global__ void __launch_bounds__(kArnThreads, 1)
     k_arnoldi(const __grid_constant__ ArnArgs<TV, TACC> a) {
   constexpr int VN = ArnVec<TV>::n;
+  constexpr int E = 16 / (int)sizeof(TV);  // elements per 16-byte chunk of x
   extern __shared__ __align__(128) unsigned char ring[];
   __shared__ uint64_t full[kArnMaxStages], empty[kArnMaxStages];
   __shared__ double tot[2 * kMaxK + 1];
   __shared__ double sred[2 * kMaxK];
   __shared__ double sg[kMaxK];
   __shared__ TACC scoef[kMaxK];
-  __shared__ int soff[kMaxDiag];
   __shared__ double snrm[kArnThreads / 32];
   __shared__ unsigned s_last;
   Ctl ctl = a.ctl;
@@ -236,10 +257,9 @@ __global__ void __launch_bounds__(kArnThreads, 1)
   const int G = gridDim.x, bid = blockIdx.x;
   const long long R0 = (long long)bid * a.units / G * kArnUnit;
   const long long R1 = (long long)(bid + 1) * a.units / G * kArnUnit;
-  const int k = a.k, TR = a.TR, S = a.S;
+  const int k = a.k, TR = a.TR, S = a.S, nd = a.dia.nd;
   const int nt = (int)((R1 - R0) / TR);
   const int N = a.N;
-  const long long Rn = R1 < N ? R1 : N;  // rows of A in this block's range
 
   if (!a.pre) {
     pdl_wait();
@@ -256,7 +276,6 @@ __global__ void __launch_bounds__(kArnThreads, 1)
     return;
   }
   const unsigned gen = *(volatile unsigned*)&a.gbar[1];  // advanced only once all arrive
-  if (threadIdx.x < kMaxDiag) soff[threadIdx.x] = a.dia.off[threadIdx.x];
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
@@ -267,43 +286,14 @@ __global__ void __launch_bounds__(kArnThreads, 1)
   __syncthreads();
 
   const TV* xj = a.V + (size_t)a.j * a.ldv;
-  const uint32_t vbytes = (uint32_t)(TR * sizeof(TV)), wbytes = (uint32_t)(TR * sizeof(TACC));
+  const uint32_t vbytes = (uint32_t)(TR * sizeof(TV)), dbytes = (uint32_t)(TR * sizeof(TACC));
   auto stage = [&](int s) { return ring + (size_t)s * a.stage_bytes; };
-  const int first = nt < S ? nt : S;
-  // ---- 1. SpMV (producer: the first stages' basis columns meanwhile) ----------------
-  if (prod) {
-    if (lane == 0)
-      for (int i = 0; i < first; ++i) mbar_arrive_expect_tx(&full[i], (uint32_t)k * vbytes + wbytes);
-    __syncwarp();
-    for (int i = 0; i < first; ++i) {
-      const long long r0 = R0 + (long long)i * TR;
-      TV* dst = reinterpret_cast<TV*>(stage(i));
-      for (int c = lane; c < k; c += 32)
-        bulk_g2s(dst + (size_t)c * TR, a.V + (size_t)c * a.ldv + r0, vbytes, &full[i]);
-    }
-  } else {
-    const TACC sig = (TACC)__ldcg(&ctl.sigma[a.j]);
-    for (long long i = R0 + ct; i < Rn; i += kArnCW * 32) {
-      const TACC v = arn_dia_row<TACC, TV, TACC>(i, N, soff, a.dia.nd, a.ldd, a.dval, xj);
-      a.w[i] = a.defl ? v : sig * v;
-    }
-  }
-  if (a.pre) {
-    pdl_wait();
-    pdl_trigger();
-  }
-  if (!prod) {
-    if (a.defl) {  // + A W s' (s' from the coarse solve), then the scale sigma_j
-      const TACC sig = (TACC)__ldcg(&ctl.sigma[a.j]);
-      for (long long i = R0 + ct; i < Rn; i += kArnCW * 32)
-        a.w[i] = sig * (a.w[i] + au_row<TACC, TACC>((int)i, a.aurp, a.aucol, a.auval, a.sdefl));
-    }
-    // the slices of w are read below by the bulk-copy (async) proxy
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-  }
-  __syncthreads();
 
-  // ---- 2. multi-dot over the ring ---------------------------------------------------
+  // ---- 1-2. SpMV and multi-dot, tile by tile, from the ring ------------------------
+  // Stage of tile i (rows r0 .. r0 + TR): the basis tile (columns 0..k-1), the diagonals,
+  // the x windows and the A W rows, all copied by the producer warp; the consumers form
+  // w for the tile's rows in the stage (and in global memory for the update), meet at a
+  // named barrier, and run the multi-dot.
   TACC acc[kArnSliceCols], acc2[kArnSliceCols];
 #pragma unroll
   for (int i = 0; i < kArnSliceCols; ++i) {
@@ -312,33 +302,116 @@ __global__ void __launch_bounds__(kArnThreads, 1)
   }
   bool ok = true;
   if (prod) {
-    if (lane == 0)
-      for (int i = 0; i < first; ++i)
-        bulk_g2s(stage(i) + (size_t)k * vbytes, a.w + R0 + (long long)i * TR, wbytes, &full[i]);
-    for (int i = first; i < nt; ++i) {
-      const int s = i % S;
-      // stage s was last used by tile i - S: all consumer warps must have released it
-      if (!mbar_wait(&empty[s], (uint32_t)(((i / S) - 1) & 1))) {
-        ok = false;
-        break;
-      }
-      const long long r0 = R0 + (long long)i * TR;
-      if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)k * vbytes + wbytes);
-      __syncwarp();
-      TV* dst = reinterpret_cast<TV*>(stage(s));
-      for (int c = lane; c < k; c += 32)
-        bulk_g2s(dst + (size_t)c * TR, a.V + (size_t)c * a.ldv + r0, vbytes, &full[s]);
-      if (lane == 0) bulk_g2s(stage(s) + (size_t)k * vbytes, a.w + r0, wbytes, &full[s]);
-    }
-  } else {
-    const int nw = slice_cols(k, warp, kArnCW);
+    // A W row pointers at the tile boundaries, 32 tiles per refresh (lane l: tile base + l)
+    int ap0 = 0, ap1 = 0, abase_tile = -32;
     for (int i = 0; i < nt; ++i) {
       const int s = i % S;
-      if (!mbar_wait(&full[s], (uint32_t)((i / S) & 1))) {
+      if (i >= S) {  // stage s was last used by tile i - S: all consumer warps released it
+        if (!mbar_wait(&empty[s], (uint32_t)(((i / S) - 1) & 1))) {
+          ok = false;
+          break;
+        }
+      }
+      const long long r0 = R0 + (long long)i * TR;
+      int abase = 0, acnt = 0;
+      if (a.defl) {
+        if (i - abase_tile >= 32) {
+          abase_tile = i;
+          const long long t0 = R0 + (long long)(i + lane) * TR, t1 = t0 + TR;
+          ap0 = __ldg(a.aurp + (t0 < R1 ? t0 : R1));
+          ap1 = __ldg(a.aurp + (t1 < R1 ? t1 : R1));
+        }
+        const int e0 = __shfl_sync(0xffffffffu, ap0, i - abase_tile);
+        const int e1 = __shfl_sync(0xffffffffu, ap1, i - abase_tile);
+        abase = e0 & ~3;
+        acnt = (e1 - abase + 3) & ~3;
+      }
+      unsigned char* st = stage(s);
+      if (lane == 0) {
+        uint32_t bytes = (uint32_t)k * vbytes + (uint32_t)nd * dbytes;
+        for (int g = 0; g < a.ng; ++g) {
+          const ArnWin wg = arn_win(a.wlo[g], a.wlen[g], a.woff[g], r0, a.ldv, E);
+          bytes += (uint32_t)((wg.ce - wg.cs) * (long long)sizeof(TV));
+        }
+        if (a.defl)
+          bytes += (uint32_t)((TR + 4) * sizeof(int)) +
+                   (uint32_t)acnt * (uint32_t)(sizeof(int) + sizeof(TACC));
+        mbar_arrive_expect_tx(&full[s], bytes);
+      }
+      __syncwarp();
+      for (int c = lane; c < k; c += 32)
+        bulk_g2s(st + (size_t)c * vbytes, a.V + (size_t)c * a.ldv + r0, vbytes, &full[s]);
+      for (int q = lane; q < nd; q += 32)
+        bulk_g2s(st + a.offD + (size_t)q * dbytes, a.dval + (size_t)q * a.ldd + r0, dbytes,
+                 &full[s]);
+      for (int g = lane; g < a.ng; g += 32) {
+        const ArnWin wg = arn_win(a.wlo[g], a.wlen[g], a.woff[g], r0, a.ldv, E);
+        bulk_g2s(st + a.offX + (size_t)(wg.xb + wg.cs) * sizeof(TV), xj + wg.cs,
+                 (uint32_t)((wg.ce - wg.cs) * (long long)sizeof(TV)), &full[s]);
+      }
+      if (a.defl) {
+        if (lane == 0)
+          bulk_g2s(st + a.offP, a.aurp + r0, (uint32_t)((TR + 4) * sizeof(int)), &full[s]);
+        if (lane == 1 && acnt > 0)
+          bulk_g2s(st + a.offC, a.aucol + abase, (uint32_t)(acnt * sizeof(int)), &full[s]);
+        if (lane == 2 && acnt > 0)
+          bulk_g2s(st + a.offA, a.auval + abase, (uint32_t)(acnt * sizeof(TACC)), &full[s]);
+      }
+    }
+  } else {
+    if (a.pre) {  // s' (the coarse solve's output) is read below
+      pdl_wait();
+      pdl_trigger();
+    }
+    const int nw = slice_cols(k, warp, kArnCW);
+    const TACC sig = (TACC)__ldcg(&ctl.sigma[a.j]);
+    for (int i = 0; i < nt; ++i) {
+      const int s = i % S;
+      const bool okw = mbar_wait(&full[s], (uint32_t)((i / S) & 1));
+      const unsigned char* st = stage(s);
+      TACC* sw = reinterpret_cast<TACC*>(const_cast<unsigned char*>(st) + a.offW);
+      const long long r0 = R0 + (long long)i * TR;
+      if (okw && ct < TR) {  // row r0 + ct of w = sigma_j (A u_j + A W s')
+        const long long row = r0 + ct;
+        TACC v = 0;
+        if (row < N) {
+          const TACC* sD = reinterpret_cast<const TACC*>(st + a.offD);
+          const TV* sX = reinterpret_cast<const TV*>(st + a.offX);
+          TACC p0 = 0, p1 = 0;
+          int q = 0;
+          for (int g = 0; g < a.ng; ++g) {
+            const ArnWin wg = arn_win(a.wlo[g], a.wlen[g], a.woff[g], r0, a.ldv, E);
+            const int qe = a.gq[g + 1];
+            for (; q < qe; ++q) {
+              long long xi = row + a.dia.off[q];
+              xi = xi < wg.cs ? wg.cs : (xi >= wg.ce ? wg.ce - 1 : xi);
+              const TACC t = sD[(size_t)q * TR + ct] * cv<TACC, TV>(sX[wg.xb + xi]);
+              if (q & 1) p1 += t;
+              else p0 += t;
+            }
+          }
+          v = p0 + p1;
+          if (a.defl) {
+            const int* sP = reinterpret_cast<const int*>(st + a.offP);
+            const int* sC = reinterpret_cast<const int*>(st + a.offC);
+            const TACC* sA = reinterpret_cast<const TACC*>(st + a.offA);
+            const int ab = sP[0] & ~3;
+            const int e1 = sP[ct + 1] - ab;
+            TACC aw = 0;
+            for (int e = sP[ct] - ab; e < e1; ++e) aw += sA[e] * __ldg(a.sdefl + sC[e]);
+            v += aw;
+          }
+          v *= sig;
+          a.w[row] = v;
+        }
+        sw[ct] = v;  // rows past n stay 0
+      }
+      // the tile's w is complete; every consumer warp learns whether all copies arrived
+      if (!bar_and(1, kArnCW * 32, okw)) {
         ok = false;
         break;
       }
-#define GG_ARN_DOTS(NW) arn_dots<NW, TV, TACC>(acc, acc2, stage(s), k, TR, warp, lane)
+#define GG_ARN_DOTS(NW) arn_dots<NW, TV, TACC>(acc, acc2, st, sw, k, TR, warp, lane)
       GG_ARN_SWITCH(nw, GG_ARN_DOTS)
 #undef GG_ARN_DOTS
       __syncwarp();
@@ -495,18 +568,64 @@ __global__ void __launch_bounds__(kArnThreads, 1)
 
 template <typename TV, typename TACC>
 struct Arn {
-  static size_t stage_bytes(int k, int TR) {
-    return ((size_t)k * TR * sizeof(TV) + (size_t)TR * sizeof(TACC) + 127) / 128 * 128;
+  struct Layout {
+    int TR, S, ng, awcap;
+    unsigned offD, offX, offP, offC, offA, offW, bytes;
+    int wlo[kMaxDiag], wlen[kMaxDiag], woff[kMaxDiag], gq[kMaxDiag + 1];
+  };
+  static unsigned up(size_t b) { return (unsigned)((b + 127) / 128 * 128); }
+  // x windows: diagonals whose sorted offsets lie within kArnGap of the previous one share
+  // a window; for tile rows TR, window g covers rows [r0 + wlo, r0 + wlo + wlen)
+  static Layout layout(const CycleArgs& c, int k, int TR, bool defl, int au_tile_max) {
+    constexpr int E = 16 / (int)sizeof(TV);
+    constexpr int kArnGap = 32;
+    Layout L{};
+    L.TR = TR;
+    const DiaOffsets& d = c.op.dia;
+    int woff = 0;
+    for (int q = 0; q < d.nd;) {
+      int qe = q + 1;
+      while (qe < d.nd && d.off[qe] - d.off[qe - 1] <= kArnGap) ++qe;
+      const int lo = d.off[q], hi = d.off[qe - 1];
+      auto fdiv = [](int a, int b) { return (a >= 0 ? a / b : -((-a + b - 1) / b)); };
+      const int wlo = fdiv(lo, E) * E;
+      const int whi = fdiv(TR + hi + E - 1, E) * E;
+      L.wlo[L.ng] = wlo;
+      L.wlen[L.ng] = whi - wlo;
+      L.woff[L.ng] = woff;
+      L.gq[L.ng] = q;
+      woff += whi - wlo;
+      ++L.ng;
+      q = qe;
+    }
+    L.gq[L.ng] = d.nd;
+    L.awcap = defl ? (au_tile_max + 8 + 3) / 4 * 4 : 0;
+    size_t off = up((size_t)k * TR * sizeof(TV));
+    L.offD = (unsigned)off;
+    off += up((size_t)d.nd * TR * sizeof(TACC));
+    L.offX = (unsigned)off;
+    off += up((size_t)woff * sizeof(TV));
+    L.offP = (unsigned)off;
+    off += defl ? up((size_t)(TR + 4) * sizeof(int)) : 0;
+    L.offC = (unsigned)off;
+    off += up((size_t)L.awcap * sizeof(int));
+    L.offA = (unsigned)off;
+    off += up((size_t)L.awcap * sizeof(TACC));
+    L.offW = (unsigned)off;
+    off += up((size_t)TR * sizeof(TACC));
+    L.bytes = (unsigned)off;
+    const int S = (int)(kArnRing / off);
+    L.S = S > kArnMaxStages ? kArnMaxStages : S;
+    return L;
   }
-  // tile rows: FP64 keeps stages near kArnStageCap (its passes are bound by the FP64 pipe,
-  // so more stages matter less than short tiles); FP32 and BF16 take 256-row tiles, which
-  // keeps every lane of a slice busy (32 lanes x 4 or 8 rows of a 16-byte load)
-  static int tile_rows(int k) {
-    constexpr int lo = 2 * 32 * ArnVec<TV>::n;  // two row sweeps of a warp at least
-    int tr = kArnUnit;
-    if (sizeof(TV) == 8)
-      while (tr > lo && stage_bytes(k, tr) > kArnStageCap) tr >>= 1;
-    return tr < lo ? lo : tr;
+  // tile rows: the largest of 256 / 128 / 64 whose stage fits the cap, and at least one
+  // full sweep of a warp (32 lanes x one 16-byte vector)
+  static Layout pick(const CycleArgs& c, int k, bool defl, int au_tile_max) {
+    constexpr int lo = 32 * ArnVec<TV>::n;
+    Layout L = layout(c, k, kArnUnit, defl, au_tile_max);
+    for (int tr = kArnUnit / 2; tr >= lo && L.bytes > arn_stage_cap<TV>(); tr >>= 1)
+      L = layout(c, k, tr, defl, au_tile_max);
+    return L;
   }
   static cudaError_t prepare() {
     return cudaFuncSetAttribute(k_arnoldi<TV, TACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -516,16 +635,30 @@ struct Arn {
     static cudaError_t prep = prepare();
     if (prep != cudaSuccess) return prep;
     ArnArgs<TV, TACC> p{};
+    const Layout L = pick(c, j + 1, defl, c.op.au_tile_max);
+    if (L.S < 2) return cudaErrorInvalidValue;  // arnoldi_fusable keeps this from happening
     p.N = c.op.n;
     p.units = (int)(c.ldv / kArnUnit);
     p.j = j;
     p.k = j + 1;
     p.m = c.m;
-    p.TR = tile_rows(p.k);
-    const size_t sb = stage_bytes(p.k, p.TR);
-    int S = (int)(kArnRing / sb);
-    p.S = S > kArnMaxStages ? kArnMaxStages : S;
-    p.stage_bytes = (unsigned)sb;
+    p.TR = L.TR;
+    p.S = L.S;
+    p.stage_bytes = L.bytes;
+    p.offD = L.offD;
+    p.offX = L.offX;
+    p.offP = L.offP;
+    p.offC = L.offC;
+    p.offA = L.offA;
+    p.offW = L.offW;
+    p.awcap = L.awcap;
+    p.ng = L.ng;
+    for (int g = 0; g < L.ng; ++g) {
+      p.wlo[g] = L.wlo[g];
+      p.wlen[g] = L.wlen[g];
+      p.woff[g] = L.woff[g];
+    }
+    for (int g = 0; g <= L.ng; ++g) p.gq[g] = L.gq[g];
     p.pre = (defl && c.pdl) ? 1 : 0;
     p.defl = defl ? 1 : 0;
     p.ldv = c.ldv;
@@ -576,9 +709,14 @@ struct Arn {
 }  // namespace
 
 bool arnoldi_fusable(const CycleArgs& a) {
-  return a.ortho == GMRES_ORTHO_MGS_LOWSYNC && a.op.dia.nd > 0 && !a.proj &&
-         a.op.defl.qd == 0 && a.ldv % kArnUnit == 0 && a.m + 1 <= kMaxK &&
-         (a.prec == P_FP64 || a.prec == P_FP32);
+  if (!(a.ortho == GMRES_ORTHO_MGS_LOWSYNC && a.op.dia.nd > 0 && !a.proj &&
+        a.op.defl.qd == 0 && a.ldv % kArnUnit == 0 && a.m + 1 <= kMaxK &&
+        a.op.ldd % kArnUnit == 0 && (a.prec == P_FP64 || a.prec == P_FP32)))
+    return false;
+  // the widest stage (k = m + 1 columns) must leave a ring of at least two stages
+  const bool defl = a.op.defl.r > 0;
+  if (a.prec == P_FP64) return Arn<double, double>::pick(a, a.m + 1, defl, a.op.au_tile_max).S >= 2;
+  return Arn<float, float>::pick(a, a.m + 1, defl, a.op.au_tile_max).S >= 2;
 }
 
 cudaError_t launch_arnoldi(const CycleArgs& a, int j, bool defl, cudaStream_t st) {

@@ -51,6 +51,7 @@ struct OpHost {
   DevMem xrp, xcol, xval, xval32;      // [A | A W] rows (deflated SpMV of a step)
   DevMem dval, dval32;                 // diagonal storage (banded operators)
   long long nau = 0;                   // entries of A W
+  int au_tile_max = 0;                 // most A W entries in a tile of 256 rows
   DiaOffsets dia{};
   long long ldd = 0;
   bool ready = false;
@@ -232,7 +233,8 @@ inline gmres_status build_dia(gmres_s* h, OpHost& o) {
     if (hs[i] != dia_empty_slot()) offs.off[offs.nd++] = hs[i];
   std::sort(offs.off, offs.off + offs.nd);
   if ((double)h->nnz < 0.8 * (double)offs.nd * (double)n) return GMRES_OK;
-  const long long ldd = ((long long)n + 31) / 32 * 32;
+  // rows padded to 256 (kernels copy whole 256-row-aligned tiles of the diagonals)
+  const long long ldd = ((long long)n + 255) / 256 * 256;
   const size_t cnt = (size_t)offs.nd * (size_t)ldd;
   CK(h, o.dval.ensure(sizeof(double) * cnt));
   CK(h, cudaMemsetAsync(o.dval.p, 0, sizeof(double) * cnt, st));
@@ -256,14 +258,21 @@ inline gmres_status build_au(gmres_s* h, OpHost& o) {
   DevMem cnt, bsum;
   CK(h, cnt.ensure(sizeof(int) * (size_t)n));
   CK(h, bsum.ensure(sizeof(int) * (size_t)(au_scan_blocks(n) + 1)));
-  CK(h, o.aurp.ensure(sizeof(int) * (size_t)(n + 1)));
+  // row pointers padded past n up to whole 256-row tiles (+ 8): tile copies stay defined
+  const long long ptot = ((long long)n + 255) / 256 * 256 + 8;
+  CK(h, o.aurp.ensure(sizeof(int) * (size_t)ptot));
   CK(h, launch_au_rows(n, o.rowptr.as<int>(), o.col.as<int>(), h->agg.as<int>(), cnt.as<int>(),
                        bsum.as<int>(), o.aurp.as<int>(), st));
-  int nau = 0;
-  CK(h, cudaMemcpyAsync(&nau, o.aurp.as<int>() + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(h, launch_au_tiles(n, ptot, 256, o.aurp.as<int>(), bsum.as<int>(), st));
+  int hv[2] = {0, 0};
+  CK(h, cudaMemcpyAsync(&hv[0], o.aurp.as<int>() + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaMemcpyAsync(&hv[1], bsum.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(h, cudaStreamSynchronize(st));
+  const int nau = hv[0];
   o.nau = nau;
-  const size_t cap = nau > 0 ? (size_t)nau : 1;
+  o.au_tile_max = hv[1];
+  // 8 entries of slack: tile copies round their range out to 16-byte boundaries
+  const size_t cap = (size_t)nau + 8;
   CK(h, o.aucol.ensure(sizeof(int) * cap));
   CK(h, o.auval.ensure(sizeof(double) * cap));
   if (h->opts.precision != GMRES_FP64) CK(h, o.auval32.ensure(sizeof(float) * cap));
@@ -317,6 +326,7 @@ inline OpDev make_op(gmres_s* h, OpHost& o) {
   op.xval = o.xval.as<double>();
   op.xval32 = o.xval32.as<float>();
   op.vec = (o.dia.nd == 0 && h->nnz >= (long long)kVecMinRowLen * h->n) ? kVecLanes : 0;
+  op.au_tile_max = o.au_tile_max;
   return op;
 }
 

@@ -41,6 +41,10 @@ cudaError_t launch_to_float(long long n, const double* a, float* b, cudaStream_t
 int au_scan_blocks(int n);
 cudaError_t launch_au_rows(int n, const int* rowptr, const int* col, const int* agg, int* cnt,
                            int* bsum, int* aurp, cudaStream_t st);
+// A W row pointers padded with nau to `total` entries; *tmax = most entries per tile of
+// `unit` rows
+cudaError_t launch_au_tiles(int n, long long total, int unit, int* aurp, int* tmax,
+                            cudaStream_t st);
 cudaError_t launch_au_fill(int n, const int* rowptr, const int* col, const double* val,
                            const int* agg, const int* aurp, int* aucol, double* auval,
                            float* auval32, cudaStream_t st);
@@ -77,6 +81,7 @@ struct OpDev {           // one operator (A or A^T) as the kernels see it
   const float* xval32;
   // lanes per row of the CSR SpMV (0: a thread per row); set for long rows
   int vec;
+  int au_tile_max;       // most A W entries in a tile of 256 rows
 };
 
 struct CycleArgs {

@@ -687,6 +687,32 @@ namespace gg {
 
 int au_scan_blocks(int n) { return (n + kScanBlock - 1) / kScanBlock; }
 
+namespace {
+// Row pointers of A W past n set to nau (up to `total` entries), so that kernels copying
+// whole tiles of rows read defined values; tmax = the most A W entries in any tile of
+// `unit` rows.
+__global__ void k_au_tiles(int n, long long total, int unit, int* __restrict__ aurp,
+                           int* __restrict__ tmax) {
+  const int nau = aurp[n];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (long long i = t0; i < total; i += stride)
+    if (i > n) aurp[i] = nau;
+  for (long long t = t0; t * unit < n; t += stride) {
+    const long long e = (t + 1) * unit < n ? (t + 1) * unit : n;
+    atomicMax(tmax, aurp[e] - aurp[t * unit]);
+  }
+}
+}  // namespace
+
+cudaError_t launch_au_tiles(int n, long long total, int unit, int* aurp, int* tmax,
+                            cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(tmax, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_au_tiles<<<grid_for(total, 256, 152 * 8), 256, 0, st>>>(n, total, unit, aurp, tmax);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_au_rows(int n, const int* rowptr, const int* col, const int* agg,
                            int* cnt /* n */, int* bsum /* blocks + 1 */, int* aurp /* n + 1 */,
                            cudaStream_t st) {
