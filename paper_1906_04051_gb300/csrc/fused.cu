@@ -3,23 +3,28 @@
 // projections (Eq. 13) in their one-reduction form, ||w|| and the plane rotations with the
 // stopping tests (Eqs. 12, 14).
 //
-// One block per multiprocessor, launched cooperatively (every block resident).  Block b
-// owns a contiguous range of rows (a multiple of 256) for the whole step:
-//   1. SpMV of its rows into w (diagonal storage; the coarse correction through the A W
-//      rows).  With deflation the diagonal part runs before the programmatic-launch wait,
-//      overlapping the coarse solve that produces s'.
-//   2. Multi-dot over the basis tiles of its rows: g = V^T w and the new row of L
-//      (u_j . u_c), by 16 consumer warps (one column slice each) from a ring of
-//      shared-memory stages that a producer warp fills with bulk asynchronous copies; each
-//      stage has a full and an empty mbarrier, so no block barrier sits in the loop.
+// One block of 16 warps per multiprocessor, launched cooperatively (every block resident).
+// Block b owns a contiguous range of rows (a multiple of 256) for the whole step, taken in
+// super-tiles of at most RS rows whose slices of w and u_j stay in shared memory:
+//   1. SpMV of the super-tile's rows (diagonal storage; the coarse correction through the
+//      A W rows, s' staged in shared memory): w into shared memory and global memory, u_j
+//      next to it.  With deflation the diagonal part of the first super-tile runs before
+//      the programmatic-launch wait, overlapping the coarse solve that produces s'.
+//   2. Multi-dot g = V^T w and the new row of L (u_j . u_c): warp s owns the columns
+//      s, s + 16, ... and streams them from HBM with 16-byte loads, several chunks of rows
+//      in flight per lane (a register pipeline), against the shared-memory slices.
 //   3. Grid barrier; every block adds the G partial sums in the same order (identical
 //      totals in every block) and solves (I + L) h = g itself.
-//   4. Update of its rows, u_{j+1} = w - V (sigma o h): each lane owns rows and reads the
-//      basis straight from global memory, in the reverse order of step 2 so that the
-//      tiles read last are still in L2; partial sums of ||u_{j+1}||^2.
+//   4. Update of its rows, u_{j+1} = w - V (sigma o h), each lane owning rows and reading
+//      the basis straight from HBM, in the reverse order of step 2 (the columns read last
+//      are the likeliest to be in L2); partial sums of ||u_{j+1}||^2.
 //   5. The last block to finish (ticket counter) adds the norm partials and applies the
 //      plane rotations and stopping tests (Eqs. 12, 14).
 // Every reduction is formed in a fixed order: runs are bitwise reproducible.
+//
+// The basis is streamed with plain vectorised loads rather than bulk asynchronous copies:
+// measured on GB300, a multiprocessor fed by bulk copies reached about 10 bytes per clock,
+// against the 22 that the HBM copy bandwidth asks of each of the 152.
 #include <type_traits>
 #include <utility>
 
@@ -30,38 +35,29 @@ namespace gg {
 
 namespace {
 
-constexpr int kArnCW = 16;                       // consumer warps (one column slice each)
-constexpr int kArnThreads = (kArnCW + 1) * 32;   // plus the producer warp
-constexpr int kArnSliceCols = (kMaxK + kArnCW - 1) / kArnCW;  // 5 accumulators per set
-constexpr int kArnMaxStages = 8;
+constexpr int kArnWarps = 16;
+constexpr int kArnThreads = kArnWarps * 32;
+constexpr int kArnSliceCols = (kMaxK + kArnWarps - 1) / kArnWarps;  // 5 accumulators per set
 constexpr int kArnUnit = 256;                    // rows per unit of the row partition
-constexpr size_t kArnRing = 200 * 1024;          // the ring (dynamic shared memory)
-// preferred stage size: FP64 (bound by its FMA pipe) keeps 128-row tiles longer, so that a
-// tile's SpMV rows occupy four warps (one per scheduler); FP32 (bound by HBM) keeps stages
-// small enough for six or more in the ring
-template <typename TV> constexpr size_t arn_stage_cap() { return sizeof(TV) == 8 ? 48 * 1024 : 28 * 1024; }
+constexpr size_t kArnSmem = 220 * 1024;          // dynamic shared memory
+constexpr size_t kArnScratch = 2 * kArnWarps * kArnSliceCols * 33 * sizeof(double);  // reductions
 constexpr long long kArnSpins = 1LL << 21;       // polls of the barrier word: about a second
 constexpr int kArnNormCol = 2 * kMaxK;           // column of ctl.part holding the norm partials
+constexpr int kArnAwRows = 12;                   // rows per thread of an A W gather batch
+// 16-byte basis loads in flight per lane in the multi-dot: FP32 (bound by HBM) asks for
+// more bytes in flight than FP64 (bound by its FMA pipe)
+template <typename TV> constexpr int arn_loads() { return sizeof(TV) == 8 ? 8 : 12; }
 
 template <typename TV, typename TACC>
 struct ArnArgs {
   int N;          // rows of A
   int units;      // ldv / kArnUnit
   int j, k, m;    // step, basis columns in use (j + 1), restart length
-  int TR, S;      // tile rows, ring stages
-  int pre;        // the predecessor is the coarse solve: the basis and operator tiles may be
-                  // prefetched before the wait
+  int pre;        // the predecessor is the coarse solve: the diagonal part of the SpMV may
+                  // run before the wait
   int defl;       // add the coarse correction A W s'
-  unsigned stage_bytes;
-  // byte offsets of a stage's parts: basis tile (k columns), diagonals (nd), x windows,
-  // A W row pointers, A W columns, A W values, and w (computed in place)
-  unsigned offD, offX, offP, offC, offA, offW;
-  int awcap;      // A W entries reserved per stage (a multiple of 4)
-  int ng;         // x windows: groups of diagonals whose offsets lie close together
-  int wlo[kMaxDiag];   // window g starts at row r0 + wlo[g] (elements, 16-byte aligned)
-  int wlen[kMaxDiag];  // its length (elements, 16-byte multiple)
-  int woff[kMaxDiag];  // its place in the stage's window part (elements)
-  int gq[kMaxDiag + 1];  // diagonals gq[g] .. gq[g+1]-1 (sorted offsets) use window g
+  int r;          // aggregates (entries of s')
+  int RS;         // rows per super-tile (a multiple of kArnUnit)
   long long ldv, ldd;
   const TV* V;    // basis, column-major (ldv)
   TACC* w;        // working vector
@@ -108,90 +104,58 @@ __device__ __forceinline__ bool arn_grid_sync(unsigned* bar, unsigned gen) {
   return s_ok != 0;
 }
 
-// Barrier of the first nthreads threads on named barrier id, returning the AND of v.
-__device__ __forceinline__ bool bar_and(int id, int nthreads, bool v) {
-  int r;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred p, %2, %3, q;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(r)
-      : "r"((int)v), "r"(id), "r"(nthreads)
-      : "memory");
-  return r != 0;
-}
-
-// Copy range of x window g for the tile at row r0: [cs, ce) clamped into [0, ldv) and
-// never shorter than one 16-byte chunk (E elements), placed at element dpos of the window's
-// part of the stage.  Element i of x is then read at  xb + clamp(i, cs, ce - 1), with
-// xb = woff + dpos - cs: outside [0, n) the diagonal entries are 0, so the clamped (finite)
-// value they meet contributes nothing.
-struct ArnWin {
-  long long cs, ce;
-  long long xb;
-};
-
-__host__ __device__ __forceinline__ ArnWin arn_win(int wlo, int wlen, int woff, long long r0,
-                                                   long long ldv, int E) {
-  const long long start = r0 + wlo, end = start + wlen;
-  ArnWin w;
-  w.cs = start < 0 ? 0 : start;
-  w.ce = end > ldv ? ldv : end;
-  long long dpos = w.cs - start;
-  if (w.ce - w.cs < E) {  // (almost) outside [0, ldv): one chunk at the window's start
-    w.cs = start < 0 ? 0 : ldv - E;
-    w.ce = w.cs + E;
-    dpos = 0;
-  }
-  w.xb = woff + dpos - w.cs;
-  return w;
-}
-
-// Multi-dot of one stage by consumer warp `sl` (columns sl, sl + 16, ...; NW of them):
-// acc += V_c . w and acc2 += V_c . u_j over the stage's TR rows.
-template <int NW, typename TV, typename TACC>
-__device__ __forceinline__ void arn_dots(TACC (&acc)[kArnSliceCols], TACC (&acc2)[kArnSliceCols],
-                                         const unsigned char* st, const TACC* sw, int k, int TR,
-                                         int sl, int lane) {
-  constexpr int VN = ArnVec<TV>::n;
-  const TV* sV = reinterpret_cast<const TV*>(st);
-  const TV* su = sV + (size_t)(k - 1) * TR;
-  for (int r = lane * VN; r < TR; r += 32 * VN) {
-    TACC wv[VN], uv[VN];
-    ld_acc<VN>(sw + r, wv);
-    ld_vec(su + r, uv);
+// dst[c] = sum_{r < nrows} src[r * ldp + c] for c < ncols, in a fixed order: the Q threads
+// of a column (consecutive lanes) take rows q, q + Q, ..., each issuing up to 8 loads at
+// once before adding them, then combine by shuffles; ends with a block barrier.  (FP64 adds
+// issue at a quarter-warp per clock on GB300: the trees are kept short.)
+__device__ __forceinline__ void arn_reduce_cols(const double* src, int nrows, int ncols, int ldp,
+                                                double* dst) {
+  constexpr int L = 8;
+  int Q = 1;
+  while (Q * 2 <= 32 && Q * 2 * ncols <= (int)blockDim.x) Q *= 2;
+  const int rounds = (ncols * Q + blockDim.x - 1) / blockDim.x;
+  for (int rd = 0; rd < rounds; ++rd) {
+    const int idx = rd * blockDim.x + threadIdx.x;
+    const int c = idx / Q, q = idx % Q;
+    double sum = 0.0;
+    if (c < ncols) {
+      for (int r0 = q; r0 < nrows; r0 += L * Q) {
+        double v[L];
 #pragma unroll
-    for (int i = 0; i < NW; ++i) {
-      TACC v[VN];
-      ld_vec(sV + (size_t)(sl + kArnCW * i) * TR + r, v);
+        for (int u = 0; u < L; ++u) {
+          const int r = r0 + u * Q;
+          v[u] = r < nrows ? __ldcg(src + (size_t)r * ldp + c) : 0.0;
+        }
 #pragma unroll
-      for (int e = 0; e < VN; ++e) {
-        acc[i] += v[e] * wv[e];
-        acc2[i] += v[e] * uv[e];
+        for (int h = L / 2; h > 0; h >>= 1)
+#pragma unroll
+          for (int u = 0; u < h; ++u) v[u] += v[u + h];
+        sum += v[0];
       }
     }
+    for (int o = 1; o < Q; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (c < ncols && q == 0) dst[c] = sum;
   }
+  __syncthreads();
 }
 
-#define GG_ARN_SWITCH(nw, CALL) \
-  switch (nw) {                 \
-    case 1: CALL(1); break;     \
-    case 2: CALL(2); break;     \
-    case 3: CALL(3); break;     \
-    case 4: CALL(4); break;     \
-    case 5: CALL(5); break;     \
-    default: break;             \
-  }
-
-// 16-byte vector load / store of VN basis elements from global memory
+// 16-byte vector load of VN basis elements from global memory, read-only and streamed past
+// L1 (the basis is read once per pass; L1 is mostly carved out for shared memory here)
 template <typename TV, typename TACC, int VN>
 __device__ __forceinline__ void arn_ldg(const TV* p, TACC (&o)[VN]) {
   if constexpr (std::is_same<TV, double>::value) {
-    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
-    o[0] = (TACC)v.x;
-    o[1] = (TACC)v.y;
+    double x, y;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];"
+                 : "=d"(x), "=d"(y)
+                 : "l"(p));
+    o[0] = (TACC)x;
+    o[1] = (TACC)y;
   } else if constexpr (std::is_same<TV, float>::value) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    float x, y, z, w;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(x), "=f"(y), "=f"(z), "=f"(w)
+                 : "l"(p));
+    o[0] = x; o[1] = y; o[2] = z; o[3] = w;
   } else {
     const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
     const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
@@ -200,24 +164,6 @@ __device__ __forceinline__ void arn_ldg(const TV* p, TACC (&o)[VN]) {
       const float2 f = __bfloat1622float2(h[e]);
       o[2 * e] = f.x;
       o[2 * e + 1] = f.y;
-    }
-  }
-}
-
-template <typename TACC, int VN>
-__device__ __forceinline__ void arn_ldw(const TACC* p, TACC (&o)[VN]) {  // w: coherent loads
-  if constexpr (sizeof(TACC) == 8) {
-#pragma unroll
-    for (int e = 0; e < VN; e += 2) {
-      const double2 v = __ldcg(reinterpret_cast<const double2*>(p + e));
-      o[e] = v.x;
-      o[e + 1] = v.y;
-    }
-  } else {
-#pragma unroll
-    for (int e = 0; e < VN; e += 4) {
-      const float4 v = __ldcg(reinterpret_cast<const float4*>(p + e));
-      o[e] = v.x; o[e + 1] = v.y; o[e + 2] = v.z; o[e + 3] = v.w;
     }
   }
 }
@@ -237,29 +183,160 @@ __device__ __forceinline__ void arn_stv(TV* p, const TACC (&v)[VN]) {
   }
 }
 
+// Diagonal part of the SpMV for B rows (row0 + b * stride) at once: all loads of the B
+// rows are issued before their products (ND > 0: ND diagonals, unrolled; ND = 0: nd at
+// run time, four at a time).  x indexes are clamped to a valid row, where the stored
+// value is 0.
+template <int B, int ND, typename TV, typename TACC>
+__device__ __forceinline__ void arn_dia_rows(TACC (&acc)[B], long long row0, long long stride,
+                                             long long Nn, int nd, const int* off,
+                                             long long ldd, const TACC* __restrict__ dval,
+                                             const TV* __restrict__ x) {
+  constexpr int NQ = ND > 0 ? ND : 4;
+#pragma unroll
+  for (int b = 0; b < B; ++b) acc[b] = 0;
+  for (int q0 = 0; q0 < (ND > 0 ? ND : nd); q0 += NQ) {
+    TACC av[B][NQ], xv[B][NQ];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const long long row = row0 + b * stride;
+      const long long rr = row < Nn ? row : Nn - 1;
+#pragma unroll
+      for (int u = 0; u < NQ; ++u) {
+        const int q = q0 + u;
+        const bool live = ND > 0 || q < nd;
+        const long long c = min(max(rr + off[live ? q : 0], 0LL), Nn - 1);
+        av[b][u] = live ? __ldg(dval + (size_t)q * ldd + rr) : (TACC)0;
+        xv[b][u] = live ? ld_as<TACC, TV>(x + c) : (TACC)0;
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+#pragma unroll
+      for (int u = 0; u < NQ; ++u) acc[b] += av[b][u] * xv[b][u];
+  }
+}
+
+// Multi-dot of one basis column (col) over chunks [0, nch) of 32 x VN rows of the
+// super-tile starting at row s0, by one warp: a1 += V_col . w and a2 += V_col . u_j per
+// lane; the column's chunks are loaded D ahead into registers.
 template <typename TV, typename TACC>
+__device__ __forceinline__ void arn_dot_column(TACC& a1, TACC& a2, const TV* V, long long ldv,
+                                               int col, long long s0, int nch, const TACC* Ws,
+                                               const TACC* Us, int lane) {
+  constexpr int VN = ArnVec<TV>::n;
+  constexpr int D = arn_loads<TV>();
+  const TV* pv = V + (size_t)col * ldv + s0 + lane * VN;
+  TACC buf[D][VN];
+#pragma unroll
+  for (int d = 0; d < D; ++d)
+    if (d < nch) arn_ldg<TV, TACC, VN>(pv + (size_t)d * 32 * VN, buf[d]);
+  pv += (size_t)D * 32 * VN;
+  const TACC* pw = Ws + lane * VN;
+  const TACC* pu = Us + lane * VN;
+  for (int q0 = 0; q0 < nch; q0 += D) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      if (q0 + d < nch) {
+        TACC wv[VN], uv[VN];
+        ld_acc<VN>(pw, wv);
+        ld_acc<VN>(pu, uv);
+        pw += 32 * VN;
+        pu += 32 * VN;
+#pragma unroll
+        for (int e = 0; e < VN; ++e) {
+          a1 += buf[d][e] * wv[e];
+          a2 += buf[d][e] * uv[e];
+        }
+        if (q0 + d + D < nch) arn_ldg<TV, TACC, VN>(pv, buf[d]);
+        pv += 32 * VN;
+      }
+    }
+  }
+}
+
+// Multi-dot in row-chunk order (FP32 basis): warp w takes the chunks w, w + 16, ... of the
+// super-tile and, per pass, a group of up to kArnGroup columns: one 16-byte load per column
+// and lane for the same rows, so the loads in flight of a warp fall in one row window of
+// many columns (on GB300 this streams about twice as fast as a warp reading one column
+// through many consecutive chunks).  At the end of a pass the lanes' partial sums of each
+// column are added by a shuffle tree and lane 0 accumulates them into wsum[set][warp][c].
+constexpr int kArnGroup = 13;
+
+template <typename TV, typename TACC>
+__device__ __forceinline__ void arn_dots_rows(double* wsum, const TV* V, long long ldv, int k,
+                                              long long s0, int nch, const TACC* Ws,
+                                              const TACC* Us, int warp, int lane) {
+  constexpr int VN = ArnVec<TV>::n;
+  constexpr int G = kArnGroup;
+  for (int g0 = 0; g0 < k; g0 += G) {
+    const int gc = k - g0 < G ? k - g0 : G;
+    TACC a1[G], a2[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      a1[u] = 0;
+      a2[u] = 0;
+    }
+    const TV* col = V + (size_t)g0 * ldv + s0 + (size_t)lane * VN;
+    for (int q = warp; q < nch; q += kArnWarps) {
+      const size_t off = (size_t)q * 32 * VN;
+      TACC v[G][VN];
+#pragma unroll
+      for (int u = 0; u < G; ++u)
+        if (u < gc) arn_ldg<TV, TACC, VN>(col + (size_t)u * ldv + off, v[u]);
+      TACC wv[VN], uv[VN];
+      ld_acc<VN>(Ws + off + lane * VN, wv);
+      ld_acc<VN>(Us + off + lane * VN, uv);
+#pragma unroll
+      for (int u = 0; u < G; ++u)
+        if (u < gc)
+#pragma unroll
+          for (int e = 0; e < VN; ++e) {
+            a1[u] += v[u][e] * wv[e];
+            a2[u] += v[u][e] * uv[e];
+          }
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u)
+      if (u < gc) {
+        const TACC t1 = warp_sum(a1[u]), t2 = warp_sum(a2[u]);
+        if (lane == 0) {
+          wsum[(size_t)warp * kMaxK + g0 + u] += (double)t1;
+          wsum[(size_t)(kArnWarps + warp) * kMaxK + g0 + u] += (double)t2;
+        }
+      }
+  }
+}
+
+template <typename TV, typename TACC, int ND>
 __global__ void __launch_bounds__(kArnThreads, 1)
     k_arnoldi(const __grid_constant__ ArnArgs<TV, TACC> a) {
+  static_assert(std::is_same<TV, TACC>::value, "w and u_j slices share the basis element type");
   constexpr int VN = ArnVec<TV>::n;
-  constexpr int E = 16 / (int)sizeof(TV);  // elements per 16-byte chunk of x
-  extern __shared__ __align__(128) unsigned char ring[];
-  __shared__ uint64_t full[kArnMaxStages], empty[kArnMaxStages];
+  constexpr int B = sizeof(TACC) == 8 ? 2 : 4;  // SpMV rows per thread and batch
+  extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double tot[2 * kMaxK + 1];
   __shared__ double sred[2 * kMaxK];
   __shared__ double sg[kMaxK];
   __shared__ TACC scoef[kMaxK];
-  __shared__ double snrm[kArnThreads / 32];
+  __shared__ double snrm[kArnWarps];
   __shared__ unsigned s_last;
   Ctl ctl = a.ctl;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool prod = warp == kArnCW;
-  const int ct = threadIdx.x;  // consumer thread index (warps 0..kArnCW-1)
+  const int t = threadIdx.x;
   const int G = gridDim.x, bid = blockIdx.x;
   const long long R0 = (long long)bid * a.units / G * kArnUnit;
   const long long R1 = (long long)(bid + 1) * a.units / G * kArnUnit;
-  const int k = a.k, TR = a.TR, S = a.S, nd = a.dia.nd;
-  const int nt = (int)((R1 - R0) / TR);
-  const int N = a.N;
+  const int k = a.k;
+  const long long N = a.N;
+  // shared memory: w and u_j of a super-tile, s' (r), reduction scratch
+  TACC* Ws = reinterpret_cast<TACC*>(smem);
+  TACC* Us = Ws + a.RS;
+  TACC* Ss = Us + a.RS;
+  double* scratch = reinterpret_cast<double*>(
+      smem + ((2 * (size_t)a.RS + (size_t)a.r) * sizeof(TACC) + 127) / 128 * 128);
+  double* sL = scratch + kArnScratch / sizeof(double);  // k x k, strictly lower part used
+  __shared__ double ssig[kMaxK];
 
   if (!a.pre) {
     pdl_wait();
@@ -276,185 +353,121 @@ __global__ void __launch_bounds__(kArnThreads, 1)
     return;
   }
   const unsigned gen = *(volatile unsigned*)&a.gbar[1];  // advanced only once all arrive
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kArnCW);
-    }
-    mbar_fence_init();
+  // the basis scales and the rows of L from the earlier steps of the cycle are final:
+  // staged now, off the path between the grid barrier and the update
+  for (int c = t; c < k; c += kArnThreads) ssig[c] = __ldcg(&ctl.sigma[c]);
+  for (int q = t; q < k * k; q += kArnThreads) {
+    const int i = q / k, c = q % k;
+    sL[q] = (c < i && i < k - 1) ? __ldcg(&ctl.L[(size_t)i * kMaxK + c]) : 0.0;
   }
-  __syncthreads();
-
   const TV* xj = a.V + (size_t)a.j * a.ldv;
-  const uint32_t vbytes = (uint32_t)(TR * sizeof(TV)), dbytes = (uint32_t)(TR * sizeof(TACC));
-  auto stage = [&](int s) { return ring + (size_t)s * a.stage_bytes; };
+  const TACC sig = (TACC)__ldcg(&ctl.sigma[a.j]);
+  const int nd = ND > 0 ? ND : a.dia.nd;
+  const int nw = slice_cols(k, warp, kArnWarps);
 
-  // ---- 1-2. SpMV and multi-dot, tile by tile, from the ring ------------------------
-  // Stage of tile i (rows r0 .. r0 + TR): the basis tile (columns 0..k-1), the diagonals,
-  // the x windows and the A W rows, all copied by the producer warp; the consumers form
-  // w for the tile's rows in the stage (and in global memory for the update), meet at a
-  // named barrier, and run the multi-dot.
-  TACC acc[kArnSliceCols], acc2[kArnSliceCols];
+  // per-lane partial sums of the multi-dot, [set][warp][column group][lane], in shared
+  // memory (each slot owned by one lane) so that they persist across super-tiles
+  double* sbuf = scratch;
+  for (int q = t; q < 2 * kArnWarps * kArnSliceCols * 33; q += kArnThreads) sbuf[q] = 0.0;
+  bool waited = !a.pre;
+  for (long long s0 = R0; s0 < R1; s0 += a.RS) {
+    const long long s1 = s0 + a.RS < R1 ? s0 + a.RS : R1;
+    // ---- 1. SpMV of the super-tile's rows: w and u_j into shared memory ----------------
+    for (long long i0 = s0 + t; i0 < s1; i0 += (long long)B * kArnThreads) {
+      TACC v[B];
+      arn_dia_rows<B, ND, TV, TACC>(v, i0, kArnThreads, N, nd, a.dia.off, a.ldd, a.dval, xj);
 #pragma unroll
-  for (int i = 0; i < kArnSliceCols; ++i) {
-    acc[i] = 0;
-    acc2[i] = 0;
-  }
-  bool ok = true;
-  if (prod) {
-    // A W row pointers at the tile boundaries, 32 tiles per refresh (lane l: tile base + l)
-    int ap0 = 0, ap1 = 0, abase_tile = -32;
-    for (int i = 0; i < nt; ++i) {
-      const int s = i % S;
-      if (i >= S) {  // stage s was last used by tile i - S: all consumer warps released it
-        if (!mbar_wait(&empty[s], (uint32_t)(((i / S) - 1) & 1))) {
-          ok = false;
-          break;
+      for (int b = 0; b < B; ++b) {
+        const long long row = i0 + (long long)b * kArnThreads;
+        if (row < s1) {
+          Ws[row - s0] = row < N ? v[b] : (TACC)0;
+          Us[row - s0] = row < N ? ld_as<TACC, TV>(xj + row) : (TACC)0;
         }
-      }
-      const long long r0 = R0 + (long long)i * TR;
-      int abase = 0, acnt = 0;
-      if (a.defl) {
-        if (i - abase_tile >= 32) {
-          abase_tile = i;
-          const long long t0 = R0 + (long long)(i + lane) * TR, t1 = t0 + TR;
-          ap0 = __ldg(a.aurp + (t0 < R1 ? t0 : R1));
-          ap1 = __ldg(a.aurp + (t1 < R1 ? t1 : R1));
-        }
-        const int e0 = __shfl_sync(0xffffffffu, ap0, i - abase_tile);
-        const int e1 = __shfl_sync(0xffffffffu, ap1, i - abase_tile);
-        abase = e0 & ~3;
-        acnt = (e1 - abase + 3) & ~3;
-      }
-      unsigned char* st = stage(s);
-      if (lane == 0) {
-        uint32_t bytes = (uint32_t)k * vbytes + (uint32_t)nd * dbytes;
-        for (int g = 0; g < a.ng; ++g) {
-          const ArnWin wg = arn_win(a.wlo[g], a.wlen[g], a.woff[g], r0, a.ldv, E);
-          bytes += (uint32_t)((wg.ce - wg.cs) * (long long)sizeof(TV));
-        }
-        if (a.defl)
-          bytes += (uint32_t)((TR + 4) * sizeof(int)) +
-                   (uint32_t)acnt * (uint32_t)(sizeof(int) + sizeof(TACC));
-        mbar_arrive_expect_tx(&full[s], bytes);
-      }
-      __syncwarp();
-      for (int c = lane; c < k; c += 32)
-        bulk_g2s(st + (size_t)c * vbytes, a.V + (size_t)c * a.ldv + r0, vbytes, &full[s]);
-      for (int q = lane; q < nd; q += 32)
-        bulk_g2s(st + a.offD + (size_t)q * dbytes, a.dval + (size_t)q * a.ldd + r0, dbytes,
-                 &full[s]);
-      for (int g = lane; g < a.ng; g += 32) {
-        const ArnWin wg = arn_win(a.wlo[g], a.wlen[g], a.woff[g], r0, a.ldv, E);
-        bulk_g2s(st + a.offX + (size_t)(wg.xb + wg.cs) * sizeof(TV), xj + wg.cs,
-                 (uint32_t)((wg.ce - wg.cs) * (long long)sizeof(TV)), &full[s]);
-      }
-      if (a.defl) {
-        if (lane == 0)
-          bulk_g2s(st + a.offP, a.aurp + r0, (uint32_t)((TR + 4) * sizeof(int)), &full[s]);
-        if (lane == 1 && acnt > 0)
-          bulk_g2s(st + a.offC, a.aucol + abase, (uint32_t)(acnt * sizeof(int)), &full[s]);
-        if (lane == 2 && acnt > 0)
-          bulk_g2s(st + a.offA, a.auval + abase, (uint32_t)(acnt * sizeof(TACC)), &full[s]);
       }
     }
-  } else {
-    if (a.pre) {  // s' (the coarse solve's output) is read below
+    if (!waited) {  // s' (the coarse solve's output) is read from here on
       pdl_wait();
       pdl_trigger();
+      waited = true;
     }
-    const int nw = slice_cols(k, warp, kArnCW);
-    const TACC sig = (TACC)__ldcg(&ctl.sigma[a.j]);
-    for (int i = 0; i < nt; ++i) {
-      const int s = i % S;
-      const bool okw = mbar_wait(&full[s], (uint32_t)((i / S) & 1));
-      const unsigned char* st = stage(s);
-      TACC* sw = reinterpret_cast<TACC*>(const_cast<unsigned char*>(st) + a.offW);
-      const long long r0 = R0 + (long long)i * TR;
-      if (okw && ct < TR) {  // row r0 + ct of w = sigma_j (A u_j + A W s')
-        const long long row = r0 + ct;
-        TACC v = 0;
-        if (row < N) {
-          const TACC* sD = reinterpret_cast<const TACC*>(st + a.offD);
-          const TV* sX = reinterpret_cast<const TV*>(st + a.offX);
-          TACC p0 = 0, p1 = 0;
-          int q = 0;
-          for (int g = 0; g < a.ng; ++g) {
-            const ArnWin wg = arn_win(a.wlo[g], a.wlen[g], a.woff[g], r0, a.ldv, E);
-            const int qe = a.gq[g + 1];
-            for (; q < qe; ++q) {
-              long long xi = row + a.dia.off[q];
-              xi = xi < wg.cs ? wg.cs : (xi >= wg.ce ? wg.ce - 1 : xi);
-              const TACC t = sD[(size_t)q * TR + ct] * cv<TACC, TV>(sX[wg.xb + xi]);
-              if (q & 1) p1 += t;
-              else p0 += t;
-            }
-          }
-          v = p0 + p1;
-          if (a.defl) {
-            const int* sP = reinterpret_cast<const int*>(st + a.offP);
-            const int* sC = reinterpret_cast<const int*>(st + a.offC);
-            const TACC* sA = reinterpret_cast<const TACC*>(st + a.offA);
-            const int ab = sP[0] & ~3;
-            const int e1 = sP[ct + 1] - ab;
-            TACC aw = 0;
-            for (int e = sP[ct] - ab; e < e1; ++e) aw += sA[e] * __ldg(a.sdefl + sC[e]);
-            v += aw;
-          }
-          v *= sig;
-          a.w[row] = v;
-        }
-        sw[ct] = v;  // rows past n stay 0
-      }
-      // the tile's w is complete; every consumer warp learns whether all copies arrived
-      if (!bar_and(1, kArnCW * 32, okw)) {
-        ok = false;
-        break;
-      }
-#define GG_ARN_DOTS(NW) arn_dots<NW, TV, TACC>(acc, acc2, st, sw, k, TR, warp, lane)
-      GG_ARN_SWITCH(nw, GG_ARN_DOTS)
-#undef GG_ARN_DOTS
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[s]);
-    }
-  }
-  if (!__syncthreads_and(ok)) {
-    // a copy never completed: drain what is still in flight (bounded), report, return
-    if (threadIdx.x == 0) {
-      for (int i = 0; i < nt; ++i) mbar_wait(&full[i % S], (uint32_t)((i / S) & 1));
-      ctl.flags[F_STATUS] = GMRES_ERR_TIMEOUT;
-      ctl.flags[F_STOP] = 1;
-      ctl.flags[F_CYCLE_DONE] = 1;
-    }
+    if (a.defl && s0 == R0)
+      for (int q = t; q < a.r; q += kArnThreads) Ss[q] = a.sdefl[q];
     __syncthreads();
-    return;
-  }
-  // per-block column sums: each column belongs to one warp; lanes' values transposed
-  // through shared memory (the ring is free now) and summed 16 at a time by lane pairs
-  {
-    double* sbuf = reinterpret_cast<double*>(ring);  // [2][kArnCW][kArnSliceCols][33]
-    if (!prod) {
-      const int nw = slice_cols(k, warp, kArnCW);
+    // + A W s' (the row's A W entries, s' from shared memory), the scale sigma_j; w also to
+    // global memory for the update when the block has more than one super-tile.  The rows
+    // are taken kArnAwRows per thread at a time, each level of the A W gather (row
+    // pointers, then the first entry of every row) issued for all of them at once.
+    for (long long i0 = s0 + t; i0 < s1; i0 += (long long)kArnAwRows * kArnThreads) {
+      int e0[kArnAwRows], e1[kArnAwRows];
 #pragma unroll
-      for (int i = 0; i < kArnSliceCols; ++i)
-        if (i < nw) {
-          sbuf[((0 * kArnCW + warp) * kArnSliceCols + i) * 33 + lane] = (double)acc[i];
-          sbuf[((1 * kArnCW + warp) * kArnSliceCols + i) * 33 + lane] = (double)acc2[i];
+      for (int b = 0; b < kArnAwRows; ++b) {
+        const long long row = i0 + (long long)b * kArnThreads;
+        const bool live = a.defl && row < N && row < s1;
+        e0[b] = live ? __ldg(a.aurp + row) : 0;
+        e1[b] = live ? __ldg(a.aurp + row + 1) : 0;
+      }
+      TACC av[kArnAwRows];
+      int ac[kArnAwRows];
+#pragma unroll
+      for (int b = 0; b < kArnAwRows; ++b) {
+        const bool has = e0[b] < e1[b];
+        av[b] = has ? __ldg(a.auval + e0[b]) : (TACC)0;
+        ac[b] = has ? __ldg(a.aucol + e0[b]) : 0;
+      }
+#pragma unroll
+      for (int b = 0; b < kArnAwRows; ++b) {
+        const long long row = i0 + (long long)b * kArnThreads;
+        if (row < s1) {
+          TACC aw = av[b] * Ss[ac[b]];
+          for (int e = e0[b] + 1; e < e1[b]; ++e) aw += __ldg(a.auval + e) * Ss[__ldg(a.aucol + e)];
+          const TACC wv = row < N ? sig * (Ws[row - s0] + aw) : (TACC)0;
+          Ws[row - s0] = wv;
+          if (row < N) a.w[row] = wv;
         }
-      __syncwarp();
-      const int p = lane >> 1, half = lane & 1;  // pair p: set p / 5, accumulator p % 5
-      const int set = p / kArnSliceCols, i = p % kArnSliceCols;
-      double v = 0.0;
-      const bool live = p < 2 * kArnSliceCols && i < nw;
-      if (live) v = tree16(sbuf + ((set * kArnCW + warp) * kArnSliceCols + i) * 33 + half * 16);
-      v += __shfl_xor_sync(0xffffffffu, v, 1);
-      if (live && half == 0) sred[set * k + warp + kArnCW * i] = v;
+      }
     }
     __syncthreads();
+    const int nch = (int)((s1 - s0) / (32 * VN));
+    if constexpr (sizeof(TV) == 8) {
+      // FP64: warp s takes the columns s, s + 16, ... (column group g = column / 16), one at
+      // a time, so that each lane's partial sums (in shared memory) need one add per lane
+      // and column in the end: the FP64 pipe is the bound, and its adds are dear
+      for (int g = 0; g < nw; ++g) {
+        TACC a1 = 0, a2 = 0;
+        arn_dot_column<TV, TACC>(a1, a2, a.V, a.ldv, warp + kArnWarps * g, s0, nch, Ws, Us, lane);
+        sbuf[((0 * kArnWarps + warp) * kArnSliceCols + g) * 33 + lane] += (double)a1;
+        sbuf[((1 * kArnWarps + warp) * kArnSliceCols + g) * 33 + lane] += (double)a2;
+      }
+    } else {
+      arn_dots_rows<TV, TACC>(sbuf, a.V, a.ldv, k, s0, nch, Ws, Us, warp, lane);
+    }
+    __syncthreads();  // the slices are rewritten by the next super-tile
+  }
+  // per-block column sums: each column belongs to one warp; its lanes' partial sums (in
+  // shared memory) are summed 16 at a time by lane pairs
+  if constexpr (sizeof(TV) == 8) {
+    const int p = lane >> 1, half = lane & 1;  // pair p: set p / 5, accumulator p % 5
+    const int set = p / kArnSliceCols, i = p % kArnSliceCols;
+    double v = 0.0;
+    const bool live = p < 2 * kArnSliceCols && i < nw;
+    if (live) v = tree16(sbuf + ((set * kArnWarps + warp) * kArnSliceCols + i) * 33 + half * 16);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    if (live && half == 0) sred[set * k + warp + kArnWarps * i] = v;
+    __syncthreads();
+  } else {  // the 16 warps' sums of each column, in warp order
+    for (int q = t; q < 2 * k; q += kArnThreads) {
+      const int set = q / k, c = q % k;
+      double v = 0.0;
+      for (int w = 0; w < kArnWarps; ++w) v += sbuf[(size_t)(set * kArnWarps + w) * kMaxK + c];
+      sred[q] = v;
+    }
+    __syncthreads();
+  }
+  {
     for (int c = threadIdx.x; c < 2 * k; c += blockDim.x)
       __stcg(&ctl.part[(size_t)bid * ctl.ldp + c], sred[c]);
   }
-  // ---- 3. grid barrier; identical totals in every block; (I + L) h = g --------------
+  // ---- 3. grid barrier; identical totals in every block; (I + L) h = g ----------------
   if (!arn_grid_sync(a.gbar, gen)) {
     if (threadIdx.x == 0) {
       ctl.flags[F_STATUS] = GMRES_ERR_TIMEOUT;
@@ -463,20 +476,19 @@ __global__ void __launch_bounds__(kArnThreads, 1)
     }
     return;
   }
-  reduce_rows(ctl.part, G, 2 * k, ctl.ldp, tot);  // ends with __syncthreads
+  arn_reduce_cols(ctl.part, G, 2 * k, ctl.ldp, tot);  // ends with __syncthreads
   {
-    double* sL = reinterpret_cast<double*>(ring);  // k x k, strictly lower part used
-    const double sj = __ldcg(&ctl.sigma[k - 1]);
-    for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
-      const int i = t / k, c = t % k;
-      double v = 0.0;
-      if (c < i) v = i < k - 1 ? __ldcg(&ctl.L[(size_t)i * kMaxK + c])
-                               : sj * __ldcg(&ctl.sigma[c]) * tot[k + c];
-      sL[t] = v;
+    // the new row of L: v_j . v_c = sigma_j sigma_c (u_j . u_c), c < j; g_c = sigma_c (u_c . w)
+    const double sj = ssig[k - 1];
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+      if (c < k - 1) sL[(size_t)(k - 1) * k + c] = sj * ssig[c] * tot[k + c];
+      sg[c] = ssig[c] * tot[c];
     }
-    for (int c = threadIdx.x; c < k; c += blockDim.x) sg[c] = __ldcg(&ctl.sigma[c]) * tot[c];
     __syncthreads();
     if (warp == 0) {  // forward substitution: h_c final when reached (entries c, c+32, c+64)
+      // sL[i][c] = 0 for c >= i, so rows at or above c take a zero update; only the
+      // 32-row groups below k are touched (one FP64 FMA per group and column)
+      const int nq = (k + 31) >> 5;
       double g[3];
 #pragma unroll
       for (int q = 0; q < 3; ++q) g[q] = lane + 32 * q < k ? sg[lane + 32 * q] : 0.0;
@@ -485,15 +497,14 @@ __global__ void __launch_bounds__(kArnThreads, 1)
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           const int i = lane + 32 * q;
-          if (i > c && i < k) g[q] -= sL[i * k + c] * hc;
+          if (q < nq) g[q] -= (i < k ? sL[i * k + c] : 0.0) * hc;
         }
       }
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const int i = lane + 32 * q;
         if (i < k) {
-          const double sc = __ldcg(&ctl.sigma[i]);
-          scoef[i] = (TACC)(sc * g[q]);
+          scoef[i] = (TACC)(ssig[i] * g[q]);
           if (bid == 0) {
             ctl.h[i] = g[q];
             if (i < k - 1) ctl.L[(size_t)(k - 1) * kMaxK + i] = sL[(k - 1) * k + i];
@@ -503,17 +514,23 @@ __global__ void __launch_bounds__(kArnThreads, 1)
     }
     __syncthreads();
   }
-  // ---- 4. update u_{j+1} = w - V (sigma o h) and ||u_{j+1}||^2 ----------------------
+  // ---- 4. update u_{j+1} = w - V (sigma o h) and ||u_{j+1}||^2 ------------------------
   double nrm = 0.0;
-  if (!prod) {
-    constexpr int U = sizeof(TV) == 8 ? 8 : 12;  // basis loads in flight per lane
+  {
+    constexpr int U = sizeof(TV) == 8 ? 13 : 12;  // basis loads in flight per lane
     const int chunk = 32 * VN;
     const long long nch = (R1 - R0) / chunk;
+    const bool wsm = R1 - R0 <= a.RS;  // the block's w is still in shared memory
     TV* __restrict__ vout = const_cast<TV*>(a.V) + (size_t)k * a.ldv;
-    for (long long q = nch - 1 - warp; q >= 0; q -= kArnCW) {
+    for (long long q = nch - 1 - warp; q >= 0; q -= kArnWarps) {
       const long long r = R0 + q * chunk + (long long)lane * VN;
       TACC wv[VN], p[VN];
-      arn_ldw<TACC, VN>(a.w + r, wv);
+      if (wsm) {
+        ld_acc<VN>(Ws + (r - R0), wv);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VN; ++e) wv[e] = r + e < N ? __ldcg(a.w + r + e) : (TACC)0;
+      }
 #pragma unroll
       for (int e = 0; e < VN; ++e) p[e] = 0;
       for (int c0 = 0; c0 < k; c0 += U) {
@@ -533,25 +550,25 @@ __global__ void __launch_bounds__(kArnThreads, 1)
 #pragma unroll
       for (int e = 0; e < VN; ++e) un[e] = wv[e] - p[e];
       arn_stv<TV, TACC, VN>(vout + r, un);
-      if constexpr (std::is_same<TV, TACC>::value) {
-        TACC s = 0;
+      TACC s = 0;
 #pragma unroll
-        for (int e = 0; e < VN; ++e) s += un[e] * un[e];
-        nrm += (double)s;
-      } else {  // the norm of the stored (rounded) vector
-        TACC s = 0;
-#pragma unroll
-        for (int e = 0; e < VN; ++e) {
-          const TACC sv = cv<TACC, TV>(st_round<TV>((float)un[e]));
-          s += sv * sv;
-        }
-        nrm += (double)s;
-      }
+      for (int e = 0; e < VN; ++e) s += un[e] * un[e];
+      nrm += (double)s;
     }
   }
   // ---- 5. norm partials; the last block applies the rotations -----------------------
   {
-    const double bs = block_sum(nrm, snrm);
+    // warp sums, then warp 0 adds the 16 of them (a block-wide final loop would issue 16
+    // FP64 adds in every warp)
+    nrm = warp_sum(nrm);
+    if (lane == 0) snrm[warp] = nrm;
+    __syncthreads();
+    double bs = 0.0;
+    if (warp == 0) {
+      bs = lane < kArnWarps ? snrm[lane] : 0.0;
+#pragma unroll
+      for (int o = kArnWarps / 2; o > 0; o >>= 1) bs += __shfl_xor_sync(0xffffffffu, bs, o);
+    }
     if (threadIdx.x == 0) {
       __stcg(&ctl.part[(size_t)bid * ctl.ldp + kArnNormCol], bs);
       __threadfence();
@@ -560,7 +577,7 @@ __global__ void __launch_bounds__(kArnThreads, 1)
     }
     __syncthreads();
     if (!s_last) return;
-    reduce_rows(ctl.part + kArnNormCol, G, 1, ctl.ldp, tot);
+    arn_reduce_cols(ctl.part + kArnNormCol, G, 1, ctl.ldp, tot);
     if (threadIdx.x == 0) ctl.ticket[0] = 0u;
     givens_step(ctl, k - 1, a.m, sqrt(tot[0]));
   }
@@ -568,99 +585,59 @@ __global__ void __launch_bounds__(kArnThreads, 1)
 
 template <typename TV, typename TACC>
 struct Arn {
-  struct Layout {
-    int TR, S, ng, awcap;
-    unsigned offD, offX, offP, offC, offA, offW, bytes;
-    int wlo[kMaxDiag], wlen[kMaxDiag], woff[kMaxDiag], gq[kMaxDiag + 1];
-  };
-  static unsigned up(size_t b) { return (unsigned)((b + 127) / 128 * 128); }
-  // x windows: diagonals whose sorted offsets lie within kArnGap of the previous one share
-  // a window; for tile rows TR, window g covers rows [r0 + wlo, r0 + wlo + wlen)
-  static Layout layout(const CycleArgs& c, int k, int TR, bool defl, int au_tile_max) {
-    constexpr int E = 16 / (int)sizeof(TV);
-    constexpr int kArnGap = 32;
-    Layout L{};
-    L.TR = TR;
-    const DiaOffsets& d = c.op.dia;
-    int woff = 0;
-    for (int q = 0; q < d.nd;) {
-      int qe = q + 1;
-      while (qe < d.nd && d.off[qe] - d.off[qe - 1] <= kArnGap) ++qe;
-      const int lo = d.off[q], hi = d.off[qe - 1];
-      auto fdiv = [](int a, int b) { return (a >= 0 ? a / b : -((-a + b - 1) / b)); };
-      const int wlo = fdiv(lo, E) * E;
-      const int whi = fdiv(TR + hi + E - 1, E) * E;
-      L.wlo[L.ng] = wlo;
-      L.wlen[L.ng] = whi - wlo;
-      L.woff[L.ng] = woff;
-      L.gq[L.ng] = q;
-      woff += whi - wlo;
-      ++L.ng;
-      q = qe;
-    }
-    L.gq[L.ng] = d.nd;
-    L.awcap = defl ? (au_tile_max + 8 + 3) / 4 * 4 : 0;
-    size_t off = up((size_t)k * TR * sizeof(TV));
-    L.offD = (unsigned)off;
-    off += up((size_t)d.nd * TR * sizeof(TACC));
-    L.offX = (unsigned)off;
-    off += up((size_t)woff * sizeof(TV));
-    L.offP = (unsigned)off;
-    off += defl ? up((size_t)(TR + 4) * sizeof(int)) : 0;
-    L.offC = (unsigned)off;
-    off += up((size_t)L.awcap * sizeof(int));
-    L.offA = (unsigned)off;
-    off += up((size_t)L.awcap * sizeof(TACC));
-    L.offW = (unsigned)off;
-    off += up((size_t)TR * sizeof(TACC));
-    L.bytes = (unsigned)off;
-    const int S = (int)(kArnRing / off);
-    L.S = S > kArnMaxStages ? kArnMaxStages : S;
-    return L;
+  // rows of a super-tile: w and u_j slices, s' and the reduction scratch in kArnSmem
+  static long long super_rows(int r) {
+    const size_t fixed = ((size_t)r * sizeof(TACC) + 127) / 128 * 128 + kArnScratch +
+                         sizeof(double) * kMaxK * kMaxK + 256;
+    if (fixed >= kArnSmem) return 0;
+    return (long long)((kArnSmem - fixed) / (2 * sizeof(TACC))) / kArnUnit * kArnUnit;
   }
-  // tile rows: the largest of 256 / 128 / 64 whose stage fits the cap, and at least one
-  // full sweep of a warp (32 lanes x one 16-byte vector)
-  static Layout pick(const CycleArgs& c, int k, bool defl, int au_tile_max) {
-    constexpr int lo = 32 * ArnVec<TV>::n;
-    Layout L = layout(c, k, kArnUnit, defl, au_tile_max);
-    for (int tr = kArnUnit / 2; tr >= lo && L.bytes > arn_stage_cap<TV>(); tr >>= 1)
-      L = layout(c, k, tr, defl, au_tile_max);
-    return L;
-  }
+  template <int ND>
   static cudaError_t prepare() {
-    return cudaFuncSetAttribute(k_arnoldi<TV, TACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kArnRing);
+    return cudaFuncSetAttribute(k_arnoldi<TV, TACC, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kArnSmem);
+  }
+  template <int ND>
+  static cudaError_t launch_nd(const CycleArgs& c, const ArnArgs<TV, TACC>& p, cudaStream_t st) {
+    static cudaError_t prep = prepare<ND>();
+    if (prep != cudaSuccess) return prep;
+    const int grid = p.units < c.sms ? p.units : c.sms;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)kArnThreads);
+    cfg.dynamicSmemBytes = kArnSmem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    // a cooperative launch with programmatic serialisation; should the runtime refuse the
+    // pair, the kernel runs cooperatively in plain stream order from then on (same result)
+    static bool pdl_ok = true;
+    cfg.numAttrs = (c.pdl && pdl_ok) ? 2 : 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_arnoldi<TV, TACC, ND>, p);
+    if (e != cudaSuccess && cfg.numAttrs == 2) {
+      (void)cudaGetLastError();
+      pdl_ok = false;
+      cfg.numAttrs = 1;
+      e = cudaLaunchKernelEx(&cfg, k_arnoldi<TV, TACC, ND>, p);
+    }
+    return e;
   }
   static cudaError_t launch(const CycleArgs& c, int j, bool defl, cudaStream_t st) {
-    static cudaError_t prep = prepare();
-    if (prep != cudaSuccess) return prep;
     ArnArgs<TV, TACC> p{};
-    const Layout L = pick(c, j + 1, defl, c.op.au_tile_max);
-    if (L.S < 2) return cudaErrorInvalidValue;  // arnoldi_fusable keeps this from happening
     p.N = c.op.n;
     p.units = (int)(c.ldv / kArnUnit);
     p.j = j;
     p.k = j + 1;
     p.m = c.m;
-    p.TR = L.TR;
-    p.S = L.S;
-    p.stage_bytes = L.bytes;
-    p.offD = L.offD;
-    p.offX = L.offX;
-    p.offP = L.offP;
-    p.offC = L.offC;
-    p.offA = L.offA;
-    p.offW = L.offW;
-    p.awcap = L.awcap;
-    p.ng = L.ng;
-    for (int g = 0; g < L.ng; ++g) {
-      p.wlo[g] = L.wlo[g];
-      p.wlen[g] = L.wlen[g];
-      p.woff[g] = L.woff[g];
-    }
-    for (int g = 0; g <= L.ng; ++g) p.gq[g] = L.gq[g];
     p.pre = (defl && c.pdl) ? 1 : 0;
     p.defl = defl ? 1 : 0;
+    p.r = defl ? c.op.defl.r : 0;
+    p.RS = (int)super_rows(p.r);
+    if (p.RS < kArnUnit) return cudaErrorInvalidValue;  // arnoldi_fusable rules this out
     p.ldv = c.ldv;
     p.ldd = c.op.ldd;
     p.V = static_cast<const TV*>(c.V);
@@ -679,30 +656,8 @@ struct Arn {
     p.aucol = c.op.defl.aucol;
     p.ctl = c.ctl;
     p.gbar = c.gbar;
-    const int grid = p.units < c.sms ? p.units : c.sms;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)kArnThreads);
-    cfg.dynamicSmemBytes = kArnRing;
-    cfg.stream = st;
-    cudaLaunchAttribute at[2];
-    at[0].id = cudaLaunchAttributeCooperative;
-    at[0].val.cooperative = 1;
-    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[1].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    // a cooperative launch with programmatic serialisation; should the runtime refuse the
-    // pair, the kernel runs cooperatively in plain stream order from then on (same result)
-    static bool pdl_ok = true;
-    cfg.numAttrs = (c.pdl && pdl_ok) ? 2 : 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_arnoldi<TV, TACC>, p);
-    if (e != cudaSuccess && cfg.numAttrs == 2) {
-      (void)cudaGetLastError();
-      pdl_ok = false;
-      cfg.numAttrs = 1;
-      e = cudaLaunchKernelEx(&cfg, k_arnoldi<TV, TACC>, p);
-    }
-    return e;
+    // the 9-point stencils of the Q1 systems take an unrolled instantiation
+    return c.op.dia.nd == 9 ? launch_nd<9>(c, p, st) : launch_nd<0>(c, p, st);
   }
 };
 
@@ -711,12 +666,11 @@ struct Arn {
 bool arnoldi_fusable(const CycleArgs& a) {
   if (!(a.ortho == GMRES_ORTHO_MGS_LOWSYNC && a.op.dia.nd > 0 && !a.proj &&
         a.op.defl.qd == 0 && a.ldv % kArnUnit == 0 && a.m + 1 <= kMaxK &&
-        a.op.ldd % kArnUnit == 0 && (a.prec == P_FP64 || a.prec == P_FP32)))
+        (a.prec == P_FP64 || a.prec == P_FP32)))
     return false;
-  // the widest stage (k = m + 1 columns) must leave a ring of at least two stages
-  const bool defl = a.op.defl.r > 0;
-  if (a.prec == P_FP64) return Arn<double, double>::pick(a, a.m + 1, defl, a.op.au_tile_max).S >= 2;
-  return Arn<float, float>::pick(a, a.m + 1, defl, a.op.au_tile_max).S >= 2;
+  const int r = a.op.defl.r;
+  if (a.prec == P_FP64) return Arn<double, double>::super_rows(r) >= kArnUnit;
+  return Arn<float, float>::super_rows(r) >= kArnUnit;
 }
 
 cudaError_t launch_arnoldi(const CycleArgs& a, int j, bool defl, cudaStream_t st) {
