@@ -30,6 +30,7 @@ class Q1Setup:
     tol: float = 1e-10
     maxit: int = 100000
     deflation_mode: int = N.DEFL_EBP
+    ortho: int = N.ORTHO_CGS2
 
 
 class GmresSolve(torch.autograd.Function):
@@ -39,7 +40,7 @@ class GmresSolve(torch.autograd.Function):
         zeros_f = torch.zeros((n + 1) ** 2, dtype=torch.float64, device=kappa.device)
         rowptr, col, val, _ = q1_assemble(n, kappa.detach().contiguous(), setup.beta, zeros_f)
         solver = Solver(rowptr, col, val, setup.agg, setup.r,
-                        deflation_mode=setup.deflation_mode)
+                        deflation_mode=setup.deflation_mode, ortho=setup.ortho)
         x, info = solver.solve(b.detach().contiguous(), m=setup.m, tol=setup.tol,
                                maxit=setup.maxit)
         if info["status"] != N.GMRES_OK:

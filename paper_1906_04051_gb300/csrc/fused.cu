@@ -370,6 +370,7 @@ __global__ void __launch_bounds__(kArnThreads, 1)
   double* sbuf = scratch;
   for (int q = t; q < 2 * kArnWarps * kArnSliceCols * 33; q += kArnThreads) sbuf[q] = 0.0;
   bool waited = !a.pre;
+  const bool multi = R1 - R0 > a.RS;  // w goes through global memory to the update
   for (long long s0 = R0; s0 < R1; s0 += a.RS) {
     const long long s1 = s0 + a.RS < R1 ? s0 + a.RS : R1;
     // ---- 1. SpMV of the super-tile's rows: w and u_j into shared memory ----------------
@@ -394,7 +395,7 @@ __global__ void __launch_bounds__(kArnThreads, 1)
       for (int q = t; q < a.r; q += kArnThreads) Ss[q] = a.sdefl[q];
     __syncthreads();
     // + A W s' (the row's A W entries, s' from shared memory), the scale sigma_j; w also to
-    // global memory for the update when the block has more than one super-tile.  The rows
+    // global memory when the block has more than one super-tile (the update reads it there).  The rows
     // are taken kArnAwRows per thread at a time, each level of the A W gather (row
     // pointers, then the first entry of every row) issued for all of them at once.
     for (long long i0 = s0 + t; i0 < s1; i0 += (long long)kArnAwRows * kArnThreads) {
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(kArnThreads, 1)
           for (int e = e0[b] + 1; e < e1[b]; ++e) aw += __ldg(a.auval + e) * Ss[__ldg(a.aucol + e)];
           const TACC wv = row < N ? sig * (Ws[row - s0] + aw) : (TACC)0;
           Ws[row - s0] = wv;
-          if (row < N) a.w[row] = wv;
+          if (multi && row < N) a.w[row] = wv;
         }
       }
     }
