@@ -37,10 +37,11 @@ namespace {
 
 constexpr int kArnWarps = 16;
 constexpr int kArnThreads = kArnWarps * 32;
-constexpr int kArnSliceCols = (kMaxK + kArnWarps - 1) / kArnWarps;  // 5 accumulators per set
 constexpr int kArnUnit = 256;                    // rows per unit of the row partition
 constexpr size_t kArnSmem = 220 * 1024;          // dynamic shared memory
-constexpr size_t kArnScratch = 2 * kArnWarps * kArnSliceCols * 33 * sizeof(double);  // reductions
+// reductions: lane-wise totals [2][kMaxK][33] (FP64) or warp sums [2][16][kMaxK] (FP32)
+constexpr size_t kArnScratch = 2 * kMaxK * 33 * sizeof(double);
+constexpr size_t kArnStaging = 2 * 2 * 16 * 32 * sizeof(double);  // FP64 multi-dot staging
 constexpr long long kArnSpins = 1LL << 21;       // polls of the barrier word: about a second
 constexpr int kArnNormCol = 2 * kMaxK;           // column of ctl.part holding the norm partials
 constexpr int kArnAwRows = 12;                   // rows per thread of an A W gather batch
@@ -217,44 +218,6 @@ __device__ __forceinline__ void arn_dia_rows(TACC (&acc)[B], long long row0, lon
   }
 }
 
-// Multi-dot of one basis column (col) over chunks [0, nch) of 32 x VN rows of the
-// super-tile starting at row s0, by one warp: a1 += V_col . w and a2 += V_col . u_j per
-// lane; the column's chunks are loaded D ahead into registers.
-template <typename TV, typename TACC>
-__device__ __forceinline__ void arn_dot_column(TACC& a1, TACC& a2, const TV* V, long long ldv,
-                                               int col, long long s0, int nch, const TACC* Ws,
-                                               const TACC* Us, int lane) {
-  constexpr int VN = ArnVec<TV>::n;
-  constexpr int D = arn_loads<TV>();
-  const TV* pv = V + (size_t)col * ldv + s0 + lane * VN;
-  TACC buf[D][VN];
-#pragma unroll
-  for (int d = 0; d < D; ++d)
-    if (d < nch) arn_ldg<TV, TACC, VN>(pv + (size_t)d * 32 * VN, buf[d]);
-  pv += (size_t)D * 32 * VN;
-  const TACC* pw = Ws + lane * VN;
-  const TACC* pu = Us + lane * VN;
-  for (int q0 = 0; q0 < nch; q0 += D) {
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      if (q0 + d < nch) {
-        TACC wv[VN], uv[VN];
-        ld_acc<VN>(pw, wv);
-        ld_acc<VN>(pu, uv);
-        pw += 32 * VN;
-        pu += 32 * VN;
-#pragma unroll
-        for (int e = 0; e < VN; ++e) {
-          a1 += buf[d][e] * wv[e];
-          a2 += buf[d][e] * uv[e];
-        }
-        if (q0 + d + D < nch) arn_ldg<TV, TACC, VN>(pv, buf[d]);
-        pv += 32 * VN;
-      }
-    }
-  }
-}
-
 // Multi-dot in row-chunk order (FP32 basis): warp w takes the chunks w, w + 16, ... of the
 // super-tile and, per pass, a group of up to kArnGroup columns: one 16-byte load per column
 // and lane for the same rows, so the loads in flight of a warp fall in one row window of
@@ -308,6 +271,74 @@ __device__ __forceinline__ void arn_dots_rows(double* wsum, const TV* V, long lo
   }
 }
 
+// Multi-dot of an FP64 basis: the 16 warps form 4 groups; group cg takes the columns
+// cg, cg + 4, ... one after the other, and its 4 warps stream each column together, warp ws
+// taking the chunks ws, ws + 4, ... (D chunks in flight per warp, the stream running on
+// across column boundaries).  Four warps on one column keep long contiguous runs of the
+// column in flight, which DRAM serves about twice as fast as one warp per column.  When a
+// column ends, the group's 4 lane-wise partial sums meet in shared memory (double-buffered
+// staging, one named barrier of the group) and warp ws = 0 adds them, in warp order, into
+// the lane-wise totals sbuf[set][c][lane]: one FP64 add per lane, warp and column.
+template <typename TV, typename TACC>
+__device__ __forceinline__ void arn_dots_group4(double* sbuf, double* stg, const TV* V,
+                                                long long ldv, int k, long long s0, int nch,
+                                                const TACC* Ws, const TACC* Us, int warp,
+                                                int lane) {
+  constexpr int VN = ArnVec<TV>::n;
+  constexpr int D = arn_loads<TV>();
+  const int cg = warp >> 2, ws = warp & 3;
+  const int ncg = cg < k ? (k - cg + 3) / 4 : 0;  // columns of this group
+  const int cpw = nch / 4;                         // chunks per warp and column
+  const int T = ncg * cpw;
+  if (T == 0) return;
+  auto src = [&](int t) {
+    const int i = t / cpw, q = ws + 4 * (t - i * cpw);
+    return V + (size_t)(cg + 4 * i) * ldv + s0 + (size_t)q * 32 * VN + lane * VN;
+  };
+  TACC buf[D][VN];
+#pragma unroll
+  for (int d = 0; d < D; ++d)
+    if (d < T) arn_ldg<TV, TACC, VN>(src(d), buf[d]);
+  TACC a1 = 0, a2 = 0;
+  int i = 0, qi = 0;  // column of the group and chunk of the warp being consumed
+  for (int t0 = 0; t0 < T; t0 += D) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const int t = t0 + d;
+      if (t < T) {
+        const int q = ws + 4 * qi;
+        TACC wv[VN], uv[VN];
+        ld_acc<VN>(Ws + (size_t)q * 32 * VN + lane * VN, wv);
+        ld_acc<VN>(Us + (size_t)q * 32 * VN + lane * VN, uv);
+#pragma unroll
+        for (int e = 0; e < VN; ++e) {
+          a1 += buf[d][e] * wv[e];
+          a2 += buf[d][e] * uv[e];
+        }
+        if (t + D < T) arn_ldg<TV, TACC, VN>(src(t + D), buf[d]);
+        if (++qi == cpw) {  // column cg + 4 i is done in this warp
+          double* sb = stg + (size_t)(i & 1) * 2 * kArnWarps * 32;
+          sb[(0 * kArnWarps + warp) * 32 + lane] = (double)a1;
+          sb[(1 * kArnWarps + warp) * 32 + lane] = (double)a2;
+          asm volatile("bar.sync %0, 128;" ::"r"(1 + cg) : "memory");
+          if (ws == 0) {
+            const int c = cg + 4 * i;
+#pragma unroll
+            for (int set = 0; set < 2; ++set) {
+              const double* g = sb + (size_t)(set * kArnWarps + 4 * cg) * 32 + lane;
+              sbuf[((size_t)set * kMaxK + c) * 33 + lane] += ((g[0] + g[32]) + (g[64] + g[96]));
+            }
+          }
+          a1 = 0;
+          a2 = 0;
+          qi = 0;
+          ++i;
+        }
+      }
+    }
+  }
+}
+
 template <typename TV, typename TACC, int ND>
 __global__ void __launch_bounds__(kArnThreads, 1)
     k_arnoldi(const __grid_constant__ ArnArgs<TV, TACC> a) {
@@ -336,6 +367,7 @@ __global__ void __launch_bounds__(kArnThreads, 1)
   double* scratch = reinterpret_cast<double*>(
       smem + ((2 * (size_t)a.RS + (size_t)a.r) * sizeof(TACC) + 127) / 128 * 128);
   double* sL = scratch + kArnScratch / sizeof(double);  // k x k, strictly lower part used
+  double* stg = sL + (size_t)kMaxK * kMaxK;  // FP64 multi-dot staging: [2][2][16 warps][32]
   __shared__ double ssig[kMaxK];
 
   if (!a.pre) {
@@ -363,12 +395,11 @@ __global__ void __launch_bounds__(kArnThreads, 1)
   const TV* xj = a.V + (size_t)a.j * a.ldv;
   const TACC sig = (TACC)__ldcg(&ctl.sigma[a.j]);
   const int nd = ND > 0 ? ND : a.dia.nd;
-  const int nw = slice_cols(k, warp, kArnWarps);
 
-  // per-lane partial sums of the multi-dot, [set][warp][column group][lane], in shared
-  // memory (each slot owned by one lane) so that they persist across super-tiles
+  // partial sums of the multi-dot in shared memory, so that they persist across super-tiles
+  // (FP64: lane-wise per column; FP32: per warp and column)
   double* sbuf = scratch;
-  for (int q = t; q < 2 * kArnWarps * kArnSliceCols * 33; q += kArnThreads) sbuf[q] = 0.0;
+  for (int q = t; q < 2 * kMaxK * 33; q += kArnThreads) sbuf[q] = 0.0;
   bool waited = !a.pre;
   const bool multi = R1 - R0 > a.RS;  // w goes through global memory to the update
   for (long long s0 = R0; s0 < R1; s0 += a.RS) {
@@ -430,15 +461,9 @@ __global__ void __launch_bounds__(kArnThreads, 1)
     __syncthreads();
     const int nch = (int)((s1 - s0) / (32 * VN));
     if constexpr (sizeof(TV) == 8) {
-      // FP64: warp s takes the columns s, s + 16, ... (column group g = column / 16), one at
-      // a time, so that each lane's partial sums (in shared memory) need one add per lane
-      // and column in the end: the FP64 pipe is the bound, and its adds are dear
-      for (int g = 0; g < nw; ++g) {
-        TACC a1 = 0, a2 = 0;
-        arn_dot_column<TV, TACC>(a1, a2, a.V, a.ldv, warp + kArnWarps * g, s0, nch, Ws, Us, lane);
-        sbuf[((0 * kArnWarps + warp) * kArnSliceCols + g) * 33 + lane] += (double)a1;
-        sbuf[((1 * kArnWarps + warp) * kArnSliceCols + g) * 33 + lane] += (double)a2;
-      }
+      // FP64 (its FMA pipe is the bound and its adds are dear): lane-wise partial sums per
+      // column, four warps per column
+      arn_dots_group4<TV, TACC>(sbuf, stg, a.V, a.ldv, k, s0, nch, Ws, Us, warp, lane);
     } else {
       arn_dots_rows<TV, TACC>(sbuf, a.V, a.ldv, k, s0, nch, Ws, Us, warp, lane);
     }
@@ -446,14 +471,17 @@ __global__ void __launch_bounds__(kArnThreads, 1)
   }
   // per-block column sums: each column belongs to one warp; its lanes' partial sums (in
   // shared memory) are summed 16 at a time by lane pairs
-  if constexpr (sizeof(TV) == 8) {
-    const int p = lane >> 1, half = lane & 1;  // pair p: set p / 5, accumulator p % 5
-    const int set = p / kArnSliceCols, i = p % kArnSliceCols;
-    double v = 0.0;
-    const bool live = p < 2 * kArnSliceCols && i < nw;
-    if (live) v = tree16(sbuf + ((set * kArnWarps + warp) * kArnSliceCols + i) * 33 + half * 16);
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    if (live && half == 0) sred[set * k + warp + kArnWarps * i] = v;
+  if constexpr (sizeof(TV) == 8) {  // the 32 lane-wise totals of each column, pairwise
+    for (int q0 = 0; q0 < 2 * k; q0 += kArnThreads / 2) {
+      const int q = q0 + (t >> 1), half = t & 1;
+      double v = 0.0;
+      if (q < 2 * k) {
+        const int set = q / k, c = q % k;
+        v = tree16(sbuf + ((size_t)set * kMaxK + c) * 33 + half * 16);
+      }
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      if (q < 2 * k && half == 0) sred[q] = v;
+    }
     __syncthreads();
   } else {  // the 16 warps' sums of each column, in warp order
     for (int q = t; q < 2 * k; q += kArnThreads) {
@@ -589,7 +617,7 @@ struct Arn {
   // rows of a super-tile: w and u_j slices, s' and the reduction scratch in kArnSmem
   static long long super_rows(int r) {
     const size_t fixed = ((size_t)r * sizeof(TACC) + 127) / 128 * 128 + kArnScratch +
-                         sizeof(double) * kMaxK * kMaxK + 256;
+                         sizeof(double) * kMaxK * kMaxK + kArnStaging + 256;
     if (fixed >= kArnSmem) return 0;
     return (long long)((kArnSmem - fixed) / (2 * sizeof(TACC))) / kArnUnit * kArnUnit;
   }

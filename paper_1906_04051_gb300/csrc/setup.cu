@@ -361,6 +361,185 @@ __global__ void __launch_bounds__(32 * kGjRowsPerBlock)
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// The same Gauss-Jordan elimination in one cooperative kernel (r small enough that every
+// block keeps its rows of [T | slots] in shared memory): block b owns the rows b, b + G, ...
+// and each step costs one grid barrier instead of one launch.  At the end of step k - 1
+// every block proposes its largest |G_{i,k}| over its unused rows and copies that row's
+// active part (left columns k .. r-1, then slots 0 .. k-1) into its candidate slot; after
+// the barrier every block picks the same pivot (largest value, then lowest row) from the G
+// proposals, reads the winning row, normalises it (its identity entry goes to slot k) and
+// eliminates column k from its own rows, exactly r entries per row.
+// ---------------------------------------------------------------------------------------
+constexpr int kGjPThreads = 512;
+constexpr long long kGjSpins = 1LL << 21;  // polls of the barrier word: about a second
+
+struct GjP {
+  double* cval;    // G candidate values
+  int* cidx;       // G candidate rows
+  double* crow;    // G x r candidate rows (active parts)
+  int* piv;        // r: pivot row of step k
+  int* slot;       // r: step at which row i was the pivot
+  unsigned* bar;   // 2 words: arrivals, generation
+  int* err;
+};
+
+__device__ __forceinline__ bool gj_grid_sync(unsigned* bar, unsigned& gen) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicExch(&bar[1], gen + 1u);
+    } else {
+      long long spins = 0;
+      while (*(volatile unsigned*)&bar[1] == gen)
+        if (++spins > kGjSpins) {
+          ok = 0;
+          break;
+        }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  ++gen;
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(kGjPThreads, 1)
+    k_gj_persistent(int r, const double* __restrict__ T, GjP x, double* __restrict__ Tinv,
+                    double* __restrict__ TinvT) {
+  extern __shared__ double gsm[];
+  __shared__ int s_used[64];
+  __shared__ int s_p, s_src;
+  __shared__ double s_ip;
+  const int G = gridDim.x, b = blockIdx.x, t = threadIdx.x;
+  const int nq = (r - b + G - 1) / G;  // rows b, b + G, ... of this block
+  double* rows = gsm;                  // nq x 2r: left columns [0, r), slots [r, 2r)
+  double* prow = gsm + (size_t)nq * 2 * r;
+  unsigned gen = *(volatile unsigned*)&x.bar[1];
+  for (int q = t; q < nq; q += blockDim.x) s_used[q] = 0;
+  for (long long e = t; e < (long long)nq * 2 * r; e += blockDim.x) {
+    const int q = (int)(e / (2 * r)), c = (int)(e % (2 * r));
+    rows[e] = c < r ? T[(size_t)(b + q * G) * r + c] : 0.0;
+  }
+  __syncthreads();
+  // proposal for step k: largest |left[k]| over the unused rows, and that row's active part
+  auto propose = [&](int k) {
+    if (t < 32) {
+      double v = -1.0;
+      int i = 0x7fffffff;
+      for (int q = t; q < nq; q += 32)
+        if (!s_used[q]) argmax_merge(v, i, fabs(rows[(size_t)q * 2 * r + k]), b + q * G);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        argmax_merge(v, i, ov, oi);
+      }
+      if (t == 0) {
+        x.cval[b] = v;
+        x.cidx[b] = i;
+        s_p = i;
+      }
+    }
+    __syncthreads();
+    const int i = s_p;
+    if (i < r) {
+      const double* row = rows + (size_t)((i - b) / G) * 2 * r;
+      double* dst = x.crow + (size_t)b * r;
+      for (int c = t; c < r; c += blockDim.x)
+        dst[c] = c < r - k ? row[k + c] : row[r + (c - (r - k))];
+    }
+  };
+  propose(0);
+  for (int k = 0; k < r; ++k) {
+    if (!gj_grid_sync(x.bar, gen)) {
+      if (t == 0) atomicOr(x.err, 16);
+      return;
+    }
+    if (t < 32) {  // the pivot: largest candidate, then lowest row (the same in every block)
+      double v = -1.0;
+      int i = 0x7fffffff, src = 0;
+      for (int q = t; q < G; q += 32) {
+        const double ov = __ldcg(x.cval + q);
+        const int oi = __ldcg(x.cidx + q);
+        if (ov > v || (ov == v && oi < i)) {
+          v = ov;
+          i = oi;
+          src = q;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        const int os = __shfl_xor_sync(0xffffffffu, src, o);
+        if (ov > v || (ov == v && oi < i)) {
+          v = ov;
+          i = oi;
+          src = os;
+        }
+      }
+      if (t == 0) {
+        if (!(v > 0.0) || i >= r) {  // singular: record it and stop
+          if (b == 0) atomicOr(x.err, 8);
+          s_p = -1;
+        } else {
+          s_p = i;
+          s_ip = 1.0 / __ldcg(x.crow + (size_t)src * r);
+          if (b == 0) {
+            x.piv[k] = i;
+            x.slot[i] = k;
+          }
+        }
+      }
+      if (t == 0) s_src = src;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p < 0) return;
+    const double ip = s_ip;
+    const double* crow = x.crow + (size_t)s_src * r;
+    // the normalised pivot row: left columns k+1 .. r-1 at prow[0 ..), slots 0 .. k at
+    // prow[r - k - 1 ..] (slot k: the identity entry 1 / pivot)
+    const int nl = r - k - 1;
+    for (int c = t; c < r; c += blockDim.x)
+      prow[c] = c < nl ? __ldcg(crow + 1 + c) * ip : (c - nl < k ? __ldcg(crow + 1 + c) * ip : ip);
+    __syncthreads();
+    // eliminate column k from every own row but the pivot; the pivot row becomes prow
+    for (int q = 0; q < nq; ++q) {
+      double* row = rows + (size_t)q * 2 * r;
+      const bool piv = b + q * G == p;
+      const double f = row[k];
+      for (int c = t; c < r; c += blockDim.x) {
+        double* dst = c < nl ? row + k + 1 + c : row + r + (c - nl);
+        *dst = piv ? prow[c] : fma(-f, prow[c], *dst);
+      }
+      if (piv && t == 0) s_used[q] = 1;
+    }
+    __syncthreads();
+    if (k + 1 < r) propose(k + 1);
+  }
+  if (!gj_grid_sync(x.bar, gen)) {
+    if (t == 0) atomicOr(x.err, 16);
+    return;
+  }
+  // own rows: row p = piv[k] holds row k of T^-1 with column j at slot(j)
+  for (long long e = t; e < (long long)nq * r; e += blockDim.x) {
+    const int q = (int)(e / r), j = (int)(e % r);
+    const int i = b + q * G;
+    const int k = __ldcg(x.slot + i);
+    const double v = rows[(size_t)q * 2 * r + r + __ldcg(x.slot + j)];
+    Tinv[(size_t)k * r + j] = v;
+    if (TinvT) TinvT[(size_t)j * r + k] = v;
+  }
+}
+
 // T^-1[a][c] = s(p_a) G[p_a][r + slot(c)]  (and its transpose)
 __global__ void k_gj_extract(int r, const double* __restrict__ G, GjAux x,
                              double* __restrict__ Tinv, double* __restrict__ TinvT) {
@@ -618,8 +797,16 @@ cudaError_t launch_coarse_T(int r, const int* rowptr, const int* col, const doub
 
 size_t gj_aux_bytes(int r) {
   return sizeof(double) * (2 * (size_t)r + 2 * kGjMaxBlocks) +
-         sizeof(int) * (3 * (size_t)r + 2 * kGjMaxBlocks);
+         sizeof(int) * (3 * (size_t)r + 2 * kGjMaxBlocks) + 4 * sizeof(unsigned);
 }
+
+namespace {
+// shared memory of the cooperative Gauss-Jordan kernel on `grid` blocks
+size_t gj_persistent_smem(int r, int grid) {
+  const size_t nq = ((size_t)r + grid - 1) / grid;
+  return sizeof(double) * (nq * 2 * (size_t)r + (size_t)r);
+}
+}  // namespace
 
 cudaError_t launch_gauss_jordan(int r, const double* T, double* G /* r*2r */, void* aux,
                                 double* Tinv, double* TinvT, int* err, cudaStream_t st) {
@@ -635,6 +822,39 @@ cudaError_t launch_gauss_jordan(int r, const double* T, double* G /* r*2r */, vo
   x.cidx = q + 3 * (size_t)r;
   x.err = err;
   cudaError_t e;
+  {  // one cooperative kernel when every block's rows fit in shared memory
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return e;
+    const int grid = r < sms ? r : sms;
+    const size_t psm = gj_persistent_smem(r, grid);
+    if (psm <= 200 * 1024 && (r + grid - 1) / grid <= 63) {
+      static cudaError_t attr = cudaFuncSetAttribute(
+          k_gj_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (attr != cudaSuccess) return attr;
+      GjP p;
+      p.cval = x.cval;
+      p.cidx = x.cidx;
+      p.crow = G;  // G x r doubles of the r x 2r work matrix
+      p.piv = x.piv;
+      p.slot = x.slot;
+      p.bar = reinterpret_cast<unsigned*>(x.cidx + 2 * kGjMaxBlocks);
+      p.err = err;
+      if ((e = cudaMemsetAsync(p.bar, 0, 2 * sizeof(unsigned), st)) != cudaSuccess) return e;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)grid);
+      cfg.blockDim = dim3((unsigned)kGjPThreads);
+      cfg.dynamicSmemBytes = psm;
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeCooperative;
+      at[0].val.cooperative = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      return cudaLaunchKernelEx(&cfg, k_gj_persistent, r, T, p, Tinv, TinvT);
+    }
+  }
   const size_t sm = sizeof(double) * (size_t)r;
   if (sm > 48 * 1024) {
     e = cudaFuncSetAttribute(k_gj_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
