@@ -124,7 +124,7 @@ __global__ void k_adapt_z(Ctl ctl, int ninv, double* __restrict__ zout, int* __r
   double hmax = 0.0;
   for (int t = lane; t < k * k; t += 32) {
     const int i = t / k, c = t % k;
-    const double v = ctl.Hr[(size_t)i * ldh + c];
+    const double v = i <= c + 1 ? ctl.Hr[(size_t)i * ldh + c] : 0.0;  // below: never written
     a[t] = v;
     hmax = fmax(hmax, fabs(v));
   }
@@ -179,8 +179,9 @@ __global__ void k_adapt_z(Ctl ctl, int ninv, double* __restrict__ zout, int* __r
   double rho = 0.0, nhz = 0.0, hz0 = 0.0, hz1 = 0.0;
   for (int c = 0; c < k; ++c) {
     const double zc = wz_get(z, c);
-    if (lane < k) hz0 += ctl.Hr[(size_t)lane * ldh + c] * zc;
-    if (lane + 32 < k) hz1 += ctl.Hr[(size_t)(lane + 32) * ldh + c] * zc;
+    // H z over the Hessenberg entries (row i has columns c >= i - 1)
+    if (lane < k && lane <= c + 1) hz0 += ctl.Hr[(size_t)lane * ldh + c] * zc;
+    if (lane + 32 < k && lane + 32 <= c + 1) hz1 += ctl.Hr[(size_t)(lane + 32) * ldh + c] * zc;
   }
   rho = warp_sum(z.z0 * hz0 + z.z1 * hz1);
   nhz = warp_sum(hz0 * hz0 + hz1 * hz1);

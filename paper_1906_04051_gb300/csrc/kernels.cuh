@@ -756,7 +756,12 @@ __device__ void ritz_warp(Ctl& ctl, double* A, double& smod, int& sfail) {
   const int lane = threadIdx.x & 31;
   if (n <= 0) return;
   const int ldh = ctl.ldh;
-  for (int t = lane; t < n * n; t += 32) A[t] = ctl.Hr[(size_t)(t / n) * ldh + t % n];
+  // the Hessenberg block as built; entries below the subdiagonal are never written, so they
+  // are taken as the zeros they are (not read from memory)
+  for (int t = lane; t < n * n; t += 32) {
+    const int i = t / n, c = t % n;
+    A[t] = i <= c + 1 ? ctl.Hr[(size_t)i * ldh + c] : 0.0;
+  }
   __syncwarp();
   __shared__ double sre, sim;
   hqr_warp(A, n, sre, sim, smod, sfail);

@@ -375,9 +375,11 @@ constexpr int kGjPThreads = 512;
 constexpr long long kGjSpins = 1LL << 21;  // polls of the barrier word: about a second
 
 struct GjP {
-  double* cval;    // G candidate values
-  int* cidx;       // G candidate rows
-  double* crow;    // G x r candidate rows (active parts)
+  // candidates of step k in buffer k & 1 (the step-(k+1) proposals of a block that has
+  // finished step k must not overwrite what a slower block still reads for step k)
+  double* cval;    // 2 x kGjMaxBlocks candidate values
+  int* cidx;       // 2 x kGjMaxBlocks candidate rows
+  double* crow;    // 2 x G x r candidate rows (active parts)
   int* piv;        // r: pivot row of step k
   int* slot;       // r: step at which row i was the pivot
   unsigned* bar;   // 2 words: arrivals, generation
@@ -442,8 +444,8 @@ __global__ void __launch_bounds__(kGjPThreads, 1)
         argmax_merge(v, i, ov, oi);
       }
       if (t == 0) {
-        x.cval[b] = v;
-        x.cidx[b] = i;
+        x.cval[(size_t)(k & 1) * kGjMaxBlocks + b] = v;
+        x.cidx[(size_t)(k & 1) * kGjMaxBlocks + b] = i;
         s_p = i;
       }
     }
@@ -451,7 +453,7 @@ __global__ void __launch_bounds__(kGjPThreads, 1)
     const int i = s_p;
     if (i < r) {
       const double* row = rows + (size_t)((i - b) / G) * 2 * r;
-      double* dst = x.crow + (size_t)b * r;
+      double* dst = x.crow + ((size_t)(k & 1) * G + b) * r;
       for (int c = t; c < r; c += blockDim.x)
         dst[c] = c < r - k ? row[k + c] : row[r + (c - (r - k))];
     }
@@ -465,9 +467,11 @@ __global__ void __launch_bounds__(kGjPThreads, 1)
     if (t < 32) {  // the pivot: largest candidate, then lowest row (the same in every block)
       double v = -1.0;
       int i = 0x7fffffff, src = 0;
+      const double* cv = x.cval + (size_t)(k & 1) * kGjMaxBlocks;
+      const int* ci = x.cidx + (size_t)(k & 1) * kGjMaxBlocks;
       for (int q = t; q < G; q += 32) {
-        const double ov = __ldcg(x.cval + q);
-        const int oi = __ldcg(x.cidx + q);
+        const double ov = __ldcg(cv + q);
+        const int oi = __ldcg(ci + q);
         if (ov > v || (ov == v && oi < i)) {
           v = ov;
           i = oi;
@@ -491,7 +495,7 @@ __global__ void __launch_bounds__(kGjPThreads, 1)
           s_p = -1;
         } else {
           s_p = i;
-          s_ip = 1.0 / __ldcg(x.crow + (size_t)src * r);
+          s_ip = 1.0 / __ldcg(x.crow + ((size_t)(k & 1) * G + src) * r);
           if (b == 0) {
             x.piv[k] = i;
             x.slot[i] = k;
@@ -504,7 +508,7 @@ __global__ void __launch_bounds__(kGjPThreads, 1)
     const int p = s_p;
     if (p < 0) return;
     const double ip = s_ip;
-    const double* crow = x.crow + (size_t)s_src * r;
+    const double* crow = x.crow + ((size_t)(k & 1) * G + s_src) * r;
     // the normalised pivot row: left columns k+1 .. r-1 at prow[0 ..), slots 0 .. k at
     // prow[r - k - 1 ..] (slot k: the identity entry 1 / pivot)
     const int nl = r - k - 1;
@@ -836,7 +840,7 @@ cudaError_t launch_gauss_jordan(int r, const double* T, double* G /* r*2r */, vo
       GjP p;
       p.cval = x.cval;
       p.cidx = x.cidx;
-      p.crow = G;  // G x r doubles of the r x 2r work matrix
+      p.crow = G;  // 2 x grid x r doubles of the r x 2r work matrix (grid <= r)
       p.piv = x.piv;
       p.slot = x.slot;
       p.bar = reinterpret_cast<unsigned*>(x.cidx + 2 * kGjMaxBlocks);
