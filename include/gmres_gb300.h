@@ -134,6 +134,19 @@ typedef enum {
                                single-system */
 } gmres_ortho;
 
+typedef enum {
+  GMRES_DOT_FP64 = 0,  /* the basis multi-dot in FP64 FMAs */
+  GMRES_DOT_DF32 = 1   /* the multi-dot V^T [w, v_j] of the one-reduction MGS step in
+                          double-FP32 on the FP32 pipe: each FP64 operand split into two
+                          floats (47 significant bits), products exact by FMA (Dekker's
+                          two-product), sums by Knuth's TwoSum, each block's totals rounded
+                          to FP64 once; magnitudes below 2^-126 count as 0.  The rest of the
+                          step (SpMV, update, norm, H, rotations) stays FP64.  FP64 solves
+                          with GMRES_ORTHO_MGS_LOWSYNC only (GMRES_ERR_INVALID_ARG
+                          otherwise); applied where the step runs fused (a diagonal-structured
+                          A, aggregate or no deflation), FP64 FMAs elsewhere */
+} gmres_dot_arith;
+
 typedef struct {
   int32_t precision;        /* gmres_precision */
   int32_t deflation_mode;   /* gmres_deflation_mode */
@@ -150,6 +163,7 @@ typedef struct {
   int32_t rmax;             /* GMRES_DEFL_ADAPTIVE: most columns of U, 1..32 (paper: 20) */
   int32_t ninv;             /* GMRES_DEFL_ADAPTIVE: inverse power iterations per restart */
   int32_t ortho;            /* gmres_ortho (default CGS2) */
+  int32_t dot_arith;        /* gmres_dot_arith (default GMRES_DOT_FP64) */
 } gmres_opts;
 
 /* Phases reported by gmres_profile (kernel groups of one solve). */

@@ -29,6 +29,7 @@ FP64, FP32_INNER, BF16_BASIS = 0, 1, 2
 DEFL_EBP, DEFL_PROJECTOR, DEFL_NONE, DEFL_ADAPTIVE = 0, 1, 2, 3
 MU_RITZ_FIRST_CYCLE, MU_USER, MU_NORM_INF = 0, 1, 2
 ORTHO_CGS2, ORTHO_MGS, ORTHO_MGS_LOWSYNC = 0, 1, 2
+DOT_FP64, DOT_DF32 = 0, 1
 PHASES = ["setup", "residual", "spmv", "dot1", "upd1dot2", "upd2norm", "defl", "cycle_end",
           "ritz", "proj_final", "adapt", "mgs", "arnoldi"]
 
@@ -48,7 +49,7 @@ class gmres_opts(C.Structure):
                 ("fixed_iterations", C.c_int32), ("r0_norm_ref", C.c_double),
                 ("timeout_ms", C.c_int32), ("inner_tol", C.c_double),
                 ("profile", C.c_int32), ("rmax", C.c_int32), ("ninv", C.c_int32),
-                ("ortho", C.c_int32)]
+                ("ortho", C.c_int32), ("dot_arith", C.c_int32)]
 
 
 class gmres_info(C.Structure):

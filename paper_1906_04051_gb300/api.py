@@ -45,7 +45,7 @@ class Solver:
                  deflation_mode=N.DEFL_EBP, mu_mode=N.MU_RITZ_FIRST_CYCLE, mu_user=0.0,
                  fixed_iterations=False, r0_norm_ref=0.0, timeout_ms=0, inner_tol=0.0,
                  profile=False, rmax=20, ninv=20, ortho=N.ORTHO_CGS2, w_dense=None,
-                 stream=None):
+                 dot_arith=N.DOT_FP64, stream=None):
         L = N.load()
         n = rowptr.numel() - 1
         _dev(rowptr, torch.int32, "rowptr")
@@ -81,6 +81,7 @@ class Solver:
         opts.rmax = int(rmax)
         opts.ninv = int(ninv)
         opts.ortho = int(ortho)
+        opts.dot_arith = int(dot_arith)
         self._stream = stream
         h = C.c_void_p()
         st = L.gmres_create(C.byref(h), C.byref(csr), C.byref(defl) if defl else None,

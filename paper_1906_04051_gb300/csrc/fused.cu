@@ -184,6 +184,124 @@ __device__ __forceinline__ void arn_stv(TV* p, const TACC (&v)[VN]) {
   }
 }
 
+// ---- double-FP32 arithmetic for the FP64 multi-dot (GMRES_DOT_DF32) ---------------------
+// GB300 issues FP64 FMAs at 2 lanes per clock and multiprocessor, FP32 FMAs at 128: the
+// FP64 multi-dot is bound by its FMA pipe, not by HBM.  In the double-FP32 form each FP64
+// operand is split into two floats, x ~ hi + lo, with integer operations only (hi = x with
+// its significand cut to 24 bits, lo = the remaining 29 bits rounded to 24: 47 significant
+// bits in all); a product takes the exact product of the high parts by an FMA (Dekker's
+// two-product), the two cross terms in FP32 (lo * lo, below 2^-46 of the product, is
+// dropped), and the running sum is a pair (s, c) advanced by Knuth's TwoSum, every rounding
+// error gathered in c.  Magnitudes between 2^-126 and 2^127 split exactly as stated; smaller
+// ones become 0 (an absolute error below 2^-126), larger ones infinity.
+__device__ __forceinline__ void arn_df_split(double v, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+  const unsigned sgn = h32 & 0x80000000u;
+  const unsigned ah = h32 & 0x7fffffffu;
+  const int E = (int)(ah >> 20);  // biased FP64 exponent
+  // exponent and top 23 significand bits, rebiased from 1023 to 127 (mod 2^32)
+  unsigned hb = ((ah << 3) | (l32 >> 29)) - (896u << 23);
+  const unsigned m29 = l32 & 0x1fffffffu;  // the significand bits below hi's
+  const unsigned fb = __float_as_uint(__uint2float_rn(m29));
+  const unsigned lb = fb + ((unsigned)(E - 1075) << 23);  // m29 * 2^(E - 1075)
+  const bool okh = E >= 897;
+  const bool okl = okh && m29 != 0u && (int)(fb >> 23) + E - 1075 >= 1;
+  hb = E > 1150 ? 0x7f800000u : hb;
+  hi = __uint_as_float(okh ? (hb | sgn) : sgn);
+  lo = __uint_as_float(okl ? (lb | sgn) : 0u);
+}
+
+// (s, c) += (ah + al) (bh + bl); the _rn intrinsics keep the compiler from contracting the
+// error-free steps into FMAs
+__device__ __forceinline__ void arn_df_fma(float& s, float& c, float ah, float al, float bh,
+                                           float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);  // exact: p + e = ah bh
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  const float t = __fadd_rn(s, p);  // TwoSum: t + err = s + p exactly
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+// (s, c) += (s2, c2)
+__device__ __forceinline__ void arn_df_add(float& s, float& c, float s2, float c2) {
+  const float t = __fadd_rn(s, s2);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2, bp));
+  s = t;
+  c = __fadd_rn(__fadd_rn(c, c2), err);
+}
+
+// Multi-dot of an FP64 basis in double-FP32 (row order): warp w takes the chunks w, w + 16,
+// ... of 64 rows of the super-tile and, per pass, G columns at the same rows (one 16-byte
+// load per column and lane, all issued before the products); w and u_j come split from
+// shared memory (float2 hi, lo per row).  At the end of a pass the lanes' pairs of each
+// column meet by a shuffle tree of TwoSums and lane 0 adds them into dfp[warp][c][set]:
+// no FP64 instruction in the loop.
+constexpr int kArnDfGroup = 7;
+
+__device__ __forceinline__ void arn_dots_df(float* dfp, const double* V, long long ldv, int k,
+                                            long long s0, int nch, const float2* Ws,
+                                            const float2* Us, int warp, int lane) {
+  constexpr int G = kArnDfGroup;
+  for (int g0 = 0; g0 < k; g0 += G) {
+    const int gc = k - g0 < G ? k - g0 : G;
+    float s1[G], c1[G], s2[G], c2[G];
+#pragma unroll
+    for (int q = 0; q < G; ++q) s1[q] = c1[q] = s2[q] = c2[q] = 0.f;
+    const double* col = V + (size_t)g0 * ldv + s0 + (size_t)lane * 2;
+    for (int ch = warp; ch < nch; ch += kArnWarps) {
+      const int r = ch * 64 + lane * 2;
+      double v[G][2];
+#pragma unroll
+      for (int q = 0; q < G; ++q)
+        if (q < gc) arn_ldg<double, double, 2>(col + (size_t)q * ldv + (size_t)ch * 64, v[q]);
+      const float4 wv = *reinterpret_cast<const float4*>(Ws + r);
+      const float4 uv = *reinterpret_cast<const float4*>(Us + r);
+#pragma unroll
+      for (int q = 0; q < G; ++q)
+        if (q < gc) {
+          float h0, l0, h1, l1;
+          arn_df_split(v[q][0], h0, l0);
+          arn_df_split(v[q][1], h1, l1);
+          arn_df_fma(s1[q], c1[q], h0, l0, wv.x, wv.y);
+          arn_df_fma(s1[q], c1[q], h1, l1, wv.z, wv.w);
+          arn_df_fma(s2[q], c2[q], h0, l0, uv.x, uv.y);
+          arn_df_fma(s2[q], c2[q], h1, l1, uv.z, uv.w);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < G; ++q)
+      if (q < gc) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float a = __shfl_xor_sync(0xffffffffu, s1[q], o);
+          const float b = __shfl_xor_sync(0xffffffffu, c1[q], o);
+          const float d = __shfl_xor_sync(0xffffffffu, s2[q], o);
+          const float e = __shfl_xor_sync(0xffffffffu, c2[q], o);
+          arn_df_add(s1[q], c1[q], a, b);
+          arn_df_add(s2[q], c2[q], d, e);
+        }
+        if (lane == 0) {
+          float* p = dfp + ((size_t)warp * kMaxK + g0 + q) * 4;
+          float a = p[0], b = p[1];
+          arn_df_add(a, b, s1[q], c1[q]);
+          p[0] = a;
+          p[1] = b;
+          a = p[2];
+          b = p[3];
+          arn_df_add(a, b, s2[q], c2[q]);
+          p[2] = a;
+          p[3] = b;
+        }
+      }
+  }
+}
+
 // Diagonal part of the SpMV for B rows (row0 + b * stride) at once: all loads of the B
 // rows are issued before their products (ND > 0: ND diagonals, unrolled; ND = 0: nd at
 // run time, four at a time).  x indexes are clamped to a valid row, where the stored
@@ -291,35 +409,59 @@ __device__ __forceinline__ void arn_dots_group4(double* sbuf, double* stg, const
   const int cpw = nch / 4;                         // chunks per warp and column
   const int T = ncg * cpw;
   if (T == 0) return;
-  auto src = [&](int t) {
-    const int i = t / cpw, q = ws + 4 * (t - i * cpw);
-    return V + (size_t)(cg + 4 * i) * ldv + s0 + (size_t)q * 32 * VN + lane * VN;
+  // load side: a pointer that steps 4 chunks down the column, then on to the group's next
+  // column (no division per load)
+  const size_t step = (size_t)4 * 32 * VN;
+  const long long jump = 4 * ldv - (long long)cpw * (long long)step;
+  const TV* pl = V + (size_t)cg * ldv + s0 + (size_t)ws * 32 * VN + lane * VN;
+  int lq = 0;
+  auto next_load = [&](TACC (&o)[VN]) {
+    arn_ldg<TV, TACC, VN>(pl, o);
+    pl += step;
+    if (++lq == cpw) {
+      lq = 0;
+      pl += jump;
+    }
   };
   TACC buf[D][VN];
 #pragma unroll
   for (int d = 0; d < D; ++d)
-    if (d < T) arn_ldg<TV, TACC, VN>(src(d), buf[d]);
-  TACC a1 = 0, a2 = 0;
+    if (d < T) next_load(buf[d]);
+  TACC a1[VN], a2[VN];  // one chain per vector element (FP64 latency hidden by ILP)
+#pragma unroll
+  for (int e = 0; e < VN; ++e) {
+    a1[e] = 0;
+    a2[e] = 0;
+  }
   int i = 0, qi = 0;  // column of the group and chunk of the warp being consumed
+  const TACC* pw = Ws + (size_t)ws * 32 * VN + lane * VN;
+  const TACC* pu = Us + (size_t)ws * 32 * VN + lane * VN;
   for (int t0 = 0; t0 < T; t0 += D) {
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       const int t = t0 + d;
       if (t < T) {
-        const int q = ws + 4 * qi;
         TACC wv[VN], uv[VN];
-        ld_acc<VN>(Ws + (size_t)q * 32 * VN + lane * VN, wv);
-        ld_acc<VN>(Us + (size_t)q * 32 * VN + lane * VN, uv);
+        ld_acc<VN>(pw + (size_t)qi * step, wv);
+        ld_acc<VN>(pu + (size_t)qi * step, uv);
 #pragma unroll
         for (int e = 0; e < VN; ++e) {
-          a1 += buf[d][e] * wv[e];
-          a2 += buf[d][e] * uv[e];
+          a1[e] += buf[d][e] * wv[e];
+          a2[e] += buf[d][e] * uv[e];
         }
-        if (t + D < T) arn_ldg<TV, TACC, VN>(src(t + D), buf[d]);
+        if (t + D < T) next_load(buf[d]);
         if (++qi == cpw) {  // column cg + 4 i is done in this warp
           double* sb = stg + (size_t)(i & 1) * 2 * kArnWarps * 32;
-          sb[(0 * kArnWarps + warp) * 32 + lane] = (double)a1;
-          sb[(1 * kArnWarps + warp) * 32 + lane] = (double)a2;
+          double s1 = 0.0, s2 = 0.0;
+#pragma unroll
+          for (int e = 0; e < VN; ++e) {
+            s1 += (double)a1[e];
+            s2 += (double)a2[e];
+            a1[e] = 0;
+            a2[e] = 0;
+          }
+          sb[(0 * kArnWarps + warp) * 32 + lane] = s1;
+          sb[(1 * kArnWarps + warp) * 32 + lane] = s2;
           asm volatile("bar.sync %0, 128;" ::"r"(1 + cg) : "memory");
           if (ws == 0) {
             const int c = cg + 4 * i;
@@ -329,8 +471,6 @@ __device__ __forceinline__ void arn_dots_group4(double* sbuf, double* stg, const
               sbuf[((size_t)set * kMaxK + c) * 33 + lane] += ((g[0] + g[32]) + (g[64] + g[96]));
             }
           }
-          a1 = 0;
-          a2 = 0;
           qi = 0;
           ++i;
         }
@@ -339,10 +479,11 @@ __device__ __forceinline__ void arn_dots_group4(double* sbuf, double* stg, const
   }
 }
 
-template <typename TV, typename TACC, int ND>
+template <typename TV, typename TACC, int ND, bool DF>
 __global__ void __launch_bounds__(kArnThreads, 1)
     k_arnoldi(const __grid_constant__ ArnArgs<TV, TACC> a) {
   static_assert(std::is_same<TV, TACC>::value, "w and u_j slices share the basis element type");
+  static_assert(!DF || sizeof(TV) == 8, "the double-FP32 multi-dot takes an FP64 basis");
   constexpr int VN = ArnVec<TV>::n;
   constexpr int B = sizeof(TACC) == 8 ? 2 : 4;  // SpMV rows per thread and batch
   extern __shared__ __align__(128) unsigned char smem[];
@@ -454,13 +595,27 @@ __global__ void __launch_bounds__(kArnThreads, 1)
           for (int e = e0[b] + 1; e < e1[b]; ++e) aw += __ldg(a.auval + e) * Ss[__ldg(a.aucol + e)];
           const TACC wv = row < N ? sig * (Ws[row - s0] + aw) : (TACC)0;
           Ws[row - s0] = wv;
-          if (multi && row < N) a.w[row] = wv;
+          if ((multi || DF) && row < N) a.w[row] = wv;
         }
       }
     }
     __syncthreads();
     const int nch = (int)((s1 - s0) / (32 * VN));
-    if constexpr (sizeof(TV) == 8) {
+    if constexpr (DF) {
+      // w and u_j split in place (float2 hi, lo in the 8 bytes of each double); the update
+      // reads w from global memory
+      for (long long q = t; q < s1 - s0; q += kArnThreads) {
+        float h1, l1, h2, l2;
+        arn_df_split((double)Ws[q], h1, l1);
+        arn_df_split((double)Us[q], h2, l2);
+        reinterpret_cast<float2*>(Ws)[q] = make_float2(h1, l1);
+        reinterpret_cast<float2*>(Us)[q] = make_float2(h2, l2);
+      }
+      __syncthreads();
+      arn_dots_df(reinterpret_cast<float*>(sbuf), reinterpret_cast<const double*>(a.V), a.ldv, k,
+                  s0, nch, reinterpret_cast<const float2*>(Ws),
+                  reinterpret_cast<const float2*>(Us), warp, lane);
+    } else if constexpr (sizeof(TV) == 8) {
       // FP64 (its FMA pipe is the bound and its adds are dear): lane-wise partial sums per
       // column, four warps per column
       arn_dots_group4<TV, TACC>(sbuf, stg, a.V, a.ldv, k, s0, nch, Ws, Us, warp, lane);
@@ -471,7 +626,19 @@ __global__ void __launch_bounds__(kArnThreads, 1)
   }
   // per-block column sums: each column belongs to one warp; its lanes' partial sums (in
   // shared memory) are summed 16 at a time by lane pairs
-  if constexpr (sizeof(TV) == 8) {  // the 32 lane-wise totals of each column, pairwise
+  if constexpr (DF) {  // the 16 warps' pairs of each column in warp order, then FP64 once
+    for (int q = t; q < 2 * k; q += kArnThreads) {
+      const int set = q / k, c = q % k;
+      const float* dfp = reinterpret_cast<const float*>(sbuf);
+      float s = 0.f, cc = 0.f;
+      for (int w = 0; w < kArnWarps; ++w) {
+        const float* p = dfp + ((size_t)w * kMaxK + c) * 4 + 2 * set;
+        arn_df_add(s, cc, p[0], p[1]);
+      }
+      sred[q] = (double)s + (double)cc;
+    }
+    __syncthreads();
+  } else if constexpr (sizeof(TV) == 8) {  // the 32 lane-wise totals of each column, pairwise
     for (int q0 = 0; q0 < 2 * k; q0 += kArnThreads / 2) {
       const int q = q0 + (t >> 1), half = t & 1;
       double v = 0.0;
@@ -549,7 +716,7 @@ __global__ void __launch_bounds__(kArnThreads, 1)
     constexpr int U = sizeof(TV) == 8 ? 13 : 12;  // basis loads in flight per lane
     const int chunk = 32 * VN;
     const long long nch = (R1 - R0) / chunk;
-    const bool wsm = R1 - R0 <= a.RS;  // the block's w is still in shared memory
+    const bool wsm = !DF && R1 - R0 <= a.RS;  // the block's w is still in shared memory
     TV* __restrict__ vout = const_cast<TV*>(a.V) + (size_t)k * a.ldv;
     for (long long q = nch - 1 - warp; q >= 0; q -= kArnWarps) {
       const long long r = R0 + q * chunk + (long long)lane * VN;
@@ -621,14 +788,14 @@ struct Arn {
     if (fixed >= kArnSmem) return 0;
     return (long long)((kArnSmem - fixed) / (2 * sizeof(TACC))) / kArnUnit * kArnUnit;
   }
-  template <int ND>
+  template <int ND, bool DF>
   static cudaError_t prepare() {
-    return cudaFuncSetAttribute(k_arnoldi<TV, TACC, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kArnSmem);
+    return cudaFuncSetAttribute(k_arnoldi<TV, TACC, ND, DF>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kArnSmem);
   }
-  template <int ND>
+  template <int ND, bool DF>
   static cudaError_t launch_nd(const CycleArgs& c, const ArnArgs<TV, TACC>& p, cudaStream_t st) {
-    static cudaError_t prep = prepare<ND>();
+    static cudaError_t prep = prepare<ND, DF>();
     if (prep != cudaSuccess) return prep;
     const int grid = p.units < c.sms ? p.units : c.sms;
     cudaLaunchConfig_t cfg = {};
@@ -646,12 +813,12 @@ struct Arn {
     // pair, the kernel runs cooperatively in plain stream order from then on (same result)
     static bool pdl_ok = true;
     cfg.numAttrs = (c.pdl && pdl_ok) ? 2 : 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_arnoldi<TV, TACC, ND>, p);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_arnoldi<TV, TACC, ND, DF>, p);
     if (e != cudaSuccess && cfg.numAttrs == 2) {
       (void)cudaGetLastError();
       pdl_ok = false;
       cfg.numAttrs = 1;
-      e = cudaLaunchKernelEx(&cfg, k_arnoldi<TV, TACC, ND>, p);
+      e = cudaLaunchKernelEx(&cfg, k_arnoldi<TV, TACC, ND, DF>, p);
     }
     return e;
   }
@@ -686,7 +853,11 @@ struct Arn {
     p.ctl = c.ctl;
     p.gbar = c.gbar;
     // the 9-point stencils of the Q1 systems take an unrolled instantiation
-    return c.op.dia.nd == 9 ? launch_nd<9>(c, p, st) : launch_nd<0>(c, p, st);
+    if constexpr (sizeof(TV) == 8) {
+      if (c.dot_arith == GMRES_DOT_DF32)
+        return c.op.dia.nd == 9 ? launch_nd<9, true>(c, p, st) : launch_nd<0, true>(c, p, st);
+    }
+    return c.op.dia.nd == 9 ? launch_nd<9, false>(c, p, st) : launch_nd<0, false>(c, p, st);
   }
 };
 

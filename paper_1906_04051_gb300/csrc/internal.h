@@ -98,6 +98,7 @@ struct CycleArgs {
   int grid_small;        // blocks of the coarse GEMV
   int pdl;               // step kernels with programmatic dependent launch
   int ortho;             // gmres_ortho
+  int dot_arith;         // gmres_dot_arith (the fused FP64 step's multi-dot)
   unsigned* gbar;        // grid barrier of the modified Gram-Schmidt kernel (2 words)
 };
 

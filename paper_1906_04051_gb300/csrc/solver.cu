@@ -91,6 +91,7 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
   a.pdl = h->prof_on ? 0 : 1;  // per-phase events would serialise the launches anyway
   a.proj = (h->r > 0 && h->opts.deflation_mode == GMRES_DEFL_PROJECTOR) ? 1 : 0;
   a.ortho = h->opts.ortho;
+  a.dot_arith = h->opts.dot_arith;
   a.gbar = h->gbar.as<unsigned>();
   const bool mgs = a.ortho == GMRES_ORTHO_MGS;
   if (mgs) {
@@ -435,8 +436,12 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
   else gmres_opts_default(&opts);
   if (opts.precision < 0 || opts.precision > 2 || opts.deflation_mode < 0 ||
       opts.deflation_mode > 3 || opts.mu_mode < 0 || opts.mu_mode > 2 || opts.ortho < 0 ||
-      opts.ortho > 2)
+      opts.ortho > 2 || opts.dot_arith < 0 || opts.dot_arith > 1)
     return fail(nullptr, GMRES_ERR_INVALID_ARG, "invalid option value");
+  if (opts.dot_arith == GMRES_DOT_DF32 &&
+      (opts.precision != GMRES_FP64 || opts.ortho != GMRES_ORTHO_MGS_LOWSYNC))
+    return fail(nullptr, GMRES_ERR_INVALID_ARG,
+                "GMRES_DOT_DF32: FP64 solves with GMRES_ORTHO_MGS_LOWSYNC only");
   if (opts.ortho == GMRES_ORTHO_MGS && opts.precision != GMRES_FP64)
     return fail(nullptr, GMRES_ERR_INVALID_ARG, "GMRES_ORTHO_MGS is FP64 only");
   if (opts.ortho == GMRES_ORTHO_MGS_LOWSYNC && opts.precision == GMRES_BF16_BASIS)

@@ -31,10 +31,12 @@ def system(orc):
     return p, A, b
 
 
-def test_full_size_fixed_iterations_match_oracle_mgs(G, orc, system):
+@pytest.mark.parametrize("dot", ["fp64", "df32"])
+def test_full_size_fixed_iterations_match_oracle_mgs(G, orc, system, dot):
     p, A, b = system
     s = gpu_solver_from_oracle(G, A, p.agg, p.r, ortho=G.ORTHO_MGS_LOWSYNC, mu_mode=1,
-                               mu_user=14.0, fixed_iterations=True)
+                               mu_user=14.0, fixed_iterations=True,
+                               dot_arith=G.DOT_DF32 if dot == "df32" else G.DOT_FP64)
     xg, ig = s.solve(to_dev(b), m=50, tol=0.0, maxit=100)
     d = orc.Deflation(A, p.agg, p.r)
     xo, io = orc.gmres(A, b, defl=d, m=50, tol=0.0, maxit=100, mu_mode=1, mu_user=14.0,

@@ -121,3 +121,56 @@ def test_mgs_limits(G, orc):
     s = gpu_solver_from_oracle(G, A, p.agg, p.r, ortho=G.ORTHO_MGS)
     with pytest.raises(G.GmresError):  # the batched solve orthogonalises by CGS2
         G.batch_solve([s], [to_dev(b)], m=30, tol=1e-8, maxit=1000)
+
+
+@pytest.mark.parametrize("mode", ["ebp", "none"])
+def test_df32_multidot_fixed_iterations_match_oracle(G, orc, mode):
+    """The double-FP32 multi-dot (FP32-pipe products and sums, error-free) in the fused
+    one-reduction step: the oracle's FP64 MGS solution to 1e-9 after 47 fixed steps, and
+    results that differ from the FP64-FMA multi-dot's (it ran) by rounding only."""
+    p = W.convdiff(40, pe=25.0, sigma=0.5, seed=140, px=2, py=3)
+    A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f)
+    defl = mode == "ebp"
+    kw = dict(deflation_mode=G.DEFL_EBP if defl else G.DEFL_NONE, mu_mode=1, mu_user=5.0,
+              fixed_iterations=True, ortho=G.ORTHO_MGS_LOWSYNC)
+    agg, r = (p.agg, p.r) if defl else (None, 0)
+    s = gpu_solver_from_oracle(G, A, agg, r, dot_arith=G.DOT_DF32, **kw)
+    xg, ig = s.solve(to_dev(b), m=15, tol=0.0, maxit=47)
+    s64 = gpu_solver_from_oracle(G, A, agg, r, **kw)
+    x64, _ = s64.solve(to_dev(b), m=15, tol=0.0, maxit=47)
+    d = orc.Deflation(A, p.agg, p.r) if defl else None
+    xo, io = orc.gmres(A, b, defl=d, defl_mode=orc.DEFL_EBP if defl else orc.DEFL_NONE, m=15,
+                       tol=0.0, maxit=47, mu_mode=1, mu_user=5.0, fixed_iterations=True,
+                       ortho=orc.MGS)
+    assert ig["iters"] == io["iters"] == 47
+    assert relerr(xg.cpu().numpy(), xo) <= 1e-9
+    assert ig["rel_res_est"] == pytest.approx(io["rel_res_est"], rel=1e-6, abs=1e-13)
+    assert not torch.equal(xg, x64)
+    assert relerr(xg.cpu().numpy(), x64.cpu().numpy()) <= 1e-10
+
+
+def test_df32_multidot_to_tolerance_and_repeats(G, orc):
+    p = W.workload1()
+    A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f, p.u)
+    s = gpu_solver_from_oracle(G, A, p.agg, p.r, ortho=G.ORTHO_MGS_LOWSYNC,
+                               dot_arith=G.DOT_DF32)
+    xg, ig = s.solve(to_dev(b), m=30, tol=1e-11, maxit=20000)
+    xg2, ig2 = s.solve(to_dev(b), m=30, tol=1e-11, maxit=20000)
+    d = orc.Deflation(A, p.agg, p.r)
+    xo, io = orc.gmres(A, b, defl=d, m=30, tol=1e-11, maxit=20000, ortho=orc.MGS)
+    assert ig["status"] == 0 and ig["rel_res_true"] <= 1e-11
+    assert relerr(xg.cpu().numpy(), xo) <= 1e-9
+    assert abs(ig["iters"] - io["iters"]) <= 2
+    assert torch.equal(xg, xg2) and ig["iters"] == ig2["iters"]  # deterministic
+
+
+def test_df32_multidot_limits(G, orc):
+    p = W.workload1()
+    A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f, p.u)
+    with pytest.raises(G.GmresError):  # the one-reduction MGS only
+        gpu_solver_from_oracle(G, A, p.agg, p.r, dot_arith=G.DOT_DF32)
+    with pytest.raises(G.GmresError):  # FP64 solves only
+        gpu_solver_from_oracle(G, A, p.agg, p.r, ortho=G.ORTHO_MGS_LOWSYNC,
+                               precision=G.FP32_INNER, dot_arith=G.DOT_DF32)
+    with pytest.raises(G.GmresError):
+        gpu_solver_from_oracle(G, A, p.agg, p.r, ortho=G.ORTHO_MGS_LOWSYNC, dot_arith=2)
