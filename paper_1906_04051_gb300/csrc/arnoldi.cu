@@ -1243,7 +1243,7 @@ struct Kern {
         k_ritz<<<1, 32, 0, st>>>(a.ctl);
         nl = 1;
         break;
-      case PH_ARNOLDI: {  // the whole step in one persistent kernel (fused.cu)
+      case PH_ARNOLDI: {  // the steps of a cycle in one persistent kernel (fused.cu; j = steps)
         const cudaError_t e = launch_arnoldi(a, j, defl, st);
         if (e != cudaSuccess) return e;
         nl = 1;

@@ -107,6 +107,12 @@ struct Defl {
   const double* uscale;   // r: 1/sqrt|agg_p|
   const double* tinv;     // r x r row-major T^-1
   int npieces;
+  // the pieces of each block of the fused Arnoldi kernel (a grid of blk_grid blocks owning
+  // consecutive row ranges; pieces are split at those ranges): block b's pieces are
+  // blk_piece[blk_piece_start[b] .. blk_piece_start[b + 1]), in aggregate order
+  const int* blk_piece_start;
+  const int* blk_piece;
+  int blk_grid;
   // A W (W = the 0/1 aggregate indicator) in CSR: row i holds, for each aggregate a met
   // in row i of A, the sum of the row's entries in the columns of a
   const int* aurp;        // N + 1

@@ -1,30 +1,36 @@
-// fused.cu -- a whole Arnoldi step of deflated GMRES(m) in one persistent kernel: the
-// SpMV w = A M^-1 v_j (Eq. 10 with Eqs. 16-17), the paper's modified Gram-Schmidt
-// projections (Eq. 13) in their one-reduction form, ||w|| and the plane rotations with the
-// stopping tests (Eqs. 12, 14).
+// fused.cu -- the Arnoldi steps of a restart cycle of deflated GMRES(m) in one persistent
+// kernel: per step the SpMV w = A M^-1 v_j (Eq. 10 with Eqs. 16-17), the paper's modified
+// Gram-Schmidt projections (Eq. 13) in their one-reduction form, ||w||, the plane rotations
+// with the stopping tests (Eqs. 12, 14) and the coarse solve of the next step's
+// preconditioner (Eq. 17: s' = U (|mu| T^-1 - I) U^T v_{j+1}).
 //
 // One block of 16 warps per multiprocessor, launched cooperatively (every block resident).
-// Block b owns a contiguous range of rows (a multiple of 256) for the whole step, taken in
-// super-tiles of at most RS rows whose slices of w and u_j stay in shared memory:
+// Block b owns a contiguous range of rows (a multiple of 256) for the whole cycle, taken in
+// super-tiles of at most RS rows whose slices of w and u_j stay in shared memory.  A step:
 //   1. SpMV of the super-tile's rows (diagonal storage; the coarse correction through the
-//      A W rows, s' staged in shared memory): w into shared memory and global memory, u_j
-//      next to it.  With deflation the diagonal part of the first super-tile runs before
-//      the programmatic-launch wait, overlapping the coarse solve that produces s'.
-//   2. Multi-dot g = V^T w and the new row of L (u_j . u_c): warp s owns the columns
-//      s, s + 16, ... and streams them from HBM with 16-byte loads, several chunks of rows
-//      in flight per lane (a register pipeline), against the shared-memory slices.
-//   3. Grid barrier; every block adds the G partial sums in the same order (identical
+//      A W rows, s' staged in shared memory): w into shared memory (and global memory when
+//      the update reads it there), u_j next to it.  Step 0's diagonal part runs before the
+//      programmatic-launch wait, overlapping the coarse-solve kernel that produces its s'.
+//   2. Multi-dot g = V^T w and the new row of L (u_j . u_c), streamed from HBM against the
+//      shared-memory slices (FP64: four warps per column; FP32: row chunks over column
+//      groups; double-FP32 on request).
+//   3. Grid barrier 1; every block adds the G partial sums in the same order (identical
 //      totals in every block) and solves (I + L) h = g itself.
-//   4. Update of its rows, u_{j+1} = w - V (sigma o h), each lane owning rows and reading
-//      the basis straight from HBM, in the reverse order of step 2 (the columns read last
-//      are the likeliest to be in L2); partial sums of ||u_{j+1}||^2.
-//   5. The last block to finish (ticket counter) adds the norm partials and applies the
-//      plane rotations and stopping tests (Eqs. 12, 14).
-// Every reduction is formed in a fixed order: runs are bitwise reproducible.
+//   4. Update of its rows, u_{j+1} = w - V (sigma o h), in the reverse order of step 2 (the
+//      columns read last are the likeliest to be in L2); partial sums of ||u_{j+1}||^2 and
+//      of u_{j+1} over the block's pieces of aggregates (U^T u_{j+1}).
+//   5. Grid barrier 2; block 0 adds the norm partials and applies the rotations and the
+//      stopping tests; the other blocks form c = U^T u_{j+1} from the piece sums and share
+//      the rows of y = T^-1 c, giving s' for step j + 1.
+//   6. Grid barrier 3: every block reads the same stopping decision and sigma_{j+1}.
+// Every reduction is formed in a fixed order: runs are bitwise reproducible.  The per-phase
+// register budgets (loads in flight) are set so that the kernel needs no local memory:
+// with 220 KB of shared memory per block, spilled registers would live in L2.
 //
 // The basis is streamed with plain vectorised loads rather than bulk asynchronous copies:
 // measured on GB300, a multiprocessor fed by bulk copies reached about 10 bytes per clock,
 // against the 22 that the HBM copy bandwidth asks of each of the 152.
+#include <algorithm>
 #include <type_traits>
 #include <utility>
 
@@ -44,18 +50,18 @@ constexpr size_t kArnScratch = 2 * kMaxK * 33 * sizeof(double);
 constexpr size_t kArnStaging = 2 * 2 * 16 * 32 * sizeof(double);  // FP64 multi-dot staging
 constexpr long long kArnSpins = 1LL << 21;       // polls of the barrier word: about a second
 constexpr int kArnNormCol = 2 * kMaxK;           // column of ctl.part holding the norm partials
-constexpr int kArnAwRows = 12;                   // rows per thread of an A W gather batch
+constexpr int kArnAwRows = 6;                   // rows per thread of an A W gather batch
 // 16-byte basis loads in flight per lane in the multi-dot: FP32 (bound by HBM) asks for
 // more bytes in flight than FP64 (bound by its FMA pipe)
-template <typename TV> constexpr int arn_loads() { return sizeof(TV) == 8 ? 8 : 12; }
+template <typename TV> constexpr int arn_loads() { return sizeof(TV) == 8 ? 6 : 12; }
 
 template <typename TV, typename TACC>
 struct ArnArgs {
   int N;          // rows of A
   int units;      // ldv / kArnUnit
-  int j, k, m;    // step, basis columns in use (j + 1), restart length
-  int pre;        // the predecessor is the coarse solve: the diagonal part of the SpMV may
-                  // run before the wait
+  int jmax, m;    // steps of this cycle (<= m), restart length
+  int pre;        // the predecessor is the coarse solve of step 0: the diagonal part of
+                  // its SpMV may run before the wait
   int defl;       // add the coarse correction A W s'
   int r;          // aggregates (entries of s')
   int RS;         // rows per super-tile (a multiple of kArnUnit)
@@ -67,7 +73,17 @@ struct ArnArgs {
   const int* aurp;
   const int* aucol;
   const TACC* auval;
-  const TACC* sdefl;
+  const TACC* sdefl;  // s' in the step's precision (step 0: from the coarse-solve kernel)
+  // the coarse solve of the next step, in the kernel: pieces of aggregates (nodes perm
+  // [piece_start[p], piece_start[p + 1]), each inside one block's rows), block b's pieces
+  // blk_piece[blk_piece_start[b] ...], T^-1 (r x r, row-major)
+  const int* perm;
+  const int* piece_start;
+  const int* agg_piece;
+  const int* blk_piece_start;
+  const int* blk_piece;
+  const double* uscale;
+  const double* tinv;
   Ctl ctl;
   unsigned* gbar;  // [0] arrivals, [1] generation
 };
@@ -184,6 +200,19 @@ __device__ __forceinline__ void arn_stv(TV* p, const TACC (&v)[VN]) {
   }
 }
 
+// a grid barrier that never completed: the solve stops with GMRES_ERR_TIMEOUT
+__device__ __forceinline__ void arn_timeout(Ctl& ctl) {
+  if (threadIdx.x == 0) {
+    ctl.flags[F_STATUS] = GMRES_ERR_TIMEOUT;
+    ctl.flags[F_STOP] = 1;
+    ctl.flags[F_CYCLE_DONE] = 1;
+  }
+}
+
+// a basis entry written earlier in this launch, read through L2 as FP64
+__device__ __forceinline__ double arn_ldcg_d(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ double arn_ldcg_d(const float* p) { return (double)__ldcg(p); }
+
 // ---- double-FP32 arithmetic for the FP64 multi-dot (GMRES_DOT_DF32) ---------------------
 // GB300 issues FP64 FMAs at 2 lanes per clock and multiprocessor, FP32 FMAs at 128: the
 // FP64 multi-dot is bound by its FMA pipe, not by HBM.  In the double-FP32 form each FP64
@@ -242,7 +271,7 @@ __device__ __forceinline__ void arn_df_add(float& s, float& c, float s2, float c
 // shared memory (float2 hi, lo per row).  At the end of a pass the lanes' pairs of each
 // column meet by a shuffle tree of TwoSums and lane 0 adds them into dfp[warp][c][set]:
 // no FP64 instruction in the loop.
-constexpr int kArnDfGroup = 7;
+constexpr int kArnDfGroup = 6;
 
 __device__ __forceinline__ void arn_dots_df(float* dfp, const double* V, long long ldv, int k,
                                             long long s0, int nch, const float2* Ws,
@@ -342,7 +371,7 @@ __device__ __forceinline__ void arn_dia_rows(TACC (&acc)[B], long long row0, lon
 // many columns (on GB300 this streams about twice as fast as a warp reading one column
 // through many consecutive chunks).  At the end of a pass the lanes' partial sums of each
 // column are added by a shuffle tree and lane 0 accumulates them into wsum[set][warp][c].
-constexpr int kArnGroup = 13;
+constexpr int kArnGroup = 10;
 
 template <typename TV, typename TACC>
 __device__ __forceinline__ void arn_dots_rows(double* wsum, const TV* V, long long ldv, int k,
@@ -479,73 +508,26 @@ __device__ __forceinline__ void arn_dots_group4(double* sbuf, double* stg, const
   }
 }
 
+// SpMV, coarse correction and multi-dot of step j over the block's super-tiles (a function
+// of its own, so that the cycle loop's state stays out of these loops' registers)
 template <typename TV, typename TACC, int ND, bool DF>
-__global__ void __launch_bounds__(kArnThreads, 1)
-    k_arnoldi(const __grid_constant__ ArnArgs<TV, TACC> a) {
-  static_assert(std::is_same<TV, TACC>::value, "w and u_j slices share the basis element type");
-  static_assert(!DF || sizeof(TV) == 8, "the double-FP32 multi-dot takes an FP64 basis");
+__device__ __forceinline__ void arn_front(const ArnArgs<TV, TACC>& a, int j, TACC sig, bool waited,
+                                       TACC* Ws, TACC* Us, TACC* Ss, double* sbuf, double* stg) {
   constexpr int VN = ArnVec<TV>::n;
   constexpr int B = sizeof(TACC) == 8 ? 2 : 4;  // SpMV rows per thread and batch
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ double tot[2 * kMaxK + 1];
-  __shared__ double sred[2 * kMaxK];
-  __shared__ double sg[kMaxK];
-  __shared__ TACC scoef[kMaxK];
-  __shared__ double snrm[kArnWarps];
-  __shared__ unsigned s_last;
-  Ctl ctl = a.ctl;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = threadIdx.x;
   const int G = gridDim.x, bid = blockIdx.x;
   const long long R0 = (long long)bid * a.units / G * kArnUnit;
   const long long R1 = (long long)(bid + 1) * a.units / G * kArnUnit;
-  const int k = a.k;
   const long long N = a.N;
-  // shared memory: w and u_j of a super-tile, s' (r), reduction scratch
-  TACC* Ws = reinterpret_cast<TACC*>(smem);
-  TACC* Us = Ws + a.RS;
-  TACC* Ss = Us + a.RS;
-  double* scratch = reinterpret_cast<double*>(
-      smem + ((2 * (size_t)a.RS + (size_t)a.r) * sizeof(TACC) + 127) / 128 * 128);
-  double* sL = scratch + kArnScratch / sizeof(double);  // k x k, strictly lower part used
-  double* stg = sL + (size_t)kMaxK * kMaxK;  // FP64 multi-dot staging: [2][2][16 warps][32]
-  __shared__ double ssig[kMaxK];
-
-  if (!a.pre) {
-    pdl_wait();
-    pdl_trigger();
-  }
-  // the flag is final here: set only by the previous step's rotations (complete before
-  // this kernel's predecessor started when pre, waited for otherwise); the same value in
-  // every block, so the whole grid returns together
-  if (__ldcg(&ctl.flags[F_CYCLE_DONE])) {
-    if (a.pre) {
-      pdl_wait();
-      pdl_trigger();
-    }
-    return;
-  }
-  const unsigned gen = *(volatile unsigned*)&a.gbar[1];  // advanced only once all arrive
-  // the basis scales and the rows of L from the earlier steps of the cycle are final:
-  // staged now, off the path between the grid barrier and the update
-  for (int c = t; c < k; c += kArnThreads) ssig[c] = __ldcg(&ctl.sigma[c]);
-  for (int q = t; q < k * k; q += kArnThreads) {
-    const int i = q / k, c = q % k;
-    sL[q] = (c < i && i < k - 1) ? __ldcg(&ctl.L[(size_t)i * kMaxK + c]) : 0.0;
-  }
-  const TV* xj = a.V + (size_t)a.j * a.ldv;
-  const TACC sig = (TACC)__ldcg(&ctl.sigma[a.j]);
+  const int k = j + 1;
+  const TV* xj = a.V + (size_t)j * a.ldv;
   const int nd = ND > 0 ? ND : a.dia.nd;
-
-  // partial sums of the multi-dot in shared memory, so that they persist across super-tiles
-  // (FP64: lane-wise per column; FP32: per warp and column)
-  double* sbuf = scratch;
-  for (int q = t; q < 2 * kMaxK * 33; q += kArnThreads) sbuf[q] = 0.0;
-  bool waited = !a.pre;
   const bool multi = R1 - R0 > a.RS;  // w goes through global memory to the update
   for (long long s0 = R0; s0 < R1; s0 += a.RS) {
     const long long s1 = s0 + a.RS < R1 ? s0 + a.RS : R1;
-    // ---- 1. SpMV of the super-tile's rows: w and u_j into shared memory ----------------
+    // ---- 1. SpMV of the super-tile's rows: w and u_j into shared memory --------------
     for (long long i0 = s0 + t; i0 < s1; i0 += (long long)B * kArnThreads) {
       TACC v[B];
       arn_dia_rows<B, ND, TV, TACC>(v, i0, kArnThreads, N, nd, a.dia.off, a.ldd, a.dval, xj);
@@ -564,12 +546,12 @@ __global__ void __launch_bounds__(kArnThreads, 1)
       waited = true;
     }
     if (a.defl && s0 == R0)
-      for (int q = t; q < a.r; q += kArnThreads) Ss[q] = a.sdefl[q];
+      for (int q = t; q < a.r; q += kArnThreads) Ss[q] = __ldcg(a.sdefl + q);
     __syncthreads();
-    // + A W s' (the row's A W entries, s' from shared memory), the scale sigma_j; w also to
-    // global memory when the block has more than one super-tile (the update reads it there).  The rows
-    // are taken kArnAwRows per thread at a time, each level of the A W gather (row
-    // pointers, then the first entry of every row) issued for all of them at once.
+    // + A W s' (the row's A W entries, s' from shared memory), the scale sigma_j; w also
+    // to global memory when the update reads it there.  The rows are taken kArnAwRows
+    // per thread at a time, each level of the A W gather (row pointers, then the first
+    // entry of every row) issued for all of them at once.
     for (long long i0 = s0 + t; i0 < s1; i0 += (long long)kArnAwRows * kArnThreads) {
       int e0[kArnAwRows], e1[kArnAwRows];
 #pragma unroll
@@ -592,7 +574,8 @@ __global__ void __launch_bounds__(kArnThreads, 1)
         const long long row = i0 + (long long)b * kArnThreads;
         if (row < s1) {
           TACC aw = av[b] * Ss[ac[b]];
-          for (int e = e0[b] + 1; e < e1[b]; ++e) aw += __ldg(a.auval + e) * Ss[__ldg(a.aucol + e)];
+          for (int e = e0[b] + 1; e < e1[b]; ++e)
+            aw += __ldg(a.auval + e) * Ss[__ldg(a.aucol + e)];
           const TACC wv = row < N ? sig * (Ws[row - s0] + aw) : (TACC)0;
           Ws[row - s0] = wv;
           if ((multi || DF) && row < N) a.w[row] = wv;
@@ -602,8 +585,8 @@ __global__ void __launch_bounds__(kArnThreads, 1)
     __syncthreads();
     const int nch = (int)((s1 - s0) / (32 * VN));
     if constexpr (DF) {
-      // w and u_j split in place (float2 hi, lo in the 8 bytes of each double); the update
-      // reads w from global memory
+      // w and u_j split in place (float2 hi, lo in the 8 bytes of each double); the
+      // update reads w from global memory
       for (long long q = t; q < s1 - s0; q += kArnThreads) {
         float h1, l1, h2, l2;
         arn_df_split((double)Ws[q], h1, l1);
@@ -612,112 +595,38 @@ __global__ void __launch_bounds__(kArnThreads, 1)
         reinterpret_cast<float2*>(Us)[q] = make_float2(h2, l2);
       }
       __syncthreads();
-      arn_dots_df(reinterpret_cast<float*>(sbuf), reinterpret_cast<const double*>(a.V), a.ldv, k,
-                  s0, nch, reinterpret_cast<const float2*>(Ws),
+      arn_dots_df(reinterpret_cast<float*>(sbuf), reinterpret_cast<const double*>(a.V), a.ldv,
+                  k, s0, nch, reinterpret_cast<const float2*>(Ws),
                   reinterpret_cast<const float2*>(Us), warp, lane);
     } else if constexpr (sizeof(TV) == 8) {
-      // FP64 (its FMA pipe is the bound and its adds are dear): lane-wise partial sums per
-      // column, four warps per column
+      // FP64 (its FMA pipe is the bound and its adds are dear): lane-wise partial sums
+      // per column, four warps per column
       arn_dots_group4<TV, TACC>(sbuf, stg, a.V, a.ldv, k, s0, nch, Ws, Us, warp, lane);
     } else {
       arn_dots_rows<TV, TACC>(sbuf, a.V, a.ldv, k, s0, nch, Ws, Us, warp, lane);
     }
     __syncthreads();  // the slices are rewritten by the next super-tile
   }
-  // per-block column sums: each column belongs to one warp; its lanes' partial sums (in
-  // shared memory) are summed 16 at a time by lane pairs
-  if constexpr (DF) {  // the 16 warps' pairs of each column in warp order, then FP64 once
-    for (int q = t; q < 2 * k; q += kArnThreads) {
-      const int set = q / k, c = q % k;
-      const float* dfp = reinterpret_cast<const float*>(sbuf);
-      float s = 0.f, cc = 0.f;
-      for (int w = 0; w < kArnWarps; ++w) {
-        const float* p = dfp + ((size_t)w * kMaxK + c) * 4 + 2 * set;
-        arn_df_add(s, cc, p[0], p[1]);
-      }
-      sred[q] = (double)s + (double)cc;
-    }
-    __syncthreads();
-  } else if constexpr (sizeof(TV) == 8) {  // the 32 lane-wise totals of each column, pairwise
-    for (int q0 = 0; q0 < 2 * k; q0 += kArnThreads / 2) {
-      const int q = q0 + (t >> 1), half = t & 1;
-      double v = 0.0;
-      if (q < 2 * k) {
-        const int set = q / k, c = q % k;
-        v = tree16(sbuf + ((size_t)set * kMaxK + c) * 33 + half * 16);
-      }
-      v += __shfl_xor_sync(0xffffffffu, v, 1);
-      if (q < 2 * k && half == 0) sred[q] = v;
-    }
-    __syncthreads();
-  } else {  // the 16 warps' sums of each column, in warp order
-    for (int q = t; q < 2 * k; q += kArnThreads) {
-      const int set = q / k, c = q % k;
-      double v = 0.0;
-      for (int w = 0; w < kArnWarps; ++w) v += sbuf[(size_t)(set * kArnWarps + w) * kMaxK + c];
-      sred[q] = v;
-    }
-    __syncthreads();
-  }
-  {
-    for (int c = threadIdx.x; c < 2 * k; c += blockDim.x)
-      __stcg(&ctl.part[(size_t)bid * ctl.ldp + c], sred[c]);
-  }
-  // ---- 3. grid barrier; identical totals in every block; (I + L) h = g ----------------
-  if (!arn_grid_sync(a.gbar, gen)) {
-    if (threadIdx.x == 0) {
-      ctl.flags[F_STATUS] = GMRES_ERR_TIMEOUT;
-      ctl.flags[F_STOP] = 1;
-      ctl.flags[F_CYCLE_DONE] = 1;
-    }
-    return;
-  }
-  arn_reduce_cols(ctl.part, G, 2 * k, ctl.ldp, tot);  // ends with __syncthreads
-  {
-    // the new row of L: v_j . v_c = sigma_j sigma_c (u_j . u_c), c < j; g_c = sigma_c (u_c . w)
-    const double sj = ssig[k - 1];
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-      if (c < k - 1) sL[(size_t)(k - 1) * k + c] = sj * ssig[c] * tot[k + c];
-      sg[c] = ssig[c] * tot[c];
-    }
-    __syncthreads();
-    if (warp == 0) {  // forward substitution: h_c final when reached (entries c, c+32, c+64)
-      // sL[i][c] = 0 for c >= i, so rows at or above c take a zero update; only the
-      // 32-row groups below k are touched (one FP64 FMA per group and column)
-      const int nq = (k + 31) >> 5;
-      double g[3];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) g[q] = lane + 32 * q < k ? sg[lane + 32 * q] : 0.0;
-      for (int c = 0; c < k; ++c) {
-        const double hc = __shfl_sync(0xffffffffu, c < 32 ? g[0] : (c < 64 ? g[1] : g[2]), c & 31);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const int i = lane + 32 * q;
-          if (q < nq) g[q] -= (i < k ? sL[i * k + c] : 0.0) * hc;
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const int i = lane + 32 * q;
-        if (i < k) {
-          scoef[i] = (TACC)(ssig[i] * g[q]);
-          if (bid == 0) {
-            ctl.h[i] = g[q];
-            if (i < k - 1) ctl.L[(size_t)(k - 1) * kMaxK + i] = sL[(k - 1) * k + i];
-          }
-        }
-      }
-    }
-    __syncthreads();
-  }
-  // ---- 4. update u_{j+1} = w - V (sigma o h) and ||u_{j+1}||^2 ------------------------
+}
+
+// u_{j+1} = w - V (sigma o h) over the block's rows (also into ush, indexed from the block's
+// first row, when given); returns the lane's part of ||u_{j+1}||^2
+template <typename TV, typename TACC, bool DF>
+__device__ __forceinline__ double arn_update(const ArnArgs<TV, TACC>& a, int k, const TACC* Ws,
+                                          const TACC* scoef, TACC* ush) {
+  constexpr int VN = ArnVec<TV>::n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int G = gridDim.x, bid = blockIdx.x;
+  const long long R0 = (long long)bid * a.units / G * kArnUnit;
+  const long long R1 = (long long)(bid + 1) * a.units / G * kArnUnit;
+  const long long N = a.N;
+  TV* __restrict__ vout = const_cast<TV*>(a.V) + (size_t)k * a.ldv;
   double nrm = 0.0;
   {
-    constexpr int U = sizeof(TV) == 8 ? 13 : 12;  // basis loads in flight per lane
+    constexpr int U = sizeof(TV) == 8 ? 10 : 8;  // basis loads in flight per lane
     const int chunk = 32 * VN;
     const long long nch = (R1 - R0) / chunk;
     const bool wsm = !DF && R1 - R0 <= a.RS;  // the block's w is still in shared memory
-    TV* __restrict__ vout = const_cast<TV*>(a.V) + (size_t)k * a.ldv;
     for (long long q = nch - 1 - warp; q >= 0; q -= kArnWarps) {
       const long long r = R0 + q * chunk + (long long)lane * VN;
       TACC wv[VN], p[VN];
@@ -746,36 +655,284 @@ __global__ void __launch_bounds__(kArnThreads, 1)
 #pragma unroll
       for (int e = 0; e < VN; ++e) un[e] = wv[e] - p[e];
       arn_stv<TV, TACC, VN>(vout + r, un);
+      if (ush) acc_store<VN>(ush + (r - R0), un);  // for the piece sums
       TACC s = 0;
 #pragma unroll
       for (int e = 0; e < VN; ++e) s += un[e] * un[e];
       nrm += (double)s;
     }
   }
-  // ---- 5. norm partials; the last block applies the rotations -----------------------
-  {
-    // warp sums, then warp 0 adds the 16 of them (a block-wide final loop would issue 16
-    // FP64 adds in every warp)
-    nrm = warp_sum(nrm);
-    if (lane == 0) snrm[warp] = nrm;
-    __syncthreads();
-    double bs = 0.0;
-    if (warp == 0) {
-      bs = lane < kArnWarps ? snrm[lane] : 0.0;
+  return nrm;
+}
+
+// Sums of u_{j+1} over this block's aggregate pieces (c of the next step's coarse solve, by
+// pieces, a warp each).  The pieces' bounds are loaded up front (lane i < 8 holds the
+// warp's i-th piece), then per piece the node indexes and the values: from the shared-memory
+// copy of the block's rows when there is one (ush, from row R0), else through L2 (this
+// block wrote them just before).  Fixed order throughout.
+template <typename TV, typename TACC>
+__device__ __forceinline__ void arn_piece_sums(const ArnArgs<TV, TACC>& a, const TV* vout,
+                                               const TACC* ush, long long R0) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bid = blockIdx.x;
+  const int p0 = __ldg(a.blk_piece_start + bid), p1 = __ldg(a.blk_piece_start + bid + 1);
+  for (int base = p0 + warp; base < p1; base += kArnWarps * 8) {
+    const int pi = base + kArnWarps * lane;
+    int mp = -1, ms = 0, me = 0;
+    if (lane < 8 && pi < p1) {
+      mp = __ldg(a.blk_piece + pi);
+      ms = __ldg(a.piece_start + mp);
+      me = __ldg(a.piece_start + mp + 1);
+    }
+    for (int i = 0; i < 8; ++i) {
+      const int p = __shfl_sync(0xffffffffu, mp, i);
+      const int s = __shfl_sync(0xffffffffu, ms, i), e = __shfl_sync(0xffffffffu, me, i);
+      if (p < 0) break;
+      double acc[2] = {0.0, 0.0};
+      for (int o = s; o < e; o += 32 * 8) {
+        int node[8];
 #pragma unroll
-      for (int o = kArnWarps / 2; o > 0; o >>= 1) bs += __shfl_xor_sync(0xffffffffu, bs, o);
+        for (int u = 0; u < 8; ++u) {
+          const int q = o + lane + 32 * u;
+          node[u] = q < e ? __ldg(a.perm + q) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          double v = 0.0;
+          if (node[u] >= 0) v = ush ? (double)ush[node[u] - R0] : arn_ldcg_d(vout + node[u]);
+          acc[u & 1] += v;
+        }
+      }
+      const double sum = warp_sum(acc[0] + acc[1]);
+      if (lane == 0) __stcg(a.ctl.cpart + p, sum);
     }
-    if (threadIdx.x == 0) {
-      __stcg(&ctl.part[(size_t)bid * ctl.ldp + kArnNormCol], bs);
-      __threadfence();
-      s_last = (atomicAdd(&ctl.ticket[0], 1u) == (unsigned)G - 1u) ? 1u : 0u;
-      if (s_last) __threadfence();
+  }
+}
+
+template <typename TV, typename TACC, int ND, bool DF>
+__global__ void __launch_bounds__(kArnThreads, 1)
+    k_arnoldi(const __grid_constant__ ArnArgs<TV, TACC> a) {
+  static_assert(std::is_same<TV, TACC>::value, "w and u_j slices share the basis element type");
+  static_assert(!DF || sizeof(TV) == 8, "the double-FP32 multi-dot takes an FP64 basis");
+  constexpr int VN = ArnVec<TV>::n;
+  constexpr int B = sizeof(TACC) == 8 ? 2 : 4;  // SpMV rows per thread and batch
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ double tot[2 * kMaxK + 1];
+  __shared__ double sred[2 * kMaxK];
+  __shared__ double sg[kMaxK];
+  __shared__ TACC scoef[kMaxK];
+  __shared__ double snrm[kArnWarps];
+  __shared__ double ssig[kMaxK + 1];
+  // the control block is read from the grid-constant parameter (no register copy)
+  Ctl& ctl = const_cast<Ctl&>(a.ctl);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = threadIdx.x;
+  const int G = gridDim.x, bid = blockIdx.x;
+  const long long R0 = (long long)bid * a.units / G * kArnUnit;
+  const long long R1 = (long long)(bid + 1) * a.units / G * kArnUnit;
+  const long long N = a.N;
+  // shared memory: w and u_j of a super-tile, s' (r), reduction scratch, the rows of L
+  // (stride kMaxK), the FP64 multi-dot staging
+  TACC* Ws = reinterpret_cast<TACC*>(smem);
+  TACC* Us = Ws + a.RS;
+  TACC* Ss = Us + a.RS;
+  double* scratch = reinterpret_cast<double*>(
+      smem + ((2 * (size_t)a.RS + (size_t)a.r) * sizeof(TACC) + 127) / 128 * 128);
+  double* sL = scratch + kArnScratch / sizeof(double);
+  double* stg = sL + (size_t)kMaxK * kMaxK;
+  double* sbuf = scratch;
+  double* sc = reinterpret_cast<double*>(smem);  // c of the coarse solve (w, u_j are dead)
+
+  if (!a.pre) {
+    pdl_wait();
+    pdl_trigger();
+  }
+  // the flag is final here (set by the previous cycle's last step, reset by the residual
+  // kernel before this one started): the same value in every block
+  if (__ldcg(&ctl.flags[F_CYCLE_DONE])) {
+    if (a.pre) {
+      pdl_wait();
+      pdl_trigger();
+    }
+    return;
+  }
+  unsigned gen = *(volatile unsigned*)&a.gbar[1];  // advanced only once all arrive
+  for (int q = t; q < kMaxK * kMaxK; q += kArnThreads) sL[q] = 0.0;
+  if (t == 0) ssig[0] = __ldcg(&ctl.sigma[0]);
+  bool waited = !a.pre;
+  __syncthreads();
+
+  for (int j = 0; j < a.jmax; ++j) {
+    const int k = j + 1;
+    const TACC sig = (TACC)ssig[j];
+    // partial sums of the multi-dot in shared memory, so that they persist across
+    // super-tiles (FP64: lane-wise per column; FP32: per warp and column; double-FP32:
+    // pairs per warp and column)
+    for (int q = t; q < 2 * kMaxK * 33; q += kArnThreads) sbuf[q] = 0.0;
+    arn_front<TV, TACC, ND, DF>(a, j, sig, waited, Ws, Us, Ss, sbuf, stg);
+    waited = true;
+    // per-block column sums (fixed order)
+    if constexpr (DF) {  // the 16 warps' pairs of each column in warp order, then FP64 once
+      for (int q = t; q < 2 * k; q += kArnThreads) {
+        const int set = q / k, c = q % k;
+        const float* dfp = reinterpret_cast<const float*>(sbuf);
+        float s = 0.f, cc = 0.f;
+        for (int w = 0; w < kArnWarps; ++w) {
+          const float* p = dfp + ((size_t)w * kMaxK + c) * 4 + 2 * set;
+          arn_df_add(s, cc, p[0], p[1]);
+        }
+        sred[q] = (double)s + (double)cc;
+      }
+    } else if constexpr (sizeof(TV) == 8) {  // the 32 lane-wise totals of each column, pairwise
+      for (int q0 = 0; q0 < 2 * k; q0 += kArnThreads / 2) {
+        const int q = q0 + (t >> 1), half = t & 1;
+        double v = 0.0;
+        if (q < 2 * k) {
+          const int set = q / k, c = q % k;
+          v = tree16(sbuf + ((size_t)set * kMaxK + c) * 33 + half * 16);
+        }
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        if (q < 2 * k && half == 0) sred[q] = v;
+      }
+    } else {  // the 16 warps' sums of each column, in warp order
+      for (int q = t; q < 2 * k; q += kArnThreads) {
+        const int set = q / k, c = q % k;
+        double v = 0.0;
+        for (int w = 0; w < kArnWarps; ++w) v += sbuf[(size_t)(set * kArnWarps + w) * kMaxK + c];
+        sred[q] = v;
+      }
     }
     __syncthreads();
-    if (!s_last) return;
-    arn_reduce_cols(ctl.part + kArnNormCol, G, 1, ctl.ldp, tot);
-    if (threadIdx.x == 0) ctl.ticket[0] = 0u;
-    givens_step(ctl, k - 1, a.m, sqrt(tot[0]));
+    for (int c = t; c < 2 * k; c += kArnThreads) __stcg(&ctl.part[(size_t)bid * ctl.ldp + c], sred[c]);
+    // ---- 3. grid barrier; identical totals in every block; (I + L) h = g ----------------
+    if (!arn_grid_sync(a.gbar, gen++)) {
+      arn_timeout(ctl);
+      return;
+    }
+    arn_reduce_cols(ctl.part, G, 2 * k, ctl.ldp, tot);  // ends with __syncthreads
+    {
+      // the new row of L: v_j . v_c = sigma_j sigma_c (u_j . u_c), c < j; g_c = sigma_c (u_c . w)
+      const double sj = ssig[k - 1];
+      for (int c = t; c < k; c += kArnThreads) {
+        if (c < k - 1) sL[(size_t)(k - 1) * kMaxK + c] = sj * ssig[c] * tot[k + c];
+        sg[c] = ssig[c] * tot[c];
+      }
+      __syncthreads();
+      if (warp == 0) {  // forward substitution: h_c final when reached (entries c, c+32, c+64)
+        // sL[i][c] = 0 for c >= i, so rows at or above c take a zero update; only the
+        // 32-row groups below k are touched (one FP64 FMA per group and column)
+        const int nq = (k + 31) >> 5;
+        double g[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) g[q] = lane + 32 * q < k ? sg[lane + 32 * q] : 0.0;
+        for (int c = 0; c < k; ++c) {
+          const double hc = __shfl_sync(0xffffffffu, c < 32 ? g[0] : (c < 64 ? g[1] : g[2]), c & 31);
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const int i = lane + 32 * q;
+            if (q < nq) g[q] -= (i < k ? sL[(size_t)i * kMaxK + c] : 0.0) * hc;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const int i = lane + 32 * q;
+          if (i < k) {
+            scoef[i] = (TACC)(ssig[i] * g[q]);
+            if (bid == 0) {
+              ctl.h[i] = g[q];
+              if (i < k - 1) ctl.L[(size_t)(k - 1) * kMaxK + i] = sL[(size_t)(k - 1) * kMaxK + i];
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // ---- 4. update u_{j+1} = w - V (sigma o h) and ||u_{j+1}||^2 ------------------------
+    TV* __restrict__ vout = const_cast<TV*>(a.V) + (size_t)k * a.ldv;
+    // a shared-memory copy of u_{j+1} for the piece sums when the block's rows fit one
+    // super-tile (u_j's slice is dead by now)
+    TACC* ush = (a.defl && k < a.jmax && R1 - R0 <= a.RS) ? Us : nullptr;
+    double nrm = arn_update<TV, TACC, DF>(a, k, Ws, scoef, ush);
+    // ---- 5. norm partial; partial sums of u_{j+1} over this block's aggregate pieces ----
+    {
+      // warp sums, then warp 0 adds the 16 of them (a block-wide final loop would issue 16
+      // FP64 adds in every warp)
+      nrm = warp_sum(nrm);
+      if (lane == 0) snrm[warp] = nrm;
+      __syncthreads();  // also orders this block's stores of u_{j+1} before the piece sums
+      if (warp == 0) {
+        double bs = lane < kArnWarps ? snrm[lane] : 0.0;
+#pragma unroll
+        for (int o = kArnWarps / 2; o > 0; o >>= 1) bs += __shfl_xor_sync(0xffffffffu, bs, o);
+        if (lane == 0) __stcg(&ctl.part[(size_t)bid * ctl.ldp + kArnNormCol], bs);
+      }
+      if (a.defl && k < a.jmax) arn_piece_sums(a, vout, ush, R0);
+    }
+    if (!arn_grid_sync(a.gbar, gen++)) {
+      arn_timeout(ctl);
+      return;
+    }
+    const bool coarse = a.defl && k < a.jmax && (bid > 0 || G == 1);
+    // ---- 6. ||u_{j+1}|| and the plane rotations with the stopping tests (block 0); the next
+    // step's coarse solve s' = U (|mu| T^-1 - I) U^T u_{j+1} (the other blocks) -------------
+    if (bid == 0) {
+      arn_reduce_cols(ctl.part + kArnNormCol, G, 1, ctl.ldp, tot);
+      givens_step(ctl, j, a.m, sqrt(tot[0]));
+    }
+    if (coarse) {
+      // c_a = uscale_a (sum of a's pieces, in piece order), every aggregate in every block
+      for (int q = t; q < a.r; q += kArnThreads) {
+        const int p0 = __ldg(a.agg_piece + q), p1 = __ldg(a.agg_piece + q + 1);
+        double sum = 0.0;
+        for (int pb = p0; pb < p1; pb += 8) {
+          double v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = pb + u < p1 ? __ldcg(ctl.cpart + pb + u) : 0.0;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) sum += v[u];
+        }
+        sc[q] = __ldg(a.uscale + q) * sum;
+      }
+      __syncthreads();
+      // y = T^-1 c: a warp per row over the warps of blocks 1 .. G-1 (all of block 0's when
+      // it is alone), TQ loads in flight per lane (a whole row up to r = 1024)
+      constexpr int TQ = 32;
+      const int gw = G == 1 ? warp : (bid - 1) * kArnWarps + warp;
+      const int nw = G == 1 ? kArnWarps : (G - 1) * kArnWarps;
+      const double mu = __ldcg(&ctl.scal[S_MU]);
+      for (int row = gw; row < a.r; row += nw) {
+        const double* tr = a.tinv + (size_t)row * a.r;
+        double acc[2] = {0.0, 0.0};
+        for (int b0 = 0; b0 < a.r; b0 += 32 * TQ) {
+          double tv[TQ];
+#pragma unroll
+          for (int u = 0; u < TQ; ++u) {
+            const int b = b0 + lane + 32 * u;
+            tv[u] = b < a.r ? __ldg(tr + b) : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < TQ; ++u) {
+            const int b = b0 + lane + 32 * u;
+            if (b < a.r) acc[u & 1] += tv[u] * sc[b];
+          }
+        }
+        const double y = warp_sum(acc[0] + acc[1]);
+        if (lane == 0) {
+          const double sd = __ldg(a.uscale + row) * (mu * y - sc[row]);
+          __stcg(ctl.sdefl + row, sd);
+          __stcg(ctl.sdefl32 + row, (float)sd);
+        }
+      }
+    }
+    if (!arn_grid_sync(a.gbar, gen++)) {
+      arn_timeout(ctl);
+      return;
+    }
+    // the rotations' outputs are visible to every block: the same decision everywhere
+    if (t == 0) ssig[k] = __ldcg(&ctl.sigma[k]);
+    const int done = __ldcg(&ctl.flags[F_CYCLE_DONE]);
+    __syncthreads();
+    if (done) break;
   }
 }
 
@@ -822,12 +979,11 @@ struct Arn {
     }
     return e;
   }
-  static cudaError_t launch(const CycleArgs& c, int j, bool defl, cudaStream_t st) {
+  static cudaError_t launch(const CycleArgs& c, int jmax, bool defl, cudaStream_t st) {
     ArnArgs<TV, TACC> p{};
     p.N = c.op.n;
     p.units = (int)(c.ldv / kArnUnit);
-    p.j = j;
-    p.k = j + 1;
+    p.jmax = jmax;
     p.m = c.m;
     p.pre = (defl && c.pdl) ? 1 : 0;
     p.defl = defl ? 1 : 0;
@@ -850,6 +1006,13 @@ struct Arn {
     }
     p.aurp = c.op.defl.aurp;
     p.aucol = c.op.defl.aucol;
+    p.perm = c.op.defl.perm;
+    p.piece_start = c.op.defl.piece_start;
+    p.agg_piece = c.op.defl.agg_piece;
+    p.blk_piece_start = c.op.defl.blk_piece_start;
+    p.blk_piece = c.op.defl.blk_piece;
+    p.uscale = c.op.defl.uscale;
+    p.tinv = c.op.defl.tinv;
     p.ctl = c.ctl;
     p.gbar = c.gbar;
     // the 9-point stencils of the Q1 systems take an unrolled instantiation
@@ -869,14 +1032,21 @@ bool arnoldi_fusable(const CycleArgs& a) {
         (a.prec == P_FP64 || a.prec == P_FP32)))
     return false;
   const int r = a.op.defl.r;
-  if (a.prec == P_FP64) return Arn<double, double>::super_rows(r) >= kArnUnit;
-  return Arn<float, float>::super_rows(r) >= kArnUnit;
+  // with deflation: the pieces split at this kernel's block rows (built at setup for a
+  // grid of min(units, SMs) blocks), and c (r doubles) fits where w and u_j lived
+  if (r > 0 && (!a.op.defl.blk_piece_start ||
+                a.op.defl.blk_grid != (int)std::min<long long>(a.ldv / kArnUnit, a.sms)))
+    return false;
+  const long long rs = a.prec == P_FP64 ? Arn<double, double>::super_rows(r)
+                                        : Arn<float, float>::super_rows(r);
+  const size_t esz = a.prec == P_FP64 ? sizeof(double) : sizeof(float);
+  return rs >= kArnUnit && (size_t)r * sizeof(double) <= 2 * (size_t)rs * esz;
 }
 
-cudaError_t launch_arnoldi(const CycleArgs& a, int j, bool defl, cudaStream_t st) {
+cudaError_t launch_arnoldi(const CycleArgs& a, int jmax, bool defl, cudaStream_t st) {
   switch (a.prec) {
-    case P_FP64: return Arn<double, double>::launch(a, j, defl, st);
-    case P_FP32: return Arn<float, float>::launch(a, j, defl, st);
+    case P_FP64: return Arn<double, double>::launch(a, jmax, defl, st);
+    case P_FP32: return Arn<float, float>::launch(a, jmax, defl, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -68,6 +68,8 @@ struct gmres_s {
   // deflation (shared by A and A^T)
   int r = 0, npieces = 0;
   DevMem agg, perm, piece_start, agg_piece, uscale;
+  int blk_grid = 0;                   // blocks of the fused kernel the pieces are cut for
+  DevMem blk_piece_start, blk_piece;  // each block's pieces
   double mu_norminf = 0.0;
   // workspace
   int ldh = 0, prec_ws = -1;
@@ -313,6 +315,9 @@ inline OpDev make_op(gmres_s* h, OpHost& o) {
   op.defl.uscale = h->uscale.as<double>();
   op.defl.tinv = o.tinv.as<double>();
   op.defl.npieces = h->npieces;
+  op.defl.blk_piece_start = h->blk_piece_start.as<int>();
+  op.defl.blk_piece = h->blk_piece.as<int>();
+  op.defl.blk_grid = h->blk_grid;
   op.defl.aurp = o.aurp.as<int>();
   op.defl.aucol = o.aucol.as<int>();
   op.defl.auval = o.auval.as<double>();

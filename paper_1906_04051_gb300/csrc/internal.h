@@ -26,9 +26,12 @@ cudaError_t launch_transpose(int n, int nnz, const int* rowptr, const int* col,
 cudaError_t launch_validate(int n, long long nnz, const int* rowptr, const int* col,
                             const int* agg, int r, int* err, cudaStream_t st);
 int agg_chunks(int n);
+// pieces cut at the row ranges of a grid of `grid` blocks over `units` units of 256 rows
+// (the fused Arnoldi kernel's partition; grid 0: no cuts), with each block's piece list
 cudaError_t launch_agg_perm(int n, int r, const int* agg, int* counts, int* aggptr, int* cnt,
                             int* perm, int* agg_piece, int* piece_start, double* uscale,
-                            int* err, cudaStream_t st);
+                            int units, int grid, int* bcnt, int* blk_piece_start,
+                            int* blk_piece, int* err, cudaStream_t st);
 cudaError_t launch_coarse_T(int r, const int* rowptr, const int* col, const double* val,
                             const int* agg, const int* perm, const int* aggptr,
                             const double* uscale, double* T, cudaStream_t st);
@@ -116,7 +119,7 @@ enum Phase {
   PH_PROJ_FINAL,    // projector: x = xh + U T^-1 U^T (b - A xh)
   PH_ADAPT,         // adaptive deflation: update of U, A U, T, T^-1 after a cycle
   PH_MGS,           // modified Gram-Schmidt step (one cooperative kernel)
-  PH_ARNOLDI,       // a whole Arnoldi step in one persistent kernel (fused.cu)
+  PH_ARNOLDI,       // the Arnoldi steps of a cycle in one persistent kernel (fused.cu)
   PH_COUNT
 };
 // c = M^T x over ncols FP64 columns of M (leading dimension ldm), pipelined multi-dot with
@@ -128,7 +131,8 @@ cudaError_t launch_phase(const CycleArgs& a, int ph, int j, bool defl, double* x
 // fused.cu: SpMV, one-reduction MGS projections, ||w|| and the rotations of step j in one
 // cooperative kernel (diagonal storage, EBP deflation or none, FP64 or FP32)
 bool arnoldi_fusable(const CycleArgs& a);
-cudaError_t launch_arnoldi(const CycleArgs& a, int j, bool defl, cudaStream_t st);
+// one launch runs the jmax steps of a restart cycle (fewer when the cycle ends early)
+cudaError_t launch_arnoldi(const CycleArgs& a, int jmax, bool defl, cudaStream_t st);
 // Control-block initialisation for a new solve.
 cudaError_t launch_init(const CycleArgs& a, double tol, double inner_tol, double r0ref,
                         double mu, int fixed, int mixed, long long maxit, cudaStream_t st);

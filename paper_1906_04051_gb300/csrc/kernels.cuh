@@ -467,6 +467,18 @@ __device__ __forceinline__ void ld_acc(const float* p, float (&o)[VN]) {
     o[e + 3] = v.w;
   }
 }
+// the inverse: VN values to shared memory (16-byte aligned)
+template <int VN>
+__device__ __forceinline__ void acc_store(double* p, const double (&v)[VN]) {
+#pragma unroll
+  for (int e = 0; e < VN; e += 2) *reinterpret_cast<double2*>(p + e) = make_double2(v[e], v[e + 1]);
+}
+template <int VN>
+__device__ __forceinline__ void acc_store(float* p, const float (&v)[VN]) {
+#pragma unroll
+  for (int e = 0; e < VN; e += 4)
+    *reinterpret_cast<float4*>(p + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+}
 
 // VN accumulator-type values to shared memory (16-byte aligned)
 template <int VN>

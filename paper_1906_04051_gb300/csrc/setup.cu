@@ -97,24 +97,132 @@ __global__ void k_agg_scatter(int n, int r, const int* __restrict__ agg,
   }
 }
 
-// pieces: aggregate a is split into ceil(cnt_a / kPiece) consecutive ranges of perm
-__global__ void k_pieces(int r, const int* __restrict__ aggptr, const int* __restrict__ cnt,
-                         int* __restrict__ agg_piece, int* __restrict__ piece_start,
-                         double* __restrict__ uscale, int* __restrict__ err) {
-  if (threadIdx.x == 0) {
-    int np = 0;
-    for (int a = 0; a < r; ++a) {
-      agg_piece[a] = np;
-      const int c = cnt[a];
-      if (c == 0) atomicOr(err, 4);
-      for (int s = 0; s < c; s += kPiece) piece_start[np++] = aggptr[a] + s;
+// Pieces: aggregate a's range of perm (its nodes in increasing order) is cut where the
+// nodes pass from one block's rows to the next block's, for a grid of G blocks owning the
+// row ranges [floor(b U / G), floor((b + 1) U / G)) x 256 of U = ldv / 256 units (the
+// fused Arnoldi kernel's partition; G = 0: no cuts), and every part into ranges of at most
+// kPiece nodes.  piece_walk counts a's pieces and, given out, writes their starts.
+__device__ __forceinline__ long long part_block(long long row, int U, int G) {
+  return ((row / 256 + 1) * G + U - 1) / U - 1;
+}
+
+__device__ int piece_walk(const int* __restrict__ perm, int s, int e, int U, int G, int* out) {
+  int np = 0;
+  for (int t = s; t < e;) {
+    int te = e;
+    if (G > 0) {
+      const long long b = part_block(perm[t], U, G);
+      const long long rend = (b + 1) * U / G * 256;
+      int lo = t + 1, hi = e;  // the first node at or past rend
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (perm[mid] < rend) lo = mid + 1;
+        else hi = mid;
+      }
+      te = lo;
     }
-    agg_piece[r] = np;
-    piece_start[np] = aggptr[r];
+    for (int q = t; q < te; q += kPiece) {
+      if (out) out[np] = q;
+      ++np;
+    }
+    t = te;
+  }
+  return np;
+}
+
+// one block of 1024 threads: pieces per aggregate, their exclusive scan (agg_piece), the
+// piece starts, 1 / sqrt|a|
+__global__ void __launch_bounds__(1024)
+    k_pieces(int r, int U, int G, const int* __restrict__ perm, const int* __restrict__ aggptr,
+             const int* __restrict__ cnt, int* __restrict__ agg_piece,
+             int* __restrict__ piece_start, double* __restrict__ uscale, int* __restrict__ err) {
+  __shared__ int ssum[1024];
+  const int t = threadIdx.x;
+  const int per = (r + 1023) / 1024;  // consecutive aggregates per thread
+  const int a0 = t * per, a1 = min(r, a0 + per);
+  int mine = 0;
+  for (int a = a0; a < a1; ++a) {
+    const int np = piece_walk(perm, aggptr[a], aggptr[a + 1], U, G, nullptr);
+    agg_piece[a] = np;
+    mine += np;
+  }
+  ssum[t] = mine;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan of the threads' totals
+    const int v = t >= o ? ssum[t - o] : 0;
+    __syncthreads();
+    ssum[t] += v;
+    __syncthreads();
+  }
+  int run = ssum[t] - mine;
+  for (int a = a0; a < a1; ++a) {
+    const int np = agg_piece[a];
+    agg_piece[a] = run;
+    piece_walk(perm, aggptr[a], aggptr[a + 1], U, G, piece_start + run);
+    run += np;
+    if (cnt[a] == 0) atomicOr(err, 4);
+    uscale[a] = cnt[a] > 0 ? 1.0 / sqrt((double)cnt[a]) : 0.0;
+  }
+  if (t == 1023) {
+    agg_piece[r] = ssum[1023];
+    piece_start[ssum[1023]] = aggptr[r];
+  }
+}
+
+// The pieces of each block of that grid, in piece (aggregate) order: block b counts the
+// pieces whose first node lies in its rows, then (second launch) writes their indexes
+// from its offset by a stable block-wide compaction.
+__global__ void k_blk_count(int U, const int* __restrict__ perm,
+                            const int* __restrict__ piece_start, const int* __restrict__ agg_piece,
+                            int r, int* __restrict__ bcnt) {
+  __shared__ int swarp[32];
+  const int np = agg_piece[r];
+  const int G = gridDim.x;
+  int c = 0;
+  for (int p = threadIdx.x; p < np; p += blockDim.x)
+    c += part_block(perm[piece_start[p]], U, G) == blockIdx.x ? 1 : 0;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) swarp[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += swarp[w];
+    bcnt[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_blk_fill(int U, const int* __restrict__ perm, const int* __restrict__ piece_start,
+                           const int* __restrict__ agg_piece, int r, const int* __restrict__ bcnt,
+                           int* __restrict__ blk_piece_start, int* __restrict__ blk_piece) {
+  __shared__ int swarp[32];
+  __shared__ int s_base;
+  const int np = agg_piece[r];
+  const int G = gridDim.x, b = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) {
+    int off = 0;
+    for (int q = 0; q < b; ++q) off += bcnt[q];
+    blk_piece_start[b] = off;
+    if (b == G - 1) blk_piece_start[G] = off + bcnt[b];
+    s_base = off;
   }
   __syncthreads();
-  for (int a = threadIdx.x; a < r; a += blockDim.x)
-    uscale[a] = cnt[a] > 0 ? 1.0 / sqrt((double)cnt[a]) : 0.0;
+  for (int p0 = 0; p0 < np; p0 += blockDim.x) {
+    const int p = p0 + threadIdx.x;
+    const bool mine = p < np && part_block(perm[piece_start[p]], U, G) == b;
+    const unsigned bal = __ballot_sync(0xffffffffu, mine);
+    if (lane == 0) swarp[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < nw; ++w) {
+      before += w < warp ? swarp[w] : 0;
+      total += swarp[w];
+    }
+    if (mine) blk_piece[s_base + before + __popc(bal & ((1u << lane) - 1u))] = p;
+    __syncthreads();
+    if (threadIdx.x == 0) s_base += total;
+    __syncthreads();
+  }
 }
 
 // T row of aggregate p: sum_{i in p} sum_{k in row i, agg(col_k) = q} a_ik, in perm order.
@@ -775,13 +883,21 @@ int agg_chunks(int n) { return (n + kChunk - 1) / kChunk; }
 cudaError_t launch_agg_perm(int n, int r, const int* agg, int* counts /* chunks*r */,
                             int* aggptr /* r+1 */, int* cnt /* r */, int* perm,
                             int* agg_piece /* r+1 */, int* piece_start, double* uscale,
-                            int* err, cudaStream_t st) {
+                            int units, int grid, int* bcnt /* grid */,
+                            int* blk_piece_start /* grid+1 */, int* blk_piece, int* err,
+                            cudaStream_t st) {
   const int nb = agg_chunks(n);
   const size_t sm = sizeof(int) * (size_t)r;
   k_agg_count<<<nb, 256, sm, st>>>(n, r, agg, counts);
   k_agg_scan<<<1, 1024, 0, st>>>(r, nb, counts, aggptr, cnt);
   k_agg_scatter<<<nb, 32, sm, st>>>(n, r, agg, counts, perm);
-  k_pieces<<<1, 256, 0, st>>>(r, aggptr, cnt, agg_piece, piece_start, uscale, err);
+  k_pieces<<<1, 1024, 0, st>>>(r, units, grid, perm, aggptr, cnt, agg_piece, piece_start, uscale,
+                               err);
+  if (grid > 0) {
+    k_blk_count<<<grid, 256, 0, st>>>(units, perm, piece_start, agg_piece, r, bcnt);
+    k_blk_fill<<<grid, 256, 0, st>>>(units, perm, piece_start, agg_piece, r, bcnt,
+                                     blk_piece_start, blk_piece);
+  }
   return cudaGetLastError();
 }
 

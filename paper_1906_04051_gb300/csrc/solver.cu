@@ -5,6 +5,7 @@
 // the true residual) and reads back a 272-byte status block once per cycle; every
 // decision inside a cycle (Givens, stopping tests, breakdown) is taken on the device, so
 // steps after an early exit return at once.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -144,12 +145,10 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
     if (defl_cycle) CK(h, phase(h, a, PH_DEFL, 0, true, x, b));
     const long long left = maxit - h->hmeta->counts[C_STEPS];
     const int jmax = (int)(left < m ? left : m);
-    for (int j = 0; j < jmax; ++j) {
-      if (fused) {
-        CK(h, phase(h, a, PH_ARNOLDI, j, defl_cycle, x, b));
-        if (defl_cycle) CK(h, phase(h, a, PH_DEFL, j + 1, true, x, b));
-        continue;
-      }
+    // the whole cycle in one launch where the step fuses; each step's coarse solve for the
+    // next step inside it
+    if (fused && jmax > 0) CK(h, phase(h, a, PH_ARNOLDI, jmax, defl_cycle, x, b));
+    for (int j = 0; j < (fused ? 0 : jmax); ++j) {
       CK(h, phase(h, a, PH_SPMV, j, defl_cycle, x, b));
       if (mgs) {
         CK(h, phase(h, a, PH_MGS, j, defl_cycle, x, b));
@@ -517,7 +516,16 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
   if (r > 0) {
     const int nb = agg_chunks(n);
     DevMem counts, aggptr, cnt, T, G, fac;
-    const int max_pieces = n / kPiece + r + 1;
+    // the fused kernel's grid: min(units of 256 rows, SMs); its row ranges cut pieces too
+    const long long units = ((long long)n + 255) / 256;
+    const int bg = (int)std::min<long long>(units, h->sms);
+    const long long max_pieces =
+        std::min<long long>((long long)n / kPiece + r + 1 + (long long)(bg - 1) * r, (long long)n + r + 1);
+    DevMem bcnt;
+    CKC(bcnt.ensure(sizeof(int) * (size_t)bg));
+    CKC(h->blk_piece_start.ensure(sizeof(int) * (size_t)(bg + 1)));
+    CKC(h->blk_piece.ensure(sizeof(int) * (size_t)max_pieces));
+    h->blk_grid = bg;
     CKC(counts.ensure(sizeof(int) * (size_t)nb * r));
     CKC(aggptr.ensure(sizeof(int) * (size_t)(r + 1)));
     CKC(cnt.ensure(sizeof(int) * (size_t)r));
@@ -527,7 +535,9 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
     CKC(h->uscale.ensure(sizeof(double) * (size_t)r));
     CKC(launch_agg_perm(n, r, h->agg.as<int>(), counts.as<int>(), aggptr.as<int>(),
                         cnt.as<int>(), h->perm.as<int>(), h->agg_piece.as<int>(),
-                        h->piece_start.as<int>(), h->uscale.as<double>(), err.as<int>(), st));
+                        h->piece_start.as<int>(), h->uscale.as<double>(), (int)units, bg,
+                        bcnt.as<int>(), h->blk_piece_start.as<int>(), h->blk_piece.as<int>(),
+                        err.as<int>(), st));
     CKC(T.ensure(sizeof(double) * (size_t)r * r));
     CKC(G.ensure(sizeof(double) * 2 * (size_t)r * r));
     CKC(fac.ensure(gj_aux_bytes(r)));
