@@ -22,7 +22,9 @@
 //   5. Grid barrier 2; block 0 adds the norm partials and applies the rotations and the
 //      stopping tests; the other blocks form c = U^T u_{j+1} from the piece sums and share
 //      the rows of y = T^-1 c, giving s' for step j + 1.
-//   6. Grid barrier 3: every block reads the same stopping decision and sigma_{j+1}.
+//   6. A split barrier: each block arrives once its share of step 5 is published, forms the
+//      diagonal part of the next step's SpMV (it needs only u_{j+1}), then waits for all
+//      arrivals and reads the same stopping decision and sigma_{j+1}.
 // Every reduction is formed in a fixed order: runs are bitwise reproducible.  The per-phase
 // register budgets (loads in flight) are set so that the kernel needs no local memory:
 // with 220 KB of shared memory per block, spilled registers would live in L2.
@@ -112,6 +114,36 @@ __device__ __forceinline__ bool arn_grid_sync(unsigned* bar, unsigned gen) {
           ok = 0;
           break;
         }
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Split grid barrier on a counter that only grows (bar[2]): a block arrives once its share
+// of a phase is published, carries on with work that does not need the other blocks'
+// shares, and waits later until the counter reaches the target (G arrivals per phase,
+// counted from the value read at the kernel's start; compared modulo 2^32).
+__device__ __forceinline__ void arn_arrive(unsigned* cnt) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(cnt, 1u);
+  }
+}
+
+__device__ __forceinline__ bool arn_wait(const unsigned* cnt, unsigned target) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    long long spins = 0;
+    while ((int)(*(volatile const unsigned*)cnt - target) < 0) {
+      if (++spins > kArnSpins) {
+        ok = 0;
+        break;
       }
     }
     __threadfence();
@@ -508,13 +540,36 @@ __device__ __forceinline__ void arn_dots_group4(double* sbuf, double* stg, const
   }
 }
 
+// Diagonal part of step j's SpMV for the rows [s0, s1) of a super-tile: (A v_j) into Ws and
+// u_j into Us (shared memory, from row s0; zeros past N)
+template <int ND, typename TV, typename TACC>
+__device__ __forceinline__ void arn_diag(const ArnArgs<TV, TACC>& a, int j, long long s0,
+                                         long long s1, TACC* Ws, TACC* Us) {
+  constexpr int B = sizeof(TACC) == 8 ? 2 : 4;  // SpMV rows per thread and batch
+  const long long N = a.N;
+  const TV* xj = a.V + (size_t)j * a.ldv;
+  const int nd = ND > 0 ? ND : a.dia.nd;
+  for (long long i0 = s0 + threadIdx.x; i0 < s1; i0 += (long long)B * kArnThreads) {
+    TACC v[B];
+    arn_dia_rows<B, ND, TV, TACC>(v, i0, kArnThreads, N, nd, a.dia.off, a.ldd, a.dval, xj);
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const long long row = i0 + (long long)b * kArnThreads;
+      if (row < s1) {
+        Ws[row - s0] = row < N ? v[b] : (TACC)0;
+        Us[row - s0] = row < N ? ld_as<TACC, TV>(xj + row) : (TACC)0;
+      }
+    }
+  }
+}
+
 // SpMV, coarse correction and multi-dot of step j over the block's super-tiles (a function
 // of its own, so that the cycle loop's state stays out of these loops' registers)
 template <typename TV, typename TACC, int ND, bool DF>
 __device__ __forceinline__ void arn_front(const ArnArgs<TV, TACC>& a, int j, TACC sig, bool waited,
-                                       TACC* Ws, TACC* Us, TACC* Ss, double* sbuf, double* stg) {
+                                       bool first_diag_done, TACC* Ws, TACC* Us, TACC* Ss,
+                                       double* sbuf, double* stg) {
   constexpr int VN = ArnVec<TV>::n;
-  constexpr int B = sizeof(TACC) == 8 ? 2 : 4;  // SpMV rows per thread and batch
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = threadIdx.x;
   const int G = gridDim.x, bid = blockIdx.x;
@@ -522,24 +577,12 @@ __device__ __forceinline__ void arn_front(const ArnArgs<TV, TACC>& a, int j, TAC
   const long long R1 = (long long)(bid + 1) * a.units / G * kArnUnit;
   const long long N = a.N;
   const int k = j + 1;
-  const TV* xj = a.V + (size_t)j * a.ldv;
-  const int nd = ND > 0 ? ND : a.dia.nd;
   const bool multi = R1 - R0 > a.RS;  // w goes through global memory to the update
   for (long long s0 = R0; s0 < R1; s0 += a.RS) {
     const long long s1 = s0 + a.RS < R1 ? s0 + a.RS : R1;
-    // ---- 1. SpMV of the super-tile's rows: w and u_j into shared memory --------------
-    for (long long i0 = s0 + t; i0 < s1; i0 += (long long)B * kArnThreads) {
-      TACC v[B];
-      arn_dia_rows<B, ND, TV, TACC>(v, i0, kArnThreads, N, nd, a.dia.off, a.ldd, a.dval, xj);
-#pragma unroll
-      for (int b = 0; b < B; ++b) {
-        const long long row = i0 + (long long)b * kArnThreads;
-        if (row < s1) {
-          Ws[row - s0] = row < N ? v[b] : (TACC)0;
-          Us[row - s0] = row < N ? ld_as<TACC, TV>(xj + row) : (TACC)0;
-        }
-      }
-    }
+    // ---- 1. SpMV of the super-tile's rows: w and u_j into shared memory (the first
+    // super-tile's may have been formed during the previous step's coarse solve) ---------
+    if (!(first_diag_done && s0 == R0)) arn_diag<ND, TV, TACC>(a, j, s0, s1, Ws, Us);
     if (!waited) {  // s' (the coarse solve's output) is read from here on
       pdl_wait();
       pdl_trigger();
@@ -709,6 +752,41 @@ __device__ __forceinline__ void arn_piece_sums(const ArnArgs<TV, TACC>& a, const
   }
 }
 
+// The same sums from the staged node list: a warp per piece, values from the shared-memory
+// copy of u_{j+1}.  FP64 rows add in FP64; FP32 rows in double-FP32 (TwoSum on the FP32
+// pipe, exact to about 2^-48 of the sum's magnitude), rounded to FP64 once per piece.
+constexpr int kArnMaxBlkPieces = 256;
+
+template <typename TACC>
+__device__ __forceinline__ void arn_piece_sums_staged(double* cpart, const TACC* ush,
+                                                      const unsigned short* snode,
+                                                      const int* spid, const int* spls, int np) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i < np; i += kArnWarps) {
+    const int ls = spls[i], le = spls[i + 1];
+    double sum;
+    if constexpr (sizeof(TACC) == 8) {
+      double acc[2] = {0.0, 0.0};
+      for (int q = ls + lane; q < le; q += 64) {
+        acc[0] += (double)ush[snode[q]];
+        if (q + 32 < le) acc[1] += (double)ush[snode[q + 32]];
+      }
+      sum = warp_sum(acc[0] + acc[1]);
+    } else {
+      float hs = 0.f, hc = 0.f;
+      for (int q = ls + lane; q < le; q += 32) arn_df_add(hs, hc, (float)ush[snode[q]], 0.f);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float a2 = __shfl_xor_sync(0xffffffffu, hs, o);
+        const float b2 = __shfl_xor_sync(0xffffffffu, hc, o);
+        arn_df_add(hs, hc, a2, b2);
+      }
+      sum = (double)hs + (double)hc;
+    }
+    if (lane == 0) __stcg(cpart + spid[i], sum);
+  }
+}
+
 template <typename TV, typename TACC, int ND, bool DF>
 __global__ void __launch_bounds__(kArnThreads, 1)
     k_arnoldi(const __grid_constant__ ArnArgs<TV, TACC> a) {
@@ -757,8 +835,53 @@ __global__ void __launch_bounds__(kArnThreads, 1)
     return;
   }
   unsigned gen = *(volatile unsigned*)&a.gbar[1];  // advanced only once all arrive
+  // the split barrier's counter: no block arrives before every block has passed the first
+  // grid barrier, so all read the same base
+  const unsigned cbase = *(volatile unsigned*)&a.gbar[2];
   for (int q = t; q < kMaxK * kMaxK; q += kArnThreads) sL[q] = 0.0;
   if (t == 0) ssig[0] = __ldcg(&ctl.sigma[0]);
+  // the block's aggregate pieces for the whole cycle: their ids, local starts and nodes (as
+  // offsets from R0, 16 bits) in shared memory, past the rows of u_j's slice, when the
+  // block's rows fit one super-tile with room to spare (else the sums read perm from L2)
+  __shared__ int spid[kArnMaxBlkPieces];
+  __shared__ int spls[kArnMaxBlkPieces + 1];
+  const long long nrows = R1 - R0;
+  unsigned short* snode = reinterpret_cast<unsigned short*>(Us + nrows);
+  const int bp0 = a.defl ? __ldg(a.blk_piece_start + bid) : 0;
+  const int bp1 = a.defl ? __ldg(a.blk_piece_start + bid + 1) : 0;
+  const bool staged = a.defl && bp1 - bp0 <= kArnMaxBlkPieces && nrows <= 65536 &&
+                      (size_t)nrows * sizeof(TACC) + (size_t)nrows * 2 <= (size_t)a.RS * sizeof(TACC);
+  if (staged) {
+    if (warp == 0) {  // ids and sizes 32 at a time, local starts by a warp scan
+      int run = 0;
+      for (int i0 = 0; i0 < bp1 - bp0; i0 += 32) {
+        const int i = i0 + lane;
+        int p = 0, n = 0;
+        if (i < bp1 - bp0) {
+          p = __ldg(a.blk_piece + bp0 + i);
+          n = __ldg(a.piece_start + p + 1) - __ldg(a.piece_start + p);
+        }
+        int inc = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += v;
+        }
+        if (i < bp1 - bp0) {
+          spid[i] = p;
+          spls[i] = run + inc - n;
+        }
+        run += __shfl_sync(0xffffffffu, inc, 31);
+      }
+      if (lane == 0) spls[bp1 - bp0] = run;
+    }
+    __syncthreads();
+    for (int i = warp; i < bp1 - bp0; i += kArnWarps) {
+      const int p = spid[i];
+      const int s = __ldg(a.piece_start + p), ls = spls[i], n = spls[i + 1] - ls;
+      for (int q = lane; q < n; q += 32) snode[ls + q] = (unsigned short)(__ldg(a.perm + s + q) - R0);
+    }
+  }
   bool waited = !a.pre;
   __syncthreads();
 
@@ -769,7 +892,7 @@ __global__ void __launch_bounds__(kArnThreads, 1)
     // super-tiles (FP64: lane-wise per column; FP32: per warp and column; double-FP32:
     // pairs per warp and column)
     for (int q = t; q < 2 * kMaxK * 33; q += kArnThreads) sbuf[q] = 0.0;
-    arn_front<TV, TACC, ND, DF>(a, j, sig, waited, Ws, Us, Ss, sbuf, stg);
+    arn_front<TV, TACC, ND, DF>(a, j, sig, waited, j > 0, Ws, Us, Ss, sbuf, stg);
     waited = true;
     // per-block column sums (fixed order)
     if constexpr (DF) {  // the 16 warps' pairs of each column in warp order, then FP64 once
@@ -866,7 +989,12 @@ __global__ void __launch_bounds__(kArnThreads, 1)
         for (int o = kArnWarps / 2; o > 0; o >>= 1) bs += __shfl_xor_sync(0xffffffffu, bs, o);
         if (lane == 0) __stcg(&ctl.part[(size_t)bid * ctl.ldp + kArnNormCol], bs);
       }
-      if (a.defl && k < a.jmax) arn_piece_sums(a, vout, ush, R0);
+      if (a.defl && k < a.jmax) {
+        if (staged && ush)
+          arn_piece_sums_staged(ctl.cpart, ush, snode, spid, spls, bp1 - bp0);
+        else
+          arn_piece_sums(a, vout, ush, R0);
+      }
     }
     if (!arn_grid_sync(a.gbar, gen++)) {
       arn_timeout(ctl);
@@ -894,10 +1022,11 @@ __global__ void __launch_bounds__(kArnThreads, 1)
         sc[q] = __ldg(a.uscale + q) * sum;
       }
       __syncthreads();
-      // y = T^-1 c: a warp per row over the warps of blocks 1 .. G-1 (all of block 0's when
-      // it is alone), TQ loads in flight per lane (a whole row up to r = 1024)
+      // y = T^-1 c: a warp per row, the rows dealt round-robin over blocks 1 .. G-1 (warp w
+      // of block b takes rows (b - 1) + (G - 1) (w + 16 i)) so that each block has few; all
+      // to block 0 when it is alone.  TQ loads in flight per lane (a whole row up to 1024)
       constexpr int TQ = 32;
-      const int gw = G == 1 ? warp : (bid - 1) * kArnWarps + warp;
+      const int gw = G == 1 ? warp : (bid - 1) + (G - 1) * warp;
       const int nw = G == 1 ? kArnWarps : (G - 1) * kArnWarps;
       const double mu = __ldcg(&ctl.scal[S_MU]);
       for (int row = gw; row < a.r; row += nw) {
@@ -924,7 +1053,13 @@ __global__ void __launch_bounds__(kArnThreads, 1)
         }
       }
     }
-    if (!arn_grid_sync(a.gbar, gen++)) {
+    // this block's s' rows and (block 0) the rotations are published: arrive, then form the
+    // diagonal part of the next step's SpMV for the first super-tile, which needs only
+    // u_{j+1} (complete since the barrier), not s' or sigma_{j+1} (it overwrites c); then
+    // wait for every block's arrival
+    arn_arrive(&a.gbar[2]);
+    if (k < a.jmax) arn_diag<ND, TV, TACC>(a, k, R0, R0 + a.RS < R1 ? R0 + a.RS : R1, Ws, Us);
+    if (!arn_wait(&a.gbar[2], cbase + (unsigned)G * (unsigned)k)) {
       arn_timeout(ctl);
       return;
     }
@@ -1033,12 +1168,13 @@ bool arnoldi_fusable(const CycleArgs& a) {
     return false;
   const int r = a.op.defl.r;
   // with deflation: the pieces split at this kernel's block rows (built at setup for a
-  // grid of min(units, SMs) blocks), and c (r doubles) fits where w and u_j lived
+  // grid of min(units, SMs) blocks)
   if (r > 0 && (!a.op.defl.blk_piece_start ||
                 a.op.defl.blk_grid != (int)std::min<long long>(a.ldv / kArnUnit, a.sms)))
     return false;
   const long long rs = a.prec == P_FP64 ? Arn<double, double>::super_rows(r)
                                         : Arn<float, float>::super_rows(r);
+  // c (r doubles) lives where w and u_j do
   const size_t esz = a.prec == P_FP64 ? sizeof(double) : sizeof(float);
   return rs >= kArnUnit && (size_t)r * sizeof(double) <= 2 * (size_t)rs * esz;
 }

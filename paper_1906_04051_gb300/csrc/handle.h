@@ -78,7 +78,7 @@ struct gmres_s {
   // adaptive deflation (GMRES_DEFL_ADAPTIVE): U, A U (ldv x rmax), T (rmax x rmax),
   // T^-1 (q x q), a work vector, small scratch; aq columns in use
   DevMem aU, aAU, aT, aTinv, au, asmall;
-  DevMem gbar;  // grid barrier words of the modified Gram-Schmidt kernel
+  DevMem gbar;  // grid barrier words of the modified Gram-Schmidt and fused Arnoldi kernels
   DevMem lmat;  // strictly lower part of V^T V (one-reduction MGS)
   // a deflation space given as dense columns W (n x dense_r), orthonormalised into the
   // dense-space buffers above (aU, aAU, aT, aTinv) at the first solve
@@ -159,7 +159,7 @@ inline gmres_status ensure_workspace(gmres_s* h, int m, int prec) {
   }
   CK(h, h->cpart.ensure(sizeof(double) * (size_t)(h->npieces + 1)));
   CK(h, h->sdefl.ensure(12 * (size_t)sdefl_len(h)));
-  CK(h, h->gbar.ensure(2 * sizeof(unsigned)));
+  CK(h, h->gbar.ensure(4 * sizeof(unsigned)));
   if (h->opts.ortho == GMRES_ORTHO_MGS_LOWSYNC)
     CK(h, h->lmat.ensure(sizeof(double) * (size_t)kMaxK * kMaxK));
   if ((h->opts.deflation_mode == GMRES_DEFL_ADAPTIVE || h->dense_r > 0) && !h->aU.p) {

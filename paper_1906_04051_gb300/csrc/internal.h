@@ -102,7 +102,7 @@ struct CycleArgs {
   int pdl;               // step kernels with programmatic dependent launch
   int ortho;             // gmres_ortho
   int dot_arith;         // gmres_dot_arith (the fused FP64 step's multi-dot)
-  unsigned* gbar;        // grid barrier of the modified Gram-Schmidt kernel (2 words)
+  unsigned* gbar;        // grid barrier words of the MGS and fused kernels (4 words)
 };
 
 // Phases of a solve; each launch_phase call enqueues the kernels of one phase.

@@ -98,7 +98,7 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
   if (mgs) {
     if (mgs_rows(h->n, h->sms) == 0)
       return fail(h, GMRES_ERR_INVALID_ARG, "GMRES_ORTHO_MGS: n exceeds 220 KiB of w per SM");
-    CK(h, cudaMemsetAsync(h->gbar.p, 0, 2 * sizeof(unsigned), st));
+    CK(h, cudaMemsetAsync(h->gbar.p, 0, 4 * sizeof(unsigned), st));
   }
 
   const bool ebp = h->r > 0 && h->opts.deflation_mode == GMRES_DEFL_EBP;
@@ -107,7 +107,7 @@ gmres_status run(gmres_s* h, OpHost& o, const double* b, const double* x0, int m
   if (ada) h->aq = 0;
   // the whole step in one persistent kernel where it applies (fused.cu)
   const bool fused = !mgs && !ada && !dw && arnoldi_fusable(a);
-  if (fused) CK(h, cudaMemsetAsync(h->gbar.p, 0, 2 * sizeof(unsigned), st));
+  if (fused) CK(h, cudaMemsetAsync(h->gbar.p, 0, 4 * sizeof(unsigned), st));
   const int mu_mode = h->opts.mu_mode;
   double mu = 0.0;
   if (mu_mode == GMRES_MU_USER) mu = std::fabs(h->opts.mu_user);
