@@ -147,15 +147,18 @@ def cycle_ks(iters, cycles, m):
     return [j + 1 for sc in per for j in range(sc)]
 
 
-def arn_units(layout, n, ks, s):
-    """Algorithmic FP64 FMAs and bytes of the fused Arnoldi step over steps with k basis
+def arn_units(layout, n, ks, s, coarse_steps=0):
+    """Algorithmic FP64 FMAs and bytes of the fused Arnoldi kernel over steps with k basis
     columns (s bytes per basis / operator element): the SpMV (nd diagonals, the A W rows,
     x), the one-reduction MGS multi-dot (2 k FMA per row: V^T w and V^T u_j; the basis read
-    once), the update (k FMA per row; the basis read again, u_{j+1} written) and the norm.
-    w and u_j stay on chip."""
-    nd, nau = layout.get("ndiag", 0), layout.get("nau", 0)
-    fma = sum(nd * n + nau + 3.0 * k * n + n for k in ks)
-    byt = sum(s * (nd * n + n + 2.0 * k * n + n) + 4.0 * (n + 1) + (4.0 + s) * nau for k in ks)
+    once), the update (k FMA per row; the basis read again, u_{j+1} written) and the norm;
+    w and u_j stay on chip.  coarse_steps of them also run the next step's coarse solve in
+    the kernel: the sums of u_{j+1} over the aggregates (n adds, from shared memory) and
+    y = T^-1 c (r^2 FMA, T^-1 read in FP64)."""
+    nd, nau, r = layout.get("ndiag", 0), layout.get("nau", 0), layout.get("r", 0)
+    fma = sum(nd * n + nau + 3.0 * k * n + n for k in ks) + coarse_steps * (r * r + 0.5 * n)
+    byt = (sum(s * (nd * n + n + 2.0 * k * n + n) + 4.0 * (n + 1) + (4.0 + s) * nau for k in ks)
+           + coarse_steps * 8.0 * r * r)
     return fma, byt
 
 
@@ -200,8 +203,8 @@ def mixed_vs_oracle(p, t, runs):
                        f"1e-12: {io['iters']} steps, {time.perf_counter() - t0:.1f} s"}
     r, c, v, b = G.q1_assemble(p.n, t(p.kappa), p.beta, t(p.f))
     a = t(p.agg, torch.int32)
-    for name, prec, orth in runs:
-        s = G.Solver(r, c, v, a, p.r, precision=prec, ortho=orth)
+    for name, prec, orth, dot in runs:
+        s = G.Solver(r, c, v, a, p.r, precision=prec, ortho=orth, dot_arith=dot)
         x, info = s.solve(b, m=p.m, tol=1e-10, maxit=200000)
         s.close()
         xn = x.cpu().numpy()
@@ -459,7 +462,10 @@ def main():
     ks = cycle_ks(it, cyc, M)
     ph = profs[-1]
     ms_arn = ph["arnoldi"][0]
-    fma, arn_bytes = arn_units(layout, N, ks, 8)
+    # every step of a deflated cycle but its last also runs the next step's coarse solve;
+    # the first cycle runs undeflated (|mu| comes from its Ritz values)
+    coarse = max(0, (it - min(it, M)) - (cyc - 1))
+    fma, arn_bytes = arn_units(layout, N, ks, 8, coarse_steps=coarse)
     # every timed step runs the same deterministic solve, so each launches what the
     # profiled one did
     launches = args.steps * sum(v[1] for v in profs[-1].values())
@@ -470,8 +476,9 @@ def main():
         _, b26 = arn_units(layout, N, [26], 8)
         traffic = statistics.mean(ARN_DRAM_BYTES_K26[8] * arn_units(layout, N, [k], 8)[1] / b26
                                   for k in ks)
-    roofline = {"kernel": "k_arnoldi (fused step: SpMV, one-reduction MGS multi-dot, update, "
-                          "norm, rotations)", "bound": "alu",
+    roofline = {"kernel": "k_arnoldi (one launch per restart cycle; per step the SpMV, the "
+                          "one-reduction MGS multi-dot, update, norm, rotations and the next "
+                          "step's coarse solve)", "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": traffic, "traffic_unit": "bytes per launch",
@@ -498,9 +505,12 @@ def main():
             ph32 = s32.profile()
             s32.close()
             ks32 = cycle_ks(i32["iters"], i32["cycles"], M)
-            _, b32 = arn_units(layout, N, ks32, 4)
+            _, b32 = arn_units(layout, N, ks32, 4, coarse_steps=i32["iters"] - i32["cycles"])
             ms32 = ph32["arnoldi"][0]
-            fp32_arnoldi = {"steps": i32["iters"], "ms": ms32,
+            fp32_arnoldi = {"kernel": "k_arnoldi, one launch per restart cycle: SpMV, the next "
+                                      "step's coarse solve, one-reduction MGS, update, "
+                                      "rotations (FP32 basis and operator)",
+                            "steps": i32["iters"], "ms": ms32,
                             "us_per_step": 1e3 * ms32 / i32["iters"],
                             "algorithmic_bytes": b32,
                             "gbs": b32 / (ms32 / 1e3) / 1e9,
@@ -564,8 +574,10 @@ def main():
             ortho = {"workload": "q1-n1024 EBP GMRES(50) tol 1e-8, solve only (T set up)",
                      "mgs_lowsync": {"ms": statistics.median(i["ms_total"] for i in infos),
                                      "iters": it}}
-            for name, o in (("cgs2", G.ORTHO_CGS2), ("mgs_per_column", G.ORTHO_MGS)):
-                so = G.Solver(rowptr, col, val, agg, p.r, ortho=o)
+            for name, o, dot in (("cgs2", G.ORTHO_CGS2, G.DOT_FP64),
+                                 ("mgs_per_column", G.ORTHO_MGS, G.DOT_FP64),
+                                 ("mgs_lowsync_df32_dots", ORTHO, G.DOT_DF32)):
+                so = G.Solver(rowptr, col, val, agg, p.r, ortho=o, dot_arith=dot)
                 so.solve(b, m=M, tol=TOL, maxit=MAXIT)  # warm-up
                 ev0.record(stream)
                 _, io = so.solve(b, m=M, tol=TOL, maxit=MAXIT)
@@ -668,10 +680,13 @@ def main():
             a3 = t(p3.agg, torch.int32)
             mixed = {"workload": "q1-n2048 GMRES(40), r = 64, tol 1e-10 (true FP64 residual)"}
             xs = {}
-            runs = (("fp64", G.FP64, ORTHO), ("fp64_cgs2", G.FP64, G.ORTHO_CGS2),
-                    ("fp32_inner", G.FP32_INNER, ORTHO), ("bf16_basis", G.BF16_BASIS, G.ORTHO_CGS2))
-            for name, prec, orth in runs:
-                s3 = G.Solver(r3, c3, v3, a3, p3.r, precision=prec, ortho=orth)
+            runs = (("fp64", G.FP64, ORTHO, G.DOT_FP64),
+                    ("fp64_cgs2", G.FP64, G.ORTHO_CGS2, G.DOT_FP64),
+                    ("fp64_df32_dots", G.FP64, ORTHO, G.DOT_DF32),
+                    ("fp32_inner", G.FP32_INNER, ORTHO, G.DOT_FP64),
+                    ("bf16_basis", G.BF16_BASIS, G.ORTHO_CGS2, G.DOT_FP64))
+            for name, prec, orth, dot in runs:
+                s3 = G.Solver(r3, c3, v3, a3, p3.r, precision=prec, ortho=orth, dot_arith=dot)
                 ev0.record(stream)
                 x3, i3 = s3.solve(b3, m=p3.m, tol=1e-10, maxit=60000)
                 ev1.record(stream)
@@ -682,7 +697,7 @@ def main():
                                "refinements": i3["refinements"], "status": i3["status"],
                                "rel_res_true": i3["rel_res_true"],
                                "ortho": "mgs_lowsync" if orth == ORTHO else "cgs2"}
-            for name in ("fp32_inner", "bf16_basis"):
+            for name in ("fp64_df32_dots", "fp32_inner", "bf16_basis"):
                 mixed[name]["speedup_vs_fp64"] = mixed["fp64"]["ms"] / mixed[name]["ms"]
                 mixed[name]["speedup_vs_fp64_cgs2"] = mixed["fp64_cgs2"]["ms"] / mixed[name]["ms"]
                 mixed[name]["rel_diff_vs_gpu_fp64"] = float(
