@@ -39,10 +39,10 @@ M, TOL, MAXIT = 50, 1e-8, 20000
 # FP64 FMA peak of GB300: 2 DFMA/clk/SM (ncu sm__sass_thread_inst_executed_op_dfma
 # peak_sustained) x 152 SMs x 2.07 GHz x 2 flop
 FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the fused Arnoldi step
-# kernel on this workload at k = 26 basis columns (one ncu capture, FP64 and FP32 basis);
-# None until captured for the kernel as it stands
-ARN_DRAM_BYTES_K26 = {8: None, 4: None}
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the fused Arnoldi kernel
+# (a full 50-step deflated cycle) on this workload, FP64 and FP32 basis (one ncu capture
+# each, profiles/k_arnoldi_cycle_q1-n1024_*.txt); None once the kernel changes
+ARN_DRAM_BYTES_CYCLE50 = {8: 25.965e9, 4: 8.293e9}
 # Arnoldi steps the deflated GMRES(50) takes to 1e-8 on this workload (deterministic;
 # the GPU arm prints its own count): used only to project the CPU sample to a full solve
 PROJECT_ITERS = 782
@@ -471,18 +471,20 @@ def main():
     launches = args.steps * sum(v[1] for v in profs[-1].values())
     achieved = 2.0 * fma / (ms_arn / 1e3) / 1e12
     hbm_peak, peak_kind = _peaks()
+    # a launch is a restart cycle: per-launch figures average over the solve's cycles; the
+    # captured traffic of a full cycle is scaled to them by their algorithmic bytes
     traffic = None
-    if ARN_DRAM_BYTES_K26[8] is not None:  # scaled to each launch by its bytes
-        _, b26 = arn_units(layout, N, [26], 8)
-        traffic = statistics.mean(ARN_DRAM_BYTES_K26[8] * arn_units(layout, N, [k], 8)[1] / b26
-                                  for k in ks)
+    if ARN_DRAM_BYTES_CYCLE50[8] is not None:
+        _, b50 = arn_units(layout, N, list(range(1, M + 1)), 8, coarse_steps=M - 1)
+        traffic = ARN_DRAM_BYTES_CYCLE50[8] * (arn_bytes / cyc) / b50
     roofline = {"kernel": "k_arnoldi (one launch per restart cycle; per step the SpMV, the "
                           "one-reduction MGS multi-dot, update, norm, rotations and the next "
                           "step's coarse solve)", "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": traffic, "traffic_unit": "bytes per launch",
-                "algorithmic_bytes_per_launch": arn_bytes / len(ks),
+                "algorithmic_bytes_per_launch": arn_bytes / cyc,
+                "launches": "one per restart cycle",
                 "peak_kind": "derived FP64 FMA rate",
                 "hbm_gbs_same_kernel": arn_bytes / (ms_arn / 1e3) / 1e9}
     # SpMV + Arnoldi algorithmic bytes over the whole solve (metric part 2): the fused
@@ -507,6 +509,10 @@ def main():
             ks32 = cycle_ks(i32["iters"], i32["cycles"], M)
             _, b32 = arn_units(layout, N, ks32, 4, coarse_steps=i32["iters"] - i32["cycles"])
             ms32 = ph32["arnoldi"][0]
+            t32 = None
+            if ARN_DRAM_BYTES_CYCLE50[4] is not None:
+                _, b50 = arn_units(layout, N, list(range(1, M + 1)), 4, coarse_steps=M - 1)
+                t32 = ARN_DRAM_BYTES_CYCLE50[4] * (b32 / i32["cycles"]) / b50
             fp32_arnoldi = {"kernel": "k_arnoldi, one launch per restart cycle: SpMV, the next "
                                       "step's coarse solve, one-reduction MGS, update, "
                                       "rotations (FP32 basis and operator)",
@@ -514,7 +520,9 @@ def main():
                             "us_per_step": 1e3 * ms32 / i32["iters"],
                             "algorithmic_bytes": b32,
                             "gbs": b32 / (ms32 / 1e3) / 1e9,
-                            "hbm_frac": b32 / (ms32 / 1e3) / 1e9 / hbm_peak}
+                            "hbm_frac": b32 / (ms32 / 1e3) / 1e9 / hbm_peak,
+                            "traffic_per_launch": t32,
+                            "algorithmic_bytes_per_launch": b32 / i32["cycles"]}
         except Exception as e:  # an optional section must not take the headline line with it
             fp32_arnoldi = {"error": f"{type(e).__name__}: {e}"}
 
