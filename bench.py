@@ -730,8 +730,13 @@ def main():
             maxit4, tol4 = 4000, 1e-10
             batched = {"workload": "q1-batch256: 256 Picard systems, 4.34M DOF, GMRES(30), "
                                    "8 EBP deflation vectors each, tol 1e-10, maxit 4000"}
-            for name, prec in (("fp64_batched", G.FP64), ("fp32_inner_batched", G.FP32_INNER)):
-                sv = [G.Solver(d[0], d[1], d[2], d[4], d[5], precision=prec) for d in sysd]
+            for name, prec, orth in (("fp64_batched", G.FP64, G.ORTHO_CGS2),
+                                     ("fp64_batched_mgs_lowsync", G.FP64, G.ORTHO_MGS_LOWSYNC),
+                                     ("fp32_inner_batched", G.FP32_INNER, G.ORTHO_CGS2),
+                                     ("fp32_inner_batched_mgs_lowsync", G.FP32_INNER,
+                                      G.ORTHO_MGS_LOWSYNC)):
+                sv = [G.Solver(d[0], d[1], d[2], d[4], d[5], precision=prec, ortho=orth)
+                      for d in sysd]
                 G.batch_solve(sv, bl, m=30, tol=tol4, maxit=maxit4)  # first call: autotune + graph
                 ev0.record(stream)
                 _, inf4, _ = G.batch_solve(sv, bl, m=30, tol=tol4, maxit=maxit4)
@@ -739,8 +744,9 @@ def main():
                 ev1.synchronize()
                 batched[name] = {"ms": ev0.elapsed_time(ev1),
                                  "converged": sum(i["status"] == 0 for i in inf4),
-                                 "steps": sum(i["iters"] for i in inf4), "graph_launches": 1}
-                if prec == G.FP64:
+                                 "steps": sum(i["iters"] for i in inf4), "graph_launches": 1,
+                                 "ortho": "mgs_lowsync" if orth == G.ORTHO_MGS_LOWSYNC else "cgs2"}
+                if name == "fp64_batched":
                     ev0.record(stream)
                     seq = [s4.solve(b4, m=30, tol=tol4, maxit=maxit4)[1] for s4, b4 in zip(sv, bl)]
                     ev1.record(stream)
@@ -751,7 +757,8 @@ def main():
                 for s4 in sv:
                     s4.close()
             base = batched["fp64_sequential"]["ms"]
-            for name in ("fp64_batched", "fp32_inner_batched"):
+            for name in ("fp64_batched", "fp64_batched_mgs_lowsync", "fp32_inner_batched",
+                         "fp32_inner_batched_mgs_lowsync"):
                 batched[name]["speedup_vs_fp64_sequential"] = base / batched[name]["ms"]
             # the systems that reach 1e-10 (the others stagnate under 8-vector EBP, as they do in
             # the oracle): time to tolerance batched and sequential on that subset alone

@@ -131,7 +131,7 @@ typedef enum {
                                (I + L) h = V^T w with L the strictly lower part of V^T V,
                                and w -= V h; two passes over the basis per step, 3k FMAs
                                per row instead of CGS2's 4k.  FP64 and FP32 inner solves,
-                               single-system */
+                               single-system and batched */
 } gmres_ortho;
 
 typedef enum {
@@ -253,8 +253,9 @@ gmres_status gmres_adjoint_solve(gmres_t h, const double* g, const double* lam0,
 /* Solves count independent systems, system i with handle hs[i] (host array), in one
  * persistent launch on `stream`.  b, x0, x: host arrays of count device pointers (x0
  * may be NULL, or contain NULLs).  infos: host array of count entries, may be NULL.
- * All handles must use the same precision, GMRES_ORTHO_CGS2, and W as aggregates (or no
- * W) with deflation_mode EBP or NONE; otherwise GMRES_ERR_INVALID_ARG before any launch.
+ * All handles must use the same precision, the same orthogonalisation (GMRES_ORTHO_CGS2,
+ * or GMRES_ORTHO_MGS_LOWSYNC with an FP64 or FP32 basis), and W as aggregates (or no W)
+ * with deflation_mode EBP or NONE; otherwise GMRES_ERR_INVALID_ARG before any launch.
  * Returns the worst status. */
 gmres_status gmres_batch_solve(int32_t count, gmres_t const* hs, const double* const* b,
                                const double* const* x0, int32_t m, double tol,

@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kSpmvRows) kb_spmv(BTab tab, int j) {
   }
 }
 
-// ---- pipelined CGS2 passes over the tiles of all systems ------------------------------
+// ---- pipelined passes over the tiles of all systems (CGS2, one-reduction MGS) ---------
 template <typename TV, typename TACC>
 struct BRing {
   unsigned char* base;
@@ -327,6 +327,90 @@ __global__ void __launch_bounds__(kThreads) kb_pass1(BTab tab, int k) {
     __syncthreads();
   };
   bring_run(R, tab, begin, body, end);
+}
+
+// One-reduction MGS (the paper's projections, Eq. 13, in the inverse compact WY form), pass
+// 1: one sweep over the basis tiles gives g = V^T w and the dots of the newest column u_j
+// (the tile's column k - 1, already in shared memory) with all columns; the system's last
+// block stores g_c = sigma_c (v_c . w) in h and the new row of L, v_j . v_c = sigma_j
+// sigma_c (u_j . u_c) for c < j.  FP64 and FP32 bases (the second multi-dot reads the tile's
+// column as the accumulator type).
+template <typename TV, typename TACC>
+__global__ void __launch_bounds__(kThreads) kb_pass1_icwy(BTab tab, int k) {
+  static_assert(sizeof(TV) == sizeof(TACC), "u_j is read from the tile as TACC");
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ uint64_t bars[kMaxStages];
+  __shared__ double swarp[kSlices * kSliceCols];
+  __shared__ double sred[2 * kMaxK], tot[2 * kMaxK];
+  const int TR = tab.TR;
+  const size_t sb = ring_stage_bytes(k, TR, sizeof(TV), sizeof(TACC));
+  const BRing<TV, TACC> R{smraw, bars, k, TR, ring_stages(sb), sb};
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = slice_cols(k, warp, kSlices);
+  TACC acc[kSliceCols], acc2[kSliceCols];
+  auto begin = [&](const BSys&) {
+#pragma unroll
+    for (int i = 0; i < kSliceCols; ++i) acc[i] = acc2[i] = 0;
+  };
+  auto body = [&](int st, const BSys&, long long) {
+#define GG_B1I(NW)                                                                        \
+  {                                                                                       \
+    tile_dot<NW, TV, TACC>(acc, R.vt(st), R.wt(st), TR, warp, lane);                      \
+    tile_dot<NW, TV, TACC>(acc2, R.vt(st), (const TACC*)(R.vt(st) + (size_t)(k - 1) * TR), \
+                           TR, warp, lane);                                               \
+  }
+    GG_SLICE_SWITCH(nw, GG_B1I)
+#undef GG_B1I
+  };
+  auto end = [&](const BSys& S) {
+    flush_cols(acc, nw, k, swarp, sred);
+    flush_cols(acc2, nw, k, swarp, sred + k);
+    if (sys_flush(S, S.tile0_p, S.ntile_p, tab.T_p, sred, 2 * k, tot)) {
+      const double sj = S.ctl.sigma[k - 1];
+      for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        S.ctl.h[c] = S.ctl.sigma[c] * tot[c];
+        if (c < k - 1) S.ctl.L[(size_t)(k - 1) * kMaxK + c] = sj * S.ctl.sigma[c] * tot[k + c];
+      }
+    }
+    __syncthreads();
+  };
+  bring_run(R, tab, begin, body, end);
+}
+
+// One-reduction MGS, the solve, a block per system in its cycle: (I + L) h = g by forward
+// substitution in one warp (L staged in shared memory), then coef_c = sigma_c h_c for the
+// update pass
+__global__ void __launch_bounds__(256) kb_icwy_solve(BTab tab, int k) {
+  __shared__ double sL[kMaxK * kMaxK];
+  const BSys& S = tab.sys[blockIdx.x];
+  if (!sys_step_active(S)) return;
+  const Ctl& ctl = S.ctl;
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    const int i = t / k, c = t % k;
+    sL[i * kMaxK + c] = c < i ? ctl.L[(size_t)i * kMaxK + c] : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  double g[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) g[q] = lane + 32 * q < k ? ctl.h[lane + 32 * q] : 0.0;
+  for (int c = 0; c < k; ++c) {
+    const double hc = __shfl_sync(0xffffffffu, c < 32 ? g[0] : (c < 64 ? g[1] : g[2]), c & 31);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int i = lane + 32 * q;
+      if (i > c && i < k) g[q] -= sL[i * kMaxK + c] * hc;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int i = lane + 32 * q;
+    if (i < k) {
+      ctl.h[i] = g[q];
+      ctl.coef[i] = ctl.sigma[i] * g[q];
+    }
+  }
 }
 
 template <typename TV, typename TACC>
@@ -588,6 +672,9 @@ struct BKern {
     int mx = 0;
     for (int k = 1; k <= m + 1; ++k) mx = std::max(mx, (int)ring_smem(k, TR));
     cudaError_t e = cudaFuncSetAttribute(kb_pass1<TV, TACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if constexpr (sizeof(TV) == sizeof(TACC))
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kb_pass1_icwy<TV, TACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_pass2<TV, TACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_pass3<TV, TACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     return e;
@@ -599,8 +686,8 @@ struct BKern {
   }
   // one restart cycle of every system; returns the number of kernels enqueued, or -1
   // with *err / *where set when a launch fails
-  static int cycle(const BTab& tab, int sms, int bps_pass, int max_r, cudaStream_t st,
-                   cudaError_t* err, const char** where) {
+  static int cycle(const BTab& tab, int sms, int bps_pass, int max_r, bool lowsync,
+                   cudaStream_t st, cudaError_t* err, const char** where) {
     const int m = tab.m;
     auto grid = [&](int T, int per_sm) { return std::max(1, std::min(T, per_sm * sms)); };
     const int gs = grid(tab.T_s, 4);
@@ -617,13 +704,27 @@ struct BKern {
       const size_t rs = ring_smem(k, tab.TR);
       kb_spmv<TA, TV, TACC><<<gs, kSpmvRows, 0, st>>>(tab, j);
       if ((*err = cudaGetLastError()) != cudaSuccess) { *where = "kb_spmv"; return -1; }
-      const int gp1 = grid(tab.T_p, std::min(bps_pass, occupancy((const void*)kb_pass1<TV, TACC>, rs)));
-      const int gp2 = grid(tab.T_p, std::min(bps_pass, occupancy((const void*)kb_pass2<TV, TACC>, rs)));
       const int gp3 = grid(tab.T_p, std::min(bps_pass, occupancy((const void*)kb_pass3<TV, TACC>, rs)));
-      kb_pass1<TV, TACC><<<gp1, kThreads, rs, st>>>(tab, k);
-      if ((*err = cudaGetLastError()) != cudaSuccess) { *where = "kb_pass1"; return -1; }
-      kb_pass2<TV, TACC><<<gp2, kThreads, rs, st>>>(tab, k);
-      if ((*err = cudaGetLastError()) != cudaSuccess) { *where = "kb_pass2"; return -1; }
+      bool icwy = false;
+      if constexpr (sizeof(TV) == sizeof(TACC)) {
+        if (lowsync) {  // one-reduction MGS: one multi-dot pass, the solve, the update
+          icwy = true;
+          const int gp1 =
+              grid(tab.T_p, std::min(bps_pass, occupancy((const void*)kb_pass1_icwy<TV, TACC>, rs)));
+          kb_pass1_icwy<TV, TACC><<<gp1, kThreads, rs, st>>>(tab, k);
+          if ((*err = cudaGetLastError()) != cudaSuccess) { *where = "kb_pass1_icwy"; return -1; }
+          kb_icwy_solve<<<tab.count, 256, 0, st>>>(tab, k);
+          if ((*err = cudaGetLastError()) != cudaSuccess) { *where = "kb_icwy_solve"; return -1; }
+        }
+      }
+      if (!icwy) {  // CGS2: pass 1, pass 2, then the update
+        const int gp1 = grid(tab.T_p, std::min(bps_pass, occupancy((const void*)kb_pass1<TV, TACC>, rs)));
+        const int gp2 = grid(tab.T_p, std::min(bps_pass, occupancy((const void*)kb_pass2<TV, TACC>, rs)));
+        kb_pass1<TV, TACC><<<gp1, kThreads, rs, st>>>(tab, k);
+        if ((*err = cudaGetLastError()) != cudaSuccess) { *where = "kb_pass1"; return -1; }
+        kb_pass2<TV, TACC><<<gp2, kThreads, rs, st>>>(tab, k);
+        if ((*err = cudaGetLastError()) != cudaSuccess) { *where = "kb_pass2"; return -1; }
+      }
       kb_pass3<TV, TACC><<<gp3, kThreads, rs, st>>>(tab, k);
       if ((*err = cudaGetLastError()) != cudaSuccess) { *where = "kb_pass3"; return -1; }
       kb_aggsum<TV><<<gpieces, kThreads, 0, st>>>(tab, k, 0);
@@ -658,7 +759,7 @@ struct BKern {
 
 struct BatchCtx {
   std::vector<gmres_s*> hs;
-  int m = 0, prec = 0, TR = 0, bps = 0, max_r = 0, count = 0;
+  int m = 0, prec = 0, TR = 0, bps = 0, max_r = 0, count = 0, ortho = 0;
   BTab tab{};
   DevMem dsys, dtile_s, dtile_p, dpiece;
   std::vector<BSys> hsys;
@@ -682,7 +783,7 @@ std::vector<std::unique_ptr<BatchCtx>>& batch_cache() {
 
 template <typename K>
 int run_cycle(const BatchCtx& c, int sms, cudaStream_t st, cudaError_t* err, const char** where) {
-  return K::cycle(c.tab, sms, c.bps, c.max_r, st, err, where);
+  return K::cycle(c.tab, sms, c.bps, c.max_r, c.ortho == GMRES_ORTHO_MGS_LOWSYNC, st, err, where);
 }
 
 int dispatch_cycle(const BatchCtx& c, int sms, cudaStream_t st, cudaError_t* err,
@@ -818,8 +919,11 @@ gmres_status batch_solve_impl(int count, gmres_t const* hs, const double* const*
     if (hs[i]->opts.deflation_mode == GMRES_DEFL_ADAPTIVE)
       return fail(nullptr, GMRES_ERR_INVALID_ARG,
                   "deflation_mode ADAPTIVE is for single-system solves");
-    if (hs[i]->opts.ortho != GMRES_ORTHO_CGS2)
-      return fail(nullptr, GMRES_ERR_INVALID_ARG, "the batched solve orthogonalises by CGS2");
+    if (hs[i]->opts.ortho != hs[0]->opts.ortho)
+      return fail(nullptr, GMRES_ERR_INVALID_ARG, "all handles of a batch must use one ortho");
+    if (hs[i]->opts.ortho == GMRES_ORTHO_MGS)
+      return fail(nullptr, GMRES_ERR_INVALID_ARG,
+                  "the batched solve orthogonalises by CGS2 or the one-reduction MGS");
     if (hs[i]->dense_r > 0)
       return fail(nullptr, GMRES_ERR_INVALID_ARG, "dense W is for single-system solves");
   }
@@ -835,7 +939,7 @@ gmres_status batch_solve_impl(int count, gmres_t const* hs, const double* const*
   // context: cached per handle list and m
   BatchCtx* ctx = nullptr;
   for (auto& c : batch_cache())
-    if (c->m == m && c->prec == prec && c->count == count &&
+    if (c->m == m && c->prec == prec && c->count == count && c->ortho == hs[0]->opts.ortho &&
         std::equal(c->hs.begin(), c->hs.end(), hs))
       ctx = c.get();
   const bool fresh = ctx == nullptr;
@@ -846,6 +950,7 @@ gmres_status batch_solve_impl(int count, gmres_t const* hs, const double* const*
     ctx->m = m;
     ctx->prec = prec;
     ctx->count = count;
+    ctx->ortho = hs[0]->opts.ortho;
   }
   ctx->hsys.resize(count);
   int max_r = 0;

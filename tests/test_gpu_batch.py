@@ -107,3 +107,44 @@ def test_batch256_full_size(G, orc):
         assert io["status"] == 0
         # both within tol 1e-8 of the same solution: bounded by cond(A) * 1e-8
         assert relerr(xs[i].cpu().numpy(), xo) <= 1e-5
+
+
+def test_batch_lowsync_fixed_iterations_parity(G, orc):
+    # the one-reduction MGS in the batched solve: every system's iterate after 37 fixed
+    # steps equals the oracle's MGS GMRES and the single-system one-reduction solve
+    probs = W.workload4(count=5, n_min=6, n_max=30, seed=78)
+    kw = dict(mu_mode=1, mu_user=5.0, fixed_iterations=True, ortho=G.ORTHO_MGS_LOWSYNC)
+    solvers, bs, sys = _build(G, orc, probs, **kw)
+    xs, infos, st = G.batch_solve(solvers, bs, m=10, tol=0.0, maxit=37)
+    xs = [x.clone() for x in xs]
+    for x, info, s, bd, p, (A, b) in zip(xs, infos, solvers, bs, probs, sys):
+        assert info["iters"] == 37
+        xo, io = orc.gmres(A, b, m=10, tol=0.0, maxit=37, defl=orc.Deflation(A, p.agg, p.r),
+                           mu_mode=1, mu_user=5.0, fixed_iterations=True, ortho=orc.MGS)
+        assert relerr(x.cpu().numpy(), xo) <= 1e-9
+        x1, _ = s.solve(bd, m=10, tol=0.0, maxit=37)
+        assert relerr(x.cpu().numpy(), x1.cpu().numpy()) <= 1e-11
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_lowsync_to_tolerance(G, orc, precision):
+    probs = W.workload4(count=6, n_min=8, n_max=48, seed=2024)
+    solvers, bs, sys = _build(G, orc, probs, ortho=G.ORTHO_MGS_LOWSYNC, precision=precision)
+    xs, infos, st = G.batch_solve(solvers, bs, m=30, tol=1e-10, maxit=50000)
+    assert st == 0, infos
+    xs = [x.clone() for x in xs]
+    xs2, _, _ = G.batch_solve(solvers, bs, m=30, tol=1e-10, maxit=50000)
+    for x, x2, info, p, (A, b) in zip(xs, xs2, infos, probs, sys):
+        xn = x.cpu().numpy()
+        assert np.linalg.norm(b - A.matvec(xn)) <= 1e-10 * np.linalg.norm(b)
+        assert torch.equal(x, x2)  # deterministic
+        xo, _ = orc.gmres(A, b, m=30, tol=1e-12, maxit=50000, defl=orc.Deflation(A, p.agg, p.r))
+        assert relerr(xn, xo) <= 1e-7
+
+
+def test_batch_ortho_limits(G, orc):
+    probs = W.workload4(count=2, n_min=6, n_max=10, seed=3)
+    s1, b1, _ = _build(G, orc, probs[:1], ortho=G.ORTHO_MGS_LOWSYNC)
+    s2, b2, _ = _build(G, orc, probs[1:], ortho=G.ORTHO_CGS2)
+    with pytest.raises(G.GmresError):  # one orthogonalisation per batch
+        G.batch_solve(s1 + s2, b1 + b2, m=10, tol=1e-8, maxit=100)
