@@ -297,6 +297,41 @@ __device__ __forceinline__ void arn_df_add(float& s, float& c, float s2, float c
   c = __fadd_rn(__fadd_rn(c, c2), err);
 }
 
+// The same over partials stored as double-FP32 pairs (two floats per slot): TwoSum on the
+// FP32 pipe in the same fixed order, rounded to FP64 once per column.
+__device__ __forceinline__ void arn_reduce_cols_df(const double* src, int nrows, int ncols,
+                                                   int ldp, double* dst) {
+  constexpr int L = 8;
+  int Q = 1;
+  while (Q * 2 <= 32 && Q * 2 * ncols <= (int)blockDim.x) Q *= 2;
+  const int rounds = (ncols * Q + blockDim.x - 1) / blockDim.x;
+  for (int rd = 0; rd < rounds; ++rd) {
+    const int idx = rd * blockDim.x + threadIdx.x;
+    const int c = idx / Q, q = idx % Q;
+    float hs = 0.f, hc = 0.f;
+    if (c < ncols) {
+      for (int r0 = q; r0 < nrows; r0 += L * Q) {
+        float2 v[L];
+#pragma unroll
+        for (int u = 0; u < L; ++u) {
+          const int r = r0 + u * Q;
+          v[u] = r < nrows ? __ldcg(reinterpret_cast<const float2*>(src + (size_t)r * ldp + c))
+                           : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < L; ++u) arn_df_add(hs, hc, v[u].x, v[u].y);
+      }
+    }
+    for (int o = 1; o < Q; o <<= 1) {
+      const float a2 = __shfl_xor_sync(0xffffffffu, hs, o);
+      const float b2 = __shfl_xor_sync(0xffffffffu, hc, o);
+      arn_df_add(hs, hc, a2, b2);
+    }
+    if (c < ncols && q == 0) dst[c] = (double)hs + (double)hc;
+  }
+  __syncthreads();
+}
+
 // Multi-dot of an FP64 basis in double-FP32 (row order): warp w takes the chunks w, w + 16,
 // ... of 64 rows of the super-tile and, per pass, G columns at the same rows (one 16-byte
 // load per column and lane, all issued before the products); w and u_j come split from
@@ -398,19 +433,19 @@ __device__ __forceinline__ void arn_dia_rows(TACC (&acc)[B], long long row0, lon
 }
 
 // Multi-dot in row-chunk order (FP32 basis): warp w takes the chunks w, w + 16, ... of the
-// super-tile and, per pass, a group of up to kArnGroup columns: one 16-byte load per column
+// super-tile and, per pass, a group of up to G columns: one 16-byte load per column
 // and lane for the same rows, so the loads in flight of a warp fall in one row window of
 // many columns (on GB300 this streams about twice as fast as a warp reading one column
 // through many consecutive chunks).  At the end of a pass the lanes' partial sums of each
 // column are added by a shuffle tree and lane 0 accumulates them into wsum[set][warp][c].
-constexpr int kArnGroup = 10;
+// (10 columns per pass: measured on q1-n1024, 12 made the whole FP32 step 7 % slower)
+template <int ND> constexpr int arn_group() { return 10; }
 
-template <typename TV, typename TACC>
+template <typename TV, typename TACC, int G>
 __device__ __forceinline__ void arn_dots_rows(double* wsum, const TV* V, long long ldv, int k,
                                               long long s0, int nch, const TACC* Ws,
                                               const TACC* Us, int warp, int lane) {
   constexpr int VN = ArnVec<TV>::n;
-  constexpr int G = kArnGroup;
   for (int g0 = 0; g0 < k; g0 += G) {
     const int gc = k - g0 < G ? k - g0 : G;
     TACC a1[G], a2[G];
@@ -443,8 +478,13 @@ __device__ __forceinline__ void arn_dots_rows(double* wsum, const TV* V, long lo
       if (u < gc) {
         const TACC t1 = warp_sum(a1[u]), t2 = warp_sum(a2[u]);
         if (lane == 0) {
-          wsum[(size_t)warp * kMaxK + g0 + u] += (double)t1;
-          wsum[(size_t)(kArnWarps + warp) * kMaxK + g0 + u] += (double)t2;
+          float2* p1 = reinterpret_cast<float2*>(wsum) + (size_t)warp * kMaxK + g0 + u;
+          float2* p2 = reinterpret_cast<float2*>(wsum) + (size_t)(kArnWarps + warp) * kMaxK + g0 + u;
+          float2 a1v = *p1, a2v = *p2;
+          arn_df_add(a1v.x, a1v.y, (float)t1, 0.f);
+          arn_df_add(a2v.x, a2v.y, (float)t2, 0.f);
+          *p1 = a1v;
+          *p2 = a2v;
         }
       }
   }
@@ -646,7 +686,7 @@ __device__ __forceinline__ void arn_front(const ArnArgs<TV, TACC>& a, int j, TAC
       // per column, four warps per column
       arn_dots_group4<TV, TACC>(sbuf, stg, a.V, a.ldv, k, s0, nch, Ws, Us, warp, lane);
     } else {
-      arn_dots_rows<TV, TACC>(sbuf, a.V, a.ldv, k, s0, nch, Ws, Us, warp, lane);
+        arn_dots_rows<TV, TACC, arn_group<ND>()>(sbuf, a.V, a.ldv, k, s0, nch, Ws, Us, warp, lane);
     }
     __syncthreads();  // the slices are rewritten by the next super-tile
   }
@@ -917,22 +957,31 @@ __global__ void __launch_bounds__(kArnThreads, 1)
         v += __shfl_xor_sync(0xffffffffu, v, 1);
         if (q < 2 * k && half == 0) sred[q] = v;
       }
-    } else {  // the 16 warps' sums of each column, in warp order
+    } else {  // the 16 warps' pairs of each column in warp order, kept as a pair
       for (int q = t; q < 2 * k; q += kArnThreads) {
         const int set = q / k, c = q % k;
-        double v = 0.0;
-        for (int w = 0; w < kArnWarps; ++w) v += sbuf[(size_t)(set * kArnWarps + w) * kMaxK + c];
-        sred[q] = v;
+        const float2* ws = reinterpret_cast<const float2*>(sbuf);
+        float hs = 0.f, hc = 0.f;
+        for (int w = 0; w < kArnWarps; ++w) {
+          const float2 v = ws[(size_t)(set * kArnWarps + w) * kMaxK + c];
+          arn_df_add(hs, hc, v.x, v.y);
+        }
+        reinterpret_cast<float2*>(sred)[q] = make_float2(hs, hc);
       }
     }
     __syncthreads();
+    // the partials: FP64 values, or double-FP32 pairs (two floats in the slot) for an FP32
+    // basis, whose cross-block sums then run on the FP32 pipe
     for (int c = t; c < 2 * k; c += kArnThreads) __stcg(&ctl.part[(size_t)bid * ctl.ldp + c], sred[c]);
     // ---- 3. grid barrier; identical totals in every block; (I + L) h = g ----------------
     if (!arn_grid_sync(a.gbar, gen++)) {
       arn_timeout(ctl);
       return;
     }
-    arn_reduce_cols(ctl.part, G, 2 * k, ctl.ldp, tot);  // ends with __syncthreads
+    if constexpr (sizeof(TV) == 4)
+      arn_reduce_cols_df(ctl.part, G, 2 * k, ctl.ldp, tot);  // ends with __syncthreads
+    else
+      arn_reduce_cols(ctl.part, G, 2 * k, ctl.ldp, tot);
     {
       // the new row of L: v_j . v_c = sigma_j sigma_c (u_j . u_c), c < j; g_c = sigma_c (u_c . w)
       const double sj = ssig[k - 1];
