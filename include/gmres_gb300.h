@@ -85,9 +85,12 @@ typedef struct {
 typedef enum {
   GMRES_FP64 = 0,        /* everything in FP64 */
   GMRES_FP32_INNER = 1,  /* each restart cycle (inner solve) runs SpMV and Arnoldi in
-                            FP32 with an FP32 basis; H, Givens, the coarse solve, the
-                            true residual r = b - A x and the update of x stay FP64
-                            (iterative refinement: one inner cycle per refinement) */
+                            FP32 with an FP32 basis; H, Givens, the true residual
+                            r = b - A x and the update of x with its coarse correction
+                            stay FP64 (iterative refinement: one inner cycle per
+                            refinement); the coarse solve of each step, whose result the
+                            FP32 SpMV reads in FP32, runs in FP32 (an FP32 copy of T^-1)
+                            where the step is fused, in FP64 elsewhere */
   GMRES_BF16_BASIS = 2   /* as GMRES_FP32_INNER, with the basis V stored in BF16 and
                             FP32 accumulation */
 } gmres_precision;

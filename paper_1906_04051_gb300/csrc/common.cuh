@@ -106,6 +106,7 @@ struct Defl {
   const int* agg_piece;   // r + 1 offsets into the piece list
   const double* uscale;   // r: 1/sqrt|agg_p|
   const double* tinv;     // r x r row-major T^-1
+  const float* tinv32;    // its FP32 copy (FP32 / BF16 solves), may be null
   int npieces;
   // the pieces of each block of the fused Arnoldi kernel (a grid of blk_grid blocks owning
   // consecutive row ranges; pieces are split at those ranges): block b's pieces are

@@ -86,6 +86,7 @@ struct ArnArgs {
   const int* blk_piece;
   const double* uscale;
   const double* tinv;
+  const float* tinv32;  // FP32 copy of T^-1 (FP32 basis)
   Ctl ctl;
   unsigned* gbar;  // [0] arrivals, [1] generation
 };
@@ -693,7 +694,7 @@ __device__ __forceinline__ void arn_front(const ArnArgs<TV, TACC>& a, int j, TAC
 }
 
 // u_{j+1} = w - V (sigma o h) over the block's rows (also into ush, indexed from the block's
-// first row, when given); returns the lane's part of ||u_{j+1}||^2
+// first row, when given); returns the warp's part of ||u_{j+1}||^2 (in every lane)
 template <typename TV, typename TACC, bool DF>
 __device__ __forceinline__ double arn_update(const ArnArgs<TV, TACC>& a, int k, const TACC* Ws,
                                           const TACC* scoef, TACC* ush) {
@@ -704,7 +705,8 @@ __device__ __forceinline__ double arn_update(const ArnArgs<TV, TACC>& a, int k, 
   const long long R1 = (long long)(bid + 1) * a.units / G * kArnUnit;
   const long long N = a.N;
   TV* __restrict__ vout = const_cast<TV*>(a.V) + (size_t)k * a.ldv;
-  double nrm = 0.0;
+  double nrm = 0.0;       // FP64 basis
+  float ns = 0.f, nc = 0.f;  // FP32 basis: a double-FP32 pair (FP64 adds are dear)
   {
     constexpr int U = sizeof(TV) == 8 ? 10 : 8;  // basis loads in flight per lane
     const int chunk = 32 * VN;
@@ -742,10 +744,21 @@ __device__ __forceinline__ double arn_update(const ArnArgs<TV, TACC>& a, int k, 
       TACC s = 0;
 #pragma unroll
       for (int e = 0; e < VN; ++e) s += un[e] * un[e];
-      nrm += (double)s;
+      if constexpr (sizeof(TACC) == 8) nrm += s;
+      else arn_df_add(ns, nc, s, 0.f);
     }
   }
-  return nrm;
+  if constexpr (sizeof(TACC) == 8) {
+    return warp_sum(nrm);
+  } else {  // the warp's total in double-FP32, rounded once
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float a2 = __shfl_xor_sync(0xffffffffu, ns, o);
+      const float b2 = __shfl_xor_sync(0xffffffffu, nc, o);
+      arn_df_add(ns, nc, a2, b2);
+    }
+    return (double)ns + (double)nc;
+  }
 }
 
 // Sums of u_{j+1} over this block's aggregate pieces (c of the next step's coarse solve, by
@@ -787,7 +800,14 @@ __device__ __forceinline__ void arn_piece_sums(const ArnArgs<TV, TACC>& a, const
         }
       }
       const double sum = warp_sum(acc[0] + acc[1]);
-      if (lane == 0) __stcg(a.ctl.cpart + p, sum);
+      if (lane == 0) {
+        if constexpr (sizeof(TACC) == 8) {
+          __stcg(a.ctl.cpart + p, sum);
+        } else {  // the pair the FP32 coarse solve reads
+          const float hs = (float)sum;
+          __stcg(reinterpret_cast<float2*>(a.ctl.cpart + p), make_float2(hs, (float)(sum - (double)hs)));
+        }
+      }
     }
   }
 }
@@ -821,7 +841,9 @@ __device__ __forceinline__ void arn_piece_sums_staged(double* cpart, const TACC*
         const float b2 = __shfl_xor_sync(0xffffffffu, hc, o);
         arn_df_add(hs, hc, a2, b2);
       }
-      sum = (double)hs + (double)hc;
+      // an FP32 basis keeps the pair (two floats in the slot) for the FP32 coarse solve
+      if (lane == 0) __stcg(reinterpret_cast<float2*>(cpart + spid[i]), make_float2(hs, hc));
+      continue;
     }
     if (lane == 0) __stcg(cpart + spid[i], sum);
   }
@@ -1027,9 +1049,8 @@ __global__ void __launch_bounds__(kArnThreads, 1)
     double nrm = arn_update<TV, TACC, DF>(a, k, Ws, scoef, ush);
     // ---- 5. norm partial; partial sums of u_{j+1} over this block's aggregate pieces ----
     {
-      // warp sums, then warp 0 adds the 16 of them (a block-wide final loop would issue 16
-      // FP64 adds in every warp)
-      nrm = warp_sum(nrm);
+      // the warp sums (formed by the update), then warp 0 adds the 16 of them (a block-wide
+      // final loop would issue 16 FP64 adds in every warp)
       if (lane == 0) snrm[warp] = nrm;
       __syncthreads();  // also orders this block's stores of u_{j+1} before the piece sums
       if (warp == 0) {
@@ -1057,48 +1078,93 @@ __global__ void __launch_bounds__(kArnThreads, 1)
       givens_step(ctl, j, a.m, sqrt(tot[0]));
     }
     if (coarse) {
-      // c_a = uscale_a (sum of a's pieces, in piece order), every aggregate in every block
-      for (int q = t; q < a.r; q += kArnThreads) {
-        const int p0 = __ldg(a.agg_piece + q), p1 = __ldg(a.agg_piece + q + 1);
-        double sum = 0.0;
-        for (int pb = p0; pb < p1; pb += 8) {
-          double v[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) v[u] = pb + u < p1 ? __ldcg(ctl.cpart + pb + u) : 0.0;
-#pragma unroll
-          for (int u = 0; u < 8; ++u) sum += v[u];
-        }
-        sc[q] = __ldg(a.uscale + q) * sum;
-      }
-      __syncthreads();
       // y = T^-1 c: a warp per row, the rows dealt round-robin over blocks 1 .. G-1 (warp w
       // of block b takes rows (b - 1) + (G - 1) (w + 16 i)) so that each block has few; all
       // to block 0 when it is alone.  TQ loads in flight per lane (a whole row up to 1024)
       constexpr int TQ = 32;
       const int gw = G == 1 ? warp : (bid - 1) + (G - 1) * warp;
       const int nw = G == 1 ? kArnWarps : (G - 1) * kArnWarps;
-      const double mu = __ldcg(&ctl.scal[S_MU]);
-      for (int row = gw; row < a.r; row += nw) {
-        const double* tr = a.tinv + (size_t)row * a.r;
-        double acc[2] = {0.0, 0.0};
-        for (int b0 = 0; b0 < a.r; b0 += 32 * TQ) {
-          double tv[TQ];
+      if constexpr (sizeof(TACC) == 8) {
+        // c_a = uscale_a (sum of a's pieces, in piece order), every aggregate in every block
+        for (int q = t; q < a.r; q += kArnThreads) {
+          const int p0 = __ldg(a.agg_piece + q), p1 = __ldg(a.agg_piece + q + 1);
+          double sum = 0.0;
+          for (int pb = p0; pb < p1; pb += 8) {
+            double v[8];
 #pragma unroll
-          for (int u = 0; u < TQ; ++u) {
-            const int b = b0 + lane + 32 * u;
-            tv[u] = b < a.r ? __ldg(tr + b) : 0.0;
+            for (int u = 0; u < 8; ++u) v[u] = pb + u < p1 ? __ldcg(ctl.cpart + pb + u) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sum += v[u];
           }
+          sc[q] = __ldg(a.uscale + q) * sum;
+        }
+        __syncthreads();
+        const double mu = __ldcg(&ctl.scal[S_MU]);
+        for (int row = gw; row < a.r; row += nw) {
+          const double* tr = a.tinv + (size_t)row * a.r;
+          double acc[2] = {0.0, 0.0};
+          for (int b0 = 0; b0 < a.r; b0 += 32 * TQ) {
+            double tv[TQ];
 #pragma unroll
-          for (int u = 0; u < TQ; ++u) {
-            const int b = b0 + lane + 32 * u;
-            if (b < a.r) acc[u & 1] += tv[u] * sc[b];
+            for (int u = 0; u < TQ; ++u) {
+              const int b = b0 + lane + 32 * u;
+              tv[u] = b < a.r ? __ldg(tr + b) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < TQ; ++u) {
+              const int b = b0 + lane + 32 * u;
+              if (b < a.r) acc[u & 1] += tv[u] * sc[b];
+            }
+          }
+          const double y = warp_sum(acc[0] + acc[1]);
+          if (lane == 0) {
+            const double sd = __ldg(a.uscale + row) * (mu * y - sc[row]);
+            __stcg(ctl.sdefl + row, sd);
+            __stcg(ctl.sdefl32 + row, (float)sd);
           }
         }
-        const double y = warp_sum(acc[0] + acc[1]);
-        if (lane == 0) {
-          const double sd = __ldg(a.uscale + row) * (mu * y - sc[row]);
-          __stcg(ctl.sdefl + row, sd);
-          __stcg(ctl.sdefl32 + row, (float)sd);
+      } else {
+        // FP32 basis: s' is used in FP32, so the coarse solve runs in FP32 too (c from the
+        // double-FP32 piece pairs, rounded once; the FP32 copy of T^-1; FP32 sums)
+        float* scf = reinterpret_cast<float*>(sc);
+        for (int q = t; q < a.r; q += kArnThreads) {
+          const int p0 = __ldg(a.agg_piece + q), p1 = __ldg(a.agg_piece + q + 1);
+          float hs = 0.f, hc = 0.f;
+          for (int pb = p0; pb < p1; pb += 8) {
+            float2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              v[u] = pb + u < p1 ? __ldcg(reinterpret_cast<const float2*>(ctl.cpart + pb + u))
+                                 : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) arn_df_add(hs, hc, v[u].x, v[u].y);
+          }
+          scf[q] = (float)__ldg(a.uscale + q) * (hs + hc);
+        }
+        __syncthreads();
+        const float mu = (float)__ldcg(&ctl.scal[S_MU]);
+        for (int row = gw; row < a.r; row += nw) {
+          const float* tr = a.tinv32 + (size_t)row * a.r;
+          float acc[4] = {0.f, 0.f, 0.f, 0.f};
+          for (int b0 = 0; b0 < a.r; b0 += 32 * TQ) {
+            float tv[TQ];
+#pragma unroll
+            for (int u = 0; u < TQ; ++u) {
+              const int b = b0 + lane + 32 * u;
+              tv[u] = b < a.r ? __ldg(tr + b) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < TQ; ++u) {
+              const int b = b0 + lane + 32 * u;
+              if (b < a.r) acc[u & 3] += tv[u] * scf[b];
+            }
+          }
+          const float y = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
+          if (lane == 0) {
+            const float sd = (float)__ldg(a.uscale + row) * (mu * y - scf[row]);
+            __stcg(ctl.sdefl + row, (double)sd);
+            __stcg(ctl.sdefl32 + row, sd);
+          }
         }
       }
     }
@@ -1197,6 +1263,7 @@ struct Arn {
     p.blk_piece = c.op.defl.blk_piece;
     p.uscale = c.op.defl.uscale;
     p.tinv = c.op.defl.tinv;
+    p.tinv32 = c.op.defl.tinv32;
     p.ctl = c.ctl;
     p.gbar = c.gbar;
     // the 9-point stencils of the Q1 systems take an unrolled instantiation
@@ -1221,6 +1288,7 @@ bool arnoldi_fusable(const CycleArgs& a) {
   if (r > 0 && (!a.op.defl.blk_piece_start ||
                 a.op.defl.blk_grid != (int)std::min<long long>(a.ldv / kArnUnit, a.sms)))
     return false;
+  if (r > 0 && a.prec == P_FP32 && !a.op.defl.tinv32) return false;  // its FP32 coarse solve
   const long long rs = a.prec == P_FP64 ? Arn<double, double>::super_rows(r)
                                         : Arn<float, float>::super_rows(r);
   // c (r doubles) lives where w and u_j do

@@ -46,7 +46,7 @@ struct Meta {  // mirrors the device status block
 };
 
 struct OpHost {
-  DevMem rowptr, col, val, val32, tinv;
+  DevMem rowptr, col, val, val32, tinv, tinv32;  // tinv32: FP32 copy (FP32 / BF16 solves)
   DevMem aurp, aucol, auval, auval32;  // A W in CSR (projector, residual)
   DevMem xrp, xcol, xval, xval32;      // [A | A W] rows (deflated SpMV of a step)
   DevMem dval, dval32;                 // diagonal storage (banded operators)
@@ -314,6 +314,7 @@ inline OpDev make_op(gmres_s* h, OpHost& o) {
   op.defl.agg_piece = h->agg_piece.as<int>();
   op.defl.uscale = h->uscale.as<double>();
   op.defl.tinv = o.tinv.as<double>();
+  op.defl.tinv32 = o.tinv32.as<float>();
   op.defl.npieces = h->npieces;
   op.defl.blk_piece_start = h->blk_piece_start.as<int>();
   op.defl.blk_piece = h->blk_piece.as<int>();

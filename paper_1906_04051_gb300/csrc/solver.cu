@@ -548,6 +548,12 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
                         aggptr.as<int>(), h->uscale.as<double>(), T.as<double>(), st));
     CKC(launch_gauss_jordan(r, T.as<double>(), G.as<double>(), fac.p,
                             h->fwd.tinv.as<double>(), h->adj.tinv.as<double>(), err.as<int>(), st));
+    if (opts.precision != GMRES_FP64) {  // the FP32 coarse solve of the fused FP32 step
+      CKC(h->fwd.tinv32.ensure(sizeof(float) * (size_t)r * r));
+      CKC(h->adj.tinv32.ensure(sizeof(float) * (size_t)r * r));
+      CKC(launch_to_float((long long)r * r, h->fwd.tinv.as<double>(), h->fwd.tinv32.as<float>(), st));
+      CKC(launch_to_float((long long)r * r, h->adj.tinv.as<double>(), h->adj.tinv32.as<float>(), st));
+    }
     int np = 0;
     CKC(cudaMemcpyAsync(&np, h->agg_piece.as<int>() + r, sizeof(int), cudaMemcpyDeviceToHost, st));
     CKC(cudaMemcpyAsync(herr, err.p, sizeof(herr), cudaMemcpyDeviceToHost, st));
@@ -585,6 +591,7 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
   // infinity norm
   h->plaunch[PH_SETUP] = 1 + (opts.precision != GMRES_FP64 ? 1 : 0) +
                          (r > 0 ? 4 + 1 + 3 + (long long)r : 0) +
+                         (r > 0 && opts.precision != GMRES_FP64 ? 2 : 0) +
                          (r > 0 && opts.deflation_mode != GMRES_DEFL_NONE ? 5 : 0) +
                          (r > 0 && opts.deflation_mode == GMRES_DEFL_EBP ? 2 : 0) +
                          1 + (h->fwd.dia.nd > 0 ? 1 : 0) +
