@@ -205,20 +205,46 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
   const TACC sigma = (TACC)ctl.sigma[j];
+  if constexpr (DEFL) {
+    if (d.qd > 0) {  // adaptive deflation: A U dense
+#pragma unroll
+      for (int u = 0; u < kDiaRows; ++u) {
+        const int i = i0 + u * blockDim.x;
+        if (i < N)
+          for (int t = 0; t < d.qd; ++t) acc[u] += (TACC)d.aud[(size_t)t * d.ldu + i] * sdefl[t];
+      }
+    } else {
+      // the A W rows of the thread's kDiaRows rows, each level of the gather (row
+      // pointers, first entries, s' at their aggregates) issued for all rows at once; the
+      // rare further entries of a row follow one by one
+      int e0[kDiaRows], e1[kDiaRows], ac[kDiaRows];
+      TACC av[kDiaRows], sv[kDiaRows];
+#pragma unroll
+      for (int u = 0; u < kDiaRows; ++u) {
+        const int i = i0 + u * blockDim.x;
+        e0[u] = i < N ? __ldg(d.aurp + i) : 0;
+        e1[u] = i < N ? __ldg(d.aurp + i + 1) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kDiaRows; ++u) {
+        const bool has = e0[u] < e1[u];
+        av[u] = has ? (TACC)__ldg(auval + e0[u]) : (TACC)0;
+        ac[u] = has ? __ldg(d.aucol + e0[u]) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kDiaRows; ++u) sv[u] = e0[u] < e1[u] ? sdefl[ac[u]] : (TACC)0;
+#pragma unroll
+      for (int u = 0; u < kDiaRows; ++u) {
+        TACC aw = av[u] * sv[u];
+        for (int e = e0[u] + 1; e < e1[u]; ++e) aw += (TACC)__ldg(auval + e) * sdefl[__ldg(d.aucol + e)];
+        acc[u] += aw;
+      }
+    }
+  }
 #pragma unroll
   for (int u = 0; u < kDiaRows; ++u) {
     const int i = i0 + u * blockDim.x;
-    if (i < N) {
-      TACC v = acc[u];
-      if constexpr (DEFL) {
-        if (d.qd > 0) {  // adaptive deflation: A U dense
-          for (int t = 0; t < d.qd; ++t) v += (TACC)d.aud[(size_t)t * d.ldu + i] * sdefl[t];
-        } else {
-          v += au_row<TA, TACC>(i, d.aurp, d.aucol, auval, sdefl);
-        }
-      }
-      w[i] = sigma * v;
-    }
+    if (i < N) w[i] = sigma * acc[u];
   }
 }
 
