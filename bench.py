@@ -42,7 +42,7 @@ FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the fused Arnoldi kernel
 # (a full 50-step deflated cycle) on this workload, FP64 and FP32 basis (one ncu capture
 # each, profiles/k_arnoldi_cycle_q1-n1024_*.txt); None once the kernel changes
-ARN_DRAM_BYTES_CYCLE50 = {8: 25.965e9, 4: 8.293e9}
+ARN_DRAM_BYTES_CYCLE50 = {8: 25.965e9, 4: None}
 # Arnoldi steps the deflated GMRES(50) takes to 1e-8 on this workload (deterministic;
 # the GPU arm prints its own count): used only to project the CPU sample to a full solve
 PROJECT_ITERS = 782
@@ -154,11 +154,11 @@ def arn_units(layout, n, ks, s, coarse_steps=0):
     once), the update (k FMA per row; the basis read again, u_{j+1} written) and the norm;
     w and u_j stay on chip.  coarse_steps of them also run the next step's coarse solve in
     the kernel: the sums of u_{j+1} over the aggregates (n adds, from shared memory) and
-    y = T^-1 c (r^2 FMA, T^-1 read in FP64)."""
+    y = T^-1 c (r^2 FMA, T^-1 read in the basis precision)."""
     nd, nau, r = layout.get("ndiag", 0), layout.get("nau", 0), layout.get("r", 0)
     fma = sum(nd * n + nau + 3.0 * k * n + n for k in ks) + coarse_steps * (r * r + 0.5 * n)
     byt = (sum(s * (nd * n + n + 2.0 * k * n + n) + 4.0 * (n + 1) + (4.0 + s) * nau for k in ks)
-           + coarse_steps * 8.0 * r * r)
+           + coarse_steps * s * r * r)
     return fma, byt
 
 

@@ -299,10 +299,10 @@ __device__ __forceinline__ void arn_df_add(float& s, float& c, float s2, float c
 }
 
 // The same over partials stored as double-FP32 pairs (two floats per slot): TwoSum on the
-// FP32 pipe in the same fixed order, rounded to FP64 once per column.
+// FP32 pipe in a fixed order, L loads in flight per thread, rounded to FP64 once per column.
+template <int L>
 __device__ __forceinline__ void arn_reduce_cols_df(const double* src, int nrows, int ncols,
                                                    int ldp, double* dst) {
-  constexpr int L = 8;
   int Q = 1;
   while (Q * 2 <= 32 && Q * 2 * ncols <= (int)blockDim.x) Q *= 2;
   const int rounds = (ncols * Q + blockDim.x - 1) / blockDim.x;
@@ -944,6 +944,29 @@ __global__ void __launch_bounds__(kArnThreads, 1)
       for (int q = lane; q < n; q += 32) snode[ls + q] = (unsigned short)(__ldg(a.perm + s + q) - R0);
     }
   }
+  // FP32 basis: the coarse solve's static data for the cycle (the aggregates' piece ranges,
+  // their scales, this block's rows of T^-1 when every warp has at most one) staged once in
+  // shared memory past the rows of w's slice, when it fits
+  int* sap = nullptr;       // agg_piece, r + 1
+  float* sus = nullptr;     // uscale, r
+  float* stinv = nullptr;   // the block's rows of T^-1 (warp w: row (b - 1) + (G - 1) w)
+  if constexpr (sizeof(TACC) == 4) {
+    const int nwr = G == 1 ? kArnWarps : (G - 1) * kArnWarps;  // warps sharing the rows
+    const int rows = (a.defl && bid > 0 && a.r <= nwr && bid - 1 < a.r)
+                         ? min(kArnWarps, (a.r - (bid - 1) + G - 2) / (G - 1)) : 0;
+    const size_t need = (size_t)(a.r + 1) * 4 + (size_t)a.r * 4 + (size_t)rows * a.r * 4;
+    if (a.defl && G > 1 && a.RS > nrows && (size_t)(a.RS - nrows) * sizeof(TACC) >= need + 16) {
+      sap = reinterpret_cast<int*>(Ws + nrows);
+      sus = reinterpret_cast<float*>(sap + a.r + 1);
+      stinv = rows > 0 ? sus + a.r : nullptr;
+      for (int q = t; q <= a.r; q += kArnThreads) sap[q] = __ldg(a.agg_piece + q);
+      for (int q = t; q < a.r; q += kArnThreads) sus[q] = (float)__ldg(a.uscale + q);
+      for (int q = t; q < rows * a.r; q += kArnThreads) {
+        const int w = q / a.r, b = q % a.r;
+        stinv[q] = __ldg(a.tinv32 + (size_t)((bid - 1) + (G - 1) * w) * a.r + b);
+      }
+    }
+  }
   bool waited = !a.pre;
   __syncthreads();
 
@@ -1001,7 +1024,8 @@ __global__ void __launch_bounds__(kArnThreads, 1)
       return;
     }
     if constexpr (sizeof(TV) == 4)
-      arn_reduce_cols_df(ctl.part, G, 2 * k, ctl.ldp, tot);  // ends with __syncthreads
+      // (a thread's 152 / 8 rows of partials in one batch of loads)
+      arn_reduce_cols_df<24>(ctl.part, G, 2 * k, ctl.ldp, tot);  // ends with __syncthreads
     else
       arn_reduce_cols(ctl.part, G, 2 * k, ctl.ldp, tot);
     {
@@ -1128,7 +1152,8 @@ __global__ void __launch_bounds__(kArnThreads, 1)
         // double-FP32 piece pairs, rounded once; the FP32 copy of T^-1; FP32 sums)
         float* scf = reinterpret_cast<float*>(sc);
         for (int q = t; q < a.r; q += kArnThreads) {
-          const int p0 = __ldg(a.agg_piece + q), p1 = __ldg(a.agg_piece + q + 1);
+          const int p0 = sap ? sap[q] : __ldg(a.agg_piece + q);
+          const int p1 = sap ? sap[q + 1] : __ldg(a.agg_piece + q + 1);
           float hs = 0.f, hc = 0.f;
           for (int pb = p0; pb < p1; pb += 8) {
             float2 v[8];
@@ -1139,19 +1164,20 @@ __global__ void __launch_bounds__(kArnThreads, 1)
 #pragma unroll
             for (int u = 0; u < 8; ++u) arn_df_add(hs, hc, v[u].x, v[u].y);
           }
-          scf[q] = (float)__ldg(a.uscale + q) * (hs + hc);
+          scf[q] = (sus ? sus[q] : (float)__ldg(a.uscale + q)) * (hs + hc);
         }
         __syncthreads();
         const float mu = (float)__ldcg(&ctl.scal[S_MU]);
         for (int row = gw; row < a.r; row += nw) {
-          const float* tr = a.tinv32 + (size_t)row * a.r;
+          // the row from shared memory when staged (a plain load), else from global memory
+          const float* tr = stinv ? stinv + (size_t)warp * a.r : a.tinv32 + (size_t)row * a.r;
           float acc[4] = {0.f, 0.f, 0.f, 0.f};
           for (int b0 = 0; b0 < a.r; b0 += 32 * TQ) {
             float tv[TQ];
 #pragma unroll
             for (int u = 0; u < TQ; ++u) {
               const int b = b0 + lane + 32 * u;
-              tv[u] = b < a.r ? __ldg(tr + b) : 0.f;
+              tv[u] = b < a.r ? tr[b] : 0.f;
             }
 #pragma unroll
             for (int u = 0; u < TQ; ++u) {
@@ -1161,7 +1187,7 @@ __global__ void __launch_bounds__(kArnThreads, 1)
           }
           const float y = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
           if (lane == 0) {
-            const float sd = (float)__ldg(a.uscale + row) * (mu * y - scf[row]);
+            const float sd = (sus ? sus[row] : (float)__ldg(a.uscale + row)) * (mu * y - scf[row]);
             __stcg(ctl.sdefl + row, (double)sd);
             __stcg(ctl.sdefl32 + row, sd);
           }
