@@ -695,7 +695,7 @@ __device__ __forceinline__ void arn_front(const ArnArgs<TV, TACC>& a, int j, TAC
 
 // u_{j+1} = w - V (sigma o h) over the block's rows (also into ush, indexed from the block's
 // first row, when given); returns the warp's part of ||u_{j+1}||^2 (in every lane)
-template <typename TV, typename TACC, bool DF>
+template <typename TV, typename TACC, int ND, bool DF>
 __device__ __forceinline__ double arn_update(const ArnArgs<TV, TACC>& a, int k, const TACC* Ws,
                                           const TACC* scoef, TACC* ush) {
   constexpr int VN = ArnVec<TV>::n;
@@ -708,7 +708,7 @@ __device__ __forceinline__ double arn_update(const ArnArgs<TV, TACC>& a, int k, 
   double nrm = 0.0;       // FP64 basis
   float ns = 0.f, nc = 0.f;  // FP32 basis: a double-FP32 pair (FP64 adds are dear)
   {
-    constexpr int U = sizeof(TV) == 8 ? 10 : 8;  // basis loads in flight per lane
+    constexpr int U = sizeof(TV) == 4 ? 8 : (ND == 9 && !DF ? 13 : 10);  // basis loads in flight per lane
     const int chunk = 32 * VN;
     const long long nch = (R1 - R0) / chunk;
     const bool wsm = !DF && R1 - R0 <= a.RS;  // the block's w is still in shared memory
@@ -1070,7 +1070,7 @@ __global__ void __launch_bounds__(kArnThreads, 1)
     // a shared-memory copy of u_{j+1} for the piece sums when the block's rows fit one
     // super-tile (u_j's slice is dead by now)
     TACC* ush = (a.defl && k < a.jmax && R1 - R0 <= a.RS) ? Us : nullptr;
-    double nrm = arn_update<TV, TACC, DF>(a, k, Ws, scoef, ush);
+    double nrm = arn_update<TV, TACC, ND, DF>(a, k, Ws, scoef, ush);
     // ---- 5. norm partial; partial sums of u_{j+1} over this block's aggregate pieces ----
     {
       // the warp sums (formed by the update), then warp 0 adds the 16 of them (a block-wide
