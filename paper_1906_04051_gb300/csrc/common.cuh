@@ -25,6 +25,10 @@ constexpr int kThreads = 256;           // threads of the streaming kernels
 constexpr int kSlices = 8;              // column slices of a multi-dot (one per warp)
 constexpr int kSliceCols = (kMaxK + kSlices - 1) / kSlices;  // 9 accumulators / thread
 constexpr int kPiece = 1024;            // nodes per piece of an aggregate sum
+// rows per unit of the fused Arnoldi kernel's row partition (block b owns the units
+// [floor(b U / G), floor((b + 1) U / G)) of the U = ldv / kPartUnit): the FP32 chunk of 128
+// rows, so that no block owns more than 128 rows above the mean
+constexpr int kPartUnit = 128;
 
 // ---- named slots of the solver control block (device memory) ----
 enum ScalarSlot {
@@ -120,6 +124,11 @@ struct Defl {
   const int* aucol;       // aggregate ids
   const double* auval;
   const float* auval32;   // FP32 copy (FP32 inner), may be null
+  // the same rows' first two entries in two planes of n (plane q at q * n): column -1 when
+  // absent; plane 1 holds -(column) - 2 when the row has more entries (from aurp[i] + 2)
+  const int* aup_col;
+  const double* aup_val;
+  const float* aup_val32;  // may be null
   // adaptive deflation: U and A U dense (qd columns of ldu rows), T^-1 (qd x qd); the
   // step's coarse term is sum_t aud[t][i] s'_t instead of the A W row
   const double* ud;

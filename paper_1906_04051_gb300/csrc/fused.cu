@@ -5,7 +5,7 @@
 // preconditioner (Eq. 17: s' = U (|mu| T^-1 - I) U^T v_{j+1}).
 //
 // One block of 16 warps per multiprocessor, launched cooperatively (every block resident).
-// Block b owns a contiguous range of rows (a multiple of 256) for the whole cycle, taken in
+// Block b owns a contiguous range of rows (a multiple of 128) for the whole cycle, taken in
 // super-tiles of at most RS rows whose slices of w and u_j stay in shared memory.  A step:
 //   1. SpMV of the super-tile's rows (diagonal storage; the coarse correction through the
 //      A W rows, s' staged in shared memory): w into shared memory (and global memory when
@@ -45,14 +45,15 @@ namespace {
 
 constexpr int kArnWarps = 16;
 constexpr int kArnThreads = kArnWarps * 32;
-constexpr int kArnUnit = 256;                    // rows per unit of the row partition
+constexpr int kArnUnit = kPartUnit;              // rows per unit of the row partition
 constexpr size_t kArnSmem = 220 * 1024;          // dynamic shared memory
 // reductions: lane-wise totals [2][kMaxK][33] (FP64) or warp sums [2][16][kMaxK] (FP32)
 constexpr size_t kArnScratch = 2 * kMaxK * 33 * sizeof(double);
 constexpr size_t kArnStaging = 2 * 2 * 16 * 32 * sizeof(double);  // FP64 multi-dot staging
 constexpr long long kArnSpins = 1LL << 21;       // polls of the barrier word: about a second
 constexpr int kArnNormCol = 2 * kMaxK;           // column of ctl.part holding the norm partials
-constexpr int kArnAwRows = 6;                   // rows per thread of an A W gather batch
+constexpr int kArnAwRows64 = 6;  // rows per thread of an A W gather batch: FP64 (CSR rows)
+constexpr int kArnAwRows32 = 7;  // FP32 (row-indexed planes)
 // 16-byte basis loads in flight per lane in the multi-dot: FP32 (bound by HBM) asks for
 // more bytes in flight than FP64 (bound by its FMA pipe)
 template <typename TV> constexpr int arn_loads() { return sizeof(TV) == 8 ? 6 : 12; }
@@ -75,6 +76,8 @@ struct ArnArgs {
   const int* aurp;
   const int* aucol;
   const TACC* auval;
+  const int* aup_col;   // the rows' first two A W entries, two planes of N
+  const TACC* aup_val;
   const TACC* sdefl;  // s' in the step's precision (step 0: from the coarse-solve kernel)
   // the coarse solve of the next step, in the kernel: pieces of aggregates (nodes perm
   // [piece_start[p], piece_start[p + 1]), each inside one block's rows), block b's pieces
@@ -434,60 +437,86 @@ __device__ __forceinline__ void arn_dia_rows(TACC (&acc)[B], long long row0, lon
 }
 
 // Multi-dot in row-chunk order (FP32 basis): warp w takes the chunks w, w + 16, ... of the
-// super-tile and, per pass, a group of up to G columns: one 16-byte load per column
-// and lane for the same rows, so the loads in flight of a warp fall in one row window of
-// many columns (on GB300 this streams about twice as fast as a warp reading one column
-// through many consecutive chunks).  At the end of a pass the lanes' partial sums of each
-// column are added by a shuffle tree and lane 0 accumulates them into wsum[set][warp][c].
-// (10 columns per pass: measured on q1-n1024, 12 made the whole FP32 step 7 % slower)
-template <int ND> constexpr int arn_group() { return 10; }
+// super-tile and, per unit, a group of up to G columns at one chunk: one 16-byte load per
+// column and lane for the same rows, so the loads in flight of a warp fall in one row window
+// of many columns (on GB300 this streams about twice as fast as a warp reading one column
+// through many consecutive chunks).  Units run group by group, the warp's chunks in order,
+// and the next unit's G loads are issued before the current one is consumed (two units in
+// flight).  At a group's last chunk the lanes' partial sums of each column are added by a
+// shuffle tree and lane 0 accumulates them into wsum[set][warp][c].  (G = 6 with two units
+// in flight: measured on q1-n1024, 20 us at k = 26 against 21 for 10 columns, one unit at a
+// time; 8 columns do not fit the register budget, nor 6 beside the run-time diagonal count
+// of the general banded instantiation, which takes 5.)
+template <int ND> constexpr int arn_group() { return ND == 9 ? 6 : 5; }
 
 template <typename TV, typename TACC, int G>
 __device__ __forceinline__ void arn_dots_rows(double* wsum, const TV* V, long long ldv, int k,
                                               long long s0, int nch, const TACC* Ws,
                                               const TACC* Us, int warp, int lane) {
   constexpr int VN = ArnVec<TV>::n;
-  for (int g0 = 0; g0 < k; g0 += G) {
+  const int nqw = warp < nch ? (nch - 1 - warp) / kArnWarps + 1 : 0;  // chunks of this warp
+  const int ng = (k + G - 1) / G;
+  const int TU = ng * nqw;
+  if (TU == 0) return;
+  TACC a1[G], a2[G];
+#pragma unroll
+  for (int u = 0; u < G; ++u) {
+    a1[u] = 0;
+    a2[u] = 0;
+  }
+  auto load_unit = [&](int un, TACC (&b)[G][VN]) {
+    const int g = un / nqw, qi = un - g * nqw;
+    const int g0 = g * G;
     const int gc = k - g0 < G ? k - g0 : G;
-    TACC a1[G], a2[G];
-#pragma unroll
-    for (int u = 0; u < G; ++u) {
-      a1[u] = 0;
-      a2[u] = 0;
-    }
-    const TV* col = V + (size_t)g0 * ldv + s0 + (size_t)lane * VN;
-    for (int q = warp; q < nch; q += kArnWarps) {
-      const size_t off = (size_t)q * 32 * VN;
-      TACC v[G][VN];
-#pragma unroll
-      for (int u = 0; u < G; ++u)
-        if (u < gc) arn_ldg<TV, TACC, VN>(col + (size_t)u * ldv + off, v[u]);
-      TACC wv[VN], uv[VN];
-      ld_acc<VN>(Ws + off + lane * VN, wv);
-      ld_acc<VN>(Us + off + lane * VN, uv);
-#pragma unroll
-      for (int u = 0; u < G; ++u)
-        if (u < gc)
-#pragma unroll
-          for (int e = 0; e < VN; ++e) {
-            a1[u] += v[u][e] * wv[e];
-            a2[u] += v[u][e] * uv[e];
-          }
-    }
+    const TV* col = V + (size_t)g0 * ldv + s0 + (size_t)lane * VN +
+                    (size_t)(warp + qi * kArnWarps) * 32 * VN;
 #pragma unroll
     for (int u = 0; u < G; ++u)
-      if (u < gc) {
-        const TACC t1 = warp_sum(a1[u]), t2 = warp_sum(a2[u]);
-        if (lane == 0) {
-          float2* p1 = reinterpret_cast<float2*>(wsum) + (size_t)warp * kMaxK + g0 + u;
-          float2* p2 = reinterpret_cast<float2*>(wsum) + (size_t)(kArnWarps + warp) * kMaxK + g0 + u;
-          float2 a1v = *p1, a2v = *p2;
-          arn_df_add(a1v.x, a1v.y, (float)t1, 0.f);
-          arn_df_add(a2v.x, a2v.y, (float)t2, 0.f);
-          *p1 = a1v;
-          *p2 = a2v;
+      if (u < gc) arn_ldg<TV, TACC, VN>(col + (size_t)u * ldv, b[u]);
+  };
+  auto consume = [&](int un, const TACC (&b)[G][VN]) {
+    const int g = un / nqw, qi = un - g * nqw;
+    const int g0 = g * G;
+    const int gc = k - g0 < G ? k - g0 : G;
+    const size_t off = (size_t)(warp + qi * kArnWarps) * 32 * VN;
+    TACC wv[VN], uv[VN];
+    ld_acc<VN>(Ws + off + lane * VN, wv);
+    ld_acc<VN>(Us + off + lane * VN, uv);
+#pragma unroll
+    for (int u = 0; u < G; ++u)
+      if (u < gc)
+#pragma unroll
+        for (int e = 0; e < VN; ++e) {
+          a1[u] += b[u][e] * wv[e];
+          a2[u] += b[u][e] * uv[e];
         }
+    if (qi == nqw - 1) {  // the group's last chunk in this warp
+#pragma unroll
+      for (int u = 0; u < G; ++u) {
+        if (u < gc) {
+          const TACC t1 = warp_sum(a1[u]), t2 = warp_sum(a2[u]);
+          if (lane == 0) {
+            float2* p1 = reinterpret_cast<float2*>(wsum) + (size_t)warp * kMaxK + g0 + u;
+            float2* p2 = reinterpret_cast<float2*>(wsum) + (size_t)(kArnWarps + warp) * kMaxK + g0 + u;
+            float2 a1v = *p1, a2v = *p2;
+            arn_df_add(a1v.x, a1v.y, (float)t1, 0.f);
+            arn_df_add(a2v.x, a2v.y, (float)t2, 0.f);
+            *p1 = a1v;
+            *p2 = a2v;
+          }
+        }
+        a1[u] = 0;
+        a2[u] = 0;
       }
+    }
+  };
+  TACC bA[G][VN], bB[G][VN];
+  load_unit(0, bA);
+  for (int un = 0; un < TU; un += 2) {
+    if (un + 1 < TU) load_unit(un + 1, bB);
+    consume(un, bA);
+    if (un + 2 < TU) load_unit(un + 2, bA);
+    if (un + 1 < TU) consume(un + 1, bB);
   }
 }
 
@@ -508,9 +537,18 @@ __device__ __forceinline__ void arn_dots_group4(double* sbuf, double* stg, const
   constexpr int D = arn_loads<TV>();
   const int cg = warp >> 2, ws = warp & 3;
   const int ncg = cg < k ? (k - cg + 3) / 4 : 0;  // columns of this group
-  const int cpw = nch / 4;                         // chunks per warp and column
+  const int cpw = (nch - ws + 3) / 4;              // chunks of this warp per column
   const int T = ncg * cpw;
-  if (T == 0) return;
+  if (ncg == 0) return;  // the same in the group's four warps
+  if (T == 0) {  // no chunk of this warp (nch < 4): zeros at the group's column ends
+    for (int i = 0; i < ncg; ++i) {
+      double* sb = stg + (size_t)(i & 1) * 2 * kArnWarps * 32;
+      sb[(0 * kArnWarps + warp) * 32 + lane] = 0.0;
+      sb[(1 * kArnWarps + warp) * 32 + lane] = 0.0;
+      asm volatile("bar.sync %0, 128;" ::"r"(1 + cg) : "memory");
+    }
+    return;
+  }
   // load side: a pointer that steps 4 chunks down the column, then on to the group's next
   // column (no division per load)
   const size_t step = (size_t)4 * 32 * VN;
@@ -624,46 +662,107 @@ __device__ __forceinline__ void arn_front(const ArnArgs<TV, TACC>& a, int j, TAC
     // ---- 1. SpMV of the super-tile's rows: w and u_j into shared memory (the first
     // super-tile's may have been formed during the previous step's coarse solve) ---------
     if (!(first_diag_done && s0 == R0)) arn_diag<ND, TV, TACC>(a, j, s0, s1, Ws, Us);
-    if (!waited) {  // s' (the coarse solve's output) is read from here on
-      pdl_wait();
-      pdl_trigger();
-      waited = true;
-    }
-    if (a.defl && s0 == R0)
-      for (int q = t; q < a.r; q += kArnThreads) Ss[q] = __ldcg(a.sdefl + q);
-    __syncthreads();
-    // + A W s' (the row's A W entries, s' from shared memory), the scale sigma_j; w also
-    // to global memory when the update reads it there.  The rows are taken kArnAwRows
-    // per thread at a time, each level of the A W gather (row pointers, then the first
-    // entry of every row) issued for all of them at once.
-    for (long long i0 = s0 + t; i0 < s1; i0 += (long long)kArnAwRows * kArnThreads) {
-      int e0[kArnAwRows], e1[kArnAwRows];
-#pragma unroll
-      for (int b = 0; b < kArnAwRows; ++b) {
-        const long long row = i0 + (long long)b * kArnThreads;
-        const bool live = a.defl && row < N && row < s1;
-        e0[b] = live ? __ldg(a.aurp + row) : 0;
-        e1[b] = live ? __ldg(a.aurp + row + 1) : 0;
+    // + A W s' (the row's A W entries, s' from shared memory), the scale sigma_j; w also to
+    // global memory when the update reads it there.
+    if constexpr (sizeof(TACC) == 8) {
+      // FP64 (every FP64 instruction costs the scarce FP64 pipe): the CSR rows, kArnAwRows64
+      // rows per thread at once, each level of the gather (row pointers, then the first entry
+      // of every row) issued for all of them; s' is staged pre-scaled by sigma_j, so that
+      // w = sigma_j Ws + sum a_iq (sigma_j s'_q) takes one multiply-add per entry and row
+      if (!waited) {  // s' (the coarse solve's output) is read from here on
+        pdl_wait();
+        pdl_trigger();
+        waited = true;
       }
-      TACC av[kArnAwRows];
-      int ac[kArnAwRows];
+      if (a.defl && s0 == R0)
+        for (int q = t; q < a.r; q += kArnThreads) Ss[q] = sig * __ldcg(a.sdefl + q);
+      __syncthreads();
+      constexpr int AWR = kArnAwRows64;
+      for (long long i0 = s0 + t; i0 < s1; i0 += (long long)AWR * kArnThreads) {
+        int e0[AWR], e1[AWR];
 #pragma unroll
-      for (int b = 0; b < kArnAwRows; ++b) {
-        const bool has = e0[b] < e1[b];
-        av[b] = has ? __ldg(a.auval + e0[b]) : (TACC)0;
-        ac[b] = has ? __ldg(a.aucol + e0[b]) : 0;
-      }
-#pragma unroll
-      for (int b = 0; b < kArnAwRows; ++b) {
-        const long long row = i0 + (long long)b * kArnThreads;
-        if (row < s1) {
-          TACC aw = av[b] * Ss[ac[b]];
-          for (int e = e0[b] + 1; e < e1[b]; ++e)
-            aw += __ldg(a.auval + e) * Ss[__ldg(a.aucol + e)];
-          const TACC wv = row < N ? sig * (Ws[row - s0] + aw) : (TACC)0;
-          Ws[row - s0] = wv;
-          if ((multi || DF) && row < N) a.w[row] = wv;
+        for (int b = 0; b < AWR; ++b) {
+          const long long row = i0 + (long long)b * kArnThreads;
+          const bool live = a.defl && row < N && row < s1;
+          e0[b] = live ? __ldg(a.aurp + row) : 0;
+          e1[b] = live ? __ldg(a.aurp + row + 1) : 0;
         }
+        TACC av[AWR];
+        int ac[AWR];
+#pragma unroll
+        for (int b = 0; b < AWR; ++b) {
+          const bool has = e0[b] < e1[b];
+          av[b] = has ? __ldg(a.auval + e0[b]) : (TACC)0;
+          ac[b] = has ? __ldg(a.aucol + e0[b]) : 0;
+        }
+#pragma unroll
+        for (int b = 0; b < AWR; ++b) {
+          const long long row = i0 + (long long)b * kArnThreads;
+          if (row < s1) {
+            TACC wv = 0;
+            if (row < N) {
+              TACC aw = a.defl ? av[b] * Ss[ac[b]] : (TACC)0;
+              for (int e = e0[b] + 1; e < e1[b]; ++e) aw += __ldg(a.auval + e) * Ss[__ldg(a.aucol + e)];
+              wv = fma(sig, Ws[row - s0], aw);
+            }
+            Ws[row - s0] = wv;
+            if ((multi || DF) && row < N) a.w[row] = wv;
+          }
+        }
+      }
+    } else {
+      // FP32: a row's first two A W entries from the row-indexed planes (one level of loads,
+      // kArnAwRows32 rows per thread at once); the first batch's loads are issued before s'
+      // is read, since they do not depend on it
+      constexpr int AWR = kArnAwRows32;
+      TACC av0[AWR], av1[AWR];
+      int ac0[AWR], ac1[AWR];
+      auto aw_load = [&](long long i0) {
+#pragma unroll
+        for (int b = 0; b < AWR; ++b) {
+          const long long row = i0 + (long long)b * kArnThreads;
+          const bool live = a.defl && row < N && row < s1;
+          ac0[b] = live ? __ldg(a.aup_col + row) : -1;
+          ac1[b] = live ? __ldg(a.aup_col + N + row) : -1;
+          av0[b] = live ? __ldg(a.aup_val + row) : (TACC)0;
+          av1[b] = live ? __ldg(a.aup_val + N + row) : (TACC)0;
+        }
+      };
+      auto aw_apply = [&](long long i0) {
+#pragma unroll
+        for (int b = 0; b < AWR; ++b) {
+          const long long row = i0 + (long long)b * kArnThreads;
+          if (row < s1) {
+            // absent entries carry the value 0 (and read s'_0, which is finite)
+            TACC aw = 0;
+            if (a.defl) {
+              aw = av0[b] * Ss[ac0[b] >= 0 ? ac0[b] : 0];
+              aw += av1[b] * Ss[ac1[b] >= 0 ? ac1[b] : (ac1[b] == -1 ? 0 : -ac1[b] - 2)];
+              if (ac1[b] < -1) {  // the row's third and later entries (rare)
+                const int e1 = __ldg(a.aurp + row + 1);
+#pragma unroll 1
+                for (int e = __ldg(a.aurp + row) + 2; e < e1; ++e)
+                  aw += __ldg(a.auval + e) * Ss[__ldg(a.aucol + e)];
+              }
+            }
+            const TACC wv = row < N ? sig * (Ws[row - s0] + aw) : (TACC)0;
+            Ws[row - s0] = wv;
+            if ((multi || DF) && row < N) a.w[row] = wv;
+          }
+        }
+      };
+      aw_load(s0 + t);
+      if (!waited) {  // s' (the coarse solve's output) is read from here on
+        pdl_wait();
+        pdl_trigger();
+        waited = true;
+      }
+      if (a.defl && s0 == R0)
+        for (int q = t; q < a.r; q += kArnThreads) Ss[q] = __ldcg(a.sdefl + q);
+      __syncthreads();
+      for (long long i0 = s0 + t; i0 < s1; i0 += (long long)AWR * kArnThreads) {
+        if (i0 != s0 + t) aw_load(i0);
+        aw_apply(i0);
       }
     }
     __syncthreads();
@@ -1274,13 +1373,16 @@ struct Arn {
     if constexpr (sizeof(TACC) == 8) {
       p.dval = c.op.dval;
       p.auval = c.op.defl.auval;
+      p.aup_val = c.op.defl.aup_val;
       p.sdefl = c.ctl.sdefl;
     } else {
       p.dval = c.op.dval32;
       p.auval = c.op.defl.auval32;
+      p.aup_val = c.op.defl.aup_val32;
       p.sdefl = c.ctl.sdefl32;
     }
     p.aurp = c.op.defl.aurp;
+    p.aup_col = c.op.defl.aup_col;
     p.aucol = c.op.defl.aucol;
     p.perm = c.op.defl.perm;
     p.piece_start = c.op.defl.piece_start;

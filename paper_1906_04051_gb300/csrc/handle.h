@@ -48,6 +48,7 @@ struct Meta {  // mirrors the device status block
 struct OpHost {
   DevMem rowptr, col, val, val32, tinv, tinv32;  // tinv32: FP32 copy (FP32 / BF16 solves)
   DevMem aurp, aucol, auval, auval32;  // A W in CSR (projector, residual)
+  DevMem aup_col, aup_val, aup_val32;  // its first two entries per row, two planes of n
   DevMem xrp, xcol, xval, xval32;      // [A | A W] rows (deflated SpMV of a step)
   DevMem dval, dval32;                 // diagonal storage (banded operators)
   long long nau = 0;                   // entries of A W
@@ -68,6 +69,7 @@ struct gmres_s {
   // deflation (shared by A and A^T)
   int r = 0, npieces = 0;
   DevMem agg, perm, piece_start, agg_piece, uscale;
+  int tband[2] = {0, 0};              // T's lower and upper bandwidth (set at create)
   int blk_grid = 0;                   // blocks of the fused kernel the pieces are cut for
   DevMem blk_piece_start, blk_piece;  // each block's pieces
   double mu_norminf = 0.0;
@@ -283,6 +285,12 @@ inline gmres_status build_au(gmres_s* h, OpHost& o) {
                        o.auval.as<double>(),
                        h->opts.precision != GMRES_FP64 ? o.auval32.as<float>() : nullptr, st));
   const bool f32 = h->opts.precision != GMRES_FP64;
+  CK(h, o.aup_col.ensure(sizeof(int) * 2 * (size_t)n));
+  CK(h, o.aup_val.ensure(sizeof(double) * 2 * (size_t)n));
+  if (f32) CK(h, o.aup_val32.ensure(sizeof(float) * 2 * (size_t)n));
+  CK(h, launch_au_planes(n, o.aurp.as<int>(), o.aucol.as<int>(), o.auval.as<double>(),
+                         f32 ? o.auval32.as<float>() : nullptr, o.aup_col.as<int>(),
+                         o.aup_val.as<double>(), f32 ? o.aup_val32.as<float>() : nullptr, st));
   if (h->opts.deflation_mode == GMRES_DEFL_EBP) {
     const long long nnz = h->nnz;
     CK(h, o.xrp.ensure(sizeof(int) * (size_t)(n + 1)));
@@ -323,6 +331,9 @@ inline OpDev make_op(gmres_s* h, OpHost& o) {
   op.defl.aucol = o.aucol.as<int>();
   op.defl.auval = o.auval.as<double>();
   op.defl.auval32 = o.auval32.as<float>();
+  op.defl.aup_col = o.aup_col.as<int>();
+  op.defl.aup_val = o.aup_val.as<double>();
+  op.defl.aup_val32 = o.aup_val32.as<float>();
   op.dia = o.dia;
   op.ldd = o.ldd;
   op.dval = o.dval.as<double>();

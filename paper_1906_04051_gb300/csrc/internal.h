@@ -36,6 +36,11 @@ cudaError_t launch_coarse_T(int r, const int* rowptr, const int* col, const doub
                             const int* agg, const int* perm, const int* aggptr,
                             const double* uscale, double* T, cudaStream_t st);
 size_t gj_aux_bytes(int r);
+// T^-1 and T^-T: band LU when T is narrowly banded, else Gauss-Jordan (band: kl, ku out;
+// nlaunch: the kernels it enqueued)
+cudaError_t launch_coarse_inverse(int r, const double* T, double* G, void* aux, double* Tinv,
+                                  double* TinvT, int* err, int* band, int* nlaunch,
+                                  cudaStream_t st);
 cudaError_t launch_gauss_jordan(int r, const double* T, double* G, void* aux, double* Tinv,
                                 double* TinvT, int* err, cudaStream_t st);
 cudaError_t launch_norm_inf(int n, const int* rowptr, const double* val,
@@ -51,6 +56,10 @@ cudaError_t launch_au_tiles(int n, long long total, int unit, int* aurp, int* tm
 cudaError_t launch_au_fill(int n, const int* rowptr, const int* col, const double* val,
                            const int* agg, const int* aurp, int* aucol, double* auval,
                            float* auval32, cudaStream_t st);
+// the first two A W entries of each row in two row-indexed planes (see setup.cu)
+cudaError_t launch_au_planes(int n, const int* aurp, const int* aucol, const double* auval,
+                             const float* auval32, int* pcol, double* pval, float* pval32,
+                             cudaStream_t st);
 cudaError_t launch_dia_detect(int n, const int* rowptr, const int* col, int* slots, int* count,
                               cudaStream_t st);
 int dia_empty_slot();

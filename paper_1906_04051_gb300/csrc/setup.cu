@@ -99,11 +99,11 @@ __global__ void k_agg_scatter(int n, int r, const int* __restrict__ agg,
 
 // Pieces: aggregate a's range of perm (its nodes in increasing order) is cut where the
 // nodes pass from one block's rows to the next block's, for a grid of G blocks owning the
-// row ranges [floor(b U / G), floor((b + 1) U / G)) x 256 of U = ldv / 256 units (the
-// fused Arnoldi kernel's partition; G = 0: no cuts), and every part into ranges of at most
-// kPiece nodes.  piece_walk counts a's pieces and, given out, writes their starts.
+// row ranges [floor(b U / G), floor((b + 1) U / G)) x kPartUnit of U = ldv / kPartUnit units
+// (the fused Arnoldi kernel's partition; G = 0: no cuts), and every part into ranges of at
+// most kPiece nodes.  piece_walk counts a's pieces and, given out, writes their starts.
 __device__ __forceinline__ long long part_block(long long row, int U, int G) {
-  return ((row / 256 + 1) * G + U - 1) / U - 1;
+  return ((row / kPartUnit + 1) * G + U - 1) / U - 1;
 }
 
 __device__ int piece_walk(const int* __restrict__ perm, int s, int e, int U, int G, int* out) {
@@ -112,7 +112,7 @@ __device__ int piece_walk(const int* __restrict__ perm, int s, int e, int U, int
     int te = e;
     if (G > 0) {
       const long long b = part_block(perm[t], U, G);
-      const long long rend = (b + 1) * U / G * 256;
+      const long long rend = (b + 1) * U / G * kPartUnit;
       int lo = t + 1, hi = e;  // the first node at or past rend
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
@@ -928,6 +928,259 @@ size_t gj_persistent_smem(int r, int grid) {
 }
 }  // namespace
 
+// ---- T^-1 of a banded T (kl sub-, ku super-diagonals, small against r): band LU with
+// partial pivoting (row interchanges within the kl rows below the diagonal), then the r
+// columns of T^-1 by forward and back substitution.  The aggregates of a structured
+// partition couple only with their neighbours (a 32 x 32 grid of aggregates under a
+// 9-point operator: kl = ku = 33), so the factorisation costs r (kl + ku) kl FMA instead
+// of the r^3 of Gauss-Jordan.
+__global__ void k_band_width(int r, const double* __restrict__ T, int* __restrict__ bw) {
+  int lo = 0, up = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)r * r;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / r), j = (int)(e % r);
+    if (T[e] != 0.0) {
+      lo = max(lo, i - j);
+      up = max(up, j - i);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = max(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    up = max(up, __shfl_xor_sync(0xffffffffu, up, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&bw[0], lo);
+    atomicMax(&bw[1], up);
+  }
+}
+
+// One block.  The active window (rows k .. k + kl, columns k .. k + kl + ku) lives in shared
+// memory, entry (i, j) at win[(i mod R) C + (j mod C)] with R = kl + 1, C = kl + ku + 1 (the
+// upper band widens by kl under interchanges).  Step k: pivot = the largest |a_ik| over the
+// window's rows (lowest row on ties), swap, multipliers, rank-1 update of the window; row k
+// (of U) and column k (of L) leave for global memory, and row k + R enters from T.
+// Outputs: U row k at Ub[k C .. k C + C) (U_{k,k+t}), 1 / U_kk at dinv[k], the multipliers
+// of step k at Lm[k kl .. k kl + kl), the pivot row at piv[k].
+constexpr int kBandThreads = 256;
+
+__global__ void __launch_bounds__(kBandThreads, 1)
+    k_band_lu(int r, int kl, int ku, const double* __restrict__ T, double* __restrict__ Ub,
+              double* __restrict__ dinv, double* __restrict__ Lm, int* __restrict__ piv,
+              int* __restrict__ err) {
+  extern __shared__ double win[];
+  __shared__ int s_p;
+  __shared__ int s_sing;
+  const int R = kl + 1, C = kl + ku + 1;
+  const int t = threadIdx.x, lane = t & 31;
+  auto at = [&](int i, int j) -> double& { return win[(i % R) * C + (j % C)]; };
+  for (int e = t; e < R * C; e += kBandThreads) {
+    const int i = e / C, j = e % C;
+    win[e] = (i < r && j < r) ? T[(size_t)i * r + j] : 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < r; ++k) {
+    const int iend = min(k + kl, r - 1), jend = min(k + kl + ku, r - 1);
+    if (t < 32) {
+      double v = -1.0;
+      int idx = 0x7fffffff;
+      for (int i = k + lane; i <= iend; i += 32) {
+        const double a = fabs(at(i, k));
+        if (a > v || (a == v && i < idx)) {
+          v = a;
+          idx = i;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ov > v || (ov == v && oi < idx)) {
+          v = ov;
+          idx = oi;
+        }
+      }
+      if (lane == 0) {
+        s_p = idx;
+        s_sing = !(v > 0.0);
+      }
+    }
+    __syncthreads();
+    if (s_sing) {
+      if (t == 0) atomicOr(err, 8);
+      return;
+    }
+    const int p = s_p;
+    if (p != k)
+      for (int j = k + t; j <= jend; j += kBandThreads) {
+        const double a = at(k, j);
+        at(k, j) = at(p, j);
+        at(p, j) = a;
+      }
+    __syncthreads();
+    const double pk = at(k, k);
+    for (int i = k + 1 + t; i <= iend; i += kBandThreads) {
+      const double l = at(i, k) / pk;
+      at(i, k) = l;
+      Lm[(size_t)k * kl + (i - k - 1)] = l;
+    }
+    for (int q = t; q < C; q += kBandThreads) Ub[(size_t)k * C + q] = k + q <= jend ? at(k, k + q) : 0.0;
+    if (t == 0) {
+      piv[k] = p;
+      dinv[k] = 1.0 / pk;
+    }
+    __syncthreads();
+    const int nr = iend - k, nc = jend - k;
+    for (int e = t; e < nr * nc; e += kBandThreads) {
+      const int i = k + 1 + e / nc, j = k + 1 + e % nc;
+      at(i, j) = fma(-at(i, k), at(k, j), at(i, j));
+    }
+    __syncthreads();
+    // row k's slot takes row k + R (its entries lie in columns k + 1 .. k + C), column k's
+    // slot takes column k + C (zero in the rows already in the window)
+    const int nrow = k + R;
+    for (int j = k + 1 + t; j <= k + C; j += kBandThreads)
+      at(nrow, j) = (nrow < r && j < r) ? T[(size_t)nrow * r + j] : 0.0;
+    for (int i = k + 1 + t; i <= k + kl; i += kBandThreads) at(i, k + C) = 0.0;
+    __syncthreads();
+  }
+}
+
+// Column j of T^-1 (one warp): x = e_j; forward, for k = 0 .. r - 2: swap x_k and x_piv[k],
+// x_{k+1..k+kl} -= l_k x_k (k starts at j - kl: x stays 0 above); back, for i = r - 1 .. 0:
+// x_i = x_i / U_ii, x_{i-t} -= U_{i-t,i} x_i.  The factors of the next kBandAhead steps are
+// loaded ahead of the substitution chain.  Writes column j of T^-1 and row j of T^-T.
+constexpr int kBandAhead = 8;
+constexpr int kBandWarps = 4;
+
+__global__ void __launch_bounds__(32 * kBandWarps)
+    k_band_inv(int r, int kl, int ku, const double* __restrict__ Ub,
+               const double* __restrict__ dinv, const double* __restrict__ Lm,
+               const int* __restrict__ piv, double* __restrict__ Tinv,
+               double* __restrict__ TinvT) {
+  extern __shared__ double xs[];
+  const int C = kl + ku + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * kBandWarps + warp;
+  if (j >= r) return;
+  double* x = xs + (size_t)warp * r;
+  for (int i = lane; i < r; i += 32) x[i] = i == j ? 1.0 : 0.0;
+  __syncwarp();
+  constexpr int D = kBandAhead;
+  // forward: each lane takes the multipliers t = lane, lane + 32 (kl <= 64)
+  {
+    const int k0 = j - kl > 0 ? j - kl : 0;
+    double la[D], lb[D];
+    int pv[D];
+    auto fetch = [&](int k, int d) {
+      const bool ok = k < r - 1;
+      pv[d] = ok ? __ldg(piv + k) : k;
+      la[d] = ok && lane < kl ? __ldg(Lm + (size_t)k * kl + lane) : 0.0;
+      lb[d] = ok && lane + 32 < kl ? __ldg(Lm + (size_t)k * kl + lane + 32) : 0.0;
+    };
+#pragma unroll
+    for (int d = 0; d < D; ++d) fetch(k0 + d, d);
+    for (int k = k0; k < r - 1; k += D) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const int kk = k + d;
+        if (kk < r - 1) {
+          const int p = pv[d];
+          if (p != kk) {
+            const double a = x[kk], b = x[p];
+            __syncwarp();
+            if (lane == 0) {
+              x[kk] = b;
+              x[p] = a;
+            }
+            __syncwarp();
+          }
+          const double xk = x[kk];
+          if (lane < kl && kk + 1 + lane < r) x[kk + 1 + lane] = fma(-la[d], xk, x[kk + 1 + lane]);
+          if (lane + 32 < kl && kk + 33 + lane < r)
+            x[kk + 33 + lane] = fma(-lb[d], xk, x[kk + 33 + lane]);
+          __syncwarp();
+          fetch(kk + D, d);
+        }
+      }
+    }
+  }
+  // back: column i of U above the diagonal, U_{i-t,i} = Ub[(i - t) C + t], t = 1 .. C - 1:
+  // lane takes t = 1 + lane + 32 s, s < 3 (C <= 97)
+  {
+    double u[D][3], dv[D];
+    auto fetch = [&](int i, int d) {
+      dv[d] = i >= 0 ? __ldg(dinv + i) : 0.0;
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        const int tt = 1 + lane + 32 * s;
+        u[d][s] = (i >= 0 && tt < C && tt <= i) ? __ldg(Ub + (size_t)(i - tt) * C + tt) : 0.0;
+      }
+    };
+#pragma unroll
+    for (int d = 0; d < D; ++d) fetch(r - 1 - d, d);
+    for (int i0 = r - 1; i0 >= 0; i0 -= D) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const int i = i0 - d;
+        if (i >= 0) {
+          const double xi = x[i] * dv[d];
+          if (lane == 0) {
+            Tinv[(size_t)i * r + j] = xi;
+            TinvT[(size_t)j * r + i] = xi;
+          }
+#pragma unroll
+          for (int s = 0; s < 3; ++s) {
+            const int tt = 1 + lane + 32 * s;
+            if (tt < C && tt <= i) x[i - tt] = fma(-u[d][s], xi, x[i - tt]);
+          }
+          __syncwarp();
+          fetch(i - D, d);
+        }
+      }
+    }
+  }
+}
+
+// the band path's limits: window and multipliers within the kernels' shapes, the band
+// narrow against r (a dense T takes Gauss-Jordan)
+static bool band_ok(int r, int kl, int ku) {
+  const int C = kl + ku + 1;
+  return kl <= 64 && C <= 97 && 2 * C <= r &&
+         sizeof(double) * (size_t)(kl + 1) * C <= 200 * 1024 &&
+         sizeof(double) * (size_t)r * kBandWarps <= 200 * 1024;
+}
+
+cudaError_t launch_band_inverse(int r, int kl, int ku, double* work, double* Tinv,
+                                double* TinvT, const double* T, int* err, cudaStream_t st) {
+  const int C = kl + ku + 1;
+  double* Ub = work;                         // r x C
+  double* Lm = Ub + (size_t)r * C;           // r x kl
+  double* dinv = Lm + (size_t)r * kl;        // r
+  int* piv = reinterpret_cast<int*>(dinv + r);
+  const size_t sm = sizeof(double) * (size_t)(kl + 1) * C;
+  static cudaError_t a1 = cudaFuncSetAttribute(k_band_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  static cudaError_t a2 = cudaFuncSetAttribute(k_band_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (a1 != cudaSuccess) return a1;
+  if (a2 != cudaSuccess) return a2;
+  k_band_lu<<<1, kBandThreads, sm, st>>>(r, kl, ku, T, Ub, dinv, Lm, piv, err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_band_inv<<<(r + kBandWarps - 1) / kBandWarps, 32 * kBandWarps,
+               sizeof(double) * (size_t)r * kBandWarps, st>>>(r, kl, ku, Ub, dinv, Lm, piv,
+                                                              Tinv, TinvT);
+  return cudaGetLastError();
+}
+
+// kernels a Gauss-Jordan inversion enqueues: one cooperative launch when every block's
+// rows fit its shared memory, else init, first pivot, one per column and the extraction
+static int gj_launches(int r) {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    (void)cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = r < sms ? r : sms;
+  return (gj_persistent_smem(r, grid) <= 200 * 1024 && (r + grid - 1) / grid <= 63) ? 1 : 3 + r;
+}
+
 cudaError_t launch_gauss_jordan(int r, const double* T, double* G /* r*2r */, void* aux,
                                 double* Tinv, double* TinvT, int* err, cudaStream_t st) {
   GjAux x;
@@ -1010,6 +1263,31 @@ cudaError_t launch_gauss_jordan(int r, const double* T, double* G /* r*2r */, vo
   return cudaGetLastError();
 }
 
+// T^-1 (and T^-T): the band path when T is narrowly banded, Gauss-Jordan otherwise.  G
+// (r x 2r doubles) is the work matrix of either.  Reads T's bandwidth back to the host.
+cudaError_t launch_coarse_inverse(int r, const double* T, double* G, void* aux, double* Tinv,
+                                  double* TinvT, int* err, int* band, int* nlaunch,
+                                  cudaStream_t st) {
+  int* bw = reinterpret_cast<int*>(G);
+  cudaError_t e = cudaMemsetAsync(bw, 0, 2 * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_band_width<<<grid_for((long long)r * r, 256, 152 * 4), 256, 0, st>>>(r, T, bw);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  int hb[2] = {0, 0};
+  if ((e = cudaMemcpyAsync(hb, bw, sizeof(hb), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  if (band) {
+    band[0] = hb[0];
+    band[1] = hb[1];
+  }
+  if (band_ok(r, hb[0], hb[1])) {
+    if (nlaunch) *nlaunch = 3;
+    return launch_band_inverse(r, hb[0], hb[1], G, Tinv, TinvT, T, err, st);
+  }
+  if (nlaunch) *nlaunch = gj_launches(r);
+  return launch_gauss_jordan(r, T, G, aux, Tinv, TinvT, err, st);
+}
+
 cudaError_t launch_norm_inf(int n, const int* rowptr, const double* val,
                             unsigned long long* out, cudaStream_t st) {
   k_norm_inf<<<grid_for(n, 256, 152 * 4), 256, 0, st>>>(n, rowptr, val, out);
@@ -1069,6 +1347,35 @@ cudaError_t launch_au_fill(int n, const int* rowptr, const int* col, const doubl
                            float* auval32, cudaStream_t st) {
   k_au_fill<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, rowptr, col, val, agg, aurp, aucol,
                                                        auval, auval32);
+  return cudaGetLastError();
+}
+
+// ---- the first two A W entries of every row in two planes of n (row-indexed, no row
+// pointer to chase): plane 0 the first entry, plane 1 the second; column -1 where a row has
+// fewer entries, and -(column) - 2 in plane 1 when the row has more than two (the rest
+// are read from the CSR rows, from entry aurp[i] + 2) ----
+__global__ void k_au_planes(int n, const int* __restrict__ aurp, const int* __restrict__ aucol,
+                            const double* __restrict__ auval, const float* __restrict__ auval32,
+                            int* __restrict__ pcol, double* __restrict__ pval,
+                            float* __restrict__ pval32) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int s = aurp[i], e = aurp[i + 1];
+    for (int q = 0; q < 2; ++q) {
+      const bool has = s + q < e;
+      int c = has ? aucol[s + q] : -1;
+      if (q == 1 && e - s > 2) c = -c - 2;
+      pcol[(size_t)q * n + i] = c;
+      pval[(size_t)q * n + i] = has ? auval[s + q] : 0.0;
+      if (pval32) pval32[(size_t)q * n + i] = has ? auval32[s + q] : 0.f;
+    }
+  }
+}
+
+cudaError_t launch_au_planes(int n, const int* aurp, const int* aucol, const double* auval,
+                             const float* auval32, int* pcol, double* pval, float* pval32,
+                             cudaStream_t st) {
+  k_au_planes<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(n, aurp, aucol, auval, auval32, pcol,
+                                                         pval, pval32);
   return cudaGetLastError();
 }
 

@@ -505,6 +505,7 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
   CKC(launch_validate(n, nnz, h->fwd.rowptr.as<int>(), h->fwd.col.as<int>(),
                       r > 0 ? h->agg.as<int>() : nullptr, r, err.as<int>(), st));
   int herr[4] = {0, 0, 0, 0};
+  int inv_launches = 0;  // kernels of the coarse inverse (band LU or Gauss-Jordan)
   CKC(cudaMemcpyAsync(herr, err.p, sizeof(herr), cudaMemcpyDeviceToHost, st));
   CKC(cudaStreamSynchronize(st));
   if (herr[0] & 1) return bail(fail(h, GMRES_ERR_INVALID_ARG, "CSR rows not sorted/in range"));
@@ -516,8 +517,9 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
   if (r > 0) {
     const int nb = agg_chunks(n);
     DevMem counts, aggptr, cnt, T, G, fac;
-    // the fused kernel's grid: min(units of 256 rows, SMs); its row ranges cut pieces too
-    const long long units = ((long long)n + 255) / 256;
+    // the fused kernel's grid: min(units of kPartUnit rows of the padded columns, SMs); its
+    // row ranges cut pieces too
+    const long long units = ((long long)n + 255) / 256 * 256 / kPartUnit;
     const int bg = (int)std::min<long long>(units, h->sms);
     const long long max_pieces =
         std::min<long long>((long long)n / kPiece + r + 1 + (long long)(bg - 1) * r, (long long)n + r + 1);
@@ -546,8 +548,9 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
     CKC(launch_coarse_T(r, h->fwd.rowptr.as<int>(), h->fwd.col.as<int>(),
                         h->fwd.val.as<double>(), h->agg.as<int>(), h->perm.as<int>(),
                         aggptr.as<int>(), h->uscale.as<double>(), T.as<double>(), st));
-    CKC(launch_gauss_jordan(r, T.as<double>(), G.as<double>(), fac.p,
-                            h->fwd.tinv.as<double>(), h->adj.tinv.as<double>(), err.as<int>(), st));
+    CKC(launch_coarse_inverse(r, T.as<double>(), G.as<double>(), fac.p,
+                              h->fwd.tinv.as<double>(), h->adj.tinv.as<double>(), err.as<int>(),
+                              h->tband, &inv_launches, st));
     if (opts.precision != GMRES_FP64) {  // the FP32 coarse solve of the fused FP32 step
       CKC(h->fwd.tinv32.ensure(sizeof(float) * (size_t)r * r));
       CKC(h->adj.tinv32.ensure(sizeof(float) * (size_t)r * r));
@@ -586,13 +589,13 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
   h->pms[PH_SETUP] = std::chrono::duration<double, std::milli>(
                          std::chrono::steady_clock::now() - t_setup).count();
   // kernels enqueued by the setup: validation, FP32 copy, aggregate permutation (4),
-  // coarse matrix, Gauss-Jordan (init, first pivot, one per column, extract), A W (count,
-  // three scan passes, fill), the rows [A | A W] (2), diagonal storage (detect, fill),
-  // infinity norm
+  // coarse matrix, its inverse (band width + band LU + substitutions, or Gauss-Jordan), A W
+  // (count, three scan passes, fill, planes), the rows [A | A W] (2), diagonal storage
+  // (detect, fill), infinity norm
   h->plaunch[PH_SETUP] = 1 + (opts.precision != GMRES_FP64 ? 1 : 0) +
-                         (r > 0 ? 4 + 1 + 3 + (long long)r : 0) +
+                         (r > 0 ? 4 + 1 + 1 + (long long)inv_launches : 0) +
                          (r > 0 && opts.precision != GMRES_FP64 ? 2 : 0) +
-                         (r > 0 && opts.deflation_mode != GMRES_DEFL_NONE ? 5 : 0) +
+                         (r > 0 && opts.deflation_mode != GMRES_DEFL_NONE ? 6 : 0) +
                          (r > 0 && opts.deflation_mode == GMRES_DEFL_EBP ? 2 : 0) +
                          1 + (h->fwd.dia.nd > 0 ? 1 : 0) +
                          (opts.mu_mode == GMRES_MU_NORM_INF ? 1 : 0);
