@@ -203,8 +203,9 @@ typedef struct {
 void gmres_opts_default(gmres_opts* o);
 
 /* Setup (Eqs. 17-18): validates and copies A and the aggregate map, builds the
- * aggregate permutation, U's scaling, T = U^T A U and T^-1 (Gauss-Jordan with partial
- * pivoting), all on the device.  *h receives the handle.  W may be NULL (no deflation).
+ * aggregate permutation, U's scaling, T = U^T A U and T^-1 (band LU with partial pivoting
+ * when T is narrowly banded, as for a structured partition into aggregates; Gauss-Jordan
+ * with partial pivoting otherwise), all on the device.  *h receives the handle.  W may be NULL (no deflation).
  * o may be NULL (defaults).  Synchronises the stream before returning.
  * Errors: INVALID_ARG (n <= 0, null pointers, unsorted/out-of-range CSR, agg out of
  * range, r > 6144), SINGULAR_COARSE (empty aggregate, zero pivot in T), OOM, CUDA. */

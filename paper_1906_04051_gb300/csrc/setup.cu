@@ -82,17 +82,30 @@ __global__ void k_agg_scan(int r, int nb, int* __restrict__ counts, int* __restr
   }
 }
 
+// Stable: the chunk's nodes of each aggregate land in increasing index order.  One warp
+// takes 32 consecutive nodes at a time; the lanes of equal aggregate find each other
+// (match), take consecutive slots in lane order, and the lowest of them advances the
+// aggregate's offset.
 __global__ void k_agg_scatter(int n, int r, const int* __restrict__ agg,
                               const int* __restrict__ counts, int* __restrict__ perm) {
   extern __shared__ int soff[];
   for (int a = threadIdx.x; a < r; a += blockDim.x) soff[a] = counts[(size_t)blockIdx.x * r + a];
   __syncthreads();
-  if (threadIdx.x == 0) {  // stable: nodes of the chunk in increasing index order
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
     const int base = blockIdx.x * kChunk;
     const int end = min(n, base + kChunk);
-    for (int i = base; i < end; ++i) {
-      const int a = agg[i];
-      if (a >= 0) perm[soff[a]++] = i;
+    for (int i0 = base; i0 < end; i0 += 32) {
+      const int i = i0 + lane;
+      const int a = i < end ? agg[i] : -1;
+      const unsigned peers = __match_any_sync(0xffffffffu, a);
+      const int off = a >= 0 ? soff[a] : 0;
+      __syncwarp();
+      if (a >= 0) {
+        perm[off + __popc(peers & ((1u << lane) - 1u))] = i;
+        if (lane == __ffs(peers) - 1) soff[a] = off + __popc(peers);
+      }
+      __syncwarp();
     }
   }
 }
@@ -961,6 +974,11 @@ __global__ void k_band_width(int r, const double* __restrict__ T, int* __restric
 // (of U) and column k (of L) leave for global memory, and row k + R enters from T.
 // Outputs: U row k at Ub[k C .. k C + C) (U_{k,k+t}), 1 / U_kk at dinv[k], the multipliers
 // of step k at Lm[k kl .. k kl + kl), the pivot row at piv[k].
+// A block on one multiprocessor issues FP64 at 2 lanes per clock, so the scalar steps stay
+// off that pipe where they can: the pivot is chosen by the magnitudes' bit patterns (for
+// finite doubles |a| < |b| exactly when the bits of |a| are below those of |b|, as
+// unsigned integers), the multipliers take one multiply by 1 / U_kk, and the row entering
+// the window is loaded a step ahead.
 constexpr int kBandThreads = 256;
 
 __global__ void __launch_bounds__(kBandThreads, 1)
@@ -970,38 +988,55 @@ __global__ void __launch_bounds__(kBandThreads, 1)
   extern __shared__ double win[];
   __shared__ int s_p;
   __shared__ int s_sing;
+  __shared__ double s_rp;
   const int R = kl + 1, C = kl + ku + 1;
   const int t = threadIdx.x, lane = t & 31;
-  auto at = [&](int i, int j) -> double& { return win[(i % R) * C + (j % C)]; };
+  // the update's 2-D split: 64 columns x 4 row groups
+  const int tx = t & 63, ty = t >> 6;
   for (int e = t; e < R * C; e += kBandThreads) {
     const int i = e / C, j = e % C;
     win[e] = (i < r && j < r) ? T[(size_t)i * r + j] : 0.0;
   }
+  // thread q < C holds entry (k + R, k + 1 + q) of T, the row that enters after step k
+  double nxt = 0.0;
+  auto fetch_row = [&](int k) {
+    const int nrow = k + R, j = k + 1 + t;
+    nxt = (t < C && nrow < r && j < r) ? __ldg(T + (size_t)nrow * r + j) : 0.0;
+  };
+  fetch_row(0);
   __syncthreads();
+  constexpr unsigned long long kMag = 0x7fffffffffffffffULL, kInf = 0x7ff0000000000000ULL;
+  int kr = 0, kc = 0;  // window slots of row k and column k (k mod R, k mod C)
   for (int k = 0; k < r; ++k) {
-    const int iend = min(k + kl, r - 1), jend = min(k + kl + ku, r - 1);
+    const int nr = min(kl, r - 1 - k), nc = min(kl + ku, r - 1 - k);  // rows, columns past k
+    // slot of row k + di (0 <= di <= R - 1) and column k + dj (0 <= dj <= C)
+    auto rs = [&](int di) { const int v = kr + di; return v >= R ? v - R : v; };
+    auto cs = [&](int dj) { const int v = kc + dj; return v >= C ? v - C : v; };
     if (t < 32) {
-      double v = -1.0;
+      unsigned long long key = 0;
       int idx = 0x7fffffff;
-      for (int i = k + lane; i <= iend; i += 32) {
-        const double a = fabs(at(i, k));
-        if (a > v || (a == v && i < idx)) {
-          v = a;
-          idx = i;
+      for (int di = lane; di <= nr; di += 32) {
+        const unsigned long long m =
+            (unsigned long long)__double_as_longlong(win[rs(di) * C + kc]) & kMag;
+        if (m > key || (m == key && k + di < idx)) {
+          key = m;
+          idx = k + di;
         }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, o);
         const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-        if (ov > v || (ov == v && oi < idx)) {
-          v = ov;
+        if (ok > key || (ok == key && oi < idx)) {
+          key = ok;
           idx = oi;
         }
       }
       if (lane == 0) {
+        const bool good = key > 0 && key < kInf;  // nonzero and finite
         s_p = idx;
-        s_sing = !(v > 0.0);
+        s_sing = !good;
+        if (good) s_rp = 1.0 / win[rs(idx - k) * C + kc];
       }
     }
     __syncthreads();
@@ -1010,38 +1045,54 @@ __global__ void __launch_bounds__(kBandThreads, 1)
       return;
     }
     const int p = s_p;
-    if (p != k)
-      for (int j = k + t; j <= jend; j += kBandThreads) {
-        const double a = at(k, j);
-        at(k, j) = at(p, j);
-        at(p, j) = a;
+    const double rp = s_rp;
+    if (p != k) {
+      double* r0 = win + rs(0) * C;
+      double* r1 = win + rs(p - k) * C;
+      for (int dj = t; dj <= nc; dj += kBandThreads) {
+        const int c = cs(dj);
+        const double a = r0[c];
+        r0[c] = r1[c];
+        r1[c] = a;
       }
-    __syncthreads();
-    const double pk = at(k, k);
-    for (int i = k + 1 + t; i <= iend; i += kBandThreads) {
-      const double l = at(i, k) / pk;
-      at(i, k) = l;
-      Lm[(size_t)k * kl + (i - k - 1)] = l;
     }
-    for (int q = t; q < C; q += kBandThreads) Ub[(size_t)k * C + q] = k + q <= jend ? at(k, k + q) : 0.0;
+    __syncthreads();
+    for (int di = 1 + t; di <= nr; di += kBandThreads) {
+      double* e = win + rs(di) * C + kc;
+      const double l = *e * rp;
+      *e = l;
+      Lm[(size_t)k * kl + (di - 1)] = l;
+    }
+    for (int q = t; q < C; q += kBandThreads) Ub[(size_t)k * C + q] = q <= nc ? win[rs(0) * C + cs(q)] : 0.0;
     if (t == 0) {
       piv[k] = p;
-      dinv[k] = 1.0 / pk;
+      dinv[k] = rp;
     }
     __syncthreads();
-    const int nr = iend - k, nc = jend - k;
-    for (int e = t; e < nr * nc; e += kBandThreads) {
-      const int i = k + 1 + e / nc, j = k + 1 + e % nc;
-      at(i, j) = fma(-at(i, k), at(k, j), at(i, j));
+    {
+      // a_ij -= l_i u_kj over rows k + 1 .. k + nr, columns k + 1 .. k + nc
+      const double* urow = win + rs(0) * C;
+      double u0 = 0.0, u1 = 0.0;
+      int c0 = 0, c1 = 0;
+      const bool h0 = 1 + tx <= nc, h1 = 65 + tx <= nc;
+      if (h0) { c0 = cs(1 + tx); u0 = urow[c0]; }
+      if (h1) { c1 = cs(65 + tx); u1 = urow[c1]; }
+      for (int di = 1 + ty; di <= nr; di += kBandThreads / 64) {
+        double* row = win + rs(di) * C;
+        const double l = row[kc];
+        if (h0) row[c0] = fma(-l, u0, row[c0]);
+        if (h1) row[c1] = fma(-l, u1, row[c1]);
+      }
     }
     __syncthreads();
     // row k's slot takes row k + R (its entries lie in columns k + 1 .. k + C), column k's
     // slot takes column k + C (zero in the rows already in the window)
-    const int nrow = k + R;
-    for (int j = k + 1 + t; j <= k + C; j += kBandThreads)
-      at(nrow, j) = (nrow < r && j < r) ? T[(size_t)nrow * r + j] : 0.0;
-    for (int i = k + 1 + t; i <= k + kl; i += kBandThreads) at(i, k + C) = 0.0;
+    if (t < C) win[rs(0) * C + cs(1 + t)] = nxt;
+    fetch_row(k + 1);
+    for (int di = 1 + t; di <= kl; di += kBandThreads) win[rs(di) * C + kc] = 0.0;
     __syncthreads();
+    kr = kr + 1 == R ? 0 : kr + 1;
+    kc = kc + 1 == C ? 0 : kc + 1;
   }
 }
 
@@ -1145,7 +1196,7 @@ __global__ void __launch_bounds__(32 * kBandWarps)
 // narrow against r (a dense T takes Gauss-Jordan)
 static bool band_ok(int r, int kl, int ku) {
   const int C = kl + ku + 1;
-  return kl <= 64 && C <= 97 && 2 * C <= r &&
+  return kl <= 64 && C <= 97 && C <= 128 && 2 * C <= r &&
          sizeof(double) * (size_t)(kl + 1) * C <= 200 * 1024 &&
          sizeof(double) * (size_t)r * kBandWarps <= 200 * 1024;
 }
