@@ -599,8 +599,15 @@ __device__ void residual_decide(Ctl& ctl, double beta, double beta_s) {
 }
 
 // Back substitution R_k y = g (Eq. 12) on a shared-memory copy of R; coef = sigma o y.
-// Block-wide; R (kMaxM^2 doubles), sg, sy (kMaxM each) are shared-memory scratch.
+// Block-wide (at least one warp); R (kMaxM^2 doubles), sg, sy (kMaxM each) are
+// shared-memory scratch.  The substitution runs column by column in warp 0: y_i = s_i / R_ii
+// (s_i times the reciprocal of R_ii, all reciprocals formed up front), then s_l -= R_li y_i
+// for every l < i at once, the lanes holding s in registers (k <= 64: two rows per lane).
+// On GB300 a dependent FP64 operation costs a few dozen cycles and a division about ten of
+// them, so the chain is k multiplies and multiply-adds instead of k^2 / 2 multiply-adds
+// and k divisions in one thread.
 __device__ void backsolve_block(Ctl& ctl, double* R, double* sg, double* sy) {
+  static_assert(kMaxM <= 64, "two rows per lane");
   const int k = ctl.flags[F_K];
   const int ldh = ctl.ldh;
   for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
@@ -609,13 +616,28 @@ __device__ void backsolve_block(Ctl& ctl, double* R, double* sg, double* sy) {
   }
   for (int i = threadIdx.x; i < k; i += blockDim.x) sg[i] = ctl.g[i];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int i = k - 1; i >= 0; --i) {
-      double s = sg[i];
-      for (int l = i + 1; l < k; ++l) s -= R[i * k + l] * sy[l];
-      sy[i] = s / R[i * k + i];
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double rinv[2], sl[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = lane + 32 * q;
+      rinv[q] = i < k ? 1.0 / R[i * k + i] : 0.0;
+      sl[q] = i < k ? sg[i] : 0.0;
     }
-    ctl.counts[C_CYCLES]++;
+    for (int i = k - 1; i >= 0; --i) {
+      const int o = i & 31;
+      const double si = __shfl_sync(0xffffffffu, i < 32 ? sl[0] : sl[1], o);
+      const double ri = __shfl_sync(0xffffffffu, i < 32 ? rinv[0] : rinv[1], o);
+      const double yi = si * ri;
+      if (lane == o) sy[i] = yi;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int l = lane + 32 * q;
+        if (l < i) sl[q] = fma(-R[l * k + i], yi, sl[q]);
+      }
+    }
+    if (lane == 0) ctl.counts[C_CYCLES]++;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
