@@ -286,7 +286,8 @@ typedef struct gmres_layout {
   int64_t ldv;        /* rows per basis column in device memory (n rounded up) */
   int32_t spmv_lanes; /* CSR SpMV: lanes per row (4 for rows of 16+ entries on average;
                          0: a thread per row, or diagonal storage) */
-  int32_t reserved;
+  int32_t coarse_band; /* T^-1 from the band LU: T's band width kl + ku + 1; 0: Gauss-Jordan
+                          (or no aggregates) */
 } gmres_layout;
 gmres_status gmres_layout_query(gmres_t h, gmres_layout* out);
 

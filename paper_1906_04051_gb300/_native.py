@@ -64,10 +64,10 @@ class gmres_info(C.Structure):
 class gmres_layout(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("r", C.c_int32), ("npieces", C.c_int32),
                 ("ndiag", C.c_int32), ("adapt_q", C.c_int32), ("nau", C.c_int64),
-                ("ldv", C.c_int64), ("spmv_lanes", C.c_int32), ("reserved", C.c_int32)]
+                ("ldv", C.c_int64), ("spmv_lanes", C.c_int32), ("coarse_band", C.c_int32)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class q2_newton_info(C.Structure):

@@ -69,7 +69,8 @@ struct gmres_s {
   // deflation (shared by A and A^T)
   int r = 0, npieces = 0;
   DevMem agg, perm, piece_start, agg_piece, uscale;
-  int tband[2] = {0, 0};              // T's lower and upper bandwidth (set at create)
+  int tband[3] = {0, 0, 0};           // T's lower and upper bandwidth, band LU used (create)
+  int coarse_band = 0;                // kl + ku + 1 when T^-1 came from the band LU, else 0
   int blk_grid = 0;                   // blocks of the fused kernel the pieces are cut for
   DevMem blk_piece_start, blk_piece;  // each block's pieces
   double mu_norminf = 0.0;

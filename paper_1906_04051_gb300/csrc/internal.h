@@ -36,8 +36,8 @@ cudaError_t launch_coarse_T(int r, const int* rowptr, const int* col, const doub
                             const int* agg, const int* perm, const int* aggptr,
                             const double* uscale, double* T, cudaStream_t st);
 size_t gj_aux_bytes(int r);
-// T^-1 and T^-T: band LU when T is narrowly banded, else Gauss-Jordan (band: kl, ku out;
-// nlaunch: the kernels it enqueued)
+// T^-1 and T^-T: band LU when T is narrowly banded, else Gauss-Jordan (band: kl, ku and
+// whether the band path ran, out; nlaunch: the kernels it enqueued)
 cudaError_t launch_coarse_inverse(int r, const double* T, double* G, void* aux, double* Tinv,
                                   double* TinvT, int* err, int* band, int* nlaunch,
                                   cudaStream_t st);

@@ -240,7 +240,10 @@ __global__ void k_blk_fill(int U, const int* __restrict__ perm, const int* __res
 
 // T row of aggregate p: sum_{i in p} sum_{k in row i, agg(col_k) = q} a_ik, in perm order.
 // Small r: lanes take nodes round-robin into private rows, summed in lane order.
-// Large r: lane 0 accumulates sequentially, the warp loads each row's entries.
+// Large r: the aggregates the block meets are found first; when there are at most kTLocal
+// of them (the neighbours of a structured partition: 9) the lanes keep private sums of
+// just those, summed in lane order; else lane 0 accumulates sequentially.
+constexpr int kTLocal = 32;
 __global__ void k_T_rows(int r, const int* __restrict__ rowptr, const int* __restrict__ col,
                          const double* __restrict__ val, const int* __restrict__ agg,
                          const int* __restrict__ perm, const int* __restrict__ aggptr,
@@ -268,6 +271,66 @@ __global__ void k_T_rows(int r, const int* __restrict__ rowptr, const int* __res
       T[(size_t)p * r + q] = acc * uscale[p] * uscale[q];
     }
   } else {
+    // the aggregates that row block p meets, as a bitmap, then their ranks (a prefix of the
+    // words' popcounts) and list
+    const int nw = (r + 31) / 32;
+    unsigned* bm = reinterpret_cast<unsigned*>(srow + r);
+    int* pre = reinterpret_cast<int*>(bm + nw);
+    int* qlist = pre + nw;  // kTLocal
+    double* priv = reinterpret_cast<double*>(qlist + kTLocal + (kTLocal & 1));
+    __shared__ int s_nq;
+    for (int w = lane; w < nw; w += 32) bm[w] = 0u;
+    __syncwarp();
+    for (int t = s + lane; t < e; t += 32) {
+      const int i = perm[t];
+      for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+        const int q = agg[col[k]];
+        if (q >= 0) atomicOr(&bm[q >> 5], 1u << (q & 31));
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      int run = 0;
+      for (int w = 0; w < nw; ++w) {
+        pre[w] = run;
+        unsigned m = bm[w];
+        while (m) {
+          const int b = __ffs(m) - 1;
+          if (run < kTLocal) qlist[run] = w * 32 + b;
+          ++run;
+          m &= m - 1u;
+        }
+      }
+      s_nq = run;
+    }
+    __syncwarp();
+    const int nq = s_nq;
+    if (nq <= kTLocal) {
+      // lane l sums the nodes l, l + 32, ... (perm order) into its own slots, one per met
+      // aggregate; the lanes' sums are then added in lane order
+      for (int q = 0; q < nq; ++q) priv[lane * (kTLocal + 1) + q] = 0.0;
+      for (int t = s + lane; t < e; t += 32) {
+        const int i = perm[t];
+        for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+          const int q = agg[col[k]];
+          if (q >= 0) {
+            const int rk = pre[q >> 5] + __popc(bm[q >> 5] & ((1u << (q & 31)) - 1u));
+            priv[lane * (kTLocal + 1) + rk] += val[k];
+          }
+        }
+      }
+      __syncwarp();
+      for (int q = lane; q < r; q += 32)
+        if (!(bm[q >> 5] & (1u << (q & 31)))) T[(size_t)p * r + q] = 0.0;
+      for (int lq = lane; lq < nq; lq += 32) {
+        double acc = 0.0;
+        for (int l = 0; l < 32; ++l) acc += priv[l * (kTLocal + 1) + lq];
+        const int q = qlist[lq];
+        T[(size_t)p * r + q] = acc * uscale[p] * uscale[q];
+      }
+      return;
+    }
+    // many aggregates met: lane 0 accumulates sequentially, the warp loads each row's entries
     for (int t = s; t < e; ++t) {
       const int i = perm[t];
       const int ks = rowptr[i], ke = rowptr[i + 1];
@@ -918,7 +981,11 @@ cudaError_t launch_coarse_T(int r, const int* rowptr, const int* col, const doub
                             const int* agg, const int* perm, const int* aggptr,
                             const double* uscale, double* T, cudaStream_t st) {
   const bool lane_rows = (r * 32 * (int)sizeof(double)) <= 48 * 1024;
-  const size_t sm = sizeof(double) * (size_t)r * (lane_rows ? 32 : 1);
+  // large r: the sequential row, the bitmap and its prefix, the list, the private sums
+  const size_t sm = lane_rows ? sizeof(double) * (size_t)r * 32
+                              : sizeof(double) * (size_t)r + 2 * sizeof(int) * ((r + 31) / 32) +
+                                    sizeof(int) * (kTLocal + (kTLocal & 1)) +
+                                    sizeof(double) * 32 * (kTLocal + 1);
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_T_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
@@ -1315,7 +1382,8 @@ cudaError_t launch_gauss_jordan(int r, const double* T, double* G /* r*2r */, vo
 }
 
 // T^-1 (and T^-T): the band path when T is narrowly banded, Gauss-Jordan otherwise.  G
-// (r x 2r doubles) is the work matrix of either.  Reads T's bandwidth back to the host.
+// (r x 2r doubles) is the work matrix of either.  Reads T's bandwidth back to the host;
+// band (3 ints, may be null) receives kl, ku and 1 if the band path ran (else 0).
 cudaError_t launch_coarse_inverse(int r, const double* T, double* G, void* aux, double* Tinv,
                                   double* TinvT, int* err, int* band, int* nlaunch,
                                   cudaStream_t st) {
@@ -1327,11 +1395,13 @@ cudaError_t launch_coarse_inverse(int r, const double* T, double* G, void* aux, 
   int hb[2] = {0, 0};
   if ((e = cudaMemcpyAsync(hb, bw, sizeof(hb), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  const bool use_band = band_ok(r, hb[0], hb[1]);
   if (band) {
     band[0] = hb[0];
     band[1] = hb[1];
+    band[2] = use_band ? 1 : 0;
   }
-  if (band_ok(r, hb[0], hb[1])) {
+  if (use_band) {
     if (nlaunch) *nlaunch = 3;
     return launch_band_inverse(r, hb[0], hb[1], G, Tinv, TinvT, T, err, st);
   }

@@ -551,6 +551,7 @@ gmres_status gmres_create(gmres_t* out, const gmres_csr* A, const gmres_defl* W,
     CKC(launch_coarse_inverse(r, T.as<double>(), G.as<double>(), fac.p,
                               h->fwd.tinv.as<double>(), h->adj.tinv.as<double>(), err.as<int>(),
                               h->tband, &inv_launches, st));
+    h->coarse_band = h->tband[2] ? h->tband[0] + h->tband[1] + 1 : 0;
     if (opts.precision != GMRES_FP64) {  // the FP32 coarse solve of the fused FP32 step
       CKC(h->fwd.tinv32.ensure(sizeof(float) * (size_t)r * r));
       CKC(h->adj.tinv32.ensure(sizeof(float) * (size_t)r * r));
@@ -687,6 +688,7 @@ gmres_status gmres_layout_query(gmres_t h, gmres_layout* out) {
   out->ldv = h->ldv;
   out->adapt_q = (h->opts.deflation_mode == GMRES_DEFL_ADAPTIVE || h->dense_r > 0) ? h->aq : 0;
   out->spmv_lanes = (h->fwd.dia.nd == 0 && h->nnz >= (long long)kVecMinRowLen * h->n) ? kVecLanes : 0;
+  out->coarse_band = h->coarse_band;
   return GMRES_OK;
 }
 

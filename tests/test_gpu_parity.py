@@ -303,3 +303,56 @@ def test_bad_restart_length(G, orc):
     for m in (0, 65):
         with pytest.raises(G.GmresError):
             s.solve(to_dev(b), m=m)
+
+
+def _swapped_band(kl, ku, n, seed):
+    """A well-conditioned banded B (kl sub-, ku super-diagonals, diagonal about 8) with
+    rows 2i and 2i+1 exchanged: the diagonal of the result holds B's off-diagonal entries,
+    so LU with partial pivoting exchanges rows at every step."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed)
+    diags, offs = [], []
+    for o in range(-kl, ku + 1):
+        d = rng.standard_normal(n - abs(o))
+        if o == 0:
+            d = d + 8.0 * np.sign(d)
+        diags.append(d)
+        offs.append(o)
+    B = sp.diags(diags, offs, shape=(n, n)).tocsr()
+    p = np.arange(n)
+    p[0:n - 1:2] += 1
+    p[1:n:2] -= 1
+    A = B[p].tocsr()
+    A.sort_indices()
+    return A
+
+
+@pytest.mark.parametrize("kl,ku", [(3, 3), (2, 4)])
+def test_band_coarse_inverse_with_row_exchanges(G, orc, kl, ku):
+    # every node its own aggregate: T = U^T A U = A, banded with kl + 1 sub- and ku + 1
+    # super-diagonals, so gmres_create inverts it by the band LU (Eqs. 17-18), with a row
+    # exchange at every step; with U = I the EBP preconditioner is |mu| T^-1, and the
+    # solution rests on T^-1 (one GMRES step in exact arithmetic)
+    n = 300
+    As = _swapped_band(kl, ku, n, seed=7)
+    A = orc.CSR(As.indptr, As.indices, As.data)
+    b = W.uniform(19, kl, n, -1, 1)
+    agg = np.arange(n, dtype=np.int32)
+    s = gpu_solver_from_oracle(G, A, agg, n, mu_mode=G.MU_USER, mu_user=1.0)
+    assert s.layout()["coarse_band"] == (kl + 1) + (ku + 1) + 1
+    xg, ig = s.solve(to_dev(b), m=30, tol=1e-12, maxit=200)
+    d = orc.Deflation(A, agg, n)
+    xo, io = orc.gmres(A, b, None, m=30, tol=1e-12, maxit=200, defl=d,
+                       mu_mode=orc.MU_USER, mu_user=1.0)
+    assert ig["status"] == 0 and io["status"] == 0, (ig, io)
+    assert relerr(xg.cpu().numpy(), xo) <= 1e-9
+    assert np.linalg.norm(As @ xg.cpu().numpy() - b) <= 1e-11 * np.linalg.norm(b)
+
+
+def test_dense_coarse_matrix_takes_gauss_jordan(G, orc):
+    # the 2 x 4 subdomains of the small workloads give a T as wide as it is long: the
+    # setup keeps Gauss-Jordan for it
+    p = W.convdiff(24, pe=10.0, sigma=0.3, seed=5, px=2, py=4)
+    A, b = orc.q1_assemble(p.n, p.kappa, p.beta, p.f)
+    s = gpu_solver_from_oracle(G, A, p.agg, p.r)
+    assert s.layout()["coarse_band"] == 0
