@@ -42,7 +42,7 @@ FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the fused Arnoldi kernel
 # (a full 50-step deflated cycle) on this workload, FP64 and FP32 basis (one ncu capture
 # each, profiles/k_arnoldi_cycle_q1-n1024_*.txt); None once the kernel changes
-ARN_DRAM_BYTES_CYCLE50 = {8: 25.991e9, 4: 8.261e9}
+ARN_DRAM_BYTES_CYCLE50 = {8: 21.859e9, 4: 8.261e9}
 # Arnoldi steps the deflated GMRES(50) takes to 1e-8 on this workload (deterministic;
 # the GPU arm prints its own count): used only to project the CPU sample to a full solve
 PROJECT_ITERS = 782

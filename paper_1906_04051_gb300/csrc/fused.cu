@@ -221,6 +221,19 @@ __device__ __forceinline__ void arn_ldg(const TV* p, TACC (&o)[VN]) {
   }
 }
 
+// An FP64 operator value read with the L2 evict-first priority: the diagonals (76 MB at
+// 1M rows) then give way to the basis columns, which the update re-reads right after the
+// multi-dot (measured on q1-n1024: FP64 step 236.4 to 228.0 us at the fixed 100-step
+// protocol; the FP32 step, whose 38 MB of diagonals stay useful in L2 across steps, went
+// from 76.9 to 80.0 us with the same hint and keeps plain loads)
+__device__ __forceinline__ double arn_ld_evict_first(const double* p) {
+  unsigned long long pol;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  double v;
+  asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
 template <typename TV, typename TACC, int VN>
 __device__ __forceinline__ void arn_stv(TV* p, const TACC (&v)[VN]) {
   if constexpr (std::is_same<TV, double>::value) {
@@ -425,7 +438,10 @@ __device__ __forceinline__ void arn_dia_rows(TACC (&acc)[B], long long row0, lon
         const int q = q0 + u;
         const bool live = ND > 0 || q < nd;
         const long long c = min(max(rr + off[live ? q : 0], 0LL), Nn - 1);
-        av[b][u] = live ? __ldg(dval + (size_t)q * ldd + rr) : (TACC)0;
+        if constexpr (sizeof(TACC) == 8)
+          av[b][u] = live ? arn_ld_evict_first(dval + (size_t)q * ldd + rr) : (TACC)0;
+        else
+          av[b][u] = live ? __ldg(dval + (size_t)q * ldd + rr) : (TACC)0;
         xv[b][u] = live ? ld_as<TACC, TV>(x + c) : (TACC)0;
       }
     }
